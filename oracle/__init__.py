@@ -1,0 +1,20 @@
+"""FP64 CPU oracle for the BART forward-model hot path (test infrastructure only).
+
+This package is the slow, plain statement of what the GPU library computes.  It
+exists to check the CUDA path and nothing else: only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import it.
+It shares no code with the CUDA path (the seeded input generators in
+``workloads`` hold none of the method's arithmetic) and never takes an input or
+expected value from it.
+
+Every function follows a passage of Harrington et al. (2022), "An Open-Source
+Bayesian Atmospheric Radiative Transfer (BART) Code: I" (arXiv:2104.12522),
+cited by section and equation.  Where the paper defers to its companion papers
+(line strengths, widths, the emission and transit integrals, the T(P)
+parameterisation), the oracle takes the reading stated in its docstring.
+
+Pins (tests/test_oracle_*.py) tie each function to something other than itself:
+closed forms, limits, invariants, brute-force quadrature and textbook constants.
+The MLP and DE-MC parts are pinned by finite differences and by sampling a
+known Gaussian target.  Nothing here is "parity unpinned".
+"""

@@ -1,0 +1,115 @@
+"""Pins of the oracle's line strengths, widths and point-sampled opacity
+(Sec. 4 items 3-4 and the sampling text after them; tests f01-f03 ideas,
+Sec. 5.1 Table 1)."""
+import dataclasses
+import numpy as np
+
+from oracle import opacity as O
+from oracle import voigt as V
+
+
+@dataclasses.dataclass
+class Lines:
+    nu0: np.ndarray
+    log10_s296: np.ndarray
+    elow: np.ndarray
+    gamma_ref: np.ndarray
+    mass_amu: float
+
+
+def _lines(nu0, logs, elow, gam, mass=18.0):
+    return Lines(np.asarray(nu0, np.float64), np.asarray(logs, np.float32),
+                 np.asarray(elow, np.float32), np.asarray(gam, np.float32), mass)
+
+
+def test_strength_at_reference_temperature():
+    s = O.line_strength(np.float32(-20.0), 2000.0, np.float32(1234.0), 296.0)
+    assert abs(s / 10.0 ** np.float64(np.float32(-20.0)) - 1.0) < 1e-14
+
+
+def test_strength_ground_state_limit():
+    # E'' = 0 and c2 nu0 / T >> 1: only the partition-function ratio remains.
+    for T in (500.0, 1500.0):
+        s = O.line_strength(0.0, 40000.0, 0.0, T)
+        assert abs(s - (296.0 / T) ** 1.5) < 1e-12
+
+
+def test_strength_boltzmann_slope():
+    # log S vs E'' at fixed nu0 is linear with slope -c2 (1/T - 1/296) / ln 10,
+    # with c2 = 1.4387769 cm K (textbook second radiation constant).
+    E = np.linspace(0, 5000, 11)
+    T = 1200.0
+    ls = np.log10(O.line_strength(np.zeros(11), np.full(11, 2000.0), E, T))
+    slope = np.polyfit(E, ls, 1)[0]
+    assert abs(slope / (-1.4387769 * (1 / T - 1 / 296.0) / np.log(10)) - 1) < 1e-6
+
+
+def test_doppler_width_textbook_constant():
+    # Doppler FWHM = 7.1623e-7 nu0 sqrt(T / M[amu]) (textbook constant)
+    fwhm = 2 * np.sqrt(2 * np.log(2)) * O.doppler_sigma(2000.0, 1500.0, 18.0)
+    assert abs(fwhm / (7.1623e-7 * 2000.0 * np.sqrt(1500.0 / 18.0)) - 1) < 2e-5
+
+
+def test_lorentz_width_scaling():
+    assert abs(O.lorentz_gamma(0.07, 1.0, 296.0) - 0.07) < 1e-16
+    assert abs(O.lorentz_gamma(0.07, 3.0, 4 * 296.0) - 0.07 * 3 / 2) < 1e-15
+
+
+def test_single_line_brute_force():
+    # f01oneline idea: one line gives S V at every point within the cutoff, 0 outside.
+    ll = _lines([1500.3], [-20.0], [800.0], [0.07])
+    p, T = 0.5, 1100.0
+    out = O.opacity_cell(ll, p, T, 1400.0, 0.1, 2000, 25.0)
+    nu = 1400.0 + np.arange(2000) * 0.1
+    S = O.line_strength(ll.log10_s296, ll.nu0, ll.elow, T)[0]
+    sig = O.doppler_sigma(1500.3, T, 18.0)
+    gam = O.lorentz_gamma(np.float32(0.07), p, T)
+    d = nu - 1500.3
+    exp = np.where(np.abs(d) <= 25.0, S * V.voigt(d, sig, gam), 0.0)
+    assert np.max(np.abs(out - exp)) <= 1e-14 * np.max(exp)
+    assert np.count_nonzero(out) == np.count_nonzero(np.abs(d) <= 25.0)
+
+
+def test_cutoff_is_inclusive_on_exact_points():
+    ll = _lines([1025.0], [-20.0], [0.0], [0.07])      # nu_0 - 25 is exactly grid point 0
+    out = O.opacity_cell(ll, 1.0, 1000.0, 1000.0, 1.0, 60, 25.0)
+    assert out[0] > 0 and out[50] > 0 and out[51] == 0.0
+
+
+def test_additivity_over_line_lists():
+    # f02/f03 idea: the opacity of a union of lists is the sum of their opacities.
+    rng = np.random.default_rng(7)
+    a = _lines(np.sort(rng.uniform(1000, 1100, 30)), rng.uniform(-24, -19, 30),
+               rng.uniform(0, 3000, 30), rng.uniform(0.05, 0.1, 30))
+    b = _lines(np.sort(rng.uniform(1000, 1100, 20)), rng.uniform(-24, -19, 20),
+               rng.uniform(0, 3000, 20), rng.uniform(0.05, 0.1, 20))
+    order = np.argsort(np.concatenate([a.nu0, b.nu0]))
+    u = _lines(np.concatenate([a.nu0, b.nu0])[order], np.concatenate([a.log10_s296, b.log10_s296])[order],
+               np.concatenate([a.elow, b.elow])[order], np.concatenate([a.gamma_ref, b.gamma_ref])[order])
+    args = (0.01, 900.0, 990.0, 0.05, 2400, 25.0)
+    oa, ob, ou = (O.opacity_cell(x, *args) for x in (a, b, u))
+    assert np.max(np.abs(ou - (oa + ob))) <= 1e-13 * np.max(ou)
+
+
+def test_linear_in_strength():
+    ll = _lines([1050.0, 1052.5], [-21.0, -22.0], [100.0, 200.0], [0.06, 0.08])
+    l2 = _lines([1050.0, 1052.5], [-21.0 + np.log10(3.0), -22.0 + np.log10(3.0)],
+                [100.0, 200.0], [0.06, 0.08])
+    o1 = O.opacity_cell(ll, 0.1, 700.0, 1000.0, 0.05, 2000, 25.0)
+    o3 = O.opacity_cell(l2, 0.1, 700.0, 1000.0, 0.05, 2000, 25.0)
+    assert np.max(np.abs(o3 - 3 * o1)) <= 1e-6 * np.max(o3)   # float32 log10 S rounding
+
+
+def test_translation_by_grid_steps():
+    # Shifting a line by k grid steps shifts its profile by k points.  S and
+    # the Doppler width depend on nu0, so compare S-normalised profiles in a
+    # Lorentz-dominated regime (50 bar), where the width change is negligible.
+    k = 7
+    T = 1000.0
+    ll = _lines([1030.0], [-20.0], [0.0], [0.07])
+    sh = _lines([1030.0 + k * 0.25], [-20.0], [0.0], [0.07])
+    o = O.opacity_cell(ll, 50.0, T, 1000.0, 0.25, 400, 25.0)
+    s = O.opacity_cell(sh, 50.0, T, 1000.0, 0.25, 400, 25.0)
+    S0 = O.line_strength(ll.log10_s296, ll.nu0, ll.elow, T)[0]
+    S1 = O.line_strength(sh.log10_s296, sh.nu0, sh.elow, T)[0]
+    assert np.max(np.abs(s[k:] / S1 - o[:-k] / S0)) <= 1e-8 * np.max(o / S0)

@@ -1,0 +1,105 @@
+"""Pins of the oracle's T(P) profile (Sec. 7.1, nine-parameter model), grid
+interpolation and transit geometry (test f01oneline transit text, Sec. 5.1)."""
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import profile as P
+from oracle import transmission as Tr
+from oracle import forward as Fw
+from oracle.constants import K_BOLTZ, AMU
+from scipy.special import expn
+
+G = 2182.73
+
+
+def _T(theta, p, t_int=100.0):
+    return P.temperature(np.asarray(theta, float), p, G, t_int, 5000.0, 0.756 * 6.957e10,
+                         0.0312 * 1.495978707e13)
+
+
+def test_e2_matches_its_integral_definition():
+    for x in (1e-3, 0.1, 1.0, 4.0, 20.0):
+        val, _ = integrate.quad(lambda t: np.exp(-x * t) / t ** 2, 1, np.inf, epsrel=1e-12)
+        assert abs(expn(2, x) / val - 1) < 1e-10
+
+
+def test_no_irradiation_reduces_to_eddington():
+    p = np.logspace(-8, 2, 50)
+    th = [-1.0, 0.2, -0.4, 0.3, 0.0]                     # beta = 0 -> T_irr = 0
+    tau = 0.1 * p * 1e6 / G
+    assert np.allclose(_T(th, p), (0.75 * 100.0 ** 4 * (2 / 3 + tau)) ** 0.25, rtol=1e-14)
+
+
+def test_top_of_atmosphere_closed_form():
+    # tau -> 0: xi(g, 0) = 2/3 + 2g/3 (E2(0) = 1)
+    th = [-2.0, 0.5, -1.0, 0.25, 1.1]
+    t_irr = 1.1 * np.sqrt(0.756 * 6.957e10 / (2 * 0.0312 * 1.495978707e13)) * 5000.0
+    g1, g2 = 10 ** 0.5, 10 ** -1.0
+    T4 = 0.75 * 100.0 ** 4 * 2 / 3 + 0.75 * t_irr ** 4 * (0.75 * (2 / 3 + 2 * g1 / 3) + 0.25 * (2 / 3 + 2 * g2 / 3))
+    assert abs(_T(th, np.array([1e-30]))[0] / T4 ** 0.25 - 1) < 1e-12
+
+
+def test_channel_swap_symmetry():
+    p = np.logspace(-8, 2, 40)
+    a = _T([-1.5, 0.4, -0.9, 0.3, 1.0], p)
+    b = _T([-1.5, -0.9, 0.4, 0.7, 1.0], p)
+    assert np.allclose(a, b, rtol=1e-13)
+
+
+def test_bracket_rule():
+    ax = np.array([500.0, 1000.0, 1500.0])
+    assert Fw.bracket(ax, 1000.0) == (1, 0.0)
+    assert Fw.bracket(ax, 1500.0) == (1, 1.0)
+    assert Fw.bracket(ax, 200.0) == (0, 0.0)
+    assert Fw.bracket(ax, 9e9) == (1, 1.0)
+    m, w = Fw.bracket(ax, 1250.0)
+    assert m == 1 and abs(w - 0.5) < 1e-15
+
+
+def test_interpolation_exact_on_linear_grids():
+    rng = np.random.default_rng(1)
+    t_ax = np.linspace(500, 3000, 6)
+    p_ax = np.logspace(-8, 2, 5)
+    a, b, c = rng.uniform(1, 2, (3, 2, 7))
+    grid = (a[:, None, None, :] + b[:, None, None, :] * t_ax[None, None, :, None]
+            + c[:, None, None, :] * np.log10(p_ax)[None, :, None, None])
+    T = rng.uniform(500, 3000, 9)
+    Pl = 10 ** rng.uniform(-8, 2, 9)
+    got = Fw.level_opacity_bilinear(grid, p_ax, t_ax, Pl, T)
+    exp = a[:, None, :] + b[:, None, :] * T[None, :, None] + c[:, None, :] * np.log10(Pl)[None, :, None]
+    assert np.allclose(got, exp, rtol=1e-12)
+
+
+def _iso_atm(L=200, T=1200.0, mu=2.3, g=G, rp=1.138 * 7.1492e9):
+    p = np.logspace(-8, 2, L)
+    return p, np.full(L, T), Tr.radii(p, np.full(L, T), rp, 0.1, g, mu)
+
+
+def test_isothermal_radii_closed_form():
+    p, T, r = _iso_atm()
+    rp = 1.138 * 7.1492e9
+    C = K_BOLTZ * 1200.0 / (2.3 * AMU * G * rp ** 2)
+    assert np.allclose(r, 1.0 / (1.0 / rp + C * np.log(p / 0.1)), rtol=1e-13)
+
+
+def test_transit_depth_limits():
+    p, T, r = _iso_atm(L=80)
+    rs = 0.756 * 6.957e10
+    d0 = Tr.transit_depth(np.zeros((80, 3)), p, T, r, rs, 2.3)
+    assert np.allclose(d0, r[-1] ** 2 / rs ** 2, rtol=1e-14)
+    dinf = Tr.transit_depth(np.full((80, 3), 1e30), p, T, r, rs, 2.3)
+    assert np.allclose(dinf, r[0] * r[1] / rs ** 2, rtol=1e-13)   # discrete closed form
+
+
+def test_scale_height_law():
+    # Constant cross-section, isothermal: R_eff(s2) - R_eff(s1) = H ln(s2/s1),
+    # H = k T / (mu m_u g(R_eff)).
+    p, T, r = _iso_atm(L=400)
+    rs = 0.756 * 6.957e10
+    d1 = Tr.transit_depth(np.full((400, 1), 1e-3), p, T, r, rs, 2.3)[0]
+    d2 = Tr.transit_depth(np.full((400, 1), 1e-3 * np.e ** 2), p, T, r, rs, 2.3)[0]
+    R1, R2 = np.sqrt(d1) * rs, np.sqrt(d2) * rs
+    g_eff = G * (1.138 * 7.1492e9 / R1) ** 2
+    H = K_BOLTZ * 1200.0 / (2.3 * AMU * g_eff)
+    assert abs((R2 - R1) / (2 * H) - 1) < 0.02

@@ -1,0 +1,117 @@
+"""Pins of the oracle's emission RT, Planck function, quadrature and band
+integration: f08isothermal (Sec. 5.1.3), f05abundance (Sec. 5.1.2, Eqs. 10-11,
+Table 2), Stefan-Boltzmann and Wien laws."""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import radiation as R
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SIGMA_SB = 5.670374419e-5          # erg cm^-2 s^-1 K^-4 (CODATA 2018)
+WIEN_X = 2.821439372122079         # peak of x^3/(e^x - 1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16])
+def test_gauss_legendre_exactness(n):
+    mu, w = R.gauss_legendre_mu(n)
+    for k in range(2 * n):
+        assert abs(np.sum(w * mu ** k) - 1.0 / (k + 1)) < 1e-14
+    assert np.all((mu > 0) & (mu < 1))
+
+
+def test_isothermal_emits_planck():
+    # Without scattering an isothermal atmosphere emits pi B(T) for any opacity.
+    rng = np.random.default_rng(3)
+    p = np.logspace(-6, 2, 60)
+    nu = np.linspace(1000, 3000, 37)
+    chi = 10 ** rng.uniform(-4, 4, (60, 37))
+    for n_ang in (1, 4, 8):
+        F = R.emission_flux(chi, p, np.full(60, 1234.5), nu, 2182.73, n_ang)
+        exp = np.pi * R.planck(nu, 1234.5)
+        assert np.max(np.abs(F / exp - 1)) < 1e-12
+
+
+def test_transparent_atmosphere_shows_interior():
+    p = np.logspace(-6, 2, 30)
+    T = np.linspace(600, 1700, 30)
+    nu = np.linspace(1000, 3000, 11)
+    F = R.emission_flux(np.zeros((30, 11)), p, T, nu, 2182.73, 4)
+    assert np.max(np.abs(F / (np.pi * R.planck(nu, 1700.0)) - 1)) < 1e-13
+
+
+def _thin_layer_flux(tau_layer, n_ang, B_top=1.0, B_bot=3.0):
+    # two levels: a single layer of optical depth tau over a hot interior
+    chi = np.array([[tau_layer], [tau_layer]])       # dtau = chi * dP / g with dP/g = 1
+    p = np.array([0.0, 1e-6])                        # bar -> dP = 1 dyn cm^-2
+    g = 1.0
+    tau = R.optical_depth(chi.T, p, g)
+    mu, w = R.gauss_legendre_mu(n_ang)
+    B = np.array([[B_top, B_bot]])
+    return 2 * np.pi * sum(w[i] * mu[i] * R.intensity(tau, B, mu[i])[0] for i in range(n_ang))
+
+
+def test_f05_thin_layer_ratio_closed_form():
+    # Per angle F0 - F = (Bbar - B_bot)(1 - exp(-tau/mu)) with Bbar the layer mean,
+    # so f(n) = sum w mu (1 - e^{-n tau/mu}) / sum w mu (1 - e^{-tau/mu}).
+    mu, w = R.gauss_legendre_mu(4)
+    tau = 2e-5
+    F0 = _thin_layer_flux(0.0, 4)
+    Fl = _thin_layer_flux(tau, 4)
+    for n in range(2, 11):
+        Fh = _thin_layer_flux(n * tau, 4)
+        f = (F0 - Fh) / (F0 - Fl)
+        closed = np.sum(w * mu * -np.expm1(-n * tau / mu)) / np.sum(w * mu * -np.expm1(-tau / mu))
+        assert abs(f - closed) < 1e-9
+
+
+def test_f05_trend_matches_paper_table():
+    # Table 2 (f05abundance) prints f slightly below the abundance ratio n with
+    # a deficit growing with n; the thin-layer law gives the same signature.
+    with open(os.path.join(GOLDEN, "f05_abundance_table2.json")) as fh:
+        table = json.load(fh)["f_vs_0.01pct"]
+    n_vals = sorted(int(k) for k in table)
+    deficits = [n - table[str(n)] for n in n_vals]
+    assert all(d > 0 for d in deficits) and all(np.diff(deficits) > 0)
+    tau = 1e-4
+    F0, Fl = _thin_layer_flux(0.0, 4), _thin_layer_flux(tau, 4)
+    ours = [n - (F0 - _thin_layer_flux(n * tau, 4)) / (F0 - Fl) for n in n_vals]
+    assert all(d > 0 for d in ours) and all(np.diff(ours) > 0)
+    assert max(abs(d) / n for d, n in zip(deficits, n_vals)) < 1e-3   # "closely obey"
+
+
+@pytest.mark.parametrize("T", [300.0, 1000.0, 2500.0])
+def test_planck_integral_stefan_boltzmann(T):
+    val, _ = integrate.quad(lambda nu: R.planck(nu, T), 1e-3, 200 * T, limit=500, epsrel=1e-12)
+    assert abs(val / (SIGMA_SB * T ** 4 / np.pi) - 1) < 1e-8
+
+
+def test_planck_wien_peak():
+    T = 1500.0
+    k_over_hc = 1.0 / 1.438776877        # cm^-1 per K
+    nu = np.linspace(2000, 4000, 200001)
+    peak = nu[np.argmax(R.planck(nu, T))]
+    assert abs(peak - WIEN_X * k_over_hc * T) < 0.02
+
+
+def test_band_constant_and_linear():
+    nu = 1000 + np.arange(2000) * 1.0
+    W = np.zeros((2, 2000), np.float32)
+    W[0, 200:601] = 1.0
+    W[1] = np.exp(-0.5 * ((nu - 1800) / 100) ** 2)
+    assert np.allclose(R.band_integrate(np.full(2000, 7.25), W), 7.25, rtol=1e-14)
+    lin = 3.0 + 0.01 * nu
+    out = R.band_integrate(lin, W)
+    assert abs(out[0] - (3.0 + 0.01 * nu[200:601].mean())) < 1e-12
+    a, b = np.random.default_rng(0).normal(size=(2, 2000))
+    assert np.allclose(R.band_integrate(2 * a - b, W), 2 * R.band_integrate(a, W) - R.band_integrate(b, W),
+                       rtol=1e-12, atol=1e-12)
+
+
+def test_band_on_span_with_no_overlap_is_zero():
+    W = np.zeros((1, 100), np.float32)
+    W[0, 80:] = 1.0
+    assert R.band_integrate(np.ones(30), W, nu_lo=10)[0] == 0.0
