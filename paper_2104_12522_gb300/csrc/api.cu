@@ -1,0 +1,108 @@
+// Context management of the C ABI: creation, streams, errors, status word and
+// scratch memory.
+#include <cstdarg>
+#include <cstring>
+
+#include "bart_internal.cuh"
+
+extern "C" int bart_abi_version(void) { return BART_ABI_VERSION; }
+
+bart_status bart_fail(bart_ctx* ctx, bart_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+bart_status bart_check_launch(bart_ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return bart_fail(ctx, BART_ECUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+  return BART_OK;
+}
+
+bart_status bart_scratch(bart_ctx* ctx, const char* name, size_t bytes, void** out) {
+  auto it = ctx->scratch.find(name);
+  if (it != ctx->scratch.end() && it->second.second >= bytes) {
+    *out = it->second.first;
+    return BART_OK;
+  }
+  if (it != ctx->scratch.end()) {
+    // The old buffer may still be in use by queued work on this stream.
+    BART_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(it->second.first);
+    ctx->scratch.erase(it);
+  }
+  void* p = nullptr;
+  size_t sz = bytes < 256 ? 256 : bytes;
+  if (cudaMalloc(&p, sz) != cudaSuccess) {
+    cudaGetLastError();
+    return bart_fail(ctx, BART_ENOMEM, "scratch '%s': cudaMalloc of %zu bytes failed", name, sz);
+  }
+  ctx->scratch[name] = {p, sz};
+  *out = p;
+  return BART_OK;
+}
+
+extern "C" bart_status bart_create(bart_ctx** out, int device, void* cuda_stream) {
+  if (!out) return BART_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return BART_EINVAL;
+  }
+  bart_ctx* ctx = new bart_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return BART_ECUDA;
+  }
+  *out = ctx;
+  return BART_OK;
+}
+
+extern "C" void bart_destroy(bart_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->scratch) cudaFree(kv.second.first);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_wtable) cudaFree(ctx->d_wtable);
+  delete ctx;
+}
+
+extern "C" bart_status bart_set_stream(bart_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return BART_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return BART_OK;
+}
+
+extern "C" const char* bart_last_error(const bart_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "NULL context";
+}
+
+extern "C" bart_status bart_sync(bart_ctx* ctx) {
+  if (!ctx) return BART_EINVAL;
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  BART_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  int st = 0;
+  BART_CUDA(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    BART_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+    if (st & BART_DEV_TIMEOUT) return bart_fail(ctx, BART_ETIMEOUT, "device watchdog expired (status %d)", st);
+    return bart_fail(ctx, BART_ERANGE, "device range check failed (status %d)", st);
+  }
+  return BART_OK;
+}

@@ -1,0 +1,109 @@
+// Real part of the Faddeeva function, Re w(x + i y) for y >= 0, in FP32.
+//
+// The Voigt profile of Sec. 5.1.1 is V = Re w(z) / (sigma sqrt(2 pi)) with
+// z = (nu + i gamma) / (sigma sqrt 2) (Eqs. 4-9).  The paper's code uses a
+// tabulated Pierluissi approximation; this library evaluates w directly with
+// three regimes chosen so that Re w keeps a relative (not only absolute)
+// error bound, also close to the real axis where Re w << |w|:
+//
+//  * |z| >= 24  one-pole truncation of the Laplace continued fraction
+//               w(z) = (i/sqrt(pi)) / (z - (1/2)/(z - 1/(z - (3/2)/(z - ...)))),
+//               w ~ (i/sqrt(pi)) z / (z^2 - 1/2), whose real part is written
+//               without cancellation as
+//               Re w = (y/sqrt(pi)) (u + 1) / (u^2 + 2 y^2),  u = x^2 + y^2 - 1/2;
+//               relative error <= 2.5/|z|^4 <= 8e-6.
+//  * 5 <= |z| < 24  the same continued fraction to depth 4 (|z| >= 8) or 6,
+//               evaluated in complex FP32; Re w = Im t / (sqrt(pi) |t|^2)
+//               where t is the fraction's denominator.  All imaginary parts
+//               stay positive, so Re w keeps its relative accuracy for small
+//               y.  Near the real axis the exponentially small term
+//               exp(y^2 - x^2) cos(2xy) that the asymptotic fraction misses is
+//               added back (y < 1).  Relative error <= 1e-6.
+//  * |z| < 5    Taylor expansion about the nearest node z0 of a 21 x 21 grid
+//               (spacing 1/4) on 0 <= x, y <= 5, with coefficients
+//               c_n = w^(n)(z0)/n! from the recurrence of the derivatives
+//               w' = -2 z w + 2i/sqrt(pi), w^(n+1) = -2 z w^(n) - 2n w^(n-1).
+//               The node values are built once in FP64 (see faddeeva.cu); on
+//               the real axis their real part is exactly exp(-x0^2).  Twelve
+//               terms, |z - z0| <= 0.18: relative error <= 3e-7.
+// Re w is even in x; all branches use |x|.
+#pragma once
+
+#include "bart_internal.cuh"
+
+namespace bartw {
+
+constexpr float INV_SQRTPI = 0.56418958354775628695f;
+
+__device__ __forceinline__ float rcp_approx(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+
+// One-pole form, used where x^2 + y^2 >= 576.  Returns Re w * sqrt(pi) / y,
+// i.e. (u + 1) / (u^2 + 2 y^2), so callers can fold constants.
+__device__ __forceinline__ float onepole_ratio(float x, float qm, float q2) {
+  float p = x * x;
+  float u = p + qm;            // qm = y^2 - 1/2
+  return (u + 1.0f) * rcp_approx(fmaf(u, u, q2));   // q2 = 2 y^2
+}
+
+__device__ __forceinline__ float onepole_re(float x, float y) {
+  float q = y * y;
+  return INV_SQRTPI * y * onepole_ratio(x, q - 0.5f, 2.0f * q);
+}
+
+// Continued fraction to `depth`, real part of w.
+__device__ __forceinline__ float cf_re(float x, float y, int depth) {
+  float tr = x, ti = y;
+  for (int k = depth; k >= 1; --k) {
+    float a = 0.5f * (float)k;
+    float inv = __frcp_rn(fmaf(tr, tr, ti * ti));
+    float qr = a * tr * inv, qi = -a * ti * inv;
+    tr = x - qr;
+    ti = y - qi;
+  }
+  return INV_SQRTPI * ti * __frcp_rn(fmaf(tr, tr, ti * ti));
+}
+
+// Taylor expansion about the nearest table node (x >= 0, x^2 + y^2 < 25).
+__device__ __forceinline__ float taylor_re(float x, float y, const float2* __restrict__ tab) {
+  int ix = min((int)(x * 4.0f + 0.5f), wtab::NX - 1);
+  int iy = min((int)(y * 4.0f + 0.5f), wtab::NY - 1);
+  float a = x - (float)ix * wtab::H;
+  float b = y - (float)iy * wtab::H;
+  const float2* c = tab + ((size_t)iy * wtab::NX + ix) * wtab::NT;
+  float2 t = __ldg(c + wtab::NT - 1);
+  float ar = t.x, ai = t.y;
+#pragma unroll
+  for (int n = wtab::NT - 2; n >= 0; --n) {
+    float2 cn = __ldg(c + n);
+    float r = fmaf(ar, a, fmaf(-ai, b, cn.x));
+    float i = fmaf(ar, b, fmaf(ai, a, cn.y));
+    ar = r;
+    ai = i;
+  }
+  return ar;
+}
+
+// Accurate branch for x^2 + y^2 < 576 (also valid beyond).
+__device__ __forceinline__ float core_re(float x, float y, const float2* __restrict__ tab) {
+  x = fabsf(x);
+  float s = fmaf(x, x, y * y);
+  if (s < 25.0f) return taylor_re(x, y, tab);
+  float v = cf_re(x, y, s >= 64.0f ? 4 : 6);
+  if (y < 1.0f) {
+    float g = y * y - x * x;
+    if (g > -87.0f) v += expf(g) * cosf(2.0f * x * y);
+  }
+  return v;
+}
+
+__device__ __forceinline__ float faddeeva_re(float x, float y, const float2* __restrict__ tab) {
+  float s = fmaf(x, x, y * y);
+  if (s >= 576.0f) return onepole_re(x, y);
+  return core_re(x, y, tab);
+}
+
+}  // namespace bartw

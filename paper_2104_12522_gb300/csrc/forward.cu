@@ -1,0 +1,442 @@
+// Per-proposal forward model on the opacity grid (Sec. 3 second pass; Sec. 4
+// items 3, 8 and 9) and the spectrum integrator (Sec. 3).
+//
+// Emission path, per batch:
+//   tp_kernel        one thread per (proposal, layer): T from the five-parameter
+//                    profile (or the given profile), clamp, temperature bracket
+//                    (m, w) on the grid axis; per proposal the mass-opacity
+//                    coefficients X_s / (mu m_u).
+//   emission_kernel  one thread per (proposal, wavenumber); layers top to
+//                    bottom: opacity interpolated in T and summed over species
+//                    (coalesced reads of grid rows), trapezoid optical depth,
+//                    Planck source, and per Gauss-Legendre angle the
+//                    multiplicative transmittance t_{k+1} = t_k exp(-dtau/mu)
+//                    with I += (B_k + B_{k+1})/2 (t_k - t_{k+1}).  The running
+//                    product replaces a cumulative tau sum (no FP64 needed:
+//                    the relative error of t grows like 1e-7 tau/mu).  Flux
+//                    F = 2 pi sum_i w_i mu_i I(mu_i).  Band numerators and
+//                    denominators are reduced per CTA (fused epilogue).
+//   band_reduce      sums the per-CTA partials in a fixed order (FP64).
+// Proposals run along blockIdx.x, so CTAs in flight share wavenumber tiles and
+// the grid rows they read stay in L2.
+#include <cmath>
+#include <vector>
+
+#include "bart_internal.cuh"
+#include "forward.cuh"
+
+namespace {
+
+constexpr int EM_THREADS = 128;
+constexpr int MAX_BANDS = 64;
+constexpr int MAX_ANGLES = 16;
+constexpr int MAX_LAYERS = 256;
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LOG2E_LO = 1.925963033500011e-08f;   // log2(e) - (float)log2(e)
+constexpr float LN2F = 0.6931471805599453f;
+
+struct LayerTW {
+  int m;        // lower temperature bracket
+  float w;      // weight of the upper bracket
+  float T;      // layer temperature, K
+  float c2_t;   // c2 / T
+};
+
+// n-point Gauss-Legendre nodes/weights on [0, 1] (Newton on P_n).
+void gauss_legendre01(int n, std::vector<double>& mu, std::vector<double>& w) {
+  mu.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(bartc::PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = x; p0 = 1.0; }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    // recompute derivative at the converged root
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = (n == 1) ? 1.0 : n * (x * p1 - p0) / (x * x - 1.0);
+    mu[i] = 0.5 * (x + 1.0);
+    w[i] = 0.5 * 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+__global__ void tp_kernel(const float* __restrict__ theta, int n_theta, const float* __restrict__ t_profile,
+                          int n, int L, int S, const float* __restrict__ p_cgs, const float* __restrict__ t_axis,
+                          int M, float inv_g, float tint4, float tirr0, float t_min, float t_max,
+                          const float* __restrict__ x0_over_mu, LayerTW* __restrict__ tw,
+                          float* __restrict__ coef, int* __restrict__ status) {
+  const int p = blockIdx.x;
+  if (p >= n) return;
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    float T;
+    if (t_profile) {
+      T = t_profile[(int64_t)p * L + k];
+    } else {
+      float th[5];
+      for (int i = 0; i < 5; ++i) th[i] = theta[(int64_t)p * n_theta + i];
+      T = bartf::tp_temperature(th, p_cgs[k], inv_g, tint4, tirr0);
+    }
+    if (!(T == T) || T <= 0.0f) {
+      atomicOr(status, BART_DEV_RANGE);
+      T = t_min > 0.0f ? t_min : 1.0f;
+    }
+    T = fminf(fmaxf(T, t_min), t_max);
+    int m = 0;
+    float w = 0.0f;
+    if (M > 1) {
+      // m = max{m : t_axis[m] <= T} limited to [0, M-2]
+      int lo = 0, hi = M;               // first index with t_axis > T
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (t_axis[mid] <= T) lo = mid + 1; else hi = mid;
+      }
+      m = min(max(lo - 1, 0), M - 2);
+      w = (T - t_axis[m]) / (t_axis[m + 1] - t_axis[m]);
+      w = fminf(fmaxf(w, 0.0f), 1.0f);
+    }
+    LayerTW r;
+    r.m = m;
+    r.w = w;
+    r.T = T;
+    r.c2_t = (float)bartc::C2 / T;
+    tw[(int64_t)p * L + k] = r;
+  }
+  if (threadIdx.x < S) {
+    float a = theta ? theta[(int64_t)p * n_theta + 5 + threadIdx.x] : 0.0f;
+    coef[(int64_t)p * S + threadIdx.x] = x0_over_mu[threadIdx.x] * exp10f(a);
+  }
+}
+
+// Planck function per unit wavenumber, B = c1nu3 / (exp(x) - 1), x = c2 nu / T.
+// exp(x) is 2^(x log2 e) with the product split in two parts so its rounding
+// does not limit the accuracy; x > 20 (not reached by the grid's wavenumbers
+// and temperatures here) takes an FP64 exponential.
+__device__ __forceinline__ float planck(float c1nu3, float x) {
+  if (x > 20.0f) return (float)((double)c1nu3 / expm1((double)x));
+  float hi = x * LOG2E;
+  float lo = fmaf(x, LOG2E, -hi) + x * LOG2E_LO;
+  float e = bartf::ex2_approx(hi) * fmaf(lo, LN2F, 1.0f);
+  return c1nu3 * bartf::rcp_approx(e - 1.0f);
+}
+
+template <int S, int NA>
+__global__ void __launch_bounds__(EM_THREADS)
+emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const LayerTW* __restrict__ tw,
+                const float* __restrict__ coef, const float* __restrict__ dpg,
+                const float* __restrict__ ang /* [2][NA]: -log2(e)/mu, 2 pi w mu / 2 */, double nu_start,
+                double dnu, const int64_t* __restrict__ nu_lo, const int64_t* __restrict__ nu_hi,
+                const int64_t* __restrict__ offs, float* __restrict__ spectra,
+                const float* __restrict__ filt, int n_bands, float2* __restrict__ partial, int n_tiles,
+                int* __restrict__ status) {
+  const int p = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int64_t lo = nu_lo ? nu_lo[p] : 0;
+  const int64_t hi = nu_hi ? nu_hi[p] : N;
+  if (lo < 0 || hi > N || lo >= hi) {          // invalid span: report, touch nothing
+    if (tid == 0 && tile == 0) atomicOr(status, BART_DEV_RANGE);
+    return;
+  }
+  const int64_t j = lo + (int64_t)tile * EM_THREADS + tid;
+  const bool active = j < hi;
+  const int64_t jj = active ? j : lo;       // inactive lanes compute on a valid index
+
+  __shared__ float s_coef[S];
+  __shared__ float2 s_red[EM_THREADS / 32][MAX_BANDS];
+  if (tid < S) s_coef[tid] = coef[(int64_t)p * S + tid];
+  __syncthreads();
+
+  const double nu = nu_start + (double)jj * dnu;
+  const float nuf = (float)nu;
+  const float c1nu3 = (float)(2.0 * bartc::H * bartc::C * bartc::C * nu * nu * nu);
+
+  float nl2mu[NA], wmu[NA], t[NA], I[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) {
+    nl2mu[i] = ang[i];
+    wmu[i] = ang[NA + i];
+    t[i] = 1.0f;
+    I[i] = 0.0f;
+  }
+  const LayerTW* twp = tw + (int64_t)p * L;
+  const int64_t sstride = (int64_t)L * M * N;
+
+  auto chi_at = [&](int k, const LayerTW& r) {
+    const float* g0 = grid + ((int64_t)k * M + r.m) * N + jj;
+    float chi = 0.0f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      float a = __ldg(g0 + s * sstride);
+      float b = (M > 1) ? __ldg(g0 + s * sstride + N) : a;
+      chi = fmaf(s_coef[s], fmaf(r.w, b - a, a), chi);
+    }
+    return chi;
+  };
+
+  LayerTW r = twp[0];
+  float chi_prev = chi_at(0, r);
+  float B_prev = planck(c1nu3, nuf * r.c2_t);
+  for (int k = 1; k < L; ++k) {
+    r = twp[k];
+    const float chi = chi_at(k, r);
+    const float B = planck(c1nu3, nuf * r.c2_t);
+    const float dtau = (chi_prev + chi) * dpg[k - 1];
+    const float Bsum = B_prev + B;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const float e = bartf::ex2_approx(dtau * nl2mu[i]);
+      const float te = t[i] * e;
+      I[i] = fmaf(Bsum, t[i] - te, I[i]);
+      t[i] = te;
+    }
+    chi_prev = chi;
+    B_prev = B;
+  }
+  float F = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NA; ++i) F = fmaf(wmu[i], fmaf(2.0f * B_prev, t[i], I[i]), F);
+  // wmu = 2 pi w mu / 2: the 1/2 of the layer-mean source is folded in, so
+  // the interior term carries 2 B.
+  if (active && spectra) {
+    const int64_t base = offs ? offs[p] : (int64_t)p * N;
+    spectra[base + (j - lo)] = F;
+  }
+  if (n_bands > 0) {
+    float dw = 0.0f;
+    if (active) dw = (hi - lo == 1) ? 1.0f : ((j == lo || j == hi - 1) ? 0.5f : 1.0f);
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int b = 0; b < n_bands; ++b) {
+      const float W = active ? __ldg(filt + (int64_t)b * N + j) * dw : 0.0f;
+      float num = W * F, den = W;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+      }
+      if (lane == 0) s_red[warp][b] = make_float2(num, den);
+    }
+    __syncthreads();
+    if (tid < n_bands) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int w = 0; w < EM_THREADS / 32; ++w) {
+        acc.x += s_red[w][tid].x;
+        acc.y += s_red[w][tid].y;
+      }
+      partial[((int64_t)p * n_tiles + tile) * n_bands + tid] = acc;
+    }
+  }
+}
+
+__global__ void band_reduce_kernel(const float2* __restrict__ partial, int n, int n_tiles, int n_bands,
+                                   float* __restrict__ bands) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n_bands) return;
+  int p = (int)(idx / n_bands), b = (int)(idx % n_bands);
+  double num = 0.0, den = 0.0;
+  for (int t = 0; t < n_tiles; ++t) {
+    float2 v = partial[((int64_t)p * n_tiles + t) * n_bands + b];
+    num += v.x;
+    den += v.y;
+  }
+  bands[idx] = den > 0.0 ? (float)(num / den) : 0.0f;
+}
+
+// Standalone spectrum integrator: one CTA per (spectrum, band).
+__global__ void band_integrate_kernel(const float* __restrict__ spectra, const int64_t* __restrict__ offs,
+                                      const int64_t* __restrict__ nu_lo, const int64_t* __restrict__ nu_hi,
+                                      int64_t N, const float* __restrict__ filt, int n_bands,
+                                      float* __restrict__ out, int* __restrict__ status) {
+  const int i = blockIdx.x, b = blockIdx.y;
+  const int64_t lo = nu_lo ? nu_lo[i] : 0, hi = nu_hi ? nu_hi[i] : N;
+  if (lo < 0 || hi > N || lo >= hi) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, BART_DEV_RANGE);
+      out[(int64_t)i * n_bands + b] = 0.0f;
+    }
+    return;
+  }
+  const int64_t base = offs ? offs[i] : (int64_t)i * N;
+  double num = 0.0, den = 0.0;
+  for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+    float dw = (hi - lo == 1) ? 1.0f : ((j == lo || j == hi - 1) ? 0.5f : 1.0f);
+    float W = __ldg(filt + (int64_t)b * N + j) * dw;
+    num += (double)(W * spectra[base + (j - lo)]);
+    den += (double)W;
+  }
+  __shared__ double sn[32], sd[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sn[threadIdx.x >> 5] = num;
+    sd[threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, d = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += sn[w];
+      d += sd[w];
+    }
+    out[(int64_t)i * n_bands + b] = d > 0.0 ? (float)(a / d) : 0.0f;
+  }
+}
+
+template <int S, int NA>
+void launch_emission(dim3 g, cudaStream_t st, const float* grid, int L, int M, int64_t N, const LayerTW* tw,
+                     const float* coef, const float* dpg, const float* ang, double nu_start, double dnu,
+                     const int64_t* lo, const int64_t* hi, const int64_t* offs, float* spectra,
+                     const float* filt, int nb, float2* partial, int n_tiles, int* status) {
+  emission_kernel<S, NA><<<g, EM_THREADS, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi,
+                                                   offs, spectra, filt, nb, partial, n_tiles, status);
+}
+
+using EmLauncher = void (*)(dim3, cudaStream_t, const float*, int, int, int64_t, const LayerTW*, const float*,
+                            const float*, const float*, double, double, const int64_t*, const int64_t*,
+                            const int64_t*, float*, const float*, int, float2*, int, int*);
+
+template <int S>
+EmLauncher pick_na(int na) {
+  switch (na) {
+    case 1: return launch_emission<S, 1>;
+    case 2: return launch_emission<S, 2>;
+    case 4: return launch_emission<S, 4>;
+    case 8: return launch_emission<S, 8>;
+    case 16: return launch_emission<S, 16>;
+    default: return nullptr;
+  }
+}
+
+EmLauncher pick_emission(int S, int na) {
+  switch (S) {
+    case 1: return pick_na<1>(na);
+    case 2: return pick_na<2>(na);
+    case 3: return pick_na<3>(na);
+    case 4: return pick_na<4>(na);
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
+                                    const bart_batch* b, float* spectra, const bart_filters* f, float* bands);
+
+extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
+                                                  const bart_batch* b, float* spectra, const bart_filters* f,
+                                                  float* bands) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, g && c && b, "NULL grid, cfg or batch");
+  BART_REQUIRE(ctx, g->grid, "grid->grid is NULL");
+  BART_REQUIRE(ctx, g->n_species >= 1 && g->n_layers >= 2 && g->n_layers <= MAX_LAYERS && g->n_temps >= 1,
+               "grid shape out of range (S >= 1, 2 <= L <= %d, M >= 1)", MAX_LAYERS);
+  BART_REQUIRE(ctx, g->p_bar && g->t_K, "grid axes are NULL");
+  BART_REQUIRE(ctx, g->nu.n_nu >= 1 && g->nu.n_nu <= (int64_t)65535 * EM_THREADS && g->nu.dnu_cm > 0,
+               "bad nu grid (1 <= n_nu <= %d, dnu > 0)", 65535 * EM_THREADS);
+  for (int k = 0; k < g->n_layers; ++k)
+    BART_REQUIRE(ctx, g->p_bar[k] > 0 && (k == 0 || g->p_bar[k] > g->p_bar[k - 1]),
+                 "p_bar must be positive and strictly increasing");
+  for (int m = 0; m < g->n_temps; ++m)
+    BART_REQUIRE(ctx, g->t_K[m] > 0 && (m == 0 || g->t_K[m] > g->t_K[m - 1]),
+                 "t_K must be positive and strictly increasing");
+  BART_REQUIRE(ctx, c->g_cgs > 0 && c->mu_amu > 0 && c->x0, "cfg: g, mu must be > 0 and x0 set");
+  BART_REQUIRE(ctx, b->n >= 1, "batch.n must be >= 1");
+  BART_REQUIRE(ctx, b->theta || b->t_profile, "batch needs theta or t_profile");
+  BART_REQUIRE(ctx, (b->nu_lo == nullptr) == (b->nu_hi == nullptr), "nu_lo and nu_hi go together");
+  int nb = 0;
+  if (bands) {
+    BART_REQUIRE(ctx, f && f->weights, "bands requested without filters");
+    nb = f->n_bands;
+    BART_REQUIRE(ctx, nb >= 1 && nb <= MAX_BANDS, "n_bands must be in [1, %d]", MAX_BANDS);
+  }
+  if (c->geometry == BART_TRANSMISSION) return bart_transmission_batch(ctx, g, c, b, spectra, f, bands);
+  BART_REQUIRE(ctx, c->geometry == BART_EMISSION, "unknown geometry %d", c->geometry);
+  BART_REQUIRE(ctx, c->n_angles >= 1 && c->n_angles <= MAX_ANGLES, "n_angles must be in [1, %d]", MAX_ANGLES);
+  const int S = g->n_species, L = g->n_layers, M = g->n_temps, n = b->n;
+  const int64_t N = g->nu.n_nu;
+  EmLauncher launch = pick_emission(S, c->n_angles);
+  if (!launch)
+    return bart_fail(ctx, BART_EUNSUPPORTED, "emission with %d species and %d angles is not instantiated "
+                     "(species 1-4; angles 1, 2, 4, 8, 16)", S, c->n_angles);
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+
+  // host-side constants
+  std::vector<double> mu, w;
+  gauss_legendre01(c->n_angles, mu, w);
+  const int NA = c->n_angles;
+  std::vector<float> hconst;                 // [p_cgs L][t_axis M][dpg L-1][ang 2NA][x0 S]
+  for (int k = 0; k < L; ++k) hconst.push_back((float)(g->p_bar[k] * bartc::BAR));
+  for (int m = 0; m < M; ++m) hconst.push_back((float)g->t_K[m]);
+  for (int k = 0; k + 1 < L; ++k)
+    hconst.push_back((float)((g->p_bar[k + 1] - g->p_bar[k]) * bartc::BAR / (2.0 * c->g_cgs)));
+  for (int i = 0; i < NA; ++i) hconst.push_back((float)(-1.4426950408889634 / mu[i]));
+  for (int i = 0; i < NA; ++i) hconst.push_back((float)(2.0 * bartc::PI * w[i] * mu[i] * 0.5));
+  for (int s = 0; s < S; ++s) hconst.push_back((float)(c->x0[s] / (c->mu_amu * bartc::AMU)));
+  const size_t off_t = L, off_dpg = off_t + M, off_ang = off_dpg + (L - 1), off_x0 = off_ang + 2 * NA;
+
+  const int64_t span_max = N;   // spans lie inside the grid
+  const int n_tiles = (int)((span_max + EM_THREADS - 1) / EM_THREADS);
+  void *p_const, *p_tw, *p_coef, *p_part = nullptr;
+  bart_status st;
+  if ((st = bart_scratch(ctx, "fw_const", hconst.size() * sizeof(float), &p_const)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "fw_tw", (size_t)n * L * sizeof(LayerTW), &p_tw)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "fw_coef", (size_t)n * S * sizeof(float), &p_coef)) != BART_OK) return st;
+  if (nb > 0 &&
+      (st = bart_scratch(ctx, "fw_part", (size_t)n * n_tiles * nb * sizeof(float2), &p_part)) != BART_OK)
+    return st;
+  BART_CUDA(ctx, cudaMemcpyAsync(p_const, hconst.data(), hconst.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  const float* dc = (const float*)p_const;
+  const double rs = c->r_star_tp_cm, a = c->a_orbit_cm;
+  const float tirr0 = (rs > 0 && a > 0) ? (float)(std::sqrt(rs / (2.0 * a)) * c->t_star_K) : 0.0f;
+  const float tint4 = (float)std::pow(c->t_int_K, 4.0);
+  tp_kernel<<<n, 128, 0, ctx->stream>>>(b->theta, 5 + S, b->t_profile, n, L, S, dc, dc + off_t, M,
+                                        (float)(1.0 / c->g_cgs), tint4, tirr0, (float)c->t_min_K,
+                                        (float)std::min(c->t_max_K, 1e30), dc + off_x0, (LayerTW*)p_tw,
+                                        (float*)p_coef, ctx->d_status);
+  if ((st = bart_check_launch(ctx, "tp_kernel")) != BART_OK) return st;
+  dim3 grid_dim((unsigned)n, (unsigned)n_tiles);
+  launch(grid_dim, ctx->stream, g->grid, L, M, N, (const LayerTW*)p_tw, (const float*)p_coef, dc + off_dpg,
+         dc + off_ang, g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
+         nb ? f->weights : nullptr, nb, (float2*)p_part, n_tiles, ctx->d_status);
+  if ((st = bart_check_launch(ctx, "emission_kernel")) != BART_OK) return st;
+  if (nb > 0) {
+    int64_t tot = (int64_t)n * nb;
+    band_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>((const float2*)p_part, n,
+                                                                               n_tiles, nb, bands);
+    if ((st = bart_check_launch(ctx, "band_reduce_kernel")) != BART_OK) return st;
+  }
+  return BART_OK;
+}
+
+extern "C" bart_status bart_band_integrate(bart_ctx* ctx, const float* spectra, const int64_t* spec_offsets,
+                                           const int64_t* nu_lo, const int64_t* nu_hi, int n_spec,
+                                           bart_nugrid nu, const bart_filters* f, float* out) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, spectra && f && f->weights && out, "NULL spectra, filters or out");
+  BART_REQUIRE(ctx, n_spec >= 1 && n_spec <= 65535 * 1024, "n_spec out of range");
+  BART_REQUIRE(ctx, f->n_bands >= 1 && f->n_bands <= 65535, "n_bands out of range");
+  BART_REQUIRE(ctx, nu.n_nu >= 1, "n_nu must be >= 1");
+  BART_REQUIRE(ctx, (nu_lo == nullptr) == (nu_hi == nullptr), "nu_lo and nu_hi go together");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  dim3 grid_dim((unsigned)n_spec, (unsigned)f->n_bands);
+  band_integrate_kernel<<<grid_dim, 256, 0, ctx->stream>>>(spectra, spec_offsets, nu_lo, nu_hi, nu.n_nu,
+                                                          f->weights, f->n_bands, out, ctx->d_status);
+  return bart_check_launch(ctx, "band_integrate_kernel");
+}

@@ -1,0 +1,149 @@
+"""GPU parity of the emission forward model and the spectrum integrator
+against the FP64 oracle (Sec. 3; f08isothermal Sec. 5.1.3)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import opacity as O, forward as Fw, radiation as R
+from gpu_common import make_ctx, max_rel
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4      # spectra and band values, relative (FP32 path vs FP64 oracle)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return make_ctx()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def _cfg(n_angles, x0):
+    return dict(geometry=0, n_angles=n_angles, g=W.HD189_GRAV_CGS, mu=W.MEAN_MOLECULAR_MASS_AMU, x0=list(x0),
+                t_int=W.T_INT_K, t_star=W.HD189_TSTAR_K, r_star_tp=W.HD189_RSTAR_CM, a_orbit=W.HD189_A_CM,
+                t_min=500.0, t_max=3000.0)
+
+
+def test_small_emission_workload_end_to_end(ctx, torch):
+    """2 species x 10,000 lines, 60 layers, 2,000 wavenumbers, 4 angles, 4
+    top-hat bands: opacity on the spot, emission, band integration."""
+    import paper_2104_12522_gb300 as bart
+    w = W.emission_small()
+    x0 = [W.BASE_VMR] * 2
+    nu = bart.NuGrid(w.nu_start, w.dnu, w.n_nu)
+    sig = ctx.opacity_cells([bart.device_lines(s) for s in w.species], w.p_bar, w.t_K, nu, w.cutoff)
+    tprof = torch.tensor(w.t_K, dtype=torch.float32, device="cuda")[None].contiguous()
+    spec = torch.empty((1, w.n_nu), dtype=torch.float32, device="cuda")
+    filt = torch.tensor(w.filters, device="cuda")
+    bands = torch.empty((1, 4), dtype=torch.float32, device="cuda")
+    cfg = _cfg(4, x0)
+    cfg.update(t_min=1.0, t_max=1e5)
+    ctx.forward_spectra_batch(sig[:, :, None, :].contiguous(), w.p_bar, [1000.0], nu, cfg, t_profile=tprof,
+                              spectra=spec, filters=filt, bands=bands, n=1)
+    ctx.sync()
+    sig_o = O.opacity_cells(w.species, w.p_bar, w.t_K, w.nu_start, w.dnu, w.n_nu, w.cutoff)
+    chi = Fw.mass_opacity(sig_o, np.asarray(x0), W.MEAN_MOLECULAR_MASS_AMU)
+    nu_ax = W.nu_axis(w.nu_start, w.dnu, w.n_nu)
+    F = R.emission_flux(chi, w.p_bar, w.t_K, nu_ax, W.HD189_GRAV_CGS, 4)
+    Bo = R.band_integrate(F, w.filters)
+    e_spec, e_band = max_rel(spec.cpu().numpy()[0], F), max_rel(bands.cpu().numpy()[0], Bo)
+    print(f"emission (small workload) FP32 vs FP64: spectrum {e_spec:.2e}, bands {e_band:.2e}")
+    assert e_spec < RTOL and e_band < RTOL
+
+
+def test_isothermal_gives_planck(ctx, torch):
+    import paper_2104_12522_gb300 as bart
+    rng = np.random.default_rng(5)
+    S, L, N = 2, 40, 777
+    p = W.log_pressures(L, 1e-6, 100.0)
+    grid = torch.tensor(10 ** rng.uniform(-26, -18, (S, L, 1, N)), dtype=torch.float32, device="cuda")
+    nu = bart.NuGrid(1000.0, 2.5, N)
+    T = torch.full((3, L), 1234.5, dtype=torch.float32, device="cuda")
+    spec = torch.empty((3, N), dtype=torch.float32, device="cuda")
+    for na in (1, 8, 16):
+        cfg = _cfg(na, [1e-4, 3e-4])
+        cfg.update(t_min=1.0, t_max=1e5)
+        ctx.forward_spectra_batch(grid, p, [1000.0], nu, cfg, t_profile=T, spectra=spec, n=3)
+        exp = np.pi * R.planck(W.nu_axis(1000.0, 2.5, N), 1234.5)
+        assert max_rel(spec.cpu().numpy(), exp[None]) < 1e-5
+
+
+def _grid_case(S=2, L=24, M=6, N=700, dnu=0.05, n_lines=400):
+    species = [W.line_list(s, n_lines, 1000.0, 1000.0 + N * dnu) for s in range(S)]
+    p = W.log_pressures(L, 1e-8, 100.0)
+    t = np.linspace(500.0, 3000.0, M)
+    return species, p, t, N, dnu
+
+
+@pytest.fixture(scope="module")
+def grid_case(ctx, torch):
+    import paper_2104_12522_gb300 as bart
+    species, p, t, N, dnu = _grid_case()
+    nu = bart.NuGrid(1000.0, dnu, N)
+    g_dev = ctx.build_opacity_grid([bart.device_lines(s) for s in species], p, t, nu, 25.0)
+    g_ora = O.opacity_grid(species, p, t, 1000.0, dnu, N, 25.0)
+    return species, p, t, N, dnu, nu, g_dev, g_ora
+
+
+@pytest.mark.parametrize("n_angles", [4, 8])
+def test_batched_emission_from_grid(ctx, torch, grid_case, n_angles):
+    """Proposals with the five-parameter T(P) profile and log-abundance
+    scalings, interpolated in T on a GPU-built grid; the oracle uses its own
+    grid.  Includes spans that end inside a CTA tile."""
+    species, p, t, N, dnu, nu, g_dev, g_ora = grid_case
+    n = 37
+    theta = W.proposals(n, generation=7, n_species=2)
+    lo = np.array([0, 5, 129] + [0] * (n - 3), np.int64)
+    hi = np.array([N, N - 3, 400] + [N] * (n - 3), np.int64)
+    offs = np.concatenate([[0], np.cumsum(hi - lo)]).astype(np.int64)
+    filt = W.gaussian_filters(W.nu_axis(1000.0, dnu, N), 5, 1002.0, 1033.0, 2.0, 12.0)
+    x0 = [W.BASE_VMR] * 2
+    cfg = _cfg(n_angles, x0)
+    dev = lambda a: torch.tensor(a, device="cuda")
+    spec = torch.empty(int(offs[-1]), dtype=torch.float32, device="cuda")
+    bands = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+    ctx.forward_spectra_batch(g_dev, p, t, nu, cfg, theta=dev(theta), nu_lo=dev(lo), nu_hi=dev(hi),
+                              spec_offsets=dev(offs), spectra=spec, filters=dev(filt), bands=bands)
+    ctx.sync()
+    spec, bands = spec.cpu().numpy(), bands.cpu().numpy()
+    ocfg = dict(g=cfg["g"], t_int=cfg["t_int"], t_star=cfg["t_star"], r_star_tp=cfg["r_star_tp"],
+                a_orbit=cfg["a_orbit"], t_min=500.0, t_max=3000.0, x0=x0, mu=cfg["mu"], n_angles=n_angles)
+    nu_ax = W.nu_axis(1000.0, dnu, N)
+    es, eb = 0.0, 0.0
+    for i in range(n):
+        F = Fw.emission_spectrum(g_ora[..., lo[i]:hi[i]], p, t, nu_ax[lo[i]:hi[i]], theta[i], ocfg)
+        es = max(es, max_rel(spec[offs[i]:offs[i + 1]], F))
+        Bo = R.band_integrate(F, filt, nu_lo=lo[i])
+        ok = Bo != 0
+        if ok.any():
+            eb = max(eb, max_rel(bands[i][ok], Bo[ok]))
+        assert np.all(bands[i][~ok] == 0.0)
+    print(f"batched emission ({n_angles} angles) FP32 vs FP64: spectra {es:.2e}, bands {eb:.2e}")
+    assert es < RTOL and eb < RTOL
+
+
+def test_band_integrate_standalone(ctx, torch):
+    rng = np.random.default_rng(9)
+    N, n = 1000, 5
+    spec = rng.uniform(0.5, 2.0, (n, N))
+    filt = W.gaussian_filters(W.nu_axis(1000.0, 1.0, N), 7, 1050.0, 1950.0, 20.0, 300.0, seed=77)
+    lo = np.array([0, 10, 500, 999, 3], np.int64)
+    hi = np.array([N, 20, 1000, 1000, 900], np.int64)
+    offs = np.concatenate([[0], np.cumsum(hi - lo)]).astype(np.int64)
+    packed = np.concatenate([spec[i, :hi[i] - lo[i]] for i in range(n)]).astype(np.float32)
+    import paper_2104_12522_gb300 as bart
+    dev = lambda a: torch.tensor(a, device="cuda")
+    out = torch.empty((n, 7), dtype=torch.float32, device="cuda")
+    ctx.band_integrate(dev(packed), dev(filt), bart.NuGrid(1000.0, 1.0, N), out, n, spec_offsets=dev(offs),
+                       nu_lo=dev(lo), nu_hi=dev(hi))
+    got = out.cpu().numpy()
+    for i in range(n):
+        ref = R.band_integrate(packed[offs[i]:offs[i + 1]].astype(np.float64), filt, nu_lo=lo[i])
+        ok = ref != 0
+        assert np.allclose(got[i][ok], ref[ok], rtol=1e-5)
+        assert np.all(got[i][~ok] == 0)

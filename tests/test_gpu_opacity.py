@@ -1,0 +1,157 @@
+"""GPU parity of the line-by-line opacity kernels against the FP64 oracle
+(Sec. 3, Sec. 4 items 3-4; Voigt profile Sec. 5.1.1 Eqs. 2-9)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import opacity as O
+from oracle import voigt as V
+from gpu_common import make_ctx, opacity_errors
+
+pytestmark = pytest.mark.gpu
+
+RTOL_OPACITY = 1e-4      # max relative error over points above 1e-6 of the row maximum
+RTOL_ROW_L2 = 1e-5       # relative L2 error of every row
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return make_ctx()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def test_faddeeva_dense_grid(ctx, torch):
+    # Re w(x + iy) against scipy's wofz (the paper's own reference, Sec. 5.1.1)
+    xs = np.concatenate([np.linspace(-40, 40, 8001), np.linspace(-6, 6, 2401)])
+    ys = np.array([1e-10, 1e-8, 1e-6, 1e-4, 1e-3, 1e-2, 0.05, 0.1, 0.2, 0.3, 0.5, 0.75, 1, 1.5, 2, 3, 4,
+                   4.9, 5.1, 6, 8, 10, 15, 23.9, 24.1, 30, 100, 1e3, 1e4])
+    X, Y = np.meshgrid(xs, ys)
+    x32, y32 = X.astype(np.float32).ravel(), Y.astype(np.float32).ravel()
+    ref = V.faddeeva_re(x32.astype(np.float64), y32.astype(np.float64))
+    got = ctx.faddeeva_re(torch.tensor(x32, device="cuda"), torch.tensor(y32, device="cuda")).cpu().numpy()
+    ok = ref > 1e-30
+    rel = np.abs(got[ok] - ref[ok]) / ref[ok]
+    print(f"Faddeeva FP32 vs FP64: max rel {rel.max():.2e}")
+    assert rel.max() < 1e-5
+
+
+def _small_case():
+    return W.emission_small()
+
+
+@pytest.fixture(scope="module")
+def small(ctx, torch):
+    w = _small_case()
+    ref = O.opacity_cells(w.species, w.p_bar, w.t_K, w.nu_start, w.dnu, w.n_nu, w.cutoff)
+    import paper_2104_12522_gb300 as bart
+    dl = [bart.device_lines(s) for s in w.species]
+    got = ctx.opacity_cells(dl, w.p_bar, w.t_K, bart.NuGrid(w.nu_start, w.dnu, w.n_nu), w.cutoff)
+    ctx.sync()
+    return w, ref, got.cpu().numpy()
+
+
+def test_opacity_cells_small_emission_workload(small):
+    w, ref, got = small
+    rel, l2 = opacity_errors(got, ref)
+    print(f"opacity (2 species x 60 layers x 2000 nu): max rel {rel:.2e}, row L2 {l2:.2e}")
+    assert rel < RTOL_OPACITY and l2 < RTOL_ROW_L2
+    assert np.all(np.isfinite(got))
+
+
+def test_opacity_cores_ragged_tail_and_edges(ctx, torch):
+    # Fine grid (cores resolved by many points), a grid that ends inside a
+    # tile, lines beyond both grid edges, the cutoff hitting grid points
+    # exactly, and pressures from the Doppler to the Lorentz regime.
+    import paper_2104_12522_gb300 as bart
+    rng = np.random.default_rng(11)
+    n_nu, dnu, start, cut = 4099, 0.005, 1500.0, 2.5
+    nu0 = np.sort(np.concatenate([rng.uniform(start - 3, start + n_nu * dnu + 3, 150),
+                                  start + np.array([-2.5, 0.0, 7.5, 10.0]),        # cutoff on grid points
+                                  [start + 1000 * dnu + 1e-9]]))
+    ll = W.LineList(nu0, rng.uniform(-24, -19, nu0.size).astype(np.float32),
+                    rng.uniform(0, 3000, nu0.size).astype(np.float32),
+                    rng.uniform(0.05, 0.1, nu0.size).astype(np.float32), 28.0)
+    p = np.array([1e-8, 1e-5, 1e-3, 0.03, 1.0, 100.0])
+    t = np.array([300.0, 800.0, 1500.0, 2200.0, 2900.0, 1000.0])
+    ref = O.opacity_cells([ll], p, t, start, dnu, n_nu, cut)
+    got = ctx.opacity_cells([bart.device_lines(ll)], p, t, bart.NuGrid(start, dnu, n_nu), cut).cpu().numpy()
+    rel, l2 = opacity_errors(got, ref)
+    print(f"opacity edges/cores: max rel {rel:.2e}, row L2 {l2:.2e}")
+    assert rel < RTOL_OPACITY and l2 < RTOL_ROW_L2
+    # points no line reaches (outside every cutoff window) stay exactly zero
+    assert np.all(got[ref == 0.0] == 0.0)
+
+
+def test_single_line_and_empty_list(ctx, torch):
+    import paper_2104_12522_gb300 as bart
+    one = W.LineList(np.array([1000.37]), np.array([-20.0], np.float32), np.array([500.0], np.float32),
+                     np.array([0.07], np.float32), 18.0)
+    empty = W.LineList(np.zeros(0), np.zeros(0, np.float32), np.zeros(0, np.float32), np.zeros(0, np.float32), 16.0)
+    p, t = np.array([1e-4, 0.5]), np.array([700.0, 1300.0])
+    got = ctx.opacity_cells([bart.device_lines(one), bart.device_lines(empty)], p, t,
+                            bart.NuGrid(990.0, 0.01, 3000), 25.0).cpu().numpy()
+    ref = O.opacity_cells([one], p, t, 990.0, 0.01, 3000, 25.0)
+    rel, l2 = opacity_errors(got[:1], ref)
+    assert rel < RTOL_OPACITY and l2 < RTOL_ROW_L2
+    assert np.all(got[1] == 0.0)
+
+
+def test_grid_equals_cells(ctx, torch):
+    import paper_2104_12522_gb300 as bart
+    ll = W.line_list(2, 500, 1000.0, 1050.0)
+    p = W.log_pressures(4, 1e-6, 10.0)
+    t = np.array([600.0, 1400.0, 2600.0])
+    nu = bart.NuGrid(1000.0, 0.02, 2500)
+    dl = [bart.device_lines(ll)]
+    g = ctx.build_opacity_grid(dl, p, t, nu, 25.0).cpu().numpy()
+    pp, tt = np.repeat(p, 3), np.tile(t, 4)
+    c = ctx.opacity_cells(dl, pp, tt, nu, 25.0).cpu().numpy().reshape(g.shape)
+    assert np.allclose(g, c, rtol=2e-7, atol=0)
+
+
+def test_invalid_arguments_are_rejected(ctx, torch):
+    import paper_2104_12522_gb300 as bart
+    ll = [bart.device_lines(W.line_list(0, 10, 1000.0, 1010.0))]
+    nu = bart.NuGrid(1000.0, 0.1, 100)
+    with pytest.raises(bart.BartError, match="EINVAL"):
+        ctx.opacity_cells(ll, [-1.0], [300.0], nu, 25.0)
+    with pytest.raises(bart.BartError, match="EINVAL"):
+        ctx.opacity_cells(ll, [1.0], [300.0], nu, 0.0)
+    with pytest.raises(bart.BartError, match="EINVAL"):
+        ctx.build_opacity_grid(ll, [1.0, 0.5], [300.0], nu, 25.0)
+    with pytest.raises(bart.BartError, match="EINVAL"):
+        ctx.opacity_cells(ll, [1.0], [300.0], bart.NuGrid(1000.0, -0.1, 100), 25.0)
+
+
+def test_opacity_grid_full_size_sampled(ctx, torch):
+    """The 5e6-line grid (3 species x 100 layers x 20 temperatures x 1e5
+    wavenumbers) in the bench's launch configuration, checked on sampled
+    (species, layer, temperature, window) cells by the oracle."""
+    import paper_2104_12522_gb300 as bart
+    ax = W.grid_axes()
+    species = W.opacity_grid_species(3)
+    dl = [bart.device_lines(s) for s in species]
+    nu = bart.NuGrid(ax.nu_start, ax.dnu, ax.n_nu)
+    grid = ctx.build_opacity_grid(dl, ax.p_bar, ax.t_K, nu, ax.cutoff)
+    ctx.sync()
+    rng = np.random.default_rng(20)
+    worst = (0.0, 0.0)
+    for _ in range(6):
+        s, k, m = int(rng.integers(3)), int(rng.integers(100)), int(rng.integers(20))
+        j0 = int(rng.integers(0, ax.n_nu - 64))
+        if _ == 0:
+            j0 = ax.n_nu - 64          # ragged end of the grid
+        ref = O.opacity_cell(species[s], ax.p_bar[k], ax.t_K[m], ax.nu_start, ax.dnu, ax.n_nu, ax.cutoff,
+                             j0, j0 + 64)
+        got = grid[s, k, m, j0:j0 + 64].cpu().numpy()
+        rel, l2 = opacity_errors(got, ref)
+        worst = (max(worst[0], rel), max(worst[1], l2))
+    print(f"full-size grid, sampled cells: max rel {worst[0]:.2e}, window L2 {worst[1]:.2e}")
+    assert worst[0] < RTOL_OPACITY and worst[1] < RTOL_ROW_L2
+    del grid
+    torch.cuda.empty_cache()
