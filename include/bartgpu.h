@@ -196,7 +196,10 @@ typedef struct {
  *                for the whole grid
  *   spec_offsets device [n+1] start of entry i's spectrum in the packed output
  *                (NULL: entry i starts at i * nu.n_nu)
- *   r_planet_cm, r_star_cm  transmission: device [n] radii */
+ *   r_planet_cm, r_star_cm  transmission: device [n] radii
+ *   active       device [n] or NULL: entries with active[i] == 0 are skipped
+ *                and their spectra and band values are left untouched (used by
+ *                the screened sampler to evaluate survivors only) */
 typedef struct {
   int32_t n;
   const float* theta;
@@ -207,6 +210,7 @@ typedef struct {
   const int64_t* spec_offsets;
   const float* r_planet_cm;
   const float* r_star_cm;
+  const int32_t* active;
 } bart_batch;
 
 /* Filter transmission curves on the grid: device [n_bands][nu.n_nu] FP32. */
@@ -241,6 +245,117 @@ bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid_desc* grid
 bart_status bart_band_integrate(bart_ctx* ctx, const float* spectra, const int64_t* spec_offsets,
                                 const int64_t* nu_lo, const int64_t* nu_hi, int n_spec,
                                 bart_nugrid nu, const bart_filters* filters, float* out);
+
+/* -------------------------------------------------------- surrogate network */
+
+/* Surrogate of the forward model used to screen sampler proposals.  The paper
+ * has no learned component (surrogates appear only as related work, Sec. 1);
+ * this network is the one the screened sampler uses: an MLP with GELU hidden
+ * layers, FP32 master weights, BF16 weights in the forward pass (optional)
+ * and FP32 accumulation, trained by Adam on mean squared error of
+ * standardised targets.
+ * Parameters are one flat FP32 vector: per layer W (row-major [out][in]) then
+ * b ([out]).  Inputs are rescaled as (x - in_shift) * in_scale; targets are
+ * standardised as (log10 t - out_shift) * out_scale if log_outputs, else
+ * (t - out_shift) * out_scale; bart_mlp_forward returns physical values. */
+typedef struct bart_mlp bart_mlp;
+
+/* widths: host [n_widths] layer widths (input first), 2 <= n_widths <= 16,
+ * each in [1, 4096]; max_batch: largest batch any call may use.
+ * The network starts with zero parameters and unit scaling. */
+bart_status bart_mlp_create(bart_ctx* ctx, const int32_t* widths, int n_widths, int bf16_weights,
+                            int log_outputs, int max_batch, bart_mlp** out);
+void bart_mlp_destroy(bart_mlp* net);
+/* Number of parameters, or -1 for NULL. */
+int64_t bart_mlp_num_params(const bart_mlp* net);
+/* Host arrays [in], [in], [out], [out]. */
+bart_status bart_mlp_set_scaling(bart_mlp* net, const float* in_shift, const float* in_scale,
+                                 const float* out_shift, const float* out_scale);
+/* params: device [num_params]; set also clears the Adam state. */
+bart_status bart_mlp_set_params(bart_mlp* net, const float* params);
+bart_status bart_mlp_get_params(bart_mlp* net, float* params);
+/* x: device [B][in] -> y: device [B][out] (physical units), 1 <= B <= max_batch. */
+bart_status bart_mlp_forward(bart_mlp* net, const float* x, int B, float* y);
+/* Loss and its gradient for inputs x [B][in] and targets t [B][out] (physical
+ * units, device).  grad: device [num_params] or NULL; loss: device [1] or NULL. */
+bart_status bart_mlp_gradient(bart_mlp* net, const float* x, const float* t, int B, float* grad,
+                              float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the batch; loss as above. */
+bart_status bart_mlp_train_step(bart_mlp* net, const float* x, const float* t, int B, float lr,
+                                float* loss);
+
+/* ------------------------------------------------------------ sampler */
+
+/* Differential-evolution MCMC (ter Braak 2006, the sampler of Sec. 3-4) over
+ * n_params parameters with a uniform prior on [lo, hi] (host arrays), with
+ * the chains split into two halves that update in alternate half-steps from
+ * differences of the other half's chains:
+ *   y_i = x_i + gamma (x_r1 - x_r2) + eps (hi - lo) N(0, 1),
+ * gamma = 2.38 / sqrt(2 n_params) when the argument is 0, and gamma = 1 on
+ * every jump_every-th generation (0 = never).  Random numbers come from a
+ * counter-based generator keyed by (seed, half_step, chain, draw).
+ * Screening is delayed acceptance: stage 1 keeps a proposal with probability
+ * min(1, exp(ls_y - ls_x)) from the surrogate log-likelihood, stage 2 accepts
+ * a survivor with probability min(1, exp((L_y - L_x) - (ls_y - ls_x))) from
+ * the exact log-likelihood, which keeps the exact posterior as the target.
+ * 6 <= n_chains <= 65536, 1 <= n_params <= 32. */
+typedef struct bart_demc bart_demc;
+bart_status bart_demc_create(bart_ctx* ctx, int n_chains, int n_params, const float* lo, const float* hi,
+                             double gamma, int jump_every, double eps, uint64_t seed, bart_demc** out);
+void bart_demc_destroy(bart_demc* s);
+/* x: device [n_chains][n_params]; loglike, loglike_s: device [n_chains] FP64
+ * (loglike_s may be NULL: surrogate values 0). */
+bart_status bart_demc_set_state(bart_demc* s, const float* x, const double* loglike, const double* loglike_s);
+bart_status bart_demc_get_state(bart_demc* s, float* x, double* loglike, double* loglike_s);
+/* Proposals of half-step `half_step` (the half updated is half_step mod 2):
+ * y device [n_chains][n_params]; inbox device [n_chains] = 1 for the updated
+ * half's proposals inside the prior box, else 0 (other rows copy x). */
+bart_status bart_demc_propose(bart_demc* s, int64_t half_step, float* y, int32_t* inbox);
+/* Stage 1: pass[i] = inbox[i] and the surrogate test (ls_y device [n_chains]
+ * FP64, or NULL for no screening). */
+bart_status bart_demc_screen(bart_demc* s, int64_t half_step, const int32_t* inbox, const double* ls_y,
+                             int32_t* pass);
+/* Stage 2 and state update: L_y device [n_chains] exact log-likelihood of the
+ * proposals (read only where pass[i]); ls_y as in the screen or NULL;
+ * accepted device [n_chains] or NULL. */
+bart_status bart_demc_accept(bart_demc* s, int64_t half_step, const float* y, const int32_t* pass,
+                             const double* L_y, const double* ls_y, int32_t* accepted);
+/* Gaussian log-likelihood of band values (Sec. 3: model bands compared to
+ * data): out[i] = -1/2 sum_b ((model[i][b] - data[b]) / sigma[b])^2 in FP64,
+ * -inf where mask[i] == 0 (mask may be NULL).  model device [n][n_bands];
+ * data, sigma device [n_bands]; out device [n]. */
+bart_status bart_loglike_bands(bart_ctx* ctx, const float* model, int n, int n_bands, const float* data,
+                               const float* sigma, const int32_t* mask, double* out);
+
+/* ------------------------------------------------------------ retrieval */
+
+typedef struct {
+  int64_t proposals;        /* proposals inside the prior box */
+  int64_t screened_out;     /* rejected by the surrogate stage */
+  int64_t exact_evals;      /* proposals evaluated by the exact forward model */
+  int64_t accepted;         /* accepted proposals */
+  double surrogate_err_sum; /* sum over accepted samples of max_b |band_s/band_exact - 1| */
+  double surrogate_err_max; /* largest such error */
+} bart_retrieval_stats;
+
+/* The retrieval loop of Sec. 3 (Fig. 1) on the GPU: n_generations DE-MC
+ * generations (two half-steps each, starting at the even half-step index
+ * first_half_step) of sampler `s` (state set beforehand with
+ * bart_demc_set_state), each proposal's spectrum from the emission forward
+ * model on `grid` integrated over `filters` and compared with `data` +-
+ * `sigma` (device [n_bands]) by bart_loglike_bands.  With a surrogate, its
+ * band values screen proposals first (delayed acceptance) and only survivors
+ * reach the exact model; the exact model judges every accepted sample and
+ * the surrogate's band error on them is accumulated in `stats`.  The sampler
+ * needs 5 + n_species parameters.  use_graph = 1 captures one generation in a
+ * CUDA graph after an eager first generation and replays it (call this before
+ * any outer stream capture).  chain: device [n_generations][n_chains][n_params]
+ * states after each generation, or NULL.  stats: host, or NULL; filled after
+ * the work completes (the call then waits for the stream). */
+bart_status bart_retrieval_run(bart_ctx* ctx, bart_demc* s, bart_mlp* surrogate, const bart_grid_desc* grid,
+                               const bart_fwd_cfg* cfg, const bart_filters* filters, const float* data,
+                               const float* sigma, int64_t first_half_step, int n_generations, int use_graph,
+                               float* chain, bart_retrieval_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,81 @@
+"""Differential-evolution MCMC and its convergence statistics, in FP64 (test
+infrastructure).
+
+Sampler (Sec. 3-4: the paper's DEMC of ter Braak 2006): chains split into two
+halves; a half-step moves every chain i of one half to
+y_i = x_i + gamma (x_r1 - x_r2) + e_i with r1 != r2 drawn from the other half,
+e_i ~ N(0, (eps * width)^2), gamma = 2.38/sqrt(2 d) (1 on every jump_every-th
+generation), uniform prior on a box.  With a surrogate log-likelihood the
+move is delayed acceptance (two-stage Metropolis-Hastings): stage 1 with
+probability min(1, exp(ls_y - ls_x)), stage 2 with
+min(1, exp((L_y - L_x) - (ls_y - ls_x))).  Random numbers come from numpy, so
+parity with the GPU sampler is distributional.
+
+Statistics (Sec. 4 "Bayesian samplers", App. C):
+* SPEIS by summing the autocorrelation from lag 0 until it first falls below a
+  small positive threshold: SPEIS = 1 + 2 sum_{k>=1} rho_k; ESS = N / SPEIS;
+* standard error of a mean, s = sigma / sqrt(ESS) (App. C, Eq. C3 reading);
+* accuracy of a credible region's probability content,
+  s_C = sqrt(C (1 - C) / ESS) (Sec. 4, Eq. 12 solved for s_C).
+"""
+import numpy as np
+
+
+def run(loglike, x0, lo, hi, n_gen, rng, gamma=None, jump_every=10, eps=1e-4, surrogate=None):
+    """Returns the chain history [n_gen+1][C][d] and acceptance counts."""
+    x = np.array(x0, np.float64)
+    C, d = x.shape
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    g0 = 2.38 / np.sqrt(2.0 * d) if gamma is None else gamma
+    L = np.array([loglike(v) for v in x])
+    Ls = np.array([surrogate(v) for v in x]) if surrogate else np.zeros(C)
+    hist = [x.copy()]
+    acc = 0
+    halves = (np.arange(0, C // 2), np.arange(C // 2, C))
+    for gen in range(n_gen):
+        gm = 1.0 if (jump_every and gen % jump_every == jump_every - 1) else g0
+        for h in (0, 1):
+            own, other = halves[h], halves[1 - h]
+            for i in own:
+                r1, r2 = rng.choice(other, 2, replace=False)
+                y = x[i] + gm * (x[r1] - x[r2]) + eps * (hi - lo) * rng.normal(size=d)
+                if np.any(y < lo) or np.any(y > hi):
+                    continue
+                ly_s = surrogate(y) if surrogate else 0.0
+                if surrogate and np.log(rng.uniform()) >= ly_s - Ls[i]:
+                    continue
+                ly = loglike(y)
+                r = (ly - L[i]) - (ly_s - Ls[i])
+                if r >= 0 or np.log(rng.uniform()) < r:
+                    x[i], L[i], Ls[i] = y, ly, ly_s
+                    acc += 1
+        hist.append(x.copy())
+    return np.array(hist), acc
+
+
+def speis(chain, threshold=0.01):
+    """Steps per effectively independent sample of a 1-D chain."""
+    c = np.asarray(chain, np.float64) - np.mean(chain)
+    n = c.size
+    var = np.dot(c, c) / n
+    if var == 0:
+        return 1.0
+    s = 1.0
+    for k in range(1, n // 2):
+        rho = np.dot(c[:-k], c[k:]) / (n * var)
+        if rho < threshold:
+            break
+        s += 2.0 * rho
+    return s
+
+
+def ess(samples_per_chain):
+    """Effective sample size of samples [n][C][d]: total samples divided by
+    the largest SPEIS over parameters (mean over chains)."""
+    n, C, d = samples_per_chain.shape
+    sp = max(np.mean([speis(samples_per_chain[:, c, q]) for c in range(C)]) for q in range(d))
+    return n * C / sp
+
+
+def credible_content_se(c_hat, ess_value):
+    return np.sqrt(c_hat * (1.0 - c_hat) / ess_value)

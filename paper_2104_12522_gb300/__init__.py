@@ -17,7 +17,7 @@ import numpy as np
 from . import _native
 from ._native import BART_EMISSION, BART_TRANSMISSION  # noqa: F401
 
-__all__ = ["Context", "BartError", "DeviceLines", "device_lines", "NuGrid", "BART_EMISSION",
+__all__ = ["Context", "BartError", "DeviceLines", "device_lines", "NuGrid", "Mlp", "Demc", "BART_EMISSION",
            "BART_TRANSMISSION"]
 
 
@@ -74,6 +74,21 @@ def _check_tensor(t, dtype: str, numel: Optional[int] = None):
         raise TypeError("expected a contiguous tensor")
     if numel is not None and t.numel() != numel:
         raise ValueError(f"expected {numel} elements, got {t.numel()}")
+
+
+def _grid_cfg(grid, p_bar, t_K, nu, cfg):
+    """bart_grid_desc and bart_fwd_cfg for a device grid [S][L][M][n_nu]; the
+    third value keeps the host arrays alive for the call."""
+    S, L, M, N = (int(v) for v in grid.shape)
+    pb, tk, x0 = _dbl(p_bar), _dbl(t_K), _dbl(cfg["x0"])
+    gd = _native.GridDesc(_ptr(grid), S, L, M, C.cast(pb, C.c_void_p), C.cast(tk, C.c_void_p), nu)
+    fc = _native.FwdCfg(int(cfg.get("geometry", 0)), int(cfg.get("n_angles", 4)), float(cfg["g"]),
+                        float(cfg["mu"]), float(cfg.get("t_int", 100.0)), float(cfg.get("t_star", 5000.0)),
+                        float(cfg.get("r_star_tp", 0.0)), float(cfg.get("a_orbit", 0.0)),
+                        float(cfg.get("t_min", 0.0)), float(cfg.get("t_max", 1e30)),
+                        float(cfg.get("p_ref", 0.1)), float(cfg.get("p_top", 1e-8)),
+                        float(cfg.get("p_bot", 100.0)), C.cast(x0, C.c_void_p))
+    return gd, fc, (pb, tk, x0)
 
 
 def _dbl(a) -> C.Array:
@@ -159,7 +174,7 @@ class Context:
     # ------------------------------------------------------------ forward model
     def forward_spectra_batch(self, grid, p_bar, t_K, nu, cfg: dict, theta=None, t_profile=None,
                               n_levels=None, nu_lo=None, nu_hi=None, spec_offsets=None, r_planet=None,
-                              r_star=None, spectra=None, filters=None, bands=None, n=None):
+                              r_star=None, spectra=None, filters=None, bands=None, n=None, active=None):
         """Spectra and/or band values of a batch; see bart_forward_spectra_batch.
 
         `grid` is the device opacity grid [S][L][M][n_nu]; `cfg` holds the
@@ -168,7 +183,7 @@ class Context:
         _check_tensor(grid, "float32")
         for t, dt in ((theta, "float32"), (t_profile, "float32"), (n_levels, "int32"), (nu_lo, "int64"),
                       (nu_hi, "int64"), (spec_offsets, "int64"), (r_planet, "float32"), (r_star, "float32"),
-                      (spectra, "float32"), (filters, "float32"), (bands, "float32")):
+                      (spectra, "float32"), (filters, "float32"), (bands, "float32"), (active, "int32")):
             _check_tensor(t, dt)
         if n is None:
             n = int(theta.shape[0]) if theta is not None else int(t_profile.shape[0])
@@ -177,24 +192,16 @@ class Context:
         if t_profile is not None and tuple(t_profile.shape) != (n, L):
             raise ValueError(f"t_profile must be [{n}][{L}]")
         for t, want in ((n_levels, n), (nu_lo, n), (nu_hi, n), (spec_offsets, n + 1), (r_planet, n),
-                        (r_star, n)):
+                        (r_star, n), (active, n)):
             if t is not None and t.numel() != want:
                 raise ValueError(f"per-entry array has {t.numel()} elements, expected {want}")
         if bands is not None and (filters is None or tuple(bands.shape) != (n, int(filters.shape[0]))):
             raise ValueError("bands must be [n][n_bands] and need filters")
         if filters is not None and tuple(filters.shape[1:]) != (N,):
             raise ValueError("filters must be [n_bands][n_nu]")
-        pb, tk = _dbl(p_bar), _dbl(t_K)
-        gd = _native.GridDesc(_ptr(grid), S, L, M, C.cast(pb, C.c_void_p), C.cast(tk, C.c_void_p), nu)
-        x0 = _dbl(cfg["x0"])
-        fc = _native.FwdCfg(int(cfg.get("geometry", 0)), int(cfg.get("n_angles", 4)), float(cfg["g"]),
-                            float(cfg["mu"]), float(cfg.get("t_int", 100.0)), float(cfg.get("t_star", 5000.0)),
-                            float(cfg.get("r_star_tp", 0.0)), float(cfg.get("a_orbit", 0.0)),
-                            float(cfg.get("t_min", 0.0)), float(cfg.get("t_max", 1e30)),
-                            float(cfg.get("p_ref", 0.1)), float(cfg.get("p_top", 1e-8)),
-                            float(cfg.get("p_bot", 100.0)), C.cast(x0, C.c_void_p))
+        gd, fc, keep = _grid_cfg(grid, p_bar, t_K, nu, cfg)
         b = _native.Batch(int(n), _ptr(theta), _ptr(t_profile), _ptr(n_levels), _ptr(nu_lo), _ptr(nu_hi),
-                          _ptr(spec_offsets), _ptr(r_planet), _ptr(r_star))
+                          _ptr(spec_offsets), _ptr(r_planet), _ptr(r_star), _ptr(active))
         fl = None
         if filters is not None:
             fl = _native.Filters(int(filters.shape[0]), _ptr(filters))
@@ -202,6 +209,31 @@ class Context:
                                                         _ptr(spectra), C.byref(fl) if fl else None,
                                                         _ptr(bands)))
         return spectra, bands
+
+    def retrieval_run(self, demc, surrogate, grid, p_bar, t_K, nu, cfg, filters, data, sigma, n_generations,
+                      first_half_step=0, use_graph=True, chain=None):
+        """bart_retrieval_run; returns the statistics as a dict."""
+        for t, dt in ((grid, "float32"), (filters, "float32"), (data, "float32"), (sigma, "float32"),
+                      (chain, "float32")):
+            _check_tensor(t, dt)
+        gd, fc, keep = _grid_cfg(grid, p_bar, t_K, nu, cfg)
+        fl = _native.Filters(int(filters.shape[0]), _ptr(filters))
+        st = _native.RetrievalStats()
+        self._check(self.lib.bart_retrieval_run(self.h, demc.h, surrogate.h if surrogate is not None else None,
+                                                C.byref(gd), C.byref(fc), C.byref(fl), _ptr(data), _ptr(sigma),
+                                                int(first_half_step), int(n_generations), int(bool(use_graph)),
+                                                _ptr(chain), C.byref(st)))
+        return {k: getattr(st, k) for k, _ in _native.RetrievalStats._fields_}
+
+    def loglike_bands(self, model, data, sigma, out, mask=None):
+        """out[i] = -1/2 sum_b ((model[i][b] - data[b]) / sigma[b])^2 (FP64)."""
+        n, nb = (int(v) for v in model.shape)
+        for t, dt in ((model, "float32"), (data, "float32"), (sigma, "float32"), (mask, "int32"),
+                      (out, "float64")):
+            _check_tensor(t, dt)
+        self._check(self.lib.bart_loglike_bands(self.h, _ptr(model), n, nb, _ptr(data), _ptr(sigma), _ptr(mask),
+                                                _ptr(out)))
+        return out
 
     def band_integrate(self, spectra, filters, nu, out, n_spec, spec_offsets=None, nu_lo=None, nu_hi=None):
         for t, dt in ((spectra, "float32"), (filters, "float32"), (out, "float32"), (spec_offsets, "int64"),
@@ -211,3 +243,122 @@ class Context:
         self._check(self.lib.bart_band_integrate(self.h, _ptr(spectra), _ptr(spec_offsets), _ptr(nu_lo),
                                                  _ptr(nu_hi), int(n_spec), nu, C.byref(fl), _ptr(out)))
         return out
+
+
+def _flt(a) -> C.Array:
+    a = np.ascontiguousarray(a, np.float32)
+    return (C.c_float * a.size)(*a.tolist())
+
+
+class Mlp:
+    """Surrogate network (bart_mlp_*) bound to a Context."""
+
+    def __init__(self, ctx: Context, widths, bf16_weights=True, log_outputs=True, max_batch=4096):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.widths = [int(w) for w in widths]
+        w = (C.c_int32 * len(self.widths))(*self.widths)
+        h = C.c_void_p()
+        ctx._check(self.lib.bart_mlp_create(ctx.h, w, len(self.widths), int(bool(bf16_weights)),
+                                            int(bool(log_outputs)), int(max_batch), C.byref(h)))
+        self.h = h
+        self.n_params = int(self.lib.bart_mlp_num_params(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bart_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_scaling(self, in_shift, in_scale, out_shift, out_scale):
+        self.ctx._check(self.lib.bart_mlp_set_scaling(self.h, _flt(in_shift), _flt(in_scale), _flt(out_shift),
+                                                      _flt(out_scale)))
+
+    def set_params(self, params):
+        _check_tensor(params, "float32", self.n_params)
+        self.ctx._check(self.lib.bart_mlp_set_params(self.h, _ptr(params)))
+
+    def get_params(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n_params, dtype=torch.float32, device=f"cuda:{self.ctx.device}")
+        _check_tensor(out, "float32", self.n_params)
+        self.ctx._check(self.lib.bart_mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def forward(self, x, out=None):
+        import torch
+        _check_tensor(x, "float32")
+        B = int(x.shape[0])
+        if out is None:
+            out = torch.empty((B, self.widths[-1]), dtype=torch.float32, device=x.device)
+        _check_tensor(out, "float32", B * self.widths[-1])
+        self.ctx._check(self.lib.bart_mlp_forward(self.h, _ptr(x), B, _ptr(out)))
+        return out
+
+    def gradient(self, x, t, grad=None, loss=None):
+        import torch
+        _check_tensor(x, "float32")
+        _check_tensor(t, "float32", int(x.shape[0]) * self.widths[-1])
+        if grad is None:
+            grad = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        self.ctx._check(self.lib.bart_mlp_gradient(self.h, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(grad),
+                                                   _ptr(loss)))
+        return grad, loss
+
+    def train_step(self, x, t, lr, loss=None):
+        _check_tensor(x, "float32")
+        _check_tensor(t, "float32", int(x.shape[0]) * self.widths[-1])
+        self.ctx._check(self.lib.bart_mlp_train_step(self.h, _ptr(x), _ptr(t), int(x.shape[0]), float(lr),
+                                                     _ptr(loss)))
+        return loss
+
+
+class Demc:
+    """Differential-evolution sampler state (bart_demc_*) bound to a Context."""
+
+    def __init__(self, ctx: Context, n_chains, lo, hi, gamma=0.0, jump_every=10, eps=1e-4, seed=6000):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.C, self.d = int(n_chains), len(lo)
+        h = C.c_void_p()
+        ctx._check(self.lib.bart_demc_create(ctx.h, self.C, self.d, _flt(lo), _flt(hi), float(gamma),
+                                             int(jump_every), float(eps), C.c_uint64(int(seed)), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bart_demc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, x, loglike, loglike_s=None):
+        _check_tensor(x, "float32", self.C * self.d)
+        _check_tensor(loglike, "float64", self.C)
+        _check_tensor(loglike_s, "float64", self.C)
+        self.ctx._check(self.lib.bart_demc_set_state(self.h, _ptr(x), _ptr(loglike), _ptr(loglike_s)))
+
+    def get_state(self, x=None, loglike=None, loglike_s=None):
+        self.ctx._check(self.lib.bart_demc_get_state(self.h, _ptr(x), _ptr(loglike), _ptr(loglike_s)))
+        return x, loglike, loglike_s
+
+    def propose(self, half_step, y, inbox):
+        self.ctx._check(self.lib.bart_demc_propose(self.h, int(half_step), _ptr(y), _ptr(inbox)))
+
+    def screen(self, half_step, inbox, ls_y, passed):
+        self.ctx._check(self.lib.bart_demc_screen(self.h, int(half_step), _ptr(inbox), _ptr(ls_y), _ptr(passed)))
+
+    def accept(self, half_step, y, passed, L_y, ls_y=None, accepted=None):
+        self.ctx._check(self.lib.bart_demc_accept(self.h, int(half_step), _ptr(y), _ptr(passed), _ptr(L_y),
+                                                  _ptr(ls_y), _ptr(accepted)))

@@ -44,11 +44,16 @@ class FwdCfg(C.Structure):
 class Batch(C.Structure):
     _fields_ = [("n", c_int32), ("theta", c_void_p), ("t_profile", c_void_p), ("n_levels", c_void_p),
                 ("nu_lo", c_void_p), ("nu_hi", c_void_p), ("spec_offsets", c_void_p),
-                ("r_planet_cm", c_void_p), ("r_star_cm", c_void_p)]
+                ("r_planet_cm", c_void_p), ("r_star_cm", c_void_p), ("active", c_void_p)]
 
 
 class Filters(C.Structure):
     _fields_ = [("n_bands", c_int32), ("weights", c_void_p)]
+
+
+class RetrievalStats(C.Structure):
+    _fields_ = [("proposals", c_int64), ("screened_out", c_int64), ("exact_evals", c_int64),
+                ("accepted", c_int64), ("surrogate_err_sum", c_double), ("surrogate_err_max", c_double)]
 
 
 P = C.POINTER
@@ -69,6 +74,26 @@ SIGNATURES = {
                                            c_void_p]),
     "bart_band_integrate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, NuGrid,
                                     P(Filters), c_void_p]),
+    "bart_mlp_create": (c_int, [c_void_p, P(c_int32), c_int, c_int, c_int, c_int, P(c_void_p)]),
+    "bart_mlp_destroy": (None, [c_void_p]),
+    "bart_mlp_num_params": (c_int64, [c_void_p]),
+    "bart_mlp_set_scaling": (c_int, [c_void_p, P(C.c_float), P(C.c_float), P(C.c_float), P(C.c_float)]),
+    "bart_mlp_set_params": (c_int, [c_void_p, c_void_p]),
+    "bart_mlp_get_params": (c_int, [c_void_p, c_void_p]),
+    "bart_mlp_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    "bart_mlp_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "bart_mlp_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, C.c_float, c_void_p]),
+    "bart_demc_create": (c_int, [c_void_p, c_int, c_int, P(C.c_float), P(C.c_float), c_double, c_int, c_double,
+                                 C.c_uint64, P(c_void_p)]),
+    "bart_demc_destroy": (None, [c_void_p]),
+    "bart_demc_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bart_demc_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bart_demc_propose": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
+    "bart_demc_screen": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "bart_demc_accept": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bart_loglike_bands": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bart_retrieval_run": (c_int, [c_void_p, c_void_p, c_void_p, P(GridDesc), P(FwdCfg), P(Filters), c_void_p,
+                                   c_void_p, c_int64, c_int, c_int, c_void_p, P(RetrievalStats)]),
 }
 
 _lib = None

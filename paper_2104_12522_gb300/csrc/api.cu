@@ -49,6 +49,21 @@ bart_status bart_scratch(bart_ctx* ctx, const char* name, size_t bytes, void** o
   return BART_OK;
 }
 
+bart_status bart_upload_const(bart_ctx* ctx, const char* name, const void* data, size_t bytes, void** dev) {
+  void* before = nullptr;
+  auto it0 = ctx->scratch.find(name);
+  if (it0 != ctx->scratch.end()) before = it0->second.first;
+  bart_status st = bart_scratch(ctx, name, bytes, dev);
+  if (st != BART_OK) return st;
+  auto& host = ctx->uploaded[name];
+  const unsigned char* src = static_cast<const unsigned char*>(data);
+  if (*dev == before && host.size() == bytes && std::memcmp(host.data(), src, bytes) == 0) return BART_OK;
+  host.assign(src, src + bytes);
+  // from the retained host copy, which outlives the asynchronous copy
+  BART_CUDA(ctx, cudaMemcpyAsync(*dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return BART_OK;
+}
+
 extern "C" bart_status bart_create(bart_ctx** out, int device, void* cuda_stream) {
   if (!out) return BART_EINVAL;
   *out = nullptr;

@@ -23,6 +23,7 @@ struct bart_ctx {
   std::string err;
   // Growable scratch: one buffer per purpose so calls can keep it resident.
   std::map<std::string, std::pair<void*, size_t>> scratch;
+  std::map<std::string, std::vector<unsigned char>> uploaded;   // host copy of each constant buffer
   int* d_status = nullptr;          // device status word
   float2* d_wtable = nullptr;       // Faddeeva Taylor-coefficient table
   bool wtable_ready = false;
@@ -47,6 +48,12 @@ bart_status bart_fail(bart_ctx* ctx, bart_status st, const char* fmt, ...);
 
 // Scratch buffer of at least `bytes` bytes named `name`, kept for later calls.
 bart_status bart_scratch(bart_ctx* ctx, const char* name, size_t bytes, void** out);
+
+// Device copy of a small host constant buffer, kept in scratch `name`.  The
+// copy is issued only when the bytes differ from the last upload, so a call
+// repeated with the same arguments launches kernels only (and can be captured
+// in a CUDA graph).
+bart_status bart_upload_const(bart_ctx* ctx, const char* name, const void* data, size_t bytes, void** dev);
 
 // Launch-error check after a kernel launch.
 bart_status bart_check_launch(bart_ctx* ctx, const char* what);

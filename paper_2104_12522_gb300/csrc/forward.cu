@@ -142,10 +142,11 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
                 double dnu, const int64_t* __restrict__ nu_lo, const int64_t* __restrict__ nu_hi,
                 const int64_t* __restrict__ offs, float* __restrict__ spectra,
                 const float* __restrict__ filt, int n_bands, float2* __restrict__ partial, int n_tiles,
-                int* __restrict__ status) {
+                const int32_t* __restrict__ act_mask, int* __restrict__ status) {
   const int p = blockIdx.x;
   const int tile = blockIdx.y;
   const int tid = threadIdx.x;
+  if (act_mask && !act_mask[p]) return;        // skipped entry: outputs untouched
   const int64_t lo = nu_lo ? nu_lo[p] : 0;
   const int64_t hi = nu_hi ? nu_hi[p] : N;
   if (lo < 0 || hi > N || lo >= hi) {          // invalid span: report, touch nothing
@@ -243,10 +244,11 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
 }
 
 __global__ void band_reduce_kernel(const float2* __restrict__ partial, int n, int n_tiles, int n_bands,
-                                   float* __restrict__ bands) {
+                                   const int32_t* __restrict__ active, float* __restrict__ bands) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * n_bands) return;
   int p = (int)(idx / n_bands), b = (int)(idx % n_bands);
+  if (active && !active[p]) return;
   double num = 0.0, den = 0.0;
   for (int t = 0; t < n_tiles; ++t) {
     float2 v = partial[((int64_t)p * n_tiles + t) * n_bands + b];
@@ -302,14 +304,14 @@ template <int S, int NA>
 void launch_emission(dim3 g, cudaStream_t st, const float* grid, int L, int M, int64_t N, const LayerTW* tw,
                      const float* coef, const float* dpg, const float* ang, double nu_start, double dnu,
                      const int64_t* lo, const int64_t* hi, const int64_t* offs, float* spectra,
-                     const float* filt, int nb, float2* partial, int n_tiles, int* status) {
+                     const float* filt, int nb, float2* partial, int n_tiles, const int32_t* active, int* status) {
   emission_kernel<S, NA><<<g, EM_THREADS, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi,
-                                                   offs, spectra, filt, nb, partial, n_tiles, status);
+                                                   offs, spectra, filt, nb, partial, n_tiles, active, status);
 }
 
 using EmLauncher = void (*)(dim3, cudaStream_t, const float*, int, int, int64_t, const LayerTW*, const float*,
                             const float*, const float*, double, double, const int64_t*, const int64_t*,
-                            const int64_t*, float*, const float*, int, float2*, int, int*);
+                            const int64_t*, float*, const float*, int, float2*, int, const int32_t*, int*);
 
 template <int S>
 EmLauncher pick_na(int na) {
@@ -394,14 +396,13 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
   const int n_tiles = (int)((span_max + EM_THREADS - 1) / EM_THREADS);
   void *p_const, *p_tw, *p_coef, *p_part = nullptr;
   bart_status st;
-  if ((st = bart_scratch(ctx, "fw_const", hconst.size() * sizeof(float), &p_const)) != BART_OK) return st;
+  if ((st = bart_upload_const(ctx, "fw_const", hconst.data(), hconst.size() * sizeof(float), &p_const)) != BART_OK)
+    return st;
   if ((st = bart_scratch(ctx, "fw_tw", (size_t)n * L * sizeof(LayerTW), &p_tw)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "fw_coef", (size_t)n * S * sizeof(float), &p_coef)) != BART_OK) return st;
   if (nb > 0 &&
       (st = bart_scratch(ctx, "fw_part", (size_t)n * n_tiles * nb * sizeof(float2), &p_part)) != BART_OK)
     return st;
-  BART_CUDA(ctx, cudaMemcpyAsync(p_const, hconst.data(), hconst.size() * sizeof(float), cudaMemcpyHostToDevice,
-                                 ctx->stream));
   const float* dc = (const float*)p_const;
   const double rs = c->r_star_tp_cm, a = c->a_orbit_cm;
   const float tirr0 = (rs > 0 && a > 0) ? (float)(std::sqrt(rs / (2.0 * a)) * c->t_star_K) : 0.0f;
@@ -414,12 +415,12 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
   dim3 grid_dim((unsigned)n, (unsigned)n_tiles);
   launch(grid_dim, ctx->stream, g->grid, L, M, N, (const LayerTW*)p_tw, (const float*)p_coef, dc + off_dpg,
          dc + off_ang, g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
-         nb ? f->weights : nullptr, nb, (float2*)p_part, n_tiles, ctx->d_status);
+         nb ? f->weights : nullptr, nb, (float2*)p_part, n_tiles, b->active, ctx->d_status);
   if ((st = bart_check_launch(ctx, "emission_kernel")) != BART_OK) return st;
   if (nb > 0) {
     int64_t tot = (int64_t)n * nb;
     band_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>((const float2*)p_part, n,
-                                                                               n_tiles, nb, bands);
+                                                                               n_tiles, nb, b->active, bands);
     if ((st = bart_check_launch(ctx, "band_reduce_kernel")) != BART_OK) return st;
   }
   return BART_OK;

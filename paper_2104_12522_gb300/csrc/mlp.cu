@@ -1,0 +1,417 @@
+// Surrogate network of the screened sampler: hand-written forward, backward
+// and Adam kernels (the paper has no learned component; the network is the
+// task's: theta -> 256 -> 256 -> 256 -> band values, GELU, BF16 weights with
+// FP32 accumulation).
+//
+// Layout: flat FP32 master parameters, per layer W_l row-major [out][in] then
+// b_l [out].  The forward pass reads either BF16 copies of the weights (made
+// after every update, round to nearest even) or the FP32 master (test mode).
+// Every layer is one tiled SIMT GEMM with a fused epilogue (bias, GELU,
+// input/target scaling); FP32 accumulation throughout.  The layers are
+// 256 wide and the batches at most a few thousand rows, so one layer is
+// ~1e8 flops: far below what would pay for tensor-core tiles, the GEMMs run on
+// the FP32 pipe.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <vector>
+
+#include "bart_internal.cuh"
+
+struct bart_mlp {
+  bart_ctx* ctx = nullptr;
+  std::vector<int> widths;
+  int n_layers = 0;
+  int64_t n_params = 0;
+  int bf16 = 1;
+  int log_outputs = 0;
+  int max_batch = 0;
+  int64_t step = 0;
+  std::vector<int64_t> w_off, b_off;   // offsets into the flat vector
+  float* p = nullptr;                  // master FP32 params
+  float* m = nullptr;                  // Adam moments
+  float* v = nullptr;
+  float* g = nullptr;                  // gradient
+  __nv_bfloat16* wb = nullptr;         // BF16 weights (same offsets as p)
+  float* act = nullptr;                // activations: per layer z and h, [max_batch][width]
+  std::vector<int64_t> z_off, h_off;
+  float* scale = nullptr;              // in_shift[in], in_scale[in], out_shift[out], out_scale[out]
+  float* loss = nullptr;
+};
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;   // CTA tile and K step
+constexpr int MLP_THREADS = 256;           // 16 x 16 threads, 4 x 4 outputs each
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
+}
+
+template <typename T>
+__device__ __forceinline__ float ld(const T* p) { return (float)p[0]; }
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(p[0]); }
+
+// C[M][N] = sum_k A(m, k) B(k, n), with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn].
+// Epilogue modes:
+//   0  C = acc                                  (plain)
+//   1  z = acc + bias[n]; C = z; H = GELU(z)    (hidden layer forward)
+//   2  C = acc + bias[n]                        (output layer forward)
+//   3  C = acc * GELU'(Z[m][n])                 (backward through a hidden layer)
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(MLP_THREADS)
+gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
+            int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc, int mode, const float* __restrict__ bias,
+            float* __restrict__ H, const float* __restrict__ Z) {
+  __shared__ float sA[TK][TM + 4];
+  __shared__ float sB[TK][TN + 4];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int e = threadIdx.x; e < TM * TK; e += MLP_THREADS) {
+      const int mm = e / TK, kk = e % TK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      sA[kk][mm] = (gm < M && gk < K) ? ld(A + gm * sam + gk * sak) : 0.f;
+    }
+    for (int e = threadIdx.x; e < TN * TK; e += MLP_THREADS) {
+      const int nn = e % TN, kk = e / TN;
+      const int gn = n0 + nn, gk = k0 + kk;
+      sB[kk][nn] = (gn < N && gk < K) ? ld(B + gk * sbk + gn * sbn) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sB[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty * 4 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn >= N) continue;
+      float v = acc[i][j];
+      const int64_t o = (int64_t)gm * ldc + gn;
+      if (mode == 1) {
+        v += bias[gn];
+        C[o] = v;
+        H[o] = gelu(v);
+      } else if (mode == 2) {
+        C[o] = v + bias[gn];
+      } else if (mode == 3) {
+        C[o] = v * gelu_grad(Z[o]);
+      } else {
+        C[o] = v;
+      }
+    }
+  }
+}
+
+// x_scaled[b][i] = (x[b][i] - shift[i]) * scale[i]
+__global__ void scale_inputs(const float* __restrict__ x, int B, int n, const float* __restrict__ shift,
+                             const float* __restrict__ scale, float* __restrict__ out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)B * n) return;
+  int i = (int)(e % n);
+  out[e] = (x[e] - shift[i]) * scale[i];
+}
+
+// Physical outputs from the standardised prediction.
+__global__ void unscale_outputs(const float* __restrict__ y, int B, int n, const float* __restrict__ shift,
+                                const float* __restrict__ scale, int log_outputs, float* __restrict__ out) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)B * n) return;
+  int i = (int)(e % n);
+  float v = y[e] / scale[i] + shift[i];
+  out[e] = log_outputs ? exp10f(v) : v;
+}
+
+// dY = 2 (y - t_std) / (B n); loss = mean (y - t_std)^2 (one CTA, fixed order).
+__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, int B, int n,
+                           const float* __restrict__ shift, const float* __restrict__ scale, int log_outputs,
+                           float* __restrict__ dy, float* __restrict__ loss) {
+  __shared__ double red[1024];
+  double acc = 0.0;
+  const float inv = 2.0f / (float)((int64_t)B * n);
+  for (int64_t e = threadIdx.x; e < (int64_t)B * n; e += blockDim.x) {
+    int i = (int)(e % n);
+    float tv = log_outputs ? log10f(t[e]) : t[e];
+    float r = y[e] - (tv - shift[i]) * scale[i];
+    dy[e] = inv * r;
+    acc += (double)r * r;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) *loss = (float)(red[0] / ((double)B * n));
+}
+
+// db[n] = sum_b dz[b][n], fixed order per column.
+__global__ void bias_grad(const float* __restrict__ dz, int B, int n, float* __restrict__ db) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += dz[(int64_t)b * n + j];
+  db[j] = s;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(p[i]);
+}
+
+unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename TA, typename TB>
+void gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
+          int64_t sbn, float* C, int64_t ldc, int mode, const float* bias = nullptr, float* H = nullptr,
+          const float* Z = nullptr) {
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+  gemm_kernel<TA, TB><<<grid, MLP_THREADS, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, mode, bias, H, Z);
+}
+
+// Forward pass of B rows already scaled into act layer 0; fills z/h of every layer.
+void run_forward(bart_mlp* net, int B) {
+  cudaStream_t st = net->ctx->stream;
+  for (int l = 0; l < net->n_layers; ++l) {
+    const int n_in = net->widths[l], n_out = net->widths[l + 1];
+    const float* h_prev = net->act + net->h_off[l];
+    float* z = net->act + net->z_off[l + 1];
+    float* h = net->act + net->h_off[l + 1];
+    const int mode = (l + 1 < net->n_layers) ? 1 : 2;
+    const float* bias = net->p + net->b_off[l];
+    // z[b][o] = sum_i h_prev[b][i] W[o][i]
+    if (net->bf16)
+      gemm<float, __nv_bfloat16>(st, B, n_out, n_in, h_prev, n_in, 1, net->wb + net->w_off[l], 1, n_in, z, n_out,
+                                 mode, bias, h);
+    else
+      gemm<float, float>(st, B, n_out, n_in, h_prev, n_in, 1, net->p + net->w_off[l], 1, n_in, z, n_out, mode,
+                         bias, h);
+  }
+}
+
+bart_status check_batch(bart_mlp* net, int B) {
+  if (B < 1 || B > net->max_batch)
+    return bart_fail(net->ctx, BART_EINVAL, "batch %d outside [1, %d]", B, net->max_batch);
+  return BART_OK;
+}
+
+bart_status backward(bart_mlp* net, const float* x, const float* t, int B, float* loss_out) {
+  cudaStream_t st = net->ctx->stream;
+  const int n_in = net->widths[0], n_out = net->widths[net->n_layers];
+  scale_inputs<<<blocks_for((int64_t)B * n_in, 256), 256, 0, st>>>(x, B, n_in, net->scale, net->scale + n_in,
+                                                                  net->act + net->h_off[0]);
+  run_forward(net, B);
+  // gradient of the standardised output: reuse the last layer's h slot as dY
+  const float* osh = net->scale + 2 * n_in;
+  const float* osc = osh + n_out;
+  float* dy = net->act + net->h_off[net->n_layers];
+  mse_kernel<<<1, 1024, 0, st>>>(net->act + net->z_off[net->n_layers], t, B, n_out, osh, osc, net->log_outputs, dy,
+                                 loss_out ? loss_out : net->loss);
+  // dz of the current layer lives in its h slot (h is dead once z is kept)
+  for (int l = net->n_layers - 1; l >= 0; --l) {
+    const int ni = net->widths[l], no = net->widths[l + 1];
+    float* dz = net->act + net->h_off[l + 1];
+    // h_prev: layer 0 input, else GELU(z_prev) recomputed below into a temp?  The
+    // hidden h of layer l is still intact: only slots above l were reused.
+    const float* h_prev = net->act + net->h_off[l];
+    // dW[o][i] = sum_b dz[b][o] h_prev[b][i]
+    gemm<float, float>(st, no, ni, B, dz, 1, no, h_prev, ni, 1, net->g + net->w_off[l], ni, 0);
+    bias_grad<<<blocks_for(no, 128), 128, 0, st>>>(dz, B, no, net->g + net->b_off[l]);
+    if (l > 0) {
+      // dh_prev[b][i] = sum_o dz[b][o] W[o][i]; then dz_prev = dh_prev * GELU'(z_prev)
+      float* dz_prev = net->act + net->h_off[l];
+      const float* z_prev = net->act + net->z_off[l];
+      // h_prev (this slot) was consumed by the dW GEMM above, which runs first on the stream.
+      if (net->bf16)
+        gemm<float, __nv_bfloat16>(st, B, ni, no, dz, no, 1, net->wb + net->w_off[l], ni, 1, dz_prev, ni, 3,
+                                   nullptr, nullptr, z_prev);
+      else
+        gemm<float, float>(st, B, ni, no, dz, no, 1, net->p + net->w_off[l], ni, 1, dz_prev, ni, 3, nullptr,
+                           nullptr, z_prev);
+    }
+  }
+  return bart_check_launch(net->ctx, "mlp backward");
+}
+
+}  // namespace
+
+extern "C" bart_status bart_mlp_create(bart_ctx* ctx, const int32_t* widths, int n_widths, int bf16_weights,
+                                       int log_outputs, int max_batch, bart_mlp** out) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, out && widths, "NULL out or widths");
+  *out = nullptr;
+  BART_REQUIRE(ctx, n_widths >= 2 && n_widths <= 16, "n_widths must be in [2, 16]");
+  for (int i = 0; i < n_widths; ++i) BART_REQUIRE(ctx, widths[i] >= 1 && widths[i] <= 4096, "width out of range");
+  BART_REQUIRE(ctx, max_batch >= 1 && max_batch <= (1 << 20), "max_batch out of range");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  bart_mlp* net = new bart_mlp();
+  net->ctx = ctx;
+  net->widths.assign(widths, widths + n_widths);
+  net->n_layers = n_widths - 1;
+  net->bf16 = bf16_weights ? 1 : 0;
+  net->log_outputs = log_outputs ? 1 : 0;
+  net->max_batch = max_batch;
+  int64_t o = 0;
+  for (int l = 0; l < net->n_layers; ++l) {
+    net->w_off.push_back(o);
+    o += (int64_t)widths[l + 1] * widths[l];
+    net->b_off.push_back(o);
+    o += widths[l + 1];
+  }
+  net->n_params = o;
+  int64_t a = 0;
+  for (int l = 0; l <= net->n_layers; ++l) {
+    net->z_off.push_back(a);
+    a += (int64_t)max_batch * widths[l];
+    net->h_off.push_back(a);
+    a += (int64_t)max_batch * widths[l];
+  }
+  const int n_scale = 2 * widths[0] + 2 * widths[n_widths - 1];
+  bool ok = cudaMalloc(&net->p, o * 4) == cudaSuccess && cudaMalloc(&net->m, o * 4) == cudaSuccess &&
+            cudaMalloc(&net->v, o * 4) == cudaSuccess && cudaMalloc(&net->g, o * 4) == cudaSuccess &&
+            cudaMalloc(&net->wb, o * 2) == cudaSuccess && cudaMalloc(&net->act, a * 4) == cudaSuccess &&
+            cudaMalloc(&net->scale, n_scale * 4) == cudaSuccess && cudaMalloc(&net->loss, 4) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    bart_mlp_destroy(net);
+    return bart_fail(ctx, BART_ENOMEM, "MLP allocation failed");
+  }
+  std::vector<float> sc(n_scale, 0.f);
+  for (int i = 0; i < widths[0]; ++i) sc[widths[0] + i] = 1.f;
+  for (int i = 0; i < widths[n_widths - 1]; ++i) sc[2 * widths[0] + widths[n_widths - 1] + i] = 1.f;
+  BART_CUDA(ctx, cudaMemcpy(net->scale, sc.data(), n_scale * 4, cudaMemcpyHostToDevice));
+  BART_CUDA(ctx, cudaMemset(net->p, 0, o * 4));
+  BART_CUDA(ctx, cudaMemset(net->m, 0, o * 4));
+  BART_CUDA(ctx, cudaMemset(net->v, 0, o * 4));
+  BART_CUDA(ctx, cudaMemset(net->wb, 0, o * 2));
+  *out = net;
+  return BART_OK;
+}
+
+extern "C" void bart_mlp_destroy(bart_mlp* net) {
+  if (!net) return;
+  cudaSetDevice(net->ctx->device);
+  cudaStreamSynchronize(net->ctx->stream);
+  for (void* q : {(void*)net->p, (void*)net->m, (void*)net->v, (void*)net->g, (void*)net->wb, (void*)net->act,
+                  (void*)net->scale, (void*)net->loss})
+    if (q) cudaFree(q);
+  delete net;
+}
+
+extern "C" int64_t bart_mlp_num_params(const bart_mlp* net) { return net ? net->n_params : -1; }
+
+extern "C" bart_status bart_mlp_set_scaling(bart_mlp* net, const float* in_shift, const float* in_scale,
+                                            const float* out_shift, const float* out_scale) {
+  if (!net) return BART_EINVAL;
+  BART_REQUIRE(net->ctx, in_shift && in_scale && out_shift && out_scale, "NULL scaling array");
+  const int ni = net->widths[0], no = net->widths[net->n_layers];
+  std::vector<float> sc;
+  sc.insert(sc.end(), in_shift, in_shift + ni);
+  sc.insert(sc.end(), in_scale, in_scale + ni);
+  sc.insert(sc.end(), out_shift, out_shift + no);
+  sc.insert(sc.end(), out_scale, out_scale + no);
+  for (float v : sc) BART_REQUIRE(net->ctx, std::isfinite(v), "non-finite scaling");
+  BART_CUDA(net->ctx, cudaMemcpyAsync(net->scale, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice,
+                                      net->ctx->stream));
+  BART_CUDA(net->ctx, cudaStreamSynchronize(net->ctx->stream));
+  return BART_OK;
+}
+
+extern "C" bart_status bart_mlp_set_params(bart_mlp* net, const float* params) {
+  if (!net) return BART_EINVAL;
+  BART_REQUIRE(net->ctx, params, "NULL params");
+  cudaStream_t st = net->ctx->stream;
+  BART_CUDA(net->ctx, cudaMemcpyAsync(net->p, params, net->n_params * 4, cudaMemcpyDeviceToDevice, st));
+  BART_CUDA(net->ctx, cudaMemsetAsync(net->m, 0, net->n_params * 4, st));
+  BART_CUDA(net->ctx, cudaMemsetAsync(net->v, 0, net->n_params * 4, st));
+  to_bf16<<<blocks_for(net->n_params, 256), 256, 0, st>>>(net->p, net->wb, net->n_params);
+  net->step = 0;
+  return bart_check_launch(net->ctx, "to_bf16");
+}
+
+extern "C" bart_status bart_mlp_get_params(bart_mlp* net, float* params) {
+  if (!net) return BART_EINVAL;
+  BART_REQUIRE(net->ctx, params, "NULL params");
+  BART_CUDA(net->ctx, cudaMemcpyAsync(params, net->p, net->n_params * 4, cudaMemcpyDeviceToDevice,
+                                      net->ctx->stream));
+  return BART_OK;
+}
+
+extern "C" bart_status bart_mlp_forward(bart_mlp* net, const float* x, int B, float* y) {
+  if (!net) return BART_EINVAL;
+  BART_REQUIRE(net->ctx, x && y, "NULL x or y");
+  bart_status st = check_batch(net, B);
+  if (st != BART_OK) return st;
+  const int ni = net->widths[0], no = net->widths[net->n_layers];
+  cudaStream_t s = net->ctx->stream;
+  scale_inputs<<<blocks_for((int64_t)B * ni, 256), 256, 0, s>>>(x, B, ni, net->scale, net->scale + ni,
+                                                               net->act + net->h_off[0]);
+  run_forward(net, B);
+  unscale_outputs<<<blocks_for((int64_t)B * no, 256), 256, 0, s>>>(net->act + net->z_off[net->n_layers], B, no,
+                                                                  net->scale + 2 * ni, net->scale + 2 * ni + no,
+                                                                  net->log_outputs, y);
+  return bart_check_launch(net->ctx, "mlp forward");
+}
+
+extern "C" bart_status bart_mlp_gradient(bart_mlp* net, const float* x, const float* t, int B, float* grad,
+                                         float* loss) {
+  if (!net) return BART_EINVAL;
+  BART_REQUIRE(net->ctx, x && t, "NULL x or t");
+  bart_status st = check_batch(net, B);
+  if (st != BART_OK) return st;
+  if ((st = backward(net, x, t, B, loss)) != BART_OK) return st;
+  if (grad)
+    BART_CUDA(net->ctx, cudaMemcpyAsync(grad, net->g, net->n_params * 4, cudaMemcpyDeviceToDevice,
+                                        net->ctx->stream));
+  return BART_OK;
+}
+
+extern "C" bart_status bart_mlp_train_step(bart_mlp* net, const float* x, const float* t, int B, float lr,
+                                           float* loss) {
+  if (!net) return BART_EINVAL;
+  BART_REQUIRE(net->ctx, x && t, "NULL x or t");
+  BART_REQUIRE(net->ctx, lr > 0 && std::isfinite(lr), "lr must be > 0");
+  bart_status st = check_batch(net, B);
+  if (st != BART_OK) return st;
+  if ((st = backward(net, x, t, B, loss)) != BART_OK) return st;
+  net->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = (float)(1.0 - std::pow(0.9, (double)net->step));
+  const float c2 = (float)(1.0 - std::pow(0.999, (double)net->step));
+  cudaStream_t s = net->ctx->stream;
+  adam_kernel<<<blocks_for(net->n_params, 256), 256, 0, s>>>(net->p, net->m, net->v, net->g, net->n_params, lr, b1,
+                                                            b2, 1e-8f, c1, c2);
+  to_bf16<<<blocks_for(net->n_params, 256), 256, 0, s>>>(net->p, net->wb, net->n_params);
+  return bart_check_launch(net->ctx, "adam");
+}

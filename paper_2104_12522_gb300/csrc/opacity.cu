@@ -289,8 +289,6 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
   if ((st = bart_scratch(ctx, "op_jlo", nl * sizeof(int), &p_jlo)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "op_jhi", nl * sizeof(int), &p_jhi)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "op_win", nl * sizeof(LineWin), &p_win)) != BART_OK) return st;
-  if ((st = bart_scratch(ctx, "op_cells", (size_t)n_species * n_cells * sizeof(CellConst), &p_cells)) != BART_OK)
-    return st;
 
   std::vector<CellConst> hc((size_t)n_species * n_cells);
   for (int s = 0; s < n_species; ++s)
@@ -304,8 +302,8 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
       k.c2_t = (float)(bartc::C2 / T);
       hc[(size_t)s * n_cells + c] = k;
     }
-  BART_CUDA(ctx, cudaMemcpyAsync(p_cells, hc.data(), hc.size() * sizeof(CellConst), cudaMemcpyHostToDevice,
-                                 ctx->stream));
+  if ((st = bart_upload_const(ctx, "op_cells", hc.data(), hc.size() * sizeof(CellConst), &p_cells)) != BART_OK)
+    return st;
 
   const int64_t n_tiles = (nu.n_nu + OP_TILE - 1) / OP_TILE;
   for (int s = 0; s < n_species; ++s) {

@@ -1,9 +1,443 @@
-// Transmission (transit) geometry of the forward model.  Filled in by the
-// transit-depth kernel; until then the geometry is reported as unsupported.
+// Transmission (transit) geometry of the forward model (Sec. 5.1, the transit
+// case of test f01oneline: slant paths through the layers, optical depth and
+// transmission along each ray, times 2 pi r, integrated over altitude).
+//
+//   trans_prologue  one CTA per instance: level pressures (log-spaced between
+//                   p_top and p_bot), T(P), hydrostatic altitudes in FP64
+//                   (g ~ r^-2, r = R_p at P_ref, trapezoid in ln P with P_ref as
+//                   a node), number densities and the bilinear (log10 P, T)
+//                   brackets on the grid.
+//   trans_kernel    persistent CTAs pulling (wavenumber tile, instance) units
+//                   from an atomic counter; tile-major order keeps the grid
+//                   slab of a tile in L2 while every instance covering it runs.
+//                   Per unit: shell extinction for 128 wavenumbers into shared
+//                   memory, then the ray optical depths
+//                   tau_i = sum_{k<i} ds_ik (alpha_k + alpha_{k+1}) / 2,
+//                   register-blocked over 8 rays per pass, chords recomputed
+//                   per pass as 2 (A - B) / (sqrt A + sqrt B) from altitude
+//                   differences (no cancellation), then the trapezoid in
+//                   impact parameter and the fused band partial sums.
+//   trans_band_reduce  per (instance, band): fixed-order FP64 sum of partials.
+#include <cmath>
+#include <vector>
+
 #include "bart_internal.cuh"
+#include "forward.cuh"
+
+namespace {
+
+constexpr int TR_THREADS = 128;          // wavenumbers per unit
+constexpr int TR_LMAX = 192;             // maximum levels per instance
+constexpr int TR_RB = 8;                 // rays per register block
+constexpr int TR_MAX_BANDS = 64;
+constexpr int TR_MAX_SPECIES = 8;
+
+struct TrLevel {
+  float z;        // altitude above r_planet, cm
+  float ndens;    // number density P / (k T), cm^-3
+  int a;          // lower grid layer of the log10 P bracket
+  float u;        // weight of the upper layer
+  int m;          // lower grid temperature of the T bracket
+  float w;        // weight of the upper temperature
+};
+
+struct TrInst {
+  int L;
+  int ok;
+  float r_planet, r_star;
+  float x[TR_MAX_SPECIES];
+};
+
+__global__ void trans_prologue(const float* __restrict__ theta, int n_theta, int n, int S,
+                               const int32_t* __restrict__ n_levels, const float* __restrict__ r_planet,
+                               const float* __restrict__ r_star, const float* __restrict__ lp_axis, int Lg,
+                               const float* __restrict__ t_axis, int M, double p_top, double p_bot,
+                               double p_ref, double g, double mu_amu, float inv_g_f, float tint4, float tirr0,
+                               float t_min, float t_max, const float* __restrict__ x0, TrLevel* __restrict__ lev,
+                               TrInst* __restrict__ inst, int* __restrict__ status) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  __shared__ double s_lnp[TR_LMAX], s_T[TR_LMAX], s_phi[TR_LMAX];
+  __shared__ int s_bad;
+  const int L = n_levels[i];
+  const float* th = theta + (int64_t)i * n_theta;
+  if (threadIdx.x == 0) s_bad = (L < 2 || L > TR_LMAX || !(r_planet[i] > 0.f) || !(r_star[i] > 0.f));
+  __syncthreads();
+  if (s_bad) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, BART_DEV_RANGE);
+      inst[i].ok = 0;
+      inst[i].L = 0;
+    }
+    return;
+  }
+  const double lt = log10(p_top), lb = log10(p_bot);
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    const double lp = lt + (lb - lt) * (double)k / (double)(L - 1);
+    const double p = exp10(lp);
+    float thv[5];
+    for (int q = 0; q < 5; ++q) thv[q] = th[q];
+    float T = bartf::tp_temperature(thv, (float)(p * bartc::BAR), inv_g_f, tint4, tirr0);
+    if (!(T == T) || T <= 0.0f) {
+      atomicOr(status, BART_DEV_RANGE);
+      T = t_min;
+    }
+    T = fminf(fmaxf(T, t_min), t_max);
+    s_lnp[k] = log(p);
+    s_T[k] = T;
+    TrLevel lv;
+    lv.ndens = (float)(p * bartc::BAR / (bartc::KB * (double)T));
+    // bracket in log10 P over the grid layers
+    const float lpf = (float)lp;
+    int a = 0;
+    float u = 0.f;
+    if (Lg > 1) {
+      int lo = 0, hi = Lg;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (lp_axis[mid] <= lpf) lo = mid + 1; else hi = mid;
+      }
+      a = min(max(lo - 1, 0), Lg - 2);
+      u = fminf(fmaxf((lpf - lp_axis[a]) / (lp_axis[a + 1] - lp_axis[a]), 0.f), 1.f);
+    }
+    int m = 0;
+    float w = 0.f;
+    if (M > 1) {
+      int lo = 0, hi = M;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (t_axis[mid] <= T) lo = mid + 1; else hi = mid;
+      }
+      m = min(max(lo - 1, 0), M - 2);
+      w = fminf(fmaxf((T - t_axis[m]) / (t_axis[m + 1] - t_axis[m]), 0.f), 1.f);
+    }
+    lv.a = a;
+    lv.u = u;
+    lv.m = m;
+    lv.w = w;
+    lv.z = 0.f;
+    lev[(int64_t)i * TR_LMAX + k] = lv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // phi_k = integral_{ln P_ref}^{ln P_k} T dlnP, trapezoid with P_ref as a node
+    const double lref = log(p_ref);
+    double t_ref;
+    if (lref <= s_lnp[0]) t_ref = s_T[0];
+    else if (lref >= s_lnp[L - 1]) t_ref = s_T[L - 1];
+    else {
+      int k = 0;
+      while (k + 1 < L && s_lnp[k + 1] < lref) ++k;
+      const double f = (lref - s_lnp[k]) / (s_lnp[k + 1] - s_lnp[k]);
+      t_ref = s_T[k] + f * (s_T[k + 1] - s_T[k]);
+    }
+    // cumulative integral from the top, then shift so that phi(P_ref) = 0
+    double cum = 0.0, cum_ref = 0.0;
+    bool ref_done = false;
+    s_phi[0] = 0.0;
+    if (lref <= s_lnp[0]) { cum_ref = -0.5 * (t_ref + s_T[0]) * (s_lnp[0] - lref); ref_done = true; }
+    for (int k = 0; k + 1 < L; ++k) {
+      if (!ref_done && lref < s_lnp[k + 1]) {
+        cum_ref = cum + 0.5 * (s_T[k] + t_ref) * (lref - s_lnp[k]);
+        ref_done = true;
+      }
+      cum += 0.5 * (s_T[k] + s_T[k + 1]) * (s_lnp[k + 1] - s_lnp[k]);
+      s_phi[k + 1] = cum;
+    }
+    if (!ref_done) cum_ref = cum + 0.5 * (s_T[L - 1] + t_ref) * (lref - s_lnp[L - 1]);
+    const double rp = (double)r_planet[i];
+    const double C = bartc::KB / (mu_amu * bartc::AMU * g * rp * rp);
+    for (int k = 0; k < L; ++k) {
+      const double cphi = C * (s_phi[k] - cum_ref);
+      // r = 1/(1/R_p + C phi): altitude r - R_p written without cancellation
+      lev[(int64_t)i * TR_LMAX + k].z = (float)(-cphi * rp * rp / (1.0 + cphi * rp));
+    }
+    TrInst in;
+    in.L = L;
+    in.ok = 1;
+    in.r_planet = r_planet[i];
+    in.r_star = r_star[i];
+    for (int s = 0; s < TR_MAX_SPECIES; ++s)
+      in.x[s] = s < S ? x0[s] * exp10f(theta[(int64_t)i * n_theta + 5 + s]) : 0.f;
+    inst[i] = in;
+  }
+}
+
+// 1 - exp(-tau) with relative accuracy for small tau.
+__device__ __forceinline__ float one_minus_exp(float tau) {
+  if (tau < 0.125f) {
+    // tau (1 - tau/2 (1 - tau/3 (1 - tau/4 (1 - tau/5 (1 - tau/6)))))
+    float s = 1.0f - tau * (1.0f / 6.0f);
+    s = 1.0f - tau * 0.2f * s;
+    s = 1.0f - tau * 0.25f * s;
+    s = 1.0f - tau * (1.0f / 3.0f) * s;
+    s = 1.0f - tau * 0.5f * s;
+    return tau * s;
+  }
+  return 1.0f - bartf::ex2_approx(-tau * 1.4426950408889634f);
+}
+
+template <int S>
+__global__ void __launch_bounds__(TR_THREADS)
+trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrLevel* __restrict__ lev,
+             const TrInst* __restrict__ inst, int n, const int64_t* __restrict__ nu_lo,
+             const int64_t* __restrict__ nu_hi, const int64_t* __restrict__ offs, float* __restrict__ spectra,
+             const float* __restrict__ filt, int n_bands, float2* __restrict__ partial, int n_gtiles,
+             unsigned long long n_units, unsigned long long* __restrict__ counter,
+             const int32_t* __restrict__ active, int* __restrict__ status) {
+  extern __shared__ float smem[];
+  float* s_alpha = smem;                                  // [TR_LMAX][TR_THREADS] shell extinction
+  float* s_ds = s_alpha + TR_LMAX * TR_THREADS;           // [TR_LMAX][TR_RB] chords of the ray block
+  __shared__ TrLevel s_lev[TR_LMAX];
+  __shared__ TrInst s_in;
+  __shared__ unsigned long long s_unit;
+  __shared__ float2 s_red[TR_THREADS / 32][TR_MAX_BANDS];
+  const int tid = threadIdx.x;
+  const int64_t sstride = (int64_t)Lg * M * N;
+
+  for (;;) {
+    if (tid == 0) s_unit = atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const unsigned long long u = s_unit;
+    if (u >= n_units) break;
+    const int g = (int)(u / (unsigned long long)n);
+    const int i = (int)(u % (unsigned long long)n);
+    if (active && !active[i]) {                   // skipped entry: outputs untouched
+      __syncthreads();
+      continue;
+    }
+    const int64_t lo = nu_lo ? nu_lo[i] : 0, hi = nu_hi ? nu_hi[i] : N;
+    const int64_t g0 = (int64_t)g * TR_THREADS;
+    if (lo < 0 || hi > N || lo >= hi) {
+      if (tid == 0 && g == 0) atomicOr(status, BART_DEV_RANGE);
+      __syncthreads();
+      continue;
+    }
+    if (g0 + TR_THREADS <= lo || g0 >= hi) {      // this tile is outside the instance's span
+      __syncthreads();
+      continue;
+    }
+    if (tid == 0) s_in = inst[i];
+    __syncthreads();
+    if (!s_in.ok) {
+      __syncthreads();
+      continue;
+    }
+    const int L = s_in.L;
+    for (int k = tid; k < L; k += TR_THREADS) s_lev[k] = lev[(int64_t)i * TR_LMAX + k];
+    __syncthreads();
+
+    const int64_t j = g0 + tid;
+    const bool active = (j >= lo) && (j < hi);
+    const int64_t jj = active ? j : lo;
+    // extinction at every level, then shell means into shared memory
+    float a_prev = 0.f;
+    for (int k = 0; k < L; ++k) {
+      const TrLevel lv = s_lev[k];
+      const float* base = grid + ((int64_t)lv.a * M + lv.m) * N + jj;
+      const int64_t dl = (Lg > 1) ? (int64_t)M * N : 0;
+      const int64_t dm = (M > 1) ? N : 0;
+      float sig = 0.f;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const float* b = base + s * sstride;
+        const float v00 = __ldg(b), v01 = __ldg(b + dm), v10 = __ldg(b + dl), v11 = __ldg(b + dl + dm);
+        const float lo_l = fmaf(lv.w, v01 - v00, v00);
+        const float hi_l = fmaf(lv.w, v11 - v10, v10);
+        sig = fmaf(s_in.x[s], fmaf(lv.u, hi_l - lo_l, lo_l), sig);
+      }
+      const float a = sig * lv.ndens;
+      if (k > 0) s_alpha[(k - 1) * TR_THREADS + tid] = 0.5f * (a_prev + a);
+      a_prev = a;
+    }
+    // rays: b_i = r_i, i = 0 .. L-1 (ray 0 grazes the top level: tau = 0)
+    const float rp = s_in.r_planet;
+    // trapezoid state: f b of the previous ray and its altitude (b = r_p + z;
+    // widths are taken as altitude differences so they keep full precision)
+    float integ = 0.f, fb_prev = 0.f, z_prev = s_lev[0].z;
+    for (int i0 = 1; i0 < L; i0 += TR_RB) {
+      __syncthreads();                                    // s_ds of the previous block is consumed
+      const int nr = min(TR_RB, L - i0);
+      const int kmax = i0 + nr - 1;                       // shells 0 .. kmax-1
+      for (int e = tid; e < kmax * TR_RB; e += TR_THREADS) {
+        const int k = e / TR_RB, r = e % TR_RB, ir = i0 + r;
+        float ds = 0.f;
+        if (r < nr && k < ir) {
+          const float zb = s_lev[ir].z;
+          const float zk = s_lev[k].z, zk1 = s_lev[k + 1].z;
+          const float A = (zk - zb) * (2.f * rp + zk + zb);
+          const float B = (k + 1 < ir) ? (zk1 - zb) * (2.f * rp + zk1 + zb) : 0.f;
+          const float AmB = (zk - zk1) * (2.f * rp + zk + zk1);
+          ds = 2.f * AmB / (sqrtf(A) + sqrtf(B));
+        }
+        s_ds[k * TR_RB + r] = ds;
+      }
+      __syncthreads();
+      float tau[TR_RB];
+#pragma unroll
+      for (int r = 0; r < TR_RB; ++r) tau[r] = 0.f;
+      for (int k = 0; k < kmax; ++k) {
+        const float a = s_alpha[k * TR_THREADS + tid];
+        const float4 d0 = *reinterpret_cast<const float4*>(s_ds + k * TR_RB);
+        const float4 d1 = *reinterpret_cast<const float4*>(s_ds + k * TR_RB + 4);
+        tau[0] = fmaf(d0.x, a, tau[0]);
+        tau[1] = fmaf(d0.y, a, tau[1]);
+        tau[2] = fmaf(d0.z, a, tau[2]);
+        tau[3] = fmaf(d0.w, a, tau[3]);
+        tau[4] = fmaf(d1.x, a, tau[4]);
+        tau[5] = fmaf(d1.y, a, tau[5]);
+        tau[6] = fmaf(d1.z, a, tau[6]);
+        tau[7] = fmaf(d1.w, a, tau[7]);
+      }
+#pragma unroll
+      for (int r = 0; r < TR_RB; ++r) {
+        if (r < nr) {
+          const float zb = s_lev[i0 + r].z;
+          const float fb = one_minus_exp(tau[r]) * (rp + zb);
+          integ = fmaf(0.5f * (fb_prev + fb), z_prev - zb, integ);
+          fb_prev = fb;
+          z_prev = zb;
+        }
+      }
+    }
+    const float rbot = rp + s_lev[L - 1].z;
+    const float rs = s_in.r_star;
+    const float delta = (rbot / rs) * (rbot / rs) + 2.f * integ / (rs * rs);
+    if (active && spectra) spectra[(offs ? offs[i] : (int64_t)i * N) + (j - lo)] = delta;
+    if (n_bands > 0) {
+      float dw = 0.f;
+      if (active) dw = (hi - lo == 1) ? 1.f : ((j == lo || j == hi - 1) ? 0.5f : 1.f);
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int b = 0; b < n_bands; ++b) {
+        const float W = active ? __ldg(filt + (int64_t)b * N + j) * dw : 0.f;
+        float num = W * delta, den = W;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          num += __shfl_xor_sync(0xffffffffu, num, o);
+          den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        if (lane == 0) s_red[warp][b] = make_float2(num, den);
+      }
+      __syncthreads();
+      if (tid < n_bands) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int w = 0; w < TR_THREADS / 32; ++w) {
+          acc.x += s_red[w][tid].x;
+          acc.y += s_red[w][tid].y;
+        }
+        partial[((int64_t)i * n_gtiles + g) * n_bands + tid] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void trans_band_reduce(const float2* __restrict__ partial, const int64_t* __restrict__ nu_lo,
+                                  const int64_t* __restrict__ nu_hi, int64_t N, int n, int n_gtiles, int nb,
+                                  const int32_t* __restrict__ active, float* __restrict__ bands) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * nb) return;
+  const int i = (int)(idx / nb), b = (int)(idx % nb);
+  if (active && !active[i]) return;
+  const int64_t lo = nu_lo ? nu_lo[i] : 0, hi = nu_hi ? nu_hi[i] : N;
+  if (lo < 0 || hi > N || lo >= hi) {
+    bands[idx] = 0.f;
+    return;
+  }
+  double num = 0.0, den = 0.0;
+  for (int64_t g = lo / TR_THREADS; g <= (hi - 1) / TR_THREADS; ++g) {
+    const float2 v = partial[((int64_t)i * n_gtiles + g) * nb + b];
+    num += v.x;
+    den += v.y;
+  }
+  bands[idx] = den > 0.0 ? (float)(num / den) : 0.f;
+}
+
+using TrLauncher = void (*)(int, size_t, cudaStream_t, const float*, int, int, int64_t, const TrLevel*,
+                            const TrInst*, int, const int64_t*, const int64_t*, const int64_t*, float*,
+                            const float*, int, float2*, int, unsigned long long, unsigned long long*,
+                            const int32_t*, int*);
+
+template <int S>
+void launch_trans(int grid_dim, size_t smem, cudaStream_t st, const float* grid, int Lg, int M, int64_t N,
+                  const TrLevel* lev, const TrInst* inst, int n, const int64_t* lo, const int64_t* hi,
+                  const int64_t* offs, float* spectra, const float* filt, int nb, float2* partial, int ngt,
+                  unsigned long long nu, unsigned long long* counter, const int32_t* active, int* status) {
+  trans_kernel<S><<<grid_dim, TR_THREADS, smem, st>>>(grid, Lg, M, N, lev, inst, n, lo, hi, offs, spectra, filt,
+                                                      nb, partial, ngt, nu, counter, active, status);
+}
+
+template <int S>
+cudaError_t set_smem(size_t smem) {
+  return cudaFuncSetAttribute(trans_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
 
 bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
                                     const bart_batch* b, float* spectra, const bart_filters* f, float* bands) {
-  (void)g; (void)c; (void)b; (void)spectra; (void)f; (void)bands;
-  return bart_fail(ctx, BART_EUNSUPPORTED, "transmission geometry is not built yet");
+  const int S = g->n_species, Lg = g->n_layers, M = g->n_temps, n = b->n;
+  const int64_t N = g->nu.n_nu;
+  BART_REQUIRE(ctx, b->theta, "transmission needs theta");
+  BART_REQUIRE(ctx, b->n_levels && b->r_planet_cm && b->r_star_cm,
+               "transmission needs n_levels, r_planet_cm and r_star_cm");
+  BART_REQUIRE(ctx, c->p_top_bar > 0 && c->p_bot_bar > c->p_top_bar && c->p_ref_bar > 0,
+               "need 0 < p_top < p_bot and p_ref > 0");
+  BART_REQUIRE(ctx, S >= 1 && S <= 4, "transmission supports 1-4 species");
+  const int nb = bands ? f->n_bands : 0;
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+
+  TrLauncher launch = nullptr;
+  cudaError_t ce = cudaSuccess;
+  const size_t smem = (size_t)(TR_LMAX * TR_THREADS + TR_LMAX * TR_RB) * sizeof(float);
+  switch (S) {
+    case 1: launch = launch_trans<1>; ce = set_smem<1>(smem); break;
+    case 2: launch = launch_trans<2>; ce = set_smem<2>(smem); break;
+    case 3: launch = launch_trans<3>; ce = set_smem<3>(smem); break;
+    case 4: launch = launch_trans<4>; ce = set_smem<4>(smem); break;
+  }
+  if (ce != cudaSuccess) return bart_fail(ctx, BART_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(ce));
+
+  std::vector<float> hconst;      // [log10 p grid Lg][t axis M][x0 S]
+  for (int k = 0; k < Lg; ++k) hconst.push_back((float)std::log10(g->p_bar[k]));
+  for (int m = 0; m < M; ++m) hconst.push_back((float)g->t_K[m]);
+  for (int s = 0; s < S; ++s) hconst.push_back((float)c->x0[s]);
+  const int n_gtiles = (int)((N + TR_THREADS - 1) / TR_THREADS);
+  void *p_const, *p_lev, *p_inst, *p_part = nullptr, *p_counter;
+  bart_status st;
+  if ((st = bart_upload_const(ctx, "tr_const", hconst.data(), hconst.size() * sizeof(float), &p_const)) != BART_OK)
+    return st;
+  if ((st = bart_scratch(ctx, "tr_lev", (size_t)n * TR_LMAX * sizeof(TrLevel), &p_lev)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "tr_inst", (size_t)n * sizeof(TrInst), &p_inst)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "tr_counter", sizeof(unsigned long long), &p_counter)) != BART_OK) return st;
+  if (nb > 0 &&
+      (st = bart_scratch(ctx, "tr_part", (size_t)n * n_gtiles * nb * sizeof(float2), &p_part)) != BART_OK)
+    return st;
+  BART_CUDA(ctx, cudaMemsetAsync(p_counter, 0, sizeof(unsigned long long), ctx->stream));
+  const float* dc = (const float*)p_const;
+  const double rs = c->r_star_tp_cm, a = c->a_orbit_cm;
+  const float tirr0 = (rs > 0 && a > 0) ? (float)(std::sqrt(rs / (2.0 * a)) * c->t_star_K) : 0.0f;
+  trans_prologue<<<n, 128, 0, ctx->stream>>>(
+      b->theta, 5 + S, n, S, b->n_levels, b->r_planet_cm, b->r_star_cm, dc, Lg, dc + Lg, M, c->p_top_bar,
+      c->p_bot_bar, c->p_ref_bar, c->g_cgs, c->mu_amu, (float)(1.0 / c->g_cgs), (float)std::pow(c->t_int_K, 4.0),
+      tirr0, (float)c->t_min_K, (float)std::min(c->t_max_K, 1e30), dc + Lg + M, (TrLevel*)p_lev,
+      (TrInst*)p_inst, ctx->d_status);
+  if ((st = bart_check_launch(ctx, "trans_prologue")) != BART_OK) return st;
+  const unsigned long long n_units = (unsigned long long)n_gtiles * (unsigned long long)n;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trans_kernel<1>, TR_THREADS, smem);
+  if (per_sm < 1) per_sm = 1;
+  int grid_dim = ctx->sm_count * per_sm;
+  if ((unsigned long long)grid_dim > n_units) grid_dim = (int)n_units;
+  launch(grid_dim, smem, ctx->stream, g->grid, Lg, M, N, (const TrLevel*)p_lev, (const TrInst*)p_inst, n,
+         b->nu_lo, b->nu_hi, b->spec_offsets, spectra, nb ? f->weights : nullptr, nb, (float2*)p_part, n_gtiles,
+         n_units, (unsigned long long*)p_counter, b->active, ctx->d_status);
+  if ((st = bart_check_launch(ctx, "trans_kernel")) != BART_OK) return st;
+  if (nb > 0) {
+    const int64_t tot = (int64_t)n * nb;
+    trans_band_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(
+        (const float2*)p_part, b->nu_lo, b->nu_hi, N, n, n_gtiles, nb, b->active, bands);
+    if ((st = bart_check_launch(ctx, "trans_band_reduce")) != BART_OK) return st;
+  }
+  return BART_OK;
 }

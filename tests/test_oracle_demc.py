@@ -1,0 +1,51 @@
+"""Pins of the oracle sampler: it recovers a correlated Gaussian's mean,
+variances and 68.27% credible-region content within the App. C standard
+errors, with and without a (deliberately wrong) surrogate screen."""
+import numpy as np
+import pytest
+from scipy.stats import chi2
+
+from oracle import demc as D
+from demc_target import target
+
+
+def _check(hist, mu, cov, burn):
+    s = hist[burn:]
+    n, C, d = s.shape
+    flat = s.reshape(-1, d)
+    e = D.ess(s)
+    sd = np.sqrt(np.diag(cov))
+    z = np.abs(flat.mean(0) - mu) / (sd / np.sqrt(e))
+    assert np.all(z < 4.5), z
+    var_ratio = flat.var(0) / sd ** 2
+    assert np.all(np.abs(var_ratio - 1) < 4.5 * np.sqrt(2.0 / e)), var_ratio
+    inv = np.linalg.inv(cov)
+    m2 = np.einsum("ij,jk,ik->i", flat - mu, inv, flat - mu)
+    c = float(np.mean(m2 <= chi2.ppf(0.6827, d)))
+    assert abs(c - 0.6827) < 4.5 * D.credible_content_se(0.6827, e), c
+    return e
+
+
+@pytest.mark.parametrize("screened", [False, True])
+def test_recovers_gaussian(screened):
+    mu, cov, lo, hi = target()
+    inv = np.linalg.inv(cov)
+    L = lambda v: -0.5 * (v - mu) @ inv @ (v - mu)
+    # a surrogate with the wrong scale: delayed acceptance keeps the exact target
+    Ls = (lambda v: -0.5 * 0.7 * (v - mu) @ inv @ (v - mu)) if screened else None
+    rng = np.random.default_rng(6000)
+    x0 = mu + rng.normal(size=(16, 9)) * np.sqrt(np.diag(cov))
+    hist, acc = D.run(L, x0, lo, hi, 3000, rng, surrogate=Ls)
+    e = _check(hist, mu, cov, burn=500)
+    assert e > 300
+
+
+def test_speis_of_white_noise_and_ar1():
+    rng = np.random.default_rng(1)
+    assert abs(D.speis(rng.normal(size=20000)) - 1.0) < 0.05
+    phi = 0.9
+    x = np.zeros(200000)
+    for t in range(1, x.size):
+        x[t] = phi * x[t - 1] + rng.normal()
+    # integrated autocorrelation time of AR(1): (1 + phi) / (1 - phi) = 19
+    assert abs(D.speis(x) - 19.0) < 2.0

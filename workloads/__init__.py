@@ -220,3 +220,18 @@ def opacity_grid_species(n_species: int = 3, total_lines: int = 5_000_000) -> li
     if n_species == 4:
         counts = counts + [counts[0]]
     return [line_list(s, counts[s]) for s in range(n_species)]
+
+
+SURROGATE_WIDTHS = (9, 256, 256, 256, 10)
+
+
+def mlp_init(widths=SURROGATE_WIDTHS, seed: int = 5000) -> np.ndarray:
+    """Flat FP32 initial parameters: per layer W [out][in] ~ N(0, 2/in) then
+    b = 0 (the layout of the surrogate network)."""
+    g = _rng(seed)
+    parts = []
+    for l in range(len(widths) - 1):
+        n_in, n_out = widths[l], widths[l + 1]
+        parts.append(g.normal(0.0, np.sqrt(2.0 / n_in), n_out * n_in))
+        parts.append(np.zeros(n_out))
+    return np.concatenate(parts).astype(np.float32)
