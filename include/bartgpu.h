@@ -357,6 +357,33 @@ bart_status bart_retrieval_run(bart_ctx* ctx, bart_demc* s, bart_mlp* surrogate,
                                const float* sigma, int64_t first_half_step, int n_generations, int use_graph,
                                float* chain, bart_retrieval_stats* stats);
 
+/* ------------------------------------------------- allocation-free variant */
+
+/* The emission path of bart_forward_spectra_batch for callers that cannot
+ * allocate device memory: code that runs where cudaMalloc is not allowed or
+ * would stall (inside another library's allocator hooks, a real-time loop with
+ * a fixed memory budget, a process that reserves all device memory up front).
+ * The paper has no counterpart; this entry point only changes where scratch
+ * lives.  It takes no context and allocates nothing: its scratch (per-layer
+ * brackets, abundance coefficients, per-tile band partial sums, constant
+ * tables, a status word; about 8.5 MB) is a fixed array that every GPU loading
+ * the library holds until the process exits.
+ *   Limits: n <= 64 entries, n_layers <= 256, n_species <= 4, n_temps <= 64,
+ *   n_nu <= 131072, n_bands <= 16, emission geometry only.  Larger requests
+ *   return BART_ERANGE before any work; malformed ones BART_EINVAL.
+ *   Arguments and results are those of bart_forward_spectra_batch; the work is
+ *   issued on cuda_stream (a cudaStream_t, NULL = default stream) of the
+ *   current device.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array and reuse it without clearing it beyond
+ *   what each call writes first: calls that overlap on the GPU (other streams,
+ *   other host threads) race and must be serialised by the caller.
+ *   Device-side range checks are not reported (there is no context). */
+bart_status bart_forward_emission_noalloc(void* cuda_stream, const bart_grid_desc* grid, const bart_fwd_cfg* cfg,
+                                          const bart_batch* batch, float* spectra, const bart_filters* filters,
+                                          float* bands);
+
 #ifdef __cplusplus
 }
 #endif

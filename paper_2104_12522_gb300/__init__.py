@@ -17,7 +17,8 @@ import numpy as np
 from . import _native
 from ._native import BART_EMISSION, BART_TRANSMISSION  # noqa: F401
 
-__all__ = ["Context", "BartError", "DeviceLines", "device_lines", "NuGrid", "Mlp", "Demc", "BART_EMISSION",
+__all__ = ["Context", "BartError", "DeviceLines", "device_lines", "NuGrid", "Mlp", "Demc",
+           "forward_emission_noalloc", "BART_EMISSION",
            "BART_TRANSMISSION"]
 
 
@@ -362,3 +363,27 @@ class Demc:
     def accept(self, half_step, y, passed, L_y, ls_y=None, accepted=None):
         self.ctx._check(self.lib.bart_demc_accept(self.h, int(half_step), _ptr(y), _ptr(passed), _ptr(L_y),
                                                   _ptr(ls_y), _ptr(accepted)))
+
+
+def forward_emission_noalloc(grid, p_bar, t_K, nu, cfg, theta=None, t_profile=None, nu_lo=None, nu_hi=None,
+                             spec_offsets=None, spectra=None, filters=None, bands=None, n=None, active=None,
+                             stream=None):
+    """bart_forward_emission_noalloc: the emission forward model without any
+    device allocation (fixed scratch in the library); returns the status code."""
+    import torch
+    lib = _native.load()
+    for t, dt in ((grid, "float32"), (theta, "float32"), (t_profile, "float32"), (nu_lo, "int64"),
+                  (nu_hi, "int64"), (spec_offsets, "int64"), (spectra, "float32"), (filters, "float32"),
+                  (bands, "float32"), (active, "int32")):
+        _check_tensor(t, dt)
+    if n is None:
+        n = int(theta.shape[0]) if theta is not None else int(t_profile.shape[0])
+    gd, fc, keep = _grid_cfg(grid, p_bar, t_K, nu, cfg)
+    b = _native.Batch(int(n), _ptr(theta), _ptr(t_profile), None, _ptr(nu_lo), _ptr(nu_hi), _ptr(spec_offsets),
+                      None, None, _ptr(active))
+    fl = _native.Filters(int(filters.shape[0]), _ptr(filters)) if filters is not None else None
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(lib.bart_forward_emission_noalloc(C.c_void_p(stream.cuda_stream), C.byref(gd), C.byref(fc),
+                                                 C.byref(b), _ptr(spectra), C.byref(fl) if fl else None,
+                                                 _ptr(bands)))

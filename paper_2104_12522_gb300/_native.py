@@ -92,6 +92,8 @@ SIGNATURES = {
     "bart_demc_screen": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "bart_demc_accept": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "bart_loglike_bands": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bart_forward_emission_noalloc": (c_int, [c_void_p, P(GridDesc), P(FwdCfg), P(Batch), c_void_p, P(Filters),
+                                              c_void_p]),
     "bart_retrieval_run": (c_int, [c_void_p, c_void_p, c_void_p, P(GridDesc), P(FwdCfg), P(Filters), c_void_p,
                                    c_void_p, c_int64, c_int, c_int, c_void_p, P(RetrievalStats)]),
 }

@@ -441,3 +441,124 @@ extern "C" bart_status bart_band_integrate(bart_ctx* ctx, const float* spectra, 
                                                           f->weights, f->n_bands, out, ctx->d_status);
   return bart_check_launch(ctx, "band_integrate_kernel");
 }
+
+// ---------------------------------------------------------------------------
+// Emission forward model that allocates nothing.
+//
+// For callers that cannot call cudaMalloc: code running where allocation is
+// not allowed or would stall (inside another library's allocator hooks, a
+// real-time loop with a fixed memory budget, a process whose device memory is
+// fully reserved up front).  It runs the same kernels as the emission path of
+// bart_forward_spectra_batch, but all of its scratch (layer temperature
+// brackets, abundance coefficients, per-tile band partial sums, constant
+// tables and a status word) lives in the fixed arrays below, which every GPU
+// that loads this library holds until the process exits.  Host code must not
+// pass an array's name to a kernel (on the host it is only a stand-in, not a
+// device address); the device addresses are looked up once per device with
+// cudaGetSymbolAddress on the first call.
+namespace {
+
+constexpr int NA_MAX_ENTRIES = 64;                   // proposals per call
+constexpr int NA_MAX_LAYERS = 256;
+constexpr int NA_MAX_SPECIES = 4;
+constexpr int NA_MAX_BANDS = 16;
+constexpr int64_t NA_MAX_NU = 131072;
+constexpr int NA_MAX_TILES = (int)(NA_MAX_NU / EM_THREADS);
+constexpr int NA_MAX_TEMPS = 64;
+constexpr int NA_CONST = NA_MAX_LAYERS + NA_MAX_TEMPS + NA_MAX_LAYERS + 2 * MAX_ANGLES + NA_MAX_SPECIES;
+
+static __device__ __align__(256) LayerTW na_tw[NA_MAX_ENTRIES * NA_MAX_LAYERS];
+static __device__ __align__(256) float na_coef[NA_MAX_ENTRIES * NA_MAX_SPECIES];
+static __device__ __align__(256) float2 na_part[(size_t)NA_MAX_ENTRIES * NA_MAX_TILES * NA_MAX_BANDS];
+static __device__ __align__(256) float na_const[NA_CONST];
+static __device__ __align__(256) int na_status[1];
+
+struct NaAddrs {
+  LayerTW* tw;
+  float* coef;
+  float2* part;
+  float* cst;
+  int* status;
+};
+constexpr int NA_MAX_DEVICES = 64;
+NaAddrs g_na[NA_MAX_DEVICES];
+bool g_na_ready[NA_MAX_DEVICES];
+
+}  // namespace
+
+extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const bart_grid_desc* g,
+                                                     const bart_fwd_cfg* c, const bart_batch* b, float* spectra,
+                                                     const bart_filters* f, float* bands) {
+  if (!g || !c || !b || !g->grid || !g->p_bar || !g->t_K || !c->x0) return BART_EINVAL;
+  const int S = g->n_species, L = g->n_layers, M = g->n_temps, n = b->n;
+  const int64_t N = g->nu.n_nu;
+  const int nb = bands ? (f ? f->n_bands : -1) : 0;
+  if (c->geometry != BART_EMISSION) return BART_EUNSUPPORTED;
+  if (S < 1 || L < 2 || M < 1 || n < 1 || N < 1 || nb < 0 || (nb > 0 && !f->weights) || !(g->nu.dnu_cm > 0) ||
+      c->n_angles < 1 || !(c->g_cgs > 0) || !(c->mu_amu > 0) || (!b->theta && !b->t_profile) ||
+      ((b->nu_lo == nullptr) != (b->nu_hi == nullptr)))
+    return BART_EINVAL;   // malformed request
+  if (S > NA_MAX_SPECIES || L > NA_MAX_LAYERS || M > NA_MAX_TEMPS || n > NA_MAX_ENTRIES || N > NA_MAX_NU ||
+      nb > NA_MAX_BANDS || c->n_angles > MAX_ANGLES)
+    return BART_ERANGE;   // beyond the fixed scratch limits above
+  for (int k = 0; k < L; ++k)
+    if (!(g->p_bar[k] > 0) || (k > 0 && !(g->p_bar[k] > g->p_bar[k - 1]))) return BART_EINVAL;
+  for (int m = 0; m < M; ++m)
+    if (!(g->t_K[m] > 0) || (m > 0 && !(g->t_K[m] > g->t_K[m - 1]))) return BART_EINVAL;
+  EmLauncher launch = pick_emission(S, c->n_angles);
+  if (!launch) return BART_EUNSUPPORTED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return BART_ECUDA;
+  if (!g_na_ready[dev]) {   // set-up once per device, with that device current
+    NaAddrs a{};
+    if (cudaGetSymbolAddress((void**)&a.tw, na_tw) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&a.coef, na_coef) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&a.part, na_part) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&a.cst, na_const) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&a.status, na_status) != cudaSuccess) {
+      cudaGetLastError();
+      return BART_ECUDA;
+    }
+    g_na[dev] = a;
+    g_na_ready[dev] = true;
+  }
+  const NaAddrs& a = g_na[dev];
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+  std::vector<double> mu, w;
+  gauss_legendre01(c->n_angles, mu, w);
+  const int NA = c->n_angles;
+  float hconst[NA_CONST];
+  int o = 0;
+  for (int k = 0; k < L; ++k) hconst[o++] = (float)(g->p_bar[k] * bartc::BAR);
+  const int off_t = o;
+  for (int m = 0; m < M; ++m) hconst[o++] = (float)g->t_K[m];
+  const int off_dpg = o;
+  for (int k = 0; k + 1 < L; ++k) hconst[o++] = (float)((g->p_bar[k + 1] - g->p_bar[k]) * bartc::BAR / (2.0 * c->g_cgs));
+  const int off_ang = o;
+  for (int i = 0; i < NA; ++i) hconst[o++] = (float)(-1.4426950408889634 / mu[i]);
+  for (int i = 0; i < NA; ++i) hconst[o++] = (float)(2.0 * bartc::PI * w[i] * mu[i] * 0.5);
+  const int off_x0 = o;
+  for (int s = 0; s < S; ++s) hconst[o++] = (float)(c->x0[s] / (c->mu_amu * bartc::AMU));
+  // pageable source: the copy is staged before cudaMemcpyAsync returns
+  if (cudaMemcpyAsync(a.cst, hconst, o * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(a.status, 0, sizeof(int), st) != cudaSuccess) {
+    cudaGetLastError();
+    return BART_ECUDA;
+  }
+  const double rs = c->r_star_tp_cm, ao = c->a_orbit_cm;
+  const float tirr0 = (rs > 0 && ao > 0) ? (float)(std::sqrt(rs / (2.0 * ao)) * c->t_star_K) : 0.0f;
+  const float tint4 = (float)std::pow(c->t_int_K, 4.0);
+  tp_kernel<<<n, 128, 0, st>>>(b->theta, 5 + S, b->t_profile, n, L, S, a.cst, a.cst + off_t, M,
+                               (float)(1.0 / c->g_cgs), tint4, tirr0, (float)c->t_min_K,
+                               (float)std::min(c->t_max_K, 1e30), a.cst + off_x0, a.tw, a.coef, a.status);
+  const int n_tiles = (int)((N + EM_THREADS - 1) / EM_THREADS);
+  launch(dim3((unsigned)n, (unsigned)n_tiles), st, g->grid, L, M, N, a.tw, a.coef, a.cst + off_dpg,
+         a.cst + off_ang, g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
+         nb ? f->weights : nullptr, nb, a.part, n_tiles, b->active, a.status);
+  if (nb > 0) {
+    const int64_t tot = (int64_t)n * nb;
+    band_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a.part, n, n_tiles, nb, b->active, bands);
+  }
+  return cudaGetLastError() == cudaSuccess ? BART_OK : BART_ECUDA;
+}
