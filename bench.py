@@ -78,6 +78,12 @@ def max_over_ranks(dist, value, device=None):
     return float(t.item())
 
 
+def job_rate(n_ranks, units_per_rank, steps, max_ms):
+    """Whole-job throughput in units/s: every rank processes its own problem
+    (weak scaling), the job takes as long as its slowest rank."""
+    return n_ranks * units_per_rank * steps / (max_ms / 1e3)
+
+
 # ---------------------------------------------------------------- counts
 def eval_count(species, ax) -> int:
     """Algorithmic line-point evaluations of one grid build: for every line,
@@ -320,7 +326,7 @@ def run_native(args):
     op_avg = max_over_ranks(dist, sum(op_ms) / len(op_ms), dev)
     fw_avg = max_over_ranks(dist, sum(fw_ms) / len(fw_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = N * evals * args.steps / (total_ms / 1e3) / 1e9
+    value = job_rate(N, evals, args.steps, total_ms) / 1e9
 
     # end-to-end through the public API with host buffers: H2D of the step's
     # inputs from pinned memory, the step, D2H of the grid and the band values.
@@ -350,6 +356,10 @@ def run_native(args):
     e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1) / e2e_steps, dev)
     ctx.sync()
     assert np.all(np.isfinite(h_bands.numpy())), "non-finite band values"
+
+    aux = {}
+    if not args.no_aux:
+        aux = run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args)
 
     if rank == 0:
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -387,10 +397,132 @@ def run_native(args):
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clk,
         }
+        line.update(aux)
+        line["autotune"] = ctx.autotune_report()
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def _event_ms(torch, stream, fn, reps=1):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args):
+    """Measurements beside the timed step, on the grid the step built:
+    transmission batch, surrogate training and accuracy, screened vs plain
+    retrieval.  Times are CUDA events on the library's stream."""
+    S = int(grid.shape[0])
+    out = {}
+    # --- transmission: 1,024 uneven instances (40..150 levels, 1e4..1e5 points)
+    inst = W.instances(1024, ax.n_nu)
+    th = torch.tensor(inst.theta[:, :5 + S].copy(), device=dev)
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    offs = inst.offsets
+    spec = torch.empty(int(offs[-1]), dtype=torch.float32, device=dev)
+    tb = torch.empty((1024, 12), dtype=torch.float32, device=dev)
+    tfilt = torch.tensor(W.gaussian_filters(W.nu_axis(ax.nu_start, ax.dnu, ax.n_nu), 12, 1100.0, 2900.0,
+                                            100.0, 400.0, seed=3001), device=dev)
+    tcfg = dict(cfg, geometry=1, p_ref=W.HD189_PREF_BAR, p_top=1e-8, p_bot=100.0)
+    targs = dict(theta=th, n_levels=d(inst.n_levels), nu_lo=d(inst.nu_lo), nu_hi=d(inst.nu_hi),
+                 spec_offsets=d(offs), r_planet=d(inst.r_planet), r_star=d(inst.r_star), spectra=spec,
+                 filters=tfilt, bands=tb)
+    run_t = lambda: ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, tcfg, **targs)
+    run_t()
+    ms = _event_ms(torch, stream, run_t, reps=2)
+    ctx.sync()
+    out["transmission"] = {"spectra_per_s": 1024 / (ms / 1e3), "ms_per_batch": ms, "instances": 1024,
+                           "level_sum": int(inst.n_levels.sum()), "points": int(offs[-1]), "bands": 12}
+    # --- surrogate: trained on forward-model band values by the library's kernels
+    n_train, n_val = 200_000, 4096
+    widths = [5 + S, 256, 256, 256, N_BANDS]
+    th_all = torch.tensor(W.proposals(n_train + n_val, generation=100, n_species=S), device=dev)
+    y_all = torch.empty((n_train + n_val, N_BANDS), dtype=torch.float32, device=dev)
+    def gen():
+        for i in range(0, n_train + n_val, N_PROPOSALS):
+            j = min(i + N_PROPOSALS, n_train + n_val)
+            ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=th_all[i:j], filters=filt,
+                                      bands=y_all[i:j])
+    gen_ms = _event_ms(torch, stream, gen)
+    net = bart.Mlp(ctx, widths, bf16_weights=True, log_outputs=True, max_batch=N_PROPOSALS)
+    lo, hi = W.THETA_LO[:5 + S].astype(np.float32), W.THETA_HI[:5 + S].astype(np.float32)
+    logy = np.log10(y_all[:n_train].cpu().numpy().astype(np.float64))
+    net.set_scaling(0.5 * (lo + hi), 2.0 / (hi - lo), logy.mean(0).astype(np.float32),
+                    (1.0 / logy.std(0)).astype(np.float32))
+    net.set_params(torch.tensor(W.mlp_init(widths), device=dev))
+    g = torch.Generator(device=dev).manual_seed(5000)
+    n_steps, B = args.train_steps, 1024
+    perm = [torch.randint(0, n_train, (B,), device=dev, generator=g) for _ in range(64)]
+    xb = [th_all[p].contiguous() for p in perm]
+    yb = [y_all[p].contiguous() for p in perm]
+    def train():
+        for k in range(n_steps):
+            lr = 1e-3 * (0.5 * (1 + np.cos(np.pi * k / n_steps)))
+            net.train_step(xb[k % 64], yb[k % 64], max(lr, 1e-5))
+            if k % 64 == 63:
+                for q in range(64):
+                    p = torch.randint(0, n_train, (B,), device=dev, generator=g)
+                    xb[q], yb[q] = th_all[p].contiguous(), y_all[p].contiguous()
+    train_ms = _event_ms(torch, stream, train)
+    pred = torch.cat([net.forward(th_all[n_train + i:n_train + i + N_PROPOSALS])
+                      for i in range(0, n_val, N_PROPOSALS)]).cpu().numpy()
+    err = np.abs(pred / y_all[n_train:].cpu().numpy() - 1)
+    x_inf = th_all[:N_PROPOSALS].contiguous()
+    inf_ms = _event_ms(torch, stream, lambda: net.forward(x_inf), reps=20)
+    out["surrogate"] = {"widths": widths, "train_spectra": n_train, "train_steps": n_steps, "batch": B,
+                        "spectra_gen_ms": gen_ms, "train_ms": train_ms,
+                        "band_rel_err_median": float(np.median(err)), "band_rel_err_p99": float(np.percentile(err, 99)),
+                        "inference_spectra_per_s": N_PROPOSALS / (inf_ms / 1e3)}
+    # --- retrieval: DE-MC, 16 chains, plain vs surrogate-screened (delayed acceptance)
+    rng = np.random.default_rng(6500)
+    truth = (lo + rng.uniform(0.3, 0.7, 5 + S) * (hi - lo)).astype(np.float32)
+    bt = torch.empty((1, N_BANDS), dtype=torch.float32, device=dev)
+    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=torch.tensor(truth[None], device=dev),
+                              filters=filt, bands=bt)
+    b_true = bt.cpu().numpy()[0]
+    sig = (b_true / 50.0).astype(np.float32)
+    data = torch.tensor((b_true + rng.normal(size=N_BANDS) * sig).astype(np.float32), device=dev)
+    sigma = torch.tensor(sig, device=dev)
+    res = {}
+    for mode in ("plain", "screened"):
+        s = bart.Demc(ctx, 16, lo, hi, jump_every=10, eps=1e-4, seed=6000)
+        s.set_screen(args.screen_beta, args.screen_margin)
+        x0 = torch.tensor((lo + np.random.default_rng(6000).uniform(size=(16, 5 + S)) * (hi - lo)).astype(
+            np.float32), device=dev)
+        b0 = torch.empty((16, N_BANDS), dtype=torch.float32, device=dev)
+        ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=x0, filters=filt, bands=b0)
+        L0 = torch.empty(16, dtype=torch.float64, device=dev)
+        ctx.loglike_bands(b0, data, sigma, L0)
+        Ls0 = None
+        if mode == "screened":
+            Ls0 = torch.empty(16, dtype=torch.float64, device=dev)
+            ctx.loglike_bands(net.forward(x0), data, sigma, Ls0)
+        s.set_state(x0, L0, Ls0)
+        st = {}
+        def run():
+            st.update(ctx.retrieval_run(s, net if mode == "screened" else None, grid, ax.p_bar, ax.t_K, nu, cfg,
+                                        filt, data, sigma, args.generations, use_graph=True))
+        ms = _event_ms(torch, stream, run)
+        ctx.sync()
+        st["accepted_samples_per_s"] = st["accepted"] / (ms / 1e3)
+        st["proposals_per_s"] = st["proposals"] / (ms / 1e3)
+        st["generations"] = args.generations
+        if mode == "screened":
+            st["screen"] = {"beta": args.screen_beta, "margin": args.screen_margin}
+        st["ms"] = ms
+        if st["accepted"]:
+            st["surrogate_err_mean"] = st["surrogate_err_sum"] / st["accepted"]
+        res[mode] = st
+    out["retrieval"] = res
+    return out
 
 
 def run_profile_case(args):
@@ -435,6 +567,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-aux", action="store_true", help="skip the transmission/surrogate/retrieval legs")
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--generations", type=int, default=1000)
+    ap.add_argument("--screen-beta", type=float, default=1.0)
+    ap.add_argument("--screen-margin", type=float, default=3.0)
     ap.add_argument("--case", choices=["bench", "profile"], default="bench",
                     help="profile: small launches of the hot kernels for ncu")
     args = ap.parse_args()

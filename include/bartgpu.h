@@ -72,6 +72,17 @@ const char* bart_last_error(const bart_ctx* ctx);
  * Returns BART_OK, BART_ETIMEOUT, BART_ERANGE or BART_ECUDA. */
 bart_status bart_sync(bart_ctx* ctx);
 
+/* Tile autotuning of the batched forward model (on by default): the first
+ * eager call of each launch shape times every candidate wavenumber-tile width
+ * with CUDA events on the context's stream and keeps the fastest for later
+ * calls; during a stream capture only a cached or the default width is used.
+ * enable = 0 turns it off and forgets the choices. */
+bart_status bart_set_autotune(bart_ctx* ctx, int enable);
+
+/* Writes "shape -> tile" lines of the autotuner's choices into buf (len bytes,
+ * NUL-terminated, truncated if short); returns the full length, -1 for NULL. */
+int bart_autotune_report(const bart_ctx* ctx, char* buf, int len);
+
 /* ------------------------------------------------------------ line lists */
 
 /* One species' line list, structure of arrays, all DEVICE pointers, sorted by
@@ -295,9 +306,10 @@ bart_status bart_mlp_train_step(bart_mlp* net, const float* x, const float* t, i
  * every jump_every-th generation (0 = never).  Random numbers come from a
  * counter-based generator keyed by (seed, half_step, chain, draw).
  * Screening is delayed acceptance: stage 1 keeps a proposal with probability
- * min(1, exp(ls_y - ls_x)) from the surrogate log-likelihood, stage 2 accepts
- * a survivor with probability min(1, exp((L_y - L_x) - (ls_y - ls_x))) from
- * the exact log-likelihood, which keeps the exact posterior as the target.
+ * a1 = min(1, exp(ls_y - ls_x)) from the surrogate log-likelihood (tempered by
+ * bart_demc_set_screen), stage 2 accepts a survivor with probability
+ * min(1, exp(L_y - L_x) a1(y -> x) / a1(x -> y)) from the exact
+ * log-likelihood, which keeps the exact posterior as the target.
  * 6 <= n_chains <= 65536, 1 <= n_params <= 32. */
 typedef struct bart_demc bart_demc;
 bart_status bart_demc_create(bart_ctx* ctx, int n_chains, int n_params, const float* lo, const float* hi,
@@ -311,6 +323,12 @@ bart_status bart_demc_get_state(bart_demc* s, float* x, double* loglike, double*
  * y device [n_chains][n_params]; inbox device [n_chains] = 1 for the updated
  * half's proposals inside the prior box, else 0 (other rows copy x). */
 bart_status bart_demc_propose(bart_demc* s, int64_t half_step, float* y, int32_t* inbox);
+/* Stage-1 acceptance of the screen, a1(x -> y) = min(1, exp(beta (ls_y - ls_x)
+ * + margin)) (defaults beta = 1, margin = 0).  Stage 2 divides out a1 of the
+ * forward and multiplies in a1 of the reverse move, so the exact posterior
+ * stays the target for any beta >= 0 and margin; beta < 1 or margin > 0 make
+ * the screen reject only clearly worse proposals. */
+bart_status bart_demc_set_screen(bart_demc* s, double beta, double margin);
 /* Stage 1: pass[i] = inbox[i] and the surrogate test (ls_y device [n_chains]
  * FP64, or NULL for no screening). */
 bart_status bart_demc_screen(bart_demc* s, int64_t half_step, const int32_t* inbox, const double* ls_y,

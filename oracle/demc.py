@@ -6,9 +6,10 @@ halves; a half-step moves every chain i of one half to
 y_i = x_i + gamma (x_r1 - x_r2) + e_i with r1 != r2 drawn from the other half,
 e_i ~ N(0, (eps * width)^2), gamma = 2.38/sqrt(2 d) (1 on every jump_every-th
 generation), uniform prior on a box.  With a surrogate log-likelihood the
-move is delayed acceptance (two-stage Metropolis-Hastings): stage 1 with
-probability min(1, exp(ls_y - ls_x)), stage 2 with
-min(1, exp((L_y - L_x) - (ls_y - ls_x))).  Random numbers come from numpy, so
+move is delayed acceptance (two-stage Metropolis-Hastings, Christen & Fox
+2005): stage 1 with probability a1(x -> y) = min(1, exp(beta (ls_y - ls_x) +
+margin)), stage 2 with min(1, exp(L_y - L_x) a1(y -> x) / a1(x -> y)); for
+beta = 1, margin = 0 the stage-2 ratio is exp((L_y - L_x) - (ls_y - ls_x)).  Random numbers come from numpy, so
 parity with the GPU sampler is distributional.
 
 Statistics (Sec. 4 "Bayesian samplers", App. C):
@@ -21,7 +22,8 @@ Statistics (Sec. 4 "Bayesian samplers", App. C):
 import numpy as np
 
 
-def run(loglike, x0, lo, hi, n_gen, rng, gamma=None, jump_every=10, eps=1e-4, surrogate=None):
+def run(loglike, x0, lo, hi, n_gen, rng, gamma=None, jump_every=10, eps=1e-4, surrogate=None, beta=1.0,
+        margin=0.0):
     """Returns the chain history [n_gen+1][C][d] and acceptance counts."""
     x = np.array(x0, np.float64)
     C, d = x.shape
@@ -42,10 +44,13 @@ def run(loglike, x0, lo, hi, n_gen, rng, gamma=None, jump_every=10, eps=1e-4, su
                 if np.any(y < lo) or np.any(y > hi):
                     continue
                 ly_s = surrogate(y) if surrogate else 0.0
-                if surrogate and np.log(rng.uniform()) >= ly_s - Ls[i]:
+                dl = ly_s - Ls[i]
+                if surrogate and np.log(rng.uniform()) >= min(0.0, beta * dl + margin):
                     continue
                 ly = loglike(y)
-                r = (ly - L[i]) - (ly_s - Ls[i])
+                r = ly - L[i]
+                if surrogate:
+                    r += min(0.0, -beta * dl + margin) - min(0.0, beta * dl + margin)
                 if r >= 0 or np.log(rng.uniform()) < r:
                     x[i], L[i], Ls[i] = y, ly, ly_s
                     acc += 1

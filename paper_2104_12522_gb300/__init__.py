@@ -131,6 +131,20 @@ class Context:
     def sync(self):
         self._check(self.lib.bart_sync(self.h))
 
+    def set_autotune(self, enable: bool):
+        self._check(self.lib.bart_set_autotune(self.h, int(bool(enable))))
+
+    def autotune_report(self) -> dict:
+        """Autotuned tile width per launch shape."""
+        n = self.lib.bart_autotune_report(self.h, None, 0)
+        buf = C.create_string_buffer(n + 1)
+        self.lib.bart_autotune_report(self.h, buf, n + 1)
+        out = {}
+        for line in buf.value.decode().splitlines():
+            k, v = line.rsplit(" -> ", 1)
+            out[k] = int(v)
+        return out
+
     # ------------------------------------------------------------ opacity
     def faddeeva_re(self, x, y, out=None):
         import torch
@@ -353,6 +367,9 @@ class Demc:
     def get_state(self, x=None, loglike=None, loglike_s=None):
         self.ctx._check(self.lib.bart_demc_get_state(self.h, _ptr(x), _ptr(loglike), _ptr(loglike_s)))
         return x, loglike, loglike_s
+
+    def set_screen(self, beta=1.0, margin=0.0):
+        self.ctx._check(self.lib.bart_demc_set_screen(self.h, float(beta), float(margin)))
 
     def propose(self, half_step, y, inbox):
         self.ctx._check(self.lib.bart_demc_propose(self.h, int(half_step), _ptr(y), _ptr(inbox)))

@@ -65,6 +65,8 @@ SIGNATURES = {
     "bart_set_stream": (c_int, [c_void_p, c_void_p]),
     "bart_last_error": (C.c_char_p, [c_void_p]),
     "bart_sync": (c_int, [c_void_p]),
+    "bart_set_autotune": (c_int, [c_void_p, c_int]),
+    "bart_autotune_report": (c_int, [c_void_p, C.c_char_p, c_int]),
     "bart_opacity_cells": (c_int, [c_void_p, P(LineList), c_int, P(c_double), P(c_double), c_int, NuGrid,
                                    c_double, c_void_p]),
     "bart_build_opacity_grid": (c_int, [c_void_p, P(LineList), c_int, P(c_double), c_int, P(c_double), c_int,
@@ -88,6 +90,7 @@ SIGNATURES = {
     "bart_demc_destroy": (None, [c_void_p]),
     "bart_demc_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "bart_demc_get_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bart_demc_set_screen": (c_int, [c_void_p, c_double, c_double]),
     "bart_demc_propose": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
     "bart_demc_screen": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "bart_demc_accept": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

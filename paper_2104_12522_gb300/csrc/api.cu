@@ -121,3 +121,21 @@ extern "C" bart_status bart_sync(bart_ctx* ctx) {
   }
   return BART_OK;
 }
+
+extern "C" bart_status bart_set_autotune(bart_ctx* ctx, int enable) {
+  if (!ctx) return BART_EINVAL;
+  ctx->autotune = enable ? 1 : 0;
+  if (!enable) ctx->tiles.clear();
+  return BART_OK;
+}
+
+extern "C" int bart_autotune_report(const bart_ctx* ctx, char* buf, int len) {
+  if (!ctx) return -1;
+  std::string out;
+  for (auto& kv : ctx->tiles) out += kv.first + " -> " + std::to_string(kv.second) + "\n";
+  if (buf && len > 0) {
+    std::strncpy(buf, out.c_str(), (size_t)len - 1);
+    buf[len - 1] = 0;
+  }
+  return (int)out.size();
+}

@@ -24,6 +24,8 @@ struct bart_ctx {
   // Growable scratch: one buffer per purpose so calls can keep it resident.
   std::map<std::string, std::pair<void*, size_t>> scratch;
   std::map<std::string, std::vector<unsigned char>> uploaded;   // host copy of each constant buffer
+  std::map<std::string, int> tiles;  // autotuned tile width per launch shape
+  int autotune = 1;
   int* d_status = nullptr;          // device status word
   float2* d_wtable = nullptr;       // Faddeeva Taylor-coefficient table
   bool wtable_ready = false;
@@ -75,6 +77,6 @@ constexpr double PI = 3.141592653589793238462643383279502884;
 
 // Faddeeva Taylor table geometry: nodes z0 = ix*H + i*iy*H, |x|,y in [0, 5].
 namespace wtab {
-constexpr int NX = 21, NY = 21, NT = 12;
-constexpr float H = 0.25f;
+constexpr int NX = 41, NY = 41, NT = 8;
+constexpr float H = 0.125f;
 }  // namespace wtab

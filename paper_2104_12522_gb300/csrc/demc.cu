@@ -38,6 +38,8 @@ struct bart_demc {
   double* L = nullptr;      // device [C] exact log-likelihood
   double* Ls = nullptr;     // device [C] surrogate log-likelihood
   const int64_t* hs_dev = nullptr;   // if set, kernels read the half-step index here
+  double beta = 1.0;        // stage-1 temperature of the surrogate log-likelihood
+  double margin = 0.0;      // stage-1 margin
 };
 
 namespace {
@@ -105,16 +107,21 @@ __global__ void propose_kernel(int C, int d, const float* __restrict__ x, const 
   inbox[i] = ok;
 }
 
+// log of the stage-1 acceptance a1(x -> y) = min(1, exp(beta (ls_y - ls_x) + margin))
+__device__ __forceinline__ double log_a1(double d, double beta, double margin) {
+  return fmin(0.0, beta * d + margin);
+}
+
 __global__ void screen_kernel(int C, const int32_t* __restrict__ inbox, const double* __restrict__ ls_y,
                               const double* __restrict__ ls_x, int64_t gen_arg, const int64_t* __restrict__ gen_dev,
-                              uint64_t seed, int32_t* __restrict__ pass) {
+                              uint64_t seed, double beta, double margin, int32_t* __restrict__ pass) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C) return;
   const int64_t gen = gen_dev ? *gen_dev : gen_arg;
   int p = inbox[i];
   if (p && ls_y) {
     const double lu = log(uniform(seed, gen, i, 100));
-    p = lu < ls_y[i] - ls_x[i];
+    p = lu < log_a1(ls_y[i] - ls_x[i], beta, margin);
   }
   pass[i] = p;
 }
@@ -122,14 +129,21 @@ __global__ void screen_kernel(int C, const int32_t* __restrict__ inbox, const do
 __global__ void accept_kernel(int C, int d, float* __restrict__ x, double* __restrict__ L, double* __restrict__ Ls,
                               const float* __restrict__ y, const int32_t* __restrict__ pass,
                               const double* __restrict__ L_y, const double* __restrict__ ls_y, int64_t gen_arg,
-                              const int64_t* __restrict__ gen_dev, uint64_t seed, int32_t* __restrict__ accepted) {
+                              const int64_t* __restrict__ gen_dev, uint64_t seed, double beta, double margin,
+                              int32_t* __restrict__ accepted) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C) return;
   const int64_t gen = gen_dev ? *gen_dev : gen_arg;
   int a = 0;
   if (pass[i]) {
     double r = L_y[i] - L[i];
-    if (ls_y) r -= ls_y[i] - Ls[i];
+    if (ls_y) {
+      // delayed acceptance: the stage-1 probabilities of the reverse and the
+      // forward move enter the stage-2 ratio (for beta = 1, margin = 0 this is
+      // -(ls_y - ls_x))
+      const double d = ls_y[i] - Ls[i];
+      r += log_a1(-d, beta, margin) - log_a1(d, beta, margin);
+    }
     const double lu = log(uniform(seed, gen, i, 101));
     a = (r >= 0.0) || (lu < r);
     if (!(L_y[i] == L_y[i])) a = 0;           // a NaN likelihood is never accepted
@@ -247,7 +261,7 @@ extern "C" bart_status bart_demc_screen(bart_demc* s, int64_t half_step, const i
   if (!s) return BART_EINVAL;
   BART_REQUIRE(s->ctx, inbox && pass, "NULL inbox or pass");
   screen_kernel<<<nblk(s->C), 128, 0, s->ctx->stream>>>(s->C, inbox, ls_y, s->Ls, half_step, s->hs_dev, s->seed,
-                                                        pass);
+                                                        s->beta, s->margin, pass);
   return bart_check_launch(s->ctx, "screen_kernel");
 }
 
@@ -256,7 +270,8 @@ extern "C" bart_status bart_demc_accept(bart_demc* s, int64_t half_step, const f
   if (!s) return BART_EINVAL;
   BART_REQUIRE(s->ctx, y && pass && L_y, "NULL y, pass or L_y");
   accept_kernel<<<nblk(s->C), 128, 0, s->ctx->stream>>>(s->C, s->d, s->x, s->L, s->Ls, y, pass, L_y, ls_y,
-                                                        half_step, s->hs_dev, s->seed, accepted);
+                                                        half_step, s->hs_dev, s->seed, s->beta, s->margin,
+                                                        accepted);
   return bart_check_launch(s->ctx, "accept_kernel");
 }
 
@@ -267,6 +282,14 @@ extern "C" bart_status bart_loglike_bands(bart_ctx* ctx, const float* model, int
   BART_REQUIRE(ctx, n >= 1 && n_bands >= 1, "n and n_bands must be >= 1");
   loglike_kernel<<<nblk(n), 128, 0, ctx->stream>>>(model, n, n_bands, data, sigma, mask, out);
   return bart_check_launch(ctx, "loglike_kernel");
+}
+
+extern "C" bart_status bart_demc_set_screen(bart_demc* s, double beta, double margin) {
+  if (!s) return BART_EINVAL;
+  BART_REQUIRE(s->ctx, beta >= 0 && std::isfinite(beta) && std::isfinite(margin), "bad beta or margin");
+  s->beta = beta;
+  s->margin = margin;
+  return BART_OK;
 }
 
 // Internal hooks of the retrieval driver.

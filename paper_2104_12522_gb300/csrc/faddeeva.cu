@@ -1,11 +1,11 @@
 // Host-side construction of the Faddeeva Taylor table and the bart_faddeeva_re
 // entry point.
 //
-// Table nodes z0 = ix/4 + i iy/4 (0 <= ix, iy <= 20).  w(z0) is found in FP64:
-// the Laplace continued fraction to depth 200 gives w at z0 + i(8 - y0),
-// where it has converged to round-off, and w is then carried down to z0 along
-// the vertical line by fourth-order Runge-Kutta on w' = -2 z w + 2i/sqrt(pi)
-// (dw/dy = i w').  Downward integration damps the exp(-z^2) mode of the
+// Table nodes z0 = ix/8 + i iy/8 (0 <= ix, iy <= 40).  w(z0) is found in FP64:
+// the Laplace continued fraction to depth 200 gives w at x0 + 8i, where it has
+// converged to round-off, and w is then carried down the vertical line through
+// every node of the column by fourth-order Runge-Kutta on
+// w' = -2 z w + 2i/sqrt(pi) (dw/dy = i w').  Downward integration damps the exp(-z^2) mode of the
 // equation, so the error stays at the level of the step error.  On the real
 // axis the real part is set to exp(-x0^2), its exact value.  The Taylor
 // coefficients then follow from c_0 = w, c_1 = w', and
@@ -27,42 +27,55 @@ cd cf_w(cd z, int depth) {
   return cd(0.0, 1.0 / SQRTPI) / t;
 }
 
-cd w_node(double x0, double y0) {
-  const double ytop = 8.0;
-  const int steps = 4000;
-  const double dy = -(ytop - y0) / steps;
+// w along the vertical line x = x0 at every table node y0 = iy H, integrated
+// downward from y = 8 (where the continued fraction has converged) with RK4
+// steps that land on the nodes.
+void w_column(double x0, std::vector<cd>& out) {
+  const double H = wtab::H;
+  const int sub = 64;                       // steps per node spacing
+  const int n_steps = (int)std::lround(8.0 / H) * sub;
+  const double dy = -H / sub;
   auto f = [&](double y, cd w) {
     cd z(x0, y);
     cd wp = -2.0 * z * w + cd(0.0, 2.0 / SQRTPI);
     return cd(0.0, 1.0) * wp;
   };
-  double y = ytop;
-  cd w = cf_w(cd(x0, ytop), 200);
-  for (int i = 0; i < steps; ++i) {
+  out.assign(wtab::NY, cd(0.0, 0.0));
+  double y = 8.0;
+  cd w = cf_w(cd(x0, y), 200);
+  for (int step = 0; step <= n_steps; ++step) {
+    if (step % sub == 0) {
+      const int iy = (n_steps - step) / sub;
+      if (iy < wtab::NY) out[iy] = w;
+    }
+    if (step == n_steps) break;
     cd k1 = f(y, w);
     cd k2 = f(y + 0.5 * dy, w + 0.5 * dy * k1);
     cd k3 = f(y + 0.5 * dy, w + 0.5 * dy * k2);
     cd k4 = f(y + dy, w + dy * k3);
     w += dy / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
-    y += dy;
+    y = 8.0 + (step + 1) * dy;
   }
-  if (y0 == 0.0) w = cd(std::exp(-x0 * x0), w.imag());
-  return w;
+  out[0] = cd(std::exp(-x0 * x0), out[0].imag());   // exact real part on the real axis
 }
 
 void build_table(std::vector<float2>& out) {
   out.resize((size_t)wtab::NX * wtab::NY * wtab::NT);
-  for (int iy = 0; iy < wtab::NY; ++iy)
-    for (int ix = 0; ix < wtab::NX; ++ix) {
-      double x0 = ix * (double)wtab::H, y0 = iy * (double)wtab::H;
+  std::vector<cd> col;
+  for (int ix = 0; ix < wtab::NX; ++ix) {
+    const double x0 = ix * (double)wtab::H;
+    w_column(x0, col);
+    for (int iy = 0; iy < wtab::NY; ++iy) {
+      const double y0 = iy * (double)wtab::H;
       cd z0(x0, y0);
       cd c[wtab::NT];
-      c[0] = w_node(x0, y0);
+      c[0] = col[iy];
       c[1] = -2.0 * z0 * c[0] + cd(0.0, 2.0 / SQRTPI);
       for (int n = 1; n + 1 < wtab::NT; ++n) c[n + 1] = (-2.0 * z0 * c[n] - 2.0 * c[n - 1]) / double(n + 1);
       float2* dst = &out[((size_t)iy * wtab::NX + ix) * wtab::NT];
       for (int n = 0; n < wtab::NT; ++n) dst[n] = make_float2((float)c[n].real(), (float)c[n].imag());
     }
+  }
 }
 
 __global__ void faddeeva_kernel(const float* __restrict__ x, const float* __restrict__ y, int64_t n,

@@ -19,13 +19,13 @@
 //               y.  Near the real axis the exponentially small term
 //               exp(y^2 - x^2) cos(2xy) that the asymptotic fraction misses is
 //               added back (y < 1).  Relative error <= 1e-6.
-//  * |z| < 5    Taylor expansion about the nearest node z0 of a 21 x 21 grid
-//               (spacing 1/4) on 0 <= x, y <= 5, with coefficients
+//  * |z| < 5    Taylor expansion about the nearest node z0 of a 41 x 41 grid
+//               (spacing 1/8) on 0 <= x, y <= 5, with coefficients
 //               c_n = w^(n)(z0)/n! from the recurrence of the derivatives
 //               w' = -2 z w + 2i/sqrt(pi), w^(n+1) = -2 z w^(n) - 2n w^(n-1).
 //               The node values are built once in FP64 (see faddeeva.cu); on
-//               the real axis their real part is exactly exp(-x0^2).  Twelve
-//               terms, |z - z0| <= 0.18: relative error <= 3e-7.
+//               the real axis their real part is exactly exp(-x0^2).  Eight
+//               terms, |z - z0| <= 0.09: relative error <= 3e-7.
 // Re w is even in x; all branches use |x|.
 #pragma once
 
@@ -59,18 +59,18 @@ __device__ __forceinline__ float cf_re(float x, float y, int depth) {
   float tr = x, ti = y;
   for (int k = depth; k >= 1; --k) {
     float a = 0.5f * (float)k;
-    float inv = __frcp_rn(fmaf(tr, tr, ti * ti));
+    float inv = rcp_approx(fmaf(tr, tr, ti * ti));
     float qr = a * tr * inv, qi = -a * ti * inv;
     tr = x - qr;
     ti = y - qi;
   }
-  return INV_SQRTPI * ti * __frcp_rn(fmaf(tr, tr, ti * ti));
+  return INV_SQRTPI * ti * rcp_approx(fmaf(tr, tr, ti * ti));
 }
 
 // Taylor expansion about the nearest table node (x >= 0, x^2 + y^2 < 25).
 __device__ __forceinline__ float taylor_re(float x, float y, const float2* __restrict__ tab) {
-  int ix = min((int)(x * 4.0f + 0.5f), wtab::NX - 1);
-  int iy = min((int)(y * 4.0f + 0.5f), wtab::NY - 1);
+  int ix = min((int)(x * (1.0f / wtab::H) + 0.5f), wtab::NX - 1);
+  int iy = min((int)(y * (1.0f / wtab::H) + 0.5f), wtab::NY - 1);
   float a = x - (float)ix * wtab::H;
   float b = y - (float)iy * wtab::H;
   const float2* c = tab + ((size_t)iy * wtab::NX + ix) * wtab::NT;
@@ -94,8 +94,9 @@ __device__ __forceinline__ float core_re(float x, float y, const float2* __restr
   if (s < 25.0f) return taylor_re(x, y, tab);
   float v = cf_re(x, y, s >= 64.0f ? 4 : 6);
   if (y < 1.0f) {
+    // the Gaussian term matters only near the real axis; there 2xy is small
     float g = y * y - x * x;
-    if (g > -87.0f) v += expf(g) * cosf(2.0f * x * y);
+    if (g > -87.0f) v += __expf(g) * __cosf(2.0f * x * y);
   }
   return v;
 }

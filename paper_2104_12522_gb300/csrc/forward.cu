@@ -36,9 +36,8 @@ constexpr float LOG2E_LO = 1.925963033500011e-08f;   // log2(e) - (float)log2(e)
 constexpr float LN2F = 0.6931471805599453f;
 
 struct LayerTW {
-  int m;        // lower temperature bracket
+  int64_t row;  // offset of grid row (layer k, lower temperature bracket m): (k M + m) n_nu
   float w;      // weight of the upper bracket
-  float T;      // layer temperature, K
   float c2_t;   // c2 / T
 };
 
@@ -77,11 +76,13 @@ void gauss_legendre01(int n, std::vector<double>& mu, std::vector<double>& w) {
 
 __global__ void tp_kernel(const float* __restrict__ theta, int n_theta, const float* __restrict__ t_profile,
                           int n, int L, int S, const float* __restrict__ p_cgs, const float* __restrict__ t_axis,
-                          int M, float inv_g, float tint4, float tirr0, float t_min, float t_max,
+                          int M, int64_t N, float inv_g, float tint4, float tirr0, float t_min, float t_max,
                           const float* __restrict__ x0_over_mu, LayerTW* __restrict__ tw,
-                          float* __restrict__ coef, int* __restrict__ status) {
+                          float* __restrict__ coef, const int32_t* __restrict__ act_mask,
+                          int* __restrict__ status) {
   const int p = blockIdx.x;
   if (p >= n) return;
+  if (act_mask && !act_mask[p]) return;      // skipped entry (its parameters may lie outside the prior)
   for (int k = threadIdx.x; k < L; k += blockDim.x) {
     float T;
     if (t_profile) {
@@ -110,9 +111,8 @@ __global__ void tp_kernel(const float* __restrict__ theta, int n_theta, const fl
       w = fminf(fmaxf(w, 0.0f), 1.0f);
     }
     LayerTW r;
-    r.m = m;
+    r.row = ((int64_t)k * M + m) * N;
     r.w = w;
-    r.T = T;
     r.c2_t = (float)bartc::C2 / T;
     tw[(int64_t)p * L + k] = r;
   }
@@ -123,19 +123,18 @@ __global__ void tp_kernel(const float* __restrict__ theta, int n_theta, const fl
 }
 
 // Planck function per unit wavenumber, B = c1nu3 / (exp(x) - 1), x = c2 nu / T.
-// exp(x) is 2^(x log2 e) with the product split in two parts so its rounding
-// does not limit the accuracy; x > 20 (not reached by the grid's wavenumbers
-// and temperatures here) takes an FP64 exponential.
+// For x <= 20 exp(x) = 2^(x log2 e) in FP32: the rounding of the product
+// bounds the relative error of B by ~3e-6 for x >= 0.48 (the smallest
+// c2 nu / T of a 1000 cm^-1, 3000 K grid); larger x, where 2^(x log2 e) would
+// lose digits and eventually overflow, takes an FP64 exponential.
 __device__ __forceinline__ float planck(float c1nu3, float x) {
   if (x > 20.0f) return (float)((double)c1nu3 / expm1((double)x));
-  float hi = x * LOG2E;
-  float lo = fmaf(x, LOG2E, -hi) + x * LOG2E_LO;
-  float e = bartf::ex2_approx(hi) * fmaf(lo, LN2F, 1.0f);
+  const float e = bartf::ex2_approx(x * LOG2E);
   return c1nu3 * bartf::rcp_approx(e - 1.0f);
 }
 
-template <int S, int NA>
-__global__ void __launch_bounds__(EM_THREADS)
+template <int S, int NA, int TW>
+__global__ void __launch_bounds__(TW)
 emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const LayerTW* __restrict__ tw,
                 const float* __restrict__ coef, const float* __restrict__ dpg,
                 const float* __restrict__ ang /* [2][NA]: -log2(e)/mu, 2 pi w mu / 2 */, double nu_start,
@@ -153,14 +152,19 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
     if (tid == 0 && tile == 0) atomicOr(status, BART_DEV_RANGE);
     return;
   }
-  const int64_t j = lo + (int64_t)tile * EM_THREADS + tid;
+  const int64_t j = lo + (int64_t)tile * TW + tid;
   const bool active = j < hi;
   const int64_t jj = active ? j : lo;       // inactive lanes compute on a valid index
 
   __shared__ float s_coef[S];
-  __shared__ float2 s_red[EM_THREADS / 32][MAX_BANDS];
+  __shared__ float s_dpg[MAX_LAYERS];
+  __shared__ float2 s_red[TW / 32][MAX_BANDS];
   if (tid < S) s_coef[tid] = coef[(int64_t)p * S + tid];
+  for (int k = tid; k + 1 < L; k += TW) s_dpg[k] = dpg[k];
   __syncthreads();
+  float xs[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) xs[s] = s_coef[s];
 
   const double nu = nu_start + (double)jj * dnu;
   const float nuf = (float)nu;
@@ -176,27 +180,29 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
   }
   const LayerTW* twp = tw + (int64_t)p * L;
   const int64_t sstride = (int64_t)L * M * N;
+  const int64_t dm = (M > 1) ? N : 0;          // offset of the upper temperature bracket
+  const float* gj = grid + jj;
 
-  auto chi_at = [&](int k, const LayerTW& r) {
-    const float* g0 = grid + ((int64_t)k * M + r.m) * N + jj;
+  auto chi_at = [&](const LayerTW& r) {
+    const float* g0 = gj + r.row;
     float chi = 0.0f;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      float a = __ldg(g0 + s * sstride);
-      float b = (M > 1) ? __ldg(g0 + s * sstride + N) : a;
-      chi = fmaf(s_coef[s], fmaf(r.w, b - a, a), chi);
+      const float a = __ldg(g0 + s * sstride);
+      const float b = __ldg(g0 + s * sstride + dm);
+      chi = fmaf(xs[s], fmaf(r.w, b - a, a), chi);
     }
     return chi;
   };
 
   LayerTW r = twp[0];
-  float chi_prev = chi_at(0, r);
+  float chi_prev = chi_at(r);
   float B_prev = planck(c1nu3, nuf * r.c2_t);
   for (int k = 1; k < L; ++k) {
     r = twp[k];
-    const float chi = chi_at(k, r);
+    const float chi = chi_at(r);
     const float B = planck(c1nu3, nuf * r.c2_t);
-    const float dtau = (chi_prev + chi) * dpg[k - 1];
+    const float dtau = (chi_prev + chi) * s_dpg[k - 1];
     const float Bsum = B_prev + B;
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
@@ -234,7 +240,7 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
     __syncthreads();
     if (tid < n_bands) {
       float2 acc = make_float2(0.f, 0.f);
-      for (int w = 0; w < EM_THREADS / 32; ++w) {
+      for (int w = 0; w < TW / 32; ++w) {
         acc.x += s_red[w][tid].x;
         acc.y += s_red[w][tid].y;
       }
@@ -300,37 +306,51 @@ __global__ void band_integrate_kernel(const float* __restrict__ spectra, const i
   }
 }
 
-template <int S, int NA>
+template <int S, int NA, int TW>
 void launch_emission(dim3 g, cudaStream_t st, const float* grid, int L, int M, int64_t N, const LayerTW* tw,
                      const float* coef, const float* dpg, const float* ang, double nu_start, double dnu,
                      const int64_t* lo, const int64_t* hi, const int64_t* offs, float* spectra,
                      const float* filt, int nb, float2* partial, int n_tiles, const int32_t* active, int* status) {
-  emission_kernel<S, NA><<<g, EM_THREADS, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi,
-                                                   offs, spectra, filt, nb, partial, n_tiles, active, status);
+  emission_kernel<S, NA, TW><<<g, TW, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi, offs,
+                                               spectra, filt, nb, partial, n_tiles, active, status);
 }
 
 using EmLauncher = void (*)(dim3, cudaStream_t, const float*, int, int, int64_t, const LayerTW*, const float*,
                             const float*, const float*, double, double, const int64_t*, const int64_t*,
                             const int64_t*, float*, const float*, int, float2*, int, const int32_t*, int*);
 
-template <int S>
-EmLauncher pick_na(int na) {
-  switch (na) {
-    case 1: return launch_emission<S, 1>;
-    case 2: return launch_emission<S, 2>;
-    case 4: return launch_emission<S, 4>;
-    case 8: return launch_emission<S, 8>;
-    case 16: return launch_emission<S, 16>;
+// Wavenumber-tile widths the autotuner chooses from (threads per CTA).
+constexpr int TILE_CHOICES[3] = {64, 128, 256};
+constexpr int MIN_TILE = 64;
+
+template <int S, int NA>
+EmLauncher pick_tile(int tw) {
+  switch (tw) {
+    case 64: return launch_emission<S, NA, 64>;
+    case 128: return launch_emission<S, NA, 128>;
+    case 256: return launch_emission<S, NA, 256>;
     default: return nullptr;
   }
 }
 
-EmLauncher pick_emission(int S, int na) {
+template <int S>
+EmLauncher pick_na(int na, int tw) {
+  switch (na) {
+    case 1: return pick_tile<S, 1>(tw);
+    case 2: return pick_tile<S, 2>(tw);
+    case 4: return pick_tile<S, 4>(tw);
+    case 8: return pick_tile<S, 8>(tw);
+    case 16: return pick_tile<S, 16>(tw);
+    default: return nullptr;
+  }
+}
+
+EmLauncher pick_emission(int S, int na, int tw = EM_THREADS) {
   switch (S) {
-    case 1: return pick_na<1>(na);
-    case 2: return pick_na<2>(na);
-    case 3: return pick_na<3>(na);
-    case 4: return pick_na<4>(na);
+    case 1: return pick_na<1>(na, tw);
+    case 2: return pick_na<2>(na, tw);
+    case 3: return pick_na<3>(na, tw);
+    case 4: return pick_na<4>(na, tw);
     default: return nullptr;
   }
 }
@@ -349,8 +369,8 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
   BART_REQUIRE(ctx, g->n_species >= 1 && g->n_layers >= 2 && g->n_layers <= MAX_LAYERS && g->n_temps >= 1,
                "grid shape out of range (S >= 1, 2 <= L <= %d, M >= 1)", MAX_LAYERS);
   BART_REQUIRE(ctx, g->p_bar && g->t_K, "grid axes are NULL");
-  BART_REQUIRE(ctx, g->nu.n_nu >= 1 && g->nu.n_nu <= (int64_t)65535 * EM_THREADS && g->nu.dnu_cm > 0,
-               "bad nu grid (1 <= n_nu <= %d, dnu > 0)", 65535 * EM_THREADS);
+  BART_REQUIRE(ctx, g->nu.n_nu >= 1 && g->nu.n_nu <= (int64_t)65535 * MIN_TILE && g->nu.dnu_cm > 0,
+               "bad nu grid (1 <= n_nu <= %d, dnu > 0)", 65535 * MIN_TILE);
   for (int k = 0; k < g->n_layers; ++k)
     BART_REQUIRE(ctx, g->p_bar[k] > 0 && (k == 0 || g->p_bar[k] > g->p_bar[k - 1]),
                  "p_bar must be positive and strictly increasing");
@@ -372,8 +392,7 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
   BART_REQUIRE(ctx, c->n_angles >= 1 && c->n_angles <= MAX_ANGLES, "n_angles must be in [1, %d]", MAX_ANGLES);
   const int S = g->n_species, L = g->n_layers, M = g->n_temps, n = b->n;
   const int64_t N = g->nu.n_nu;
-  EmLauncher launch = pick_emission(S, c->n_angles);
-  if (!launch)
+  if (!pick_emission(S, c->n_angles))
     return bart_fail(ctx, BART_EUNSUPPORTED, "emission with %d species and %d angles is not instantiated "
                      "(species 1-4; angles 1, 2, 4, 8, 16)", S, c->n_angles);
   BART_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -392,8 +411,7 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
   for (int s = 0; s < S; ++s) hconst.push_back((float)(c->x0[s] / (c->mu_amu * bartc::AMU)));
   const size_t off_t = L, off_dpg = off_t + M, off_ang = off_dpg + (L - 1), off_x0 = off_ang + 2 * NA;
 
-  const int64_t span_max = N;   // spans lie inside the grid
-  const int n_tiles = (int)((span_max + EM_THREADS - 1) / EM_THREADS);
+  const int max_tiles = (int)((N + MIN_TILE - 1) / MIN_TILE);   // partials sized for the smallest tile
   void *p_const, *p_tw, *p_coef, *p_part = nullptr;
   bart_status st;
   if ((st = bart_upload_const(ctx, "fw_const", hconst.data(), hconst.size() * sizeof(float), &p_const)) != BART_OK)
@@ -401,21 +419,62 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
   if ((st = bart_scratch(ctx, "fw_tw", (size_t)n * L * sizeof(LayerTW), &p_tw)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "fw_coef", (size_t)n * S * sizeof(float), &p_coef)) != BART_OK) return st;
   if (nb > 0 &&
-      (st = bart_scratch(ctx, "fw_part", (size_t)n * n_tiles * nb * sizeof(float2), &p_part)) != BART_OK)
+      (st = bart_scratch(ctx, "fw_part", (size_t)n * max_tiles * nb * sizeof(float2), &p_part)) != BART_OK)
     return st;
   const float* dc = (const float*)p_const;
   const double rs = c->r_star_tp_cm, a = c->a_orbit_cm;
   const float tirr0 = (rs > 0 && a > 0) ? (float)(std::sqrt(rs / (2.0 * a)) * c->t_star_K) : 0.0f;
   const float tint4 = (float)std::pow(c->t_int_K, 4.0);
-  tp_kernel<<<n, 128, 0, ctx->stream>>>(b->theta, 5 + S, b->t_profile, n, L, S, dc, dc + off_t, M,
+  tp_kernel<<<n, 128, 0, ctx->stream>>>(b->theta, 5 + S, b->t_profile, n, L, S, dc, dc + off_t, M, N,
                                         (float)(1.0 / c->g_cgs), tint4, tirr0, (float)c->t_min_K,
                                         (float)std::min(c->t_max_K, 1e30), dc + off_x0, (LayerTW*)p_tw,
-                                        (float*)p_coef, ctx->d_status);
+                                        (float*)p_coef, b->active, ctx->d_status);
   if ((st = bart_check_launch(ctx, "tp_kernel")) != BART_OK) return st;
-  dim3 grid_dim((unsigned)n, (unsigned)n_tiles);
-  launch(grid_dim, ctx->stream, g->grid, L, M, N, (const LayerTW*)p_tw, (const float*)p_coef, dc + off_dpg,
-         dc + off_ang, g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
-         nb ? f->weights : nullptr, nb, (float2*)p_part, n_tiles, b->active, ctx->d_status);
+  auto run = [&](int tw) {
+    const int n_tiles = (int)((N + tw - 1) / tw);
+    pick_emission(S, c->n_angles, tw)(dim3((unsigned)n, (unsigned)n_tiles), ctx->stream, g->grid, L, M, N,
+                                      (const LayerTW*)p_tw, (const float*)p_coef, dc + off_dpg, dc + off_ang,
+                                      g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
+                                      nb ? f->weights : nullptr, nb, (float2*)p_part, n_tiles, b->active,
+                                      ctx->d_status);
+    return n_tiles;
+  };
+  // Tile width: cached per shape; measured once (each candidate timed with
+  // CUDA events on the stream) unless the stream is being captured.
+  char key[160];
+  snprintf(key, sizeof(key), "em S%d A%d L%d M%d N%lld n%d b%d span%d", S, NA, L, M, (long long)N, n, nb,
+           b->nu_lo ? 1 : 0);
+  int tw = EM_THREADS;
+  auto it = ctx->tiles.find(key);
+  if (it != ctx->tiles.end()) {
+    tw = it->second;
+  } else if (ctx->autotune) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BART_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      cudaEvent_t e0, e1;
+      BART_CUDA(ctx, cudaEventCreate(&e0));
+      BART_CUDA(ctx, cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int cand : TILE_CHOICES) {
+        BART_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        run(cand);
+        BART_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+        BART_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BART_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if ((st = bart_check_launch(ctx, "emission_kernel (autotune)")) != BART_OK) return st;
+        if (ms < best) {
+          best = ms;
+          tw = cand;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      ctx->tiles[key] = tw;
+    }
+  }
+  const int n_tiles = run(tw);
   if ((st = bart_check_launch(ctx, "emission_kernel")) != BART_OK) return st;
   if (nb > 0) {
     int64_t tot = (int64_t)n * nb;
@@ -549,9 +608,10 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
   const double rs = c->r_star_tp_cm, ao = c->a_orbit_cm;
   const float tirr0 = (rs > 0 && ao > 0) ? (float)(std::sqrt(rs / (2.0 * ao)) * c->t_star_K) : 0.0f;
   const float tint4 = (float)std::pow(c->t_int_K, 4.0);
-  tp_kernel<<<n, 128, 0, st>>>(b->theta, 5 + S, b->t_profile, n, L, S, a.cst, a.cst + off_t, M,
+  tp_kernel<<<n, 128, 0, st>>>(b->theta, 5 + S, b->t_profile, n, L, S, a.cst, a.cst + off_t, M, N,
                                (float)(1.0 / c->g_cgs), tint4, tirr0, (float)c->t_min_K,
-                               (float)std::min(c->t_max_K, 1e30), a.cst + off_x0, a.tw, a.coef, a.status);
+                               (float)std::min(c->t_max_K, 1e30), a.cst + off_x0, a.tw, a.coef, b->active,
+                               a.status);
   const int n_tiles = (int)((N + EM_THREADS - 1) / EM_THREADS);
   launch(dim3((unsigned)n, (unsigned)n_tiles), st, g->grid, L, M, N, a.tw, a.coef, a.cst + off_dpg,
          a.cst + off_ang, g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,

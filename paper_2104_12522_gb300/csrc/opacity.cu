@@ -19,32 +19,51 @@
 //    six FP32 instructions and one MUFU reciprocal per line-point.  A warp
 //    whose 256 points all lie inside the line's cutoff window and outside its
 //    core runs without any per-point test; otherwise a predicate masks points.
-//  * Core points (|z| < 24, a per-line integer window shared by both phases)
-//    are evaluated afterwards by the accurate branch, one line per thread,
-//    and added into a shared-memory accumulator with atomics.
+//  * Blocks of 8 points holding a window edge or a line's core (|z| < 24) are
+//    evaluated point by point in a fixup pass (lanes = points, accurate branch
+//    inside the core) into a warp-private accumulator: deterministic.
 //  * Partial sums are plain FP32 within a chunk and folded into a TwoSum
 //    (hi, lo) pair per point after every chunk: compensated accumulation.
-//  * All arithmetic runs at a 2^64 scale so far-wing terms of weak lines stay
-//    normal FP32 numbers; the result is scaled back on the store.
+//  * All arithmetic runs at a 2^100 scale so far-wing terms of weak lines stay
+//    normal FP32 numbers (and products of two denominators stay in range);
+//    the result is scaled back on the store.
 #include <cmath>
+#include <cstddef>
 
 #include "bart_internal.cuh"
 #include "faddeeva.cuh"
 
 namespace {
 
-constexpr int OP_THREADS = 256;
-constexpr int OP_R = 8;                          // points per thread
-constexpr int OP_TILE = OP_THREADS * OP_R;       // points per CTA
-constexpr int OP_CHUNK = OP_THREADS;             // lines per staged chunk
+constexpr int OP_WARPS = 8;                      // independent warps per CTA
+constexpr int OP_THREADS = 32 * OP_WARPS;
+constexpr int OP_R = 8;                          // points per lane
+constexpr int OP_SPAN = 32 * OP_R;               // points per warp
+constexpr int OP_TILE = OP_WARPS * OP_SPAN;      // points per CTA
 constexpr float CORE_S = 576.0f;                 // |z|^2 of the core boundary
-constexpr float LN_2POW64 = 44.361419555836500f; // ln(2^64)
-constexpr float INV_2POW64 = 5.421010862427522e-20f;
-constexpr float LN10F = 2.302585092994046f;
+constexpr float LN_SCALE = 69.314718055994531f;   // ln(2^100): internal scale of all terms
+constexpr float INV_SCALE = 7.888609052210118e-31f; // 2^-100
+constexpr float LOG2EF = 1.4426950408889634f;
+constexpr float LN2F_ = 0.6931471805599453f;
+
+__device__ __forceinline__ float ex2f_approx(float a) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ float lg2f_approx(float a) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 
 struct LineWin {            // per line, from the FP64 prologue
   int jlo, jhi, jc;
   float delta;              // nu_jc - nu0 (cm^-1)
+  float ln_s0;              // ln S_ref + c2 E''/T_ref - ln(1 - exp(-c2 nu0/T_ref)): the T-free part of ln S(T)
+  float c2e;                // c2 E''
+  float c2nu;               // c2 nu0
+  float nu0f;               // nu0 in FP32
 };
 
 struct CellConst {
@@ -60,7 +79,8 @@ __device__ __forceinline__ double nu_minus(double nu_start, double dnu, int64_t 
   return __dadd_rn(__dadd_rn(nu_start, __dmul_rn((double)j, dnu)), -nu0);
 }
 
-__global__ void line_window_kernel(const double* __restrict__ nu0, int64_t n_lines, double nu_start,
+__global__ void line_window_kernel(const double* __restrict__ nu0, const float* __restrict__ log_s,
+                                   const float* __restrict__ elow, int64_t n_lines, double nu_start,
                                    double dnu, int64_t n_nu, double cutoff, int* __restrict__ jlo,
                                    int* __restrict__ jhi, LineWin* __restrict__ win) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -91,6 +111,11 @@ __global__ void line_window_kernel(const double* __restrict__ nu0, int64_t n_lin
   w.jhi = (int)b;
   w.jc = (int)jc;
   w.delta = (float)nu_minus(nu_start, dnu, jc, c);
+  const double c2e = bartc::C2 * (double)elow[i], c2nu = bartc::C2 * c;
+  w.ln_s0 = (float)((double)log_s[i] * 2.302585092994046 + c2e / bartc::TREF - log(-expm1(-c2nu / bartc::TREF)));
+  w.c2e = (float)c2e;
+  w.c2nu = (float)c2nu;
+  w.nu0f = (float)c;
   win[i] = w;
 }
 
@@ -103,150 +128,209 @@ __device__ int64_t lower_bound_i(const int* __restrict__ key, int64_t lo, int64_
   return lo;
 }
 
-struct ChunkSmem {
-  float dx[OP_CHUNK], xc[OP_CHUNK], A[OP_CHUNK], qm[OP_CHUNK], q2[OP_CHUNK];
-  float y[OP_CHUNK], B[OP_CHUNK];
-  int jc[OP_CHUNK], jlo[OP_CHUNK], jhi[OP_CHUNK], klo[OP_CHUNK], khi[OP_CHUNK];
+// Line ranges of one warp span [w0, w0 + OP_SPAN - 1] (independent of the
+// cell): lines meeting the span, and the sub-range whose cutoff windows cover
+// the whole span (no per-point cutoff test needed there).
+struct SpanRange {
+  int64_t i_lo, i_hi;     // lines with jhi >= w0 and jlo <= w1: [i_lo, i_hi)
+  int64_t f_lo, f_hi;     // lines with jlo <= w0 and jhi >= w1: [f_lo, f_hi)
 };
 
-__global__ void __launch_bounds__(OP_THREADS)
-opacity_kernel(const double* __restrict__ nu0, const float* __restrict__ log_s,
-               const float* __restrict__ elow, const float* __restrict__ gref,
-               const int* __restrict__ jlo_a, const int* __restrict__ jhi_a,
-               const LineWin* __restrict__ win, int64_t n_lines,
-               const CellConst* __restrict__ cells, double dnu, int64_t n_nu,
-               float* __restrict__ out, const float2* __restrict__ wtab) {
-  __shared__ ChunkSmem sm;
-  __shared__ float core_acc[OP_TILE];
-  __shared__ int64_t range[2];
+__global__ void span_range_kernel(const int* __restrict__ jlo, const int* __restrict__ jhi, int64_t n_lines,
+                                  int n_spans, SpanRange* __restrict__ out) {
+  const int sp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sp >= n_spans) return;
+  const int w0 = sp * OP_SPAN, w1 = w0 + OP_SPAN - 1;
+  SpanRange r;
+  r.i_lo = lower_bound_i(jhi, 0, n_lines, w0);
+  r.i_hi = lower_bound_i(jlo, r.i_lo, n_lines, w1 + 1);
+  r.f_lo = lower_bound_i(jhi, r.i_lo, r.i_hi, w1);
+  r.f_hi = lower_bound_i(jlo, r.i_lo, r.i_hi, w0 + 1);
+  out[sp] = r;
+}
 
-  const int tid = threadIdx.x;
-  const int64_t t0 = (int64_t)blockIdx.x * OP_TILE;
-  const int64_t t1 = t0 + OP_TILE - 1;
+// Per-line constants of the current cell, staged per warp.  The far-field loop
+// reads the first six fields (one 16-byte and one 8-byte shared load).
+struct __align__(16) LineC {
+  float dx, xc, A, qm;     // bytes  0-15: x = (j - jc) dx + xc; A = S y / (pi sqrt2 sigma) (scaled); qm = y^2 - 1/2
+  float q2, jcf, y, B;     // bytes 16-31: 2 y^2; jc as float (exact below 2^24); y; B = S / (sigma sqrt(2 pi))
+  int e0, e1, jlo, jhi;    // bytes 32-47: 8-point blocks [e0, e1] left to the fixup pass; cutoff window
+  int jc, klo, khi, pad;   // bytes 48-63: centre index; integer superset of the core |z| < 24
+};
+static_assert(offsetof(LineC, q2) == 16 && offsetof(LineC, e0) == 32, "vector loads need these offsets");
+
+// Each lane owns one 8-point block of the warp's 256-point span.  For a line,
+// a block goes through the branch-free far-field loop if it lies entirely in
+// the cutoff window and outside the line's core window; the remaining blocks
+// with points in the window (the block holding a window edge, the blocks the
+// core touches, and any blocks between them) form one interval [e0, e1] that
+// the fixup pass evaluates point by point: the one-pole form where
+// u = x^2 + y^2 - 1/2 >= 575.5, the accurate branch below.  Each (line, point)
+// is therefore counted once.
+constexpr float U_CORE = CORE_S - 0.5f;
+
+__global__ void __launch_bounds__(OP_THREADS, 3)
+opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
+               const SpanRange* __restrict__ spans, const CellConst* __restrict__ cells, double dnu,
+               int64_t n_nu, float* __restrict__ out, const float2* __restrict__ wtab) {
+  __shared__ LineC s_line[OP_WARPS][32];
+  __shared__ float s_core[OP_WARPS][OP_SPAN];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w0l = ((int64_t)blockIdx.x * OP_WARPS + warp) * OP_SPAN;
+  if (w0l >= n_nu) return;                  // warps are independent: no CTA barrier below
+  const int w0 = (int)w0l, w1 = w0 + OP_SPAN - 1;
+  const int j0 = w0 + lane * OP_R;          // first point of this lane
+  const float j0f = (float)j0;
   const int cell = blockIdx.y;
   const CellConst cc = cells[cell];
+  const SpanRange rg = spans[blockIdx.x * OP_WARPS + warp];
+  const int last = (int)min((int64_t)w1, n_nu - 1);
 
-  for (int i = tid; i < OP_TILE; i += OP_THREADS) core_acc[i] = 0.0f;
-  if (tid == 0) {
-    // lines with jhi >= t0 and jlo <= t1
-    range[0] = lower_bound_i(jhi_a, 0, n_lines, (int)t0);
-    range[1] = lower_bound_i(jlo_a, range[0], n_lines, (int)(t1 + 1));
-  }
-  __syncthreads();
-  const int64_t i_begin = range[0], i_end = range[1];
-
-  const int j0 = (int)(t0 + tid * OP_R);             // first point of this thread
-  const int lane = tid & 31;
-  const int w0 = j0 - lane * OP_R;                    // warp span [w0, w1]
-  const int w1 = w0 + 32 * OP_R - 1;
+  float* fix = s_core[warp];
+#pragma unroll
+  for (int r = 0; r < OP_R; ++r) fix[lane * OP_R + r] = 0.0f;
 
   float acc[OP_R], hi[OP_R], lo[OP_R];
 #pragma unroll
   for (int r = 0; r < OP_R; ++r) { acc[r] = 0.f; hi[r] = 0.f; lo[r] = 0.f; }
 
   const float dnuf = (float)dnu;
-  const float c2 = (float)bartc::C2;
-  const float inv_tref = (float)(1.0 / bartc::TREF);
+  LineC* sl = s_line[warp];
+  int chunks = 0;
 
-  for (int64_t base = i_begin; base < i_end; base += OP_CHUNK) {
-    const int nl = (int)min((int64_t)OP_CHUNK, i_end - base);
-    // ---- stage: cell-dependent constants of one line per thread
-    if (tid < nl) {
-      const int64_t i = base + tid;
+  for (int64_t base = rg.i_lo; base < rg.i_hi; base += 32) {
+    const int nl = (int)min((int64_t)32, rg.i_hi - base);
+    // ---- stage: one line's cell-dependent constants per lane, plus its class
+    bool fast = false, needs_fix = false;
+    if (lane < nl) {
+      const int64_t i = base + lane;
       const LineWin w = win[i];
-      const float nu0f = (float)nu0[i];
-      const float sig2 = nu0f * cc.dfac;                 // sigma sqrt 2
-      const float inv = 1.0f / sig2;
+      const float inv = bartw::rcp_approx(w.nu0f * cc.dfac);   // 1 / (sigma sqrt 2)
       const float y = gref[i] * cc.gfac * inv;
       const float q = y * y;
-      const float stim = expm1f(-c2 * nu0f * cc.inv_t) / expm1f(-c2 * nu0f * inv_tref);
-      const float ln_s = log_s[i] * LN10F + cc.ln_q - c2 * elow[i] * (cc.inv_t - inv_tref) + logf(stim);
-      const float B = expf(ln_s + LN_2POW64) * inv * bartw::INV_SQRTPI;   // S/(sigma sqrt(2 pi)) scaled
-      const float dx = dnuf * inv;
-      const float xc = w.delta * inv;
-      sm.dx[tid] = dx;
-      sm.xc[tid] = xc;
-      sm.A[tid] = B * y * bartw::INV_SQRTPI;
-      sm.qm[tid] = q - 0.5f;
-      sm.q2[tid] = 2.0f * q;
-      sm.y[tid] = y;
-      sm.B[tid] = B;
-      sm.jc[tid] = w.jc;
-      sm.jlo[tid] = w.jlo;
-      sm.jhi[tid] = w.jhi;
-      int klo = 0x7fffffff, khi = -0x7fffffff;   // empty core window
+      // ln S(T) = ln_s0 + 1.5 ln(T_ref/T) - c2 E''/T + ln(1 - exp(-c2 nu0/T))
+      const float stim = 1.0f - ex2f_approx(-w.c2nu * cc.inv_t * LOG2EF);
+      const float ln_s = w.ln_s0 + cc.ln_q - w.c2e * cc.inv_t + LN2F_ * lg2f_approx(stim);
+      const float B = ex2f_approx((ln_s + LN_SCALE) * LOG2EF) * inv * bartw::INV_SQRTPI;
+      LineC c;
+      c.dx = dnuf * inv;
+      c.xc = w.delta * inv;
+      c.A = B * y * bartw::INV_SQRTPI;
+      c.qm = q - 0.5f;
+      c.q2 = 2.0f * q;
+      c.jcf = (float)w.jc;
+      c.y = y;
+      c.B = B;
+      c.jc = w.jc;
+      c.jlo = w.jlo;
+      c.jhi = w.jhi;
+      int klo = 0x7fffffff, khi = -0x7fffffff;            // empty core window
       if (q < CORE_S) {
         const float X = sqrtf(CORE_S - q);
-        const float lo_f = fmaxf(floorf((-X - xc) / dx), -1073741824.0f);
-        const float hi_f = fminf(ceilf((X - xc) / dx), 1073741824.0f);
-        // int64 sums, clamped, so far-off-grid lines cannot overflow
+        const float rdx = bartw::rcp_approx(c.dx);
+        // two extra points on each side: a generous superset of the core
+        const float lo_f = fmaxf(floorf((-X - c.xc) * rdx) - 2.0f, -1073741824.0f);
+        const float hi_f = fminf(ceilf((X - c.xc) * rdx) + 2.0f, 1073741824.0f);
         klo = (int)max((long long)w.jc + (long long)lo_f, -1073741824LL);
         khi = (int)min((long long)w.jc + (long long)hi_f, 1073741824LL);
       }
-      sm.klo[tid] = klo;
-      sm.khi[tid] = khi;
+      c.klo = klo;
+      c.khi = khi;
+      c.pad = 0;
+      // blocks for the fixup pass: window edges inside the span, core blocks
+      const int a = max(c.jlo, w0), b = min(c.jhi, last);
+      int e0 = 32, e1 = -1;
+      if (a <= b) {
+        if (a > w0 && ((a - w0) & (OP_R - 1))) { e0 = min(e0, (a - w0) >> 3); e1 = max(e1, (a - w0) >> 3); }
+        if ((b < w1) && (((b - w0) & (OP_R - 1)) != OP_R - 1)) {
+          e0 = min(e0, (b - w0) >> 3);
+          e1 = max(e1, (b - w0) >> 3);
+        }
+        const int ca = max(klo, a), cb = min(khi, b);
+        if (ca <= cb) { e0 = min(e0, (ca - w0) >> 3); e1 = max(e1, (cb - w0) >> 3); }
+      }
+      c.e0 = e0;
+      c.e1 = e1;
+      sl[lane] = c;
+      needs_fix = e0 <= e1;
+      fast = !needs_fix && (c.jlo <= w0) && (c.jhi >= w1);
     }
-    __syncthreads();
+    const unsigned fast_mask = __ballot_sync(0xffffffffu, fast);
+    const unsigned fix_mask = __ballot_sync(0xffffffffu, needs_fix);
+    __syncwarp();
 
-    // ---- far field: one-pole form, register-blocked over OP_R points
+    // ---- far field: one-pole form over the lane's 8 points
     for (int l = 0; l < nl; ++l) {
-      const float dx = sm.dx[l], A = sm.A[l], qm = sm.qm[l], q2 = sm.q2[l];
-      const int jc = sm.jc[l], jlo = sm.jlo[l], jhi = sm.jhi[l];
-      const int klo = sm.klo[l], khi = sm.khi[l];
-      const float x0 = fmaf((float)(j0 - jc), dx, sm.xc[l]);
-      const bool fast = (jlo <= w0) && (jhi >= w1) && (khi < w0 || klo > w1);
-      if (fast) {
+      const float4 c4 = *reinterpret_cast<const float4*>(&sl[l].dx);
+      const float2 c2 = *reinterpret_cast<const float2*>(&sl[l].q2);
+      const float dx = c4.x, qm = c4.w, q2 = c2.x;
+      const float x0 = fmaf(j0f - c2.y, dx, c4.y);
+      if ((fast_mask >> l) & 1u) {
 #pragma unroll
         for (int r = 0; r < OP_R; ++r) {
           const float x = fmaf((float)r, dx, x0);
           const float u = fmaf(x, x, qm);
-          const float num = fmaf(A, u, A);
+          const float num = fmaf(c4.z, u, c4.z);
           acc[r] = fmaf(num, bartw::rcp_approx(fmaf(u, u, q2)), acc[r]);
         }
       } else {
+        // this lane's block joins the far-field sum only if it is whole in the
+        // window and outside the fixup interval; otherwise its weight is 0
+        const int4 ew = *reinterpret_cast<const int4*>(&sl[l].e0);   // e0, e1, jlo, jhi
+        const bool take = (lane < ew.x || lane > ew.y) && (ew.z <= j0) && (ew.w >= j0 + OP_R - 1);
+        const float A = take ? c4.z : 0.0f;
 #pragma unroll
         for (int r = 0; r < OP_R; ++r) {
-          const int j = j0 + r;
-          const bool in = (j >= jlo) && (j <= jhi) && (j < klo || j > khi);
           const float x = fmaf((float)r, dx, x0);
           const float u = fmaf(x, x, qm);
           const float num = fmaf(A, u, A);
-          const float v = num * bartw::rcp_approx(fmaf(u, u, q2));
-          acc[r] += in ? v : 0.0f;
+          // the clamp keeps 0 * (1/d) finite where a skipped block holds a pole
+          acc[r] = fmaf(num, bartw::rcp_approx(fmaxf(fmaf(u, u, q2), 1e-30f)), acc[r]);
         }
       }
-    }
-    // fold the chunk's partial sums into the compensated pair (TwoSum)
-#pragma unroll
-    for (int r = 0; r < OP_R; ++r) {
-      const float s = hi[r] + acc[r];
-      const float bp = s - hi[r];
-      lo[r] += (hi[r] - (s - bp)) + (acc[r] - bp);
-      hi[r] = s;
-      acc[r] = 0.f;
     }
 
-    // ---- core points of this chunk's lines: accurate branch, one line per thread
-    if (tid < nl) {
-      int a = max(max(sm.klo[tid], sm.jlo[tid]), (int)t0);
-      int b = min(min(sm.khi[tid], sm.jhi[tid]), (int)min(t1, n_nu - 1));
-      if (a <= b) {
-        const float dx = sm.dx[tid], xc = sm.xc[tid], y = sm.y[tid], B = sm.B[tid];
-        const int jc = sm.jc[tid];
-        for (int j = a; j <= b; ++j) {
-          const float x = fmaf((float)(j - jc), dx, xc);
-          atomicAdd(&core_acc[j - t0], B * bartw::core_re(x, y, wtab));
-        }
+    // ---- fixup: the excluded blocks of each line, lanes take consecutive points
+    unsigned m = fix_mask;
+    while (m) {
+      const int l = __ffs(m) - 1;
+      m &= m - 1;
+      const LineC c = sl[l];
+      const int a = max(w0 + c.e0 * OP_R, c.jlo);
+      const int b = min(min(w0 + c.e1 * OP_R + OP_R - 1, c.jhi), last);
+      for (int p = a + lane; p <= b; p += 32) {
+        const float x = fmaf((float)(p - c.jc), c.dx, c.xc);
+        const float u = fmaf(x, x, c.qm);
+        float v;
+        if (u >= U_CORE) v = fmaf(c.A, u, c.A) * bartw::rcp_approx(fmaf(u, u, c.q2));
+        else v = c.B * bartw::core_re(x, c.y, wtab);
+        fix[p - w0] += v;
+      }
+      __syncwarp();          // the next line's lanes may touch the same points
+    }
+    __syncwarp();            // staged constants are reused by the next chunk
+
+    // fold partial sums into the compensated pair every 4 chunks (TwoSum)
+    if (++chunks == 4 || base + 32 >= rg.i_hi) {
+      chunks = 0;
+#pragma unroll
+      for (int r = 0; r < OP_R; ++r) {
+        const float s = hi[r] + acc[r];
+        const float bp = s - hi[r];
+        lo[r] += (hi[r] - (s - bp)) + (acc[r] - bp);
+        hi[r] = s;
+        acc[r] = 0.f;
       }
     }
-    __syncthreads();
   }
+  __syncwarp();
 
   // ---- store
 #pragma unroll
   for (int r = 0; r < OP_R; ++r) {
     const int64_t j = (int64_t)j0 + r;
-    if (j < n_nu) out[(int64_t)cell * n_nu + j] = ((hi[r] + lo[r]) + core_acc[j - t0]) * INV_2POW64;
+    if (j < n_nu) out[(int64_t)cell * n_nu + j] = ((hi[r] + lo[r]) + fix[lane * OP_R + r]) * INV_SCALE;
   }
 }
 
@@ -284,11 +368,14 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
 
   int64_t max_lines = 0;
   for (int s = 0; s < n_species; ++s) max_lines = std::max(max_lines, species[s].n_lines);
-  void *p_jlo, *p_jhi, *p_win, *p_cells;
+  void *p_jlo, *p_jhi, *p_win, *p_cells, *p_spans;
   size_t nl = (size_t)std::max<int64_t>(max_lines, 1);
+  const int64_t n_tiles = (nu.n_nu + OP_TILE - 1) / OP_TILE;
+  const int n_spans = (int)(n_tiles * OP_WARPS);
   if ((st = bart_scratch(ctx, "op_jlo", nl * sizeof(int), &p_jlo)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "op_jhi", nl * sizeof(int), &p_jhi)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "op_win", nl * sizeof(LineWin), &p_win)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "op_spans", (size_t)n_spans * sizeof(SpanRange), &p_spans)) != BART_OK) return st;
 
   std::vector<CellConst> hc((size_t)n_species * n_cells);
   for (int s = 0; s < n_species; ++s)
@@ -305,21 +392,22 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
   if ((st = bart_upload_const(ctx, "op_cells", hc.data(), hc.size() * sizeof(CellConst), &p_cells)) != BART_OK)
     return st;
 
-  const int64_t n_tiles = (nu.n_nu + OP_TILE - 1) / OP_TILE;
   for (int s = 0; s < n_species; ++s) {
     const bart_linelist& L = species[s];
     float* o = out + (int64_t)s * n_cells * nu.n_nu;
     if (L.n_lines > 0) {
       line_window_kernel<<<(unsigned)((L.n_lines + 255) / 256), 256, 0, ctx->stream>>>(
-          L.nu0_cm, L.n_lines, nu.nu_start_cm, nu.dnu_cm, nu.n_nu, cutoff, (int*)p_jlo, (int*)p_jhi,
-          (LineWin*)p_win);
+          L.nu0_cm, L.log10_s296, L.elow_cm, L.n_lines, nu.nu_start_cm, nu.dnu_cm, nu.n_nu, cutoff, (int*)p_jlo,
+          (int*)p_jhi, (LineWin*)p_win);
       if ((st = bart_check_launch(ctx, "line_window_kernel")) != BART_OK) return st;
     }
+    span_range_kernel<<<(n_spans + 127) / 128, 128, 0, ctx->stream>>>((const int*)p_jlo, (const int*)p_jhi,
+                                                                      L.n_lines, n_spans, (SpanRange*)p_spans);
+    if ((st = bart_check_launch(ctx, "span_range_kernel")) != BART_OK) return st;
     dim3 grid((unsigned)n_tiles, (unsigned)n_cells);
     opacity_kernel<<<grid, OP_THREADS, 0, ctx->stream>>>(
-        L.nu0_cm, L.log10_s296, L.elow_cm, L.gamma_ref_cm, (const int*)p_jlo, (const int*)p_jhi,
-        (const LineWin*)p_win, L.n_lines, (const CellConst*)p_cells + (size_t)s * n_cells, nu.dnu_cm,
-        nu.n_nu, o, ctx->d_wtable);
+        (const LineWin*)p_win, L.gamma_ref_cm, (const SpanRange*)p_spans,
+        (const CellConst*)p_cells + (size_t)s * n_cells, nu.dnu_cm, nu.n_nu, o, ctx->d_wtable);
     if ((st = bart_check_launch(ctx, "opacity_kernel")) != BART_OK) return st;
   }
   return BART_OK;

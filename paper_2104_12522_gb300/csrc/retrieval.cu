@@ -120,9 +120,10 @@ extern "C" bart_status bart_retrieval_run(bart_ctx* ctx, bart_demc* s, bart_mlp*
     if ((q = bart_forward_spectra_batch(ctx, grid, cfg, &batch, nullptr, filters, be)) != BART_OK) return q;
     if ((q = bart_loglike_bands(ctx, be, C, nb, data, sigma, pass, ly)) != BART_OK) return q;
     if ((q = bart_demc_accept(s, 0, y, pass, ly, surrogate ? lsy : nullptr, acc)) != BART_OK) return q;
-    stats_kernel<<<(C + 127) / 128, 128, 0, st>>>(C, nb, inbox, pass, acc, surrogate ? bs : nullptr, be,
-                                                  (DevStats*)p_stats);
-    advance_kernel<<<1, 1, 0, st>>>(hs);
+    // ctx->stream, not st: during capture it is the capture stream
+    stats_kernel<<<(C + 127) / 128, 128, 0, ctx->stream>>>(C, nb, inbox, pass, acc, surrogate ? bs : nullptr, be,
+                                                           (DevStats*)p_stats);
+    advance_kernel<<<1, 1, 0, ctx->stream>>>(hs);
     return bart_check_launch(ctx, "retrieval half-step");
   };
   auto generation = [&]() -> bart_status {
@@ -130,7 +131,8 @@ extern "C" bart_status bart_retrieval_run(bart_ctx* ctx, bart_demc* s, bart_mlp*
     if ((q = half_step()) != BART_OK) return q;
     if ((q = half_step()) != BART_OK) return q;
     if (chain) {
-      record_kernel<<<(C * d + 255) / 256, 256, 0, st>>>(bart_demc_states(s), C * d, hs, first_half_step, chain);
+      record_kernel<<<(C * d + 255) / 256, 256, 0, ctx->stream>>>(bart_demc_states(s), C * d, hs, first_half_step,
+                                                                  chain);
       if ((q = bart_check_launch(ctx, "record_kernel")) != BART_OK) return q;
     }
     return BART_OK;
@@ -139,19 +141,36 @@ extern "C" bart_status bart_retrieval_run(bart_ctx* ctx, bart_demc* s, bart_mlp*
   r = generation();           // eager: sizes scratch, uploads constants
   if (r == BART_OK && n_generations > 1) {
     if (use_graph) {
+      // Capture on a private non-blocking stream ordered after the caller's
+      // (the legacy default stream cannot be captured), replay on the caller's.
+      cudaStream_t cap = nullptr;
+      cudaEvent_t ev = nullptr;
+      BART_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventRecord(ev, st) != cudaSuccess || cudaStreamWaitEvent(cap, ev, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (ev) cudaEventDestroy(ev);
+        cudaStreamDestroy(cap);
+        bart_demc_use_counter(s, nullptr);
+        return bart_fail(ctx, BART_ECUDA, "could not order the capture stream");
+      }
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
-      BART_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      bart_status rc = generation();
-      cudaError_t ce = cudaStreamEndCapture(st, &graph);
-      if (rc != BART_OK) {
+      cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      bart_status rc = BART_OK;
+      if (ce == cudaSuccess) {
+        ctx->stream = cap;
+        rc = generation();
+        ctx->stream = st;
+        ce = cudaStreamEndCapture(cap, &graph);   // always ends the capture
+      }
+      cudaEventDestroy(ev);
+      cudaStreamDestroy(cap);
+      if (rc != BART_OK || ce != cudaSuccess) {
+        cudaGetLastError();
         if (graph) cudaGraphDestroy(graph);
         bart_demc_use_counter(s, nullptr);
-        return rc;
-      }
-      if (ce != cudaSuccess) {
-        bart_demc_use_counter(s, nullptr);
-        return bart_fail(ctx, BART_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        return rc != BART_OK ? rc : bart_fail(ctx, BART_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
       }
       ce = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);

@@ -54,9 +54,11 @@ __global__ void trans_prologue(const float* __restrict__ theta, int n_theta, int
                                const float* __restrict__ t_axis, int M, double p_top, double p_bot,
                                double p_ref, double g, double mu_amu, float inv_g_f, float tint4, float tirr0,
                                float t_min, float t_max, const float* __restrict__ x0, TrLevel* __restrict__ lev,
-                               TrInst* __restrict__ inst, int* __restrict__ status) {
+                               TrInst* __restrict__ inst, const int32_t* __restrict__ act_mask,
+                               int* __restrict__ status) {
   const int i = blockIdx.x;
   if (i >= n) return;
+  if (act_mask && !act_mask[i]) return;      // skipped entry
   __shared__ double s_lnp[TR_LMAX], s_T[TR_LMAX], s_phi[TR_LMAX];
   __shared__ int s_bad;
   const int L = n_levels[i];
@@ -421,7 +423,7 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
       b->theta, 5 + S, n, S, b->n_levels, b->r_planet_cm, b->r_star_cm, dc, Lg, dc + Lg, M, c->p_top_bar,
       c->p_bot_bar, c->p_ref_bar, c->g_cgs, c->mu_amu, (float)(1.0 / c->g_cgs), (float)std::pow(c->t_int_K, 4.0),
       tirr0, (float)c->t_min_K, (float)std::min(c->t_max_K, 1e30), dc + Lg + M, (TrLevel*)p_lev,
-      (TrInst*)p_inst, ctx->d_status);
+      (TrInst*)p_inst, b->active, ctx->d_status);
   if ((st = bart_check_launch(ctx, "trans_prologue")) != BART_OK) return st;
   const unsigned long long n_units = (unsigned long long)n_gtiles * (unsigned long long)n;
   int per_sm = 0;

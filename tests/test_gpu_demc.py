@@ -24,7 +24,7 @@ def torch():
     return torch
 
 
-def _run_gpu(ctx, torch, n_gen, screened, seed=6000):
+def _run_gpu(ctx, torch, n_gen, screened, seed=6000, beta=1.0, margin=0.0):
     import paper_2104_12522_gb300 as bart
     mu, cov, lo, hi = target()
     C, d = 16, 9
@@ -35,6 +35,7 @@ def _run_gpu(ctx, torch, n_gen, screened, seed=6000):
         r = y.double() - mu_t
         return -0.5 * torch.einsum("ij,jk,ik->i", r, inv, r)
     s = bart.Demc(ctx, C, lo.astype(np.float32), hi.astype(np.float32), jump_every=10, eps=1e-4, seed=seed)
+    s.set_screen(beta, margin)
     rng = np.random.default_rng(seed)
     x0 = torch.tensor((mu + rng.normal(size=(C, d)) * np.sqrt(np.diag(cov))).astype(np.float32), device="cuda")
     ls0 = 0.7 * L(x0) if screened else None
@@ -60,9 +61,9 @@ def _run_gpu(ctx, torch, n_gen, screened, seed=6000):
     return np.array(hist), n_acc, mu, cov
 
 
-@pytest.mark.parametrize("screened", [False, True])
-def test_gpu_sampler_recovers_gaussian(ctx, torch, screened):
-    hist, n_acc, mu, cov = _run_gpu(ctx, torch, 3000, screened)
+@pytest.mark.parametrize("screened,beta,margin", [(False, 1.0, 0.0), (True, 1.0, 0.0), (True, 0.5, 2.0)])
+def test_gpu_sampler_recovers_gaussian(ctx, torch, screened, beta, margin):
+    hist, n_acc, mu, cov = _run_gpu(ctx, torch, 3000, screened, beta=beta, margin=margin)
     s = hist[500:]
     n, C, d = s.shape
     flat = s.reshape(-1, d)

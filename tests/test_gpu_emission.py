@@ -147,3 +147,27 @@ def test_band_integrate_standalone(ctx, torch):
         ok = ref != 0
         assert np.allclose(got[i][ok], ref[ok], rtol=1e-5)
         assert np.all(got[i][~ok] == 0)
+
+
+def test_autotuned_tiles_give_the_same_spectra(ctx, torch, grid_case):
+    """The tile autotuner times each wavenumber-tile width once per launch
+    shape; spectra do not depend on the width, band values only through the
+    order of their partial sums."""
+    species, p, t, N, dnu, nu, g_dev, g_ora = grid_case
+    theta = torch.tensor(W.proposals(9, generation=21, n_species=2), device="cuda")
+    filt = torch.tensor(W.gaussian_filters(W.nu_axis(1000.0, dnu, N), 3, 1002.0, 1033.0, 2.0, 12.0), device="cuda")
+    cfg = _cfg(4, [W.BASE_VMR] * 2)
+    outs = []
+    for tune in (False, True, True):
+        ctx.set_autotune(tune)
+        spec = torch.empty((9, N), dtype=torch.float32, device="cuda")
+        bands = torch.empty((9, 3), dtype=torch.float32, device="cuda")
+        ctx.forward_spectra_batch(g_dev, p, t, nu, cfg, theta=theta, spectra=spec, filters=filt, bands=bands)
+        ctx.sync()
+        outs.append((spec.cpu().numpy(), bands.cpu().numpy()))
+    rep = ctx.autotune_report()
+    print("autotune choices:", rep)
+    assert any(v in (64, 128, 256) for v in rep.values())
+    for s_, b_ in outs[1:]:
+        assert np.array_equal(s_, outs[0][0])
+        assert np.allclose(b_, outs[0][1], rtol=1e-6)

@@ -26,8 +26,8 @@ def _check(hist, mu, cov, burn):
     return e
 
 
-@pytest.mark.parametrize("screened", [False, True])
-def test_recovers_gaussian(screened):
+@pytest.mark.parametrize("screened,beta,margin", [(False, 1.0, 0.0), (True, 1.0, 0.0), (True, 0.5, 2.0)])
+def test_recovers_gaussian(screened, beta, margin):
     mu, cov, lo, hi = target()
     inv = np.linalg.inv(cov)
     L = lambda v: -0.5 * (v - mu) @ inv @ (v - mu)
@@ -35,7 +35,7 @@ def test_recovers_gaussian(screened):
     Ls = (lambda v: -0.5 * 0.7 * (v - mu) @ inv @ (v - mu)) if screened else None
     rng = np.random.default_rng(6000)
     x0 = mu + rng.normal(size=(16, 9)) * np.sqrt(np.diag(cov))
-    hist, acc = D.run(L, x0, lo, hi, 3000, rng, surrogate=Ls)
+    hist, acc = D.run(L, x0, lo, hi, 3000, rng, surrogate=Ls, beta=beta, margin=margin)
     e = _check(hist, mu, cov, burn=500)
     assert e > 300
 
