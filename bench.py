@@ -441,7 +441,17 @@ def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args):
     ctx.sync()
     out["transmission"] = {"spectra_per_s": 1024 / (ms / 1e3), "ms_per_batch": ms, "instances": 1024,
                            "level_sum": int(inst.n_levels.sum()), "points": int(offs[-1]), "bands": 12}
-    # --- surrogate: trained on forward-model band values by the library's kernels
+    net, out["surrogate"] = train_surrogate(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S,
+                                            args.train_steps)
+    out["retrieval"] = run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net,
+                                     args.generations, args.burn, args.screen_beta, args.screen_margin)
+    return out
+
+
+def train_surrogate(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, n_steps):
+    """MLP (5 + S) -> 256 -> 256 -> 256 -> bands trained by the library's
+    kernels on 200,000 forward-model band vectors; returns (net, report)."""
+
     n_train, n_val = 200_000, 4096
     widths = [5 + S, 256, 256, 256, N_BANDS]
     th_all = torch.tensor(W.proposals(n_train + n_val, generation=100, n_species=S), device=dev)
@@ -459,7 +469,7 @@ def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args):
                     (1.0 / logy.std(0)).astype(np.float32))
     net.set_params(torch.tensor(W.mlp_init(widths), device=dev))
     g = torch.Generator(device=dev).manual_seed(5000)
-    n_steps, B = args.train_steps, 1024
+    B = 1024
     perm = [torch.randint(0, n_train, (B,), device=dev, generator=g) for _ in range(64)]
     xb = [th_all[p].contiguous() for p in perm]
     yb = [y_all[p].contiguous() for p in perm]
@@ -477,11 +487,18 @@ def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args):
     err = np.abs(pred / y_all[n_train:].cpu().numpy() - 1)
     x_inf = th_all[:N_PROPOSALS].contiguous()
     inf_ms = _event_ms(torch, stream, lambda: net.forward(x_inf), reps=20)
-    out["surrogate"] = {"widths": widths, "train_spectra": n_train, "train_steps": n_steps, "batch": B,
+    report = {"widths": widths, "train_spectra": n_train, "train_steps": n_steps, "batch": B,
                         "spectra_gen_ms": gen_ms, "train_ms": train_ms,
                         "band_rel_err_median": float(np.median(err)), "band_rel_err_p99": float(np.percentile(err, 99)),
                         "inference_spectra_per_s": N_PROPOSALS / (inf_ms / 1e3)}
-    # --- retrieval: DE-MC, 16 chains, plain vs surrogate-screened (delayed acceptance)
+    return net, report
+
+
+def run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net, generations, n_burn, beta,
+                  margin):
+    """DE-MC with 16 chains on synthetic band data (S/N = 50): an exact-model
+    burn-in, then plain and surrogate-screened runs from the same state."""
+    lo, hi = W.THETA_LO[:5 + S].astype(np.float32), W.THETA_HI[:5 + S].astype(np.float32)
     rng = np.random.default_rng(6500)
     truth = (lo + rng.uniform(0.3, 0.7, 5 + S) * (hi - lo)).astype(np.float32)
     bt = torch.empty((1, N_BANDS), dtype=torch.float32, device=dev)
@@ -492,37 +509,84 @@ def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args):
     data = torch.tensor((b_true + rng.normal(size=N_BANDS) * sig).astype(np.float32), device=dev)
     sigma = torch.tensor(sig, device=dev)
     res = {}
+    # burn-in with the exact model from a uniform start; both measured runs
+    # continue from the same burnt-in state (the surrogate screen is meant for
+    # the sampling phase, where its errors are small against the posterior width)
+    C = 16
+    x0 = torch.tensor((lo + np.random.default_rng(6000).uniform(size=(C, 5 + S)) * (hi - lo)).astype(
+        np.float32), device=dev)
+    b0 = torch.empty((C, N_BANDS), dtype=torch.float32, device=dev)
+    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=x0, filters=filt, bands=b0)
+    L0 = torch.empty(C, dtype=torch.float64, device=dev)
+    ctx.loglike_bands(b0, data, sigma, L0)
+    burn = bart.Demc(ctx, C, lo, hi, jump_every=10, eps=1e-4, seed=6100)
+    burn.set_state(x0, L0)
+    burn_ms = _event_ms(torch, stream, lambda: ctx.retrieval_run(burn, None, grid, ax.p_bar, ax.t_K, nu, cfg, filt,
+                                                                 data, sigma, n_burn, use_graph=True))
+    xb_, Lb_ = torch.empty_like(x0), torch.empty_like(L0)
+    burn.get_state(xb_, Lb_)
+    res["burn_in"] = {"generations": n_burn, "ms": burn_ms}
     for mode in ("plain", "screened"):
-        s = bart.Demc(ctx, 16, lo, hi, jump_every=10, eps=1e-4, seed=6000)
-        s.set_screen(args.screen_beta, args.screen_margin)
-        x0 = torch.tensor((lo + np.random.default_rng(6000).uniform(size=(16, 5 + S)) * (hi - lo)).astype(
-            np.float32), device=dev)
-        b0 = torch.empty((16, N_BANDS), dtype=torch.float32, device=dev)
-        ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=x0, filters=filt, bands=b0)
-        L0 = torch.empty(16, dtype=torch.float64, device=dev)
-        ctx.loglike_bands(b0, data, sigma, L0)
+        s = bart.Demc(ctx, C, lo, hi, jump_every=10, eps=1e-4, seed=6000)
+        s.set_screen(beta, margin)
         Ls0 = None
         if mode == "screened":
-            Ls0 = torch.empty(16, dtype=torch.float64, device=dev)
-            ctx.loglike_bands(net.forward(x0), data, sigma, Ls0)
-        s.set_state(x0, L0, Ls0)
+            Ls0 = torch.empty(C, dtype=torch.float64, device=dev)
+            ctx.loglike_bands(net.forward(xb_), data, sigma, Ls0)
+        s.set_state(xb_, Lb_, Ls0)
         st = {}
         def run():
             st.update(ctx.retrieval_run(s, net if mode == "screened" else None, grid, ax.p_bar, ax.t_K, nu, cfg,
-                                        filt, data, sigma, args.generations, use_graph=True))
+                                        filt, data, sigma, generations, use_graph=True))
         ms = _event_ms(torch, stream, run)
         ctx.sync()
         st["accepted_samples_per_s"] = st["accepted"] / (ms / 1e3)
         st["proposals_per_s"] = st["proposals"] / (ms / 1e3)
-        st["generations"] = args.generations
+        st["generations"] = generations
         if mode == "screened":
-            st["screen"] = {"beta": args.screen_beta, "margin": args.screen_margin}
+            st["screen"] = {"beta": beta, "margin": margin}
         st["ms"] = ms
         if st["accepted"]:
             st["surrogate_err_mean"] = st["surrogate_err_sum"] / st["accepted"]
         res[mode] = st
-    out["retrieval"] = res
-    return out
+    res["false_rejection"] = screen_false_rejections(ctx, bart, torch, dev, grid, ax, nu, filt, cfg, S, net, lo, hi,
+                                                     xb_, Lb_, data, sigma, beta, margin)
+    return res
+
+
+def screen_false_rejections(ctx, bart, torch, dev, grid, ax, nu, filt, cfg, S, net, lo, hi, x, L, data, sigma,
+                            beta, margin, n_half_steps=400):
+    """Proposals from the burnt-in state, screened by the surrogate and all
+    evaluated by the exact model: the mean exact Metropolis acceptance
+    probability min(1, exp(L_y - L_x)) of the screened-out ones is the
+    false-rejection rate (the state is held fixed; nothing is accepted)."""
+    C = x.shape[0]
+    s = bart.Demc(ctx, C, lo, hi, jump_every=10, eps=1e-4, seed=6200)
+    s.set_screen(beta, margin)
+    ls_x = torch.empty(C, dtype=torch.float64, device=dev)
+    ctx.loglike_bands(net.forward(x), data, sigma, ls_x)
+    s.set_state(x, L, ls_x)
+    y = torch.empty((C, 5 + S), dtype=torch.float32, device=dev)
+    inbox = torch.empty(C, dtype=torch.int32, device=dev)
+    passed = torch.empty(C, dtype=torch.int32, device=dev)
+    ls_y = torch.empty(C, dtype=torch.float64, device=dev)
+    L_y = torch.empty(C, dtype=torch.float64, device=dev)
+    b_y = torch.empty((C, N_BANDS), dtype=torch.float32, device=dev)
+    Lx = L.cpu().numpy()
+    p_rej, p_all = [], []
+    for h in range(n_half_steps):
+        s.propose(h, y, inbox)
+        ctx.loglike_bands(net.forward(y), data, sigma, ls_y, mask=inbox)
+        s.screen(h, inbox, ls_y, passed)
+        ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=y, filters=filt, bands=b_y, active=inbox)
+        ctx.loglike_bands(b_y, data, sigma, L_y, mask=inbox)
+        ib, ps, ly = inbox.cpu().numpy(), passed.cpu().numpy(), L_y.cpu().numpy()
+        pa = np.minimum(1.0, np.exp(np.minimum(ly - Lx, 0.0)))
+        p_all += list(pa[ib == 1])
+        p_rej += list(pa[(ib == 1) & (ps == 0)])
+    return {"half_steps": n_half_steps, "proposals_in_box": len(p_all), "screened_out": len(p_rej),
+            "false_rejection_rate": float(np.mean(p_rej)) if p_rej else 0.0,
+            "exact_acceptance_in_box": float(np.mean(p_all)) if p_all else 0.0}
 
 
 def run_profile_case(args):
@@ -538,6 +602,7 @@ def run_profile_case(args):
     species = W.opacity_grid_species(3)
     dl = [bart.device_lines(s) for s in species]
     ctx = bart.Context(0)
+    ctx.set_autotune(False)          # one emission launch, at the default tile width
     nu = bart.NuGrid(ax.nu_start, ax.dnu, ax.n_nu)
     k3 = ax.p_bar[[0, 50, 99]]
     out = ctx.build_opacity_grid(dl[:1], k3, ax.t_K, nu, ax.cutoff)
@@ -568,10 +633,11 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip the transmission/surrogate/retrieval legs")
-    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--train-steps", type=int, default=12000)
     ap.add_argument("--generations", type=int, default=1000)
+    ap.add_argument("--burn", type=int, default=3000, help="exact-model burn-in generations before the retrieval legs")
     ap.add_argument("--screen-beta", type=float, default=1.0)
-    ap.add_argument("--screen-margin", type=float, default=3.0)
+    ap.add_argument("--screen-margin", type=float, default=1.0)
     ap.add_argument("--case", choices=["bench", "profile"], default="bench",
                     help="profile: small launches of the hot kernels for ncu")
     args = ap.parse_args()

@@ -68,15 +68,17 @@ __device__ __forceinline__ float cf_re(float x, float y, int depth) {
 }
 
 // Taylor expansion about the nearest table node (x >= 0, x^2 + y^2 < 25).
+// UNROLL bounds the coefficient loads in flight (register pressure).
+template <int UNROLL = wtab::NT - 1>
 __device__ __forceinline__ float taylor_re(float x, float y, const float2* __restrict__ tab) {
-  int ix = min((int)(x * (1.0f / wtab::H) + 0.5f), wtab::NX - 1);
-  int iy = min((int)(y * (1.0f / wtab::H) + 0.5f), wtab::NY - 1);
+  int ix = max(min((int)(x * (1.0f / wtab::H) + 0.5f), wtab::NX - 1), 0);
+  int iy = max(min((int)(y * (1.0f / wtab::H) + 0.5f), wtab::NY - 1), 0);
   float a = x - (float)ix * wtab::H;
   float b = y - (float)iy * wtab::H;
   const float2* c = tab + ((size_t)iy * wtab::NX + ix) * wtab::NT;
   float2 t = __ldg(c + wtab::NT - 1);
   float ar = t.x, ai = t.y;
-#pragma unroll
+#pragma unroll UNROLL
   for (int n = wtab::NT - 2; n >= 0; --n) {
     float2 cn = __ldg(c + n);
     float r = fmaf(ar, a, fmaf(-ai, b, cn.x));

@@ -127,13 +127,16 @@ __global__ void tp_kernel(const float* __restrict__ theta, int n_theta, const fl
 // bounds the relative error of B by ~3e-6 for x >= 0.48 (the smallest
 // c2 nu / T of a 1000 cm^-1, 3000 K grid); larger x, where 2^(x log2 e) would
 // lose digits and eventually overflow, takes an FP64 exponential.
+// WIDE_X: instantiated only where c2 nu / T can exceed 20 on this grid (the
+// host bounds it by c2 nu_max / t_min), so the usual kernel has no branch.
+template <bool WIDE_X>
 __device__ __forceinline__ float planck(float c1nu3, float x) {
-  if (x > 20.0f) return (float)((double)c1nu3 / expm1((double)x));
+  if (WIDE_X && x > 20.0f) return (float)((double)c1nu3 / expm1((double)x));
   const float e = bartf::ex2_approx(x * LOG2E);
   return c1nu3 * bartf::rcp_approx(e - 1.0f);
 }
 
-template <int S, int NA, int TW>
+template <int S, int NA, int TW, bool WIDE_X>
 __global__ void __launch_bounds__(TW)
 emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const LayerTW* __restrict__ tw,
                 const float* __restrict__ coef, const float* __restrict__ dpg,
@@ -170,11 +173,15 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
   const float nuf = (float)nu;
   const float c1nu3 = (float)(2.0 * bartc::H * bartc::C * bartc::C * nu * nu * nu);
 
-  float nl2mu[NA], wmu[NA], t[NA], I[NA];
+  // per angle: lt = log2 of the transmittance to the current level (a sum of
+  // positive optical-depth terms times -log2(e)/mu), t = 2^lt, and the
+  // intensity I accumulated over layers with positive terms only
+  float nl2mu[NA], wmu[NA], lt[NA], t[NA], I[NA];
 #pragma unroll
   for (int i = 0; i < NA; ++i) {
     nl2mu[i] = ang[i];
     wmu[i] = ang[NA + i];
+    lt[i] = 0.0f;
     t[i] = 1.0f;
     I[i] = 0.0f;
   }
@@ -197,17 +204,17 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
 
   LayerTW r = twp[0];
   float chi_prev = chi_at(r);
-  float B_prev = planck(c1nu3, nuf * r.c2_t);
+  float B_prev = planck<WIDE_X>(c1nu3, nuf * r.c2_t);
   for (int k = 1; k < L; ++k) {
     r = twp[k];
     const float chi = chi_at(r);
-    const float B = planck(c1nu3, nuf * r.c2_t);
+    const float B = planck<WIDE_X>(c1nu3, nuf * r.c2_t);
     const float dtau = (chi_prev + chi) * s_dpg[k - 1];
     const float Bsum = B_prev + B;
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      const float e = bartf::ex2_approx(dtau * nl2mu[i]);
-      const float te = t[i] * e;
+      lt[i] = fmaf(dtau, nl2mu[i], lt[i]);
+      const float te = bartf::ex2_approx(lt[i]);
       I[i] = fmaf(Bsum, t[i] - te, I[i]);
       t[i] = te;
     }
@@ -306,12 +313,12 @@ __global__ void band_integrate_kernel(const float* __restrict__ spectra, const i
   }
 }
 
-template <int S, int NA, int TW>
+template <int S, int NA, int TW, bool WIDE_X>
 void launch_emission(dim3 g, cudaStream_t st, const float* grid, int L, int M, int64_t N, const LayerTW* tw,
                      const float* coef, const float* dpg, const float* ang, double nu_start, double dnu,
                      const int64_t* lo, const int64_t* hi, const int64_t* offs, float* spectra,
                      const float* filt, int nb, float2* partial, int n_tiles, const int32_t* active, int* status) {
-  emission_kernel<S, NA, TW><<<g, TW, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi, offs,
+  emission_kernel<S, NA, TW, WIDE_X><<<g, TW, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi, offs,
                                                spectra, filt, nb, partial, n_tiles, active, status);
 }
 
@@ -323,34 +330,47 @@ using EmLauncher = void (*)(dim3, cudaStream_t, const float*, int, int, int64_t,
 constexpr int TILE_CHOICES[3] = {64, 128, 256};
 constexpr int MIN_TILE = 64;
 
-template <int S, int NA>
+template <int S, int NA, bool WIDE_X>
 EmLauncher pick_tile(int tw) {
   switch (tw) {
-    case 64: return launch_emission<S, NA, 64>;
-    case 128: return launch_emission<S, NA, 128>;
-    case 256: return launch_emission<S, NA, 256>;
+    case 64: return launch_emission<S, NA, 64, WIDE_X>;
+    case 128: return launch_emission<S, NA, 128, WIDE_X>;
+    case 256: return launch_emission<S, NA, 256, WIDE_X>;
+    default: return nullptr;
+  }
+}
+
+template <int S, bool WIDE_X>
+EmLauncher pick_na(int na, int tw) {
+  switch (na) {
+    case 1: return pick_tile<S, 1, WIDE_X>(tw);
+    case 2: return pick_tile<S, 2, WIDE_X>(tw);
+    case 4: return pick_tile<S, 4, WIDE_X>(tw);
+    case 8: return pick_tile<S, 8, WIDE_X>(tw);
+    case 16: return pick_tile<S, 16, WIDE_X>(tw);
     default: return nullptr;
   }
 }
 
 template <int S>
-EmLauncher pick_na(int na, int tw) {
-  switch (na) {
-    case 1: return pick_tile<S, 1>(tw);
-    case 2: return pick_tile<S, 2>(tw);
-    case 4: return pick_tile<S, 4>(tw);
-    case 8: return pick_tile<S, 8>(tw);
-    case 16: return pick_tile<S, 16>(tw);
-    default: return nullptr;
-  }
+EmLauncher pick_wide(int na, int tw, bool wide) {
+  return wide ? pick_na<S, true>(na, tw) : pick_na<S, false>(na, tw);
 }
 
-EmLauncher pick_emission(int S, int na, int tw = EM_THREADS) {
+// True where x = c2 nu / T can exceed 20 on the grid: T is clamped to
+// [t_min, t_max] by tp_kernel, so x <= c2 nu_max / t_min.
+bool planck_wide(const bart_nugrid& nu, double t_min) {
+  if (!(t_min > 0)) return true;
+  const double nu_max = nu.nu_start_cm + (double)(nu.n_nu - 1) * nu.dnu_cm;
+  return bartc::C2 * nu_max / t_min > 19.9;
+}
+
+EmLauncher pick_emission(int S, int na, int tw = EM_THREADS, bool wide = true) {
   switch (S) {
-    case 1: return pick_na<1>(na, tw);
-    case 2: return pick_na<2>(na, tw);
-    case 3: return pick_na<3>(na, tw);
-    case 4: return pick_na<4>(na, tw);
+    case 1: return pick_wide<1>(na, tw, wide);
+    case 2: return pick_wide<2>(na, tw, wide);
+    case 3: return pick_wide<3>(na, tw, wide);
+    case 4: return pick_wide<4>(na, tw, wide);
     default: return nullptr;
   }
 }
@@ -430,9 +450,10 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
                                         (float)std::min(c->t_max_K, 1e30), dc + off_x0, (LayerTW*)p_tw,
                                         (float*)p_coef, b->active, ctx->d_status);
   if ((st = bart_check_launch(ctx, "tp_kernel")) != BART_OK) return st;
+  const bool wide = planck_wide(g->nu, c->t_min_K);
   auto run = [&](int tw) {
     const int n_tiles = (int)((N + tw - 1) / tw);
-    pick_emission(S, c->n_angles, tw)(dim3((unsigned)n, (unsigned)n_tiles), ctx->stream, g->grid, L, M, N,
+    pick_emission(S, c->n_angles, tw, wide)(dim3((unsigned)n, (unsigned)n_tiles), ctx->stream, g->grid, L, M, N,
                                       (const LayerTW*)p_tw, (const float*)p_coef, dc + off_dpg, dc + off_ang,
                                       g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
                                       nb ? f->weights : nullptr, nb, (float2*)p_part, n_tiles, b->active,
@@ -442,8 +463,8 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
   // Tile width: cached per shape; measured once (each candidate timed with
   // CUDA events on the stream) unless the stream is being captured.
   char key[160];
-  snprintf(key, sizeof(key), "em S%d A%d L%d M%d N%lld n%d b%d span%d", S, NA, L, M, (long long)N, n, nb,
-           b->nu_lo ? 1 : 0);
+  snprintf(key, sizeof(key), "em S%d A%d L%d M%d N%lld n%d b%d span%d w%d", S, NA, L, M, (long long)N, n, nb,
+           b->nu_lo ? 1 : 0, wide ? 1 : 0);
   int tw = EM_THREADS;
   auto it = ctx->tiles.find(key);
   if (it != ctx->tiles.end()) {
@@ -564,7 +585,7 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
     if (!(g->p_bar[k] > 0) || (k > 0 && !(g->p_bar[k] > g->p_bar[k - 1]))) return BART_EINVAL;
   for (int m = 0; m < M; ++m)
     if (!(g->t_K[m] > 0) || (m > 0 && !(g->t_K[m] > g->t_K[m - 1]))) return BART_EINVAL;
-  EmLauncher launch = pick_emission(S, c->n_angles);
+  EmLauncher launch = pick_emission(S, c->n_angles, EM_THREADS, planck_wide(g->nu, c->t_min_K));
   if (!launch) return BART_EUNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return BART_ECUDA;

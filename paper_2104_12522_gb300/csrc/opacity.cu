@@ -3,27 +3,35 @@
 // grid, each line cut off at |nu_j - nu0| <= cutoff and point-sampled at the
 // grid wavenumbers (Sec. 4, text after the list of optimisations).
 //
-// Design (GB300, FP32 pipe bound):
+// Design (GB300, bound by FP32 instruction issue):
 //  * A prologue finds, per line and in FP64, the grid-index window of its
 //    cutoff [jlo, jhi], the nearest grid index jc and the offset
-//    delta = nu_jc - nu0 (all differences taken as (nu_start + j dnu) - nu0).
-//  * The main kernel gives each CTA one (cell, 2048-point tile) of one
-//    species.  Lines whose window meets the tile are staged through shared
-//    memory in chunks of 256; per chunk every thread computes one line's
-//    cell-dependent constants (strength, widths) once.
-//  * Each thread owns 8 consecutive points and keeps their partial sums in
-//    registers.  Line constants are shared-memory broadcasts.  The offset
-//    x = (j - jc) dnu / (sigma sqrt 2) + delta / (sigma sqrt 2) is formed from
-//    exact integer differences, so it stays relatively accurate near the core.
-//  * Points outside a line's core (|z| >= 24) use the one-pole Faddeeva form:
-//    six FP32 instructions and one MUFU reciprocal per line-point.  A warp
-//    whose 256 points all lie inside the line's cutoff window and outside its
-//    core runs without any per-point test; otherwise a predicate masks points.
-//  * Blocks of 8 points holding a window edge or a line's core (|z| < 24) are
-//    evaluated point by point in a fixup pass (lanes = points, accurate branch
-//    inside the core) into a warp-private accumulator: deterministic.
-//  * Partial sums are plain FP32 within a chunk and folded into a TwoSum
-//    (hi, lo) pair per point after every chunk: compensated accumulation.
+//    delta = nu_jc - nu0 (all differences taken as (nu_start + j dnu) - nu0),
+//    and the temperature-free part of ln S.  A second prologue finds, per
+//    512-point warp span, the range of lines whose windows meet it (binary
+//    searches on the monotone windows).
+//  * A CTA holds 8 independent warps, each one (cell, 512-point span).  A warp
+//    walks its own line range 32 lines at a time: each lane computes one
+//    line's cell-dependent constants (strength, widths, core window, lane
+//    mask, class) and stores them, sorted by class, in warp-private shared
+//    memory.  No CTA-wide barrier.
+//  * Each lane owns 16 consecutive points and keeps their partial sums in
+//    registers.  The offset x = (j - jc) dnu / (sigma sqrt 2) + delta /
+//    (sigma sqrt 2) is formed from exact integer differences, so it stays
+//    relatively accurate near the core.
+//  * Far field: where every point of the span has x^2 + y^2 large enough,
+//    the shifted Lorentz form (three FFMA and one MUFU reciprocal per
+//    line-point); elsewhere outside the core the one-pole form (five FFMA and
+//    one reciprocal).  Lines covering the whole span run without any
+//    per-lane weight; the others take a per-lane weight from a lane mask.
+//  * Blocks of 16 points holding a window edge or a line's core (|z| < 24) are
+//    evaluated point by point in a fixup pass; core points are gathered into
+//    two per-warp lists (Taylor table, continued fraction) and evaluated 32
+//    at a time, so lanes do not diverge across the branches.  All fixup sums
+//    go to a warp-private accumulator in a fixed order: deterministic.
+//  * Partial sums are plain FP32 over 4 chunks of 32 lines and folded into a
+//    TwoSum (hi, lo) pair per point kept in shared memory: compensated
+//    accumulation.
 //  * All arithmetic runs at a 2^100 scale so far-wing terms of weak lines stay
 //    normal FP32 numbers (and products of two denominators stay in range);
 //    the result is scaled back on the store.
@@ -37,7 +45,8 @@ namespace {
 
 constexpr int OP_WARPS = 8;                      // independent warps per CTA
 constexpr int OP_THREADS = 32 * OP_WARPS;
-constexpr int OP_R = 8;                          // points per lane
+constexpr int OP_R = 16;                         // points per lane
+constexpr int OP_R_LOG = 4;
 constexpr int OP_SPAN = 32 * OP_R;               // points per warp
 constexpr int OP_TILE = OP_WARPS * OP_SPAN;      // points per CTA
 constexpr float CORE_S = 576.0f;                 // |z|^2 of the core boundary
@@ -149,60 +158,167 @@ __global__ void span_range_kernel(const int* __restrict__ jlo, const int* __rest
   out[sp] = r;
 }
 
-// Per-line constants of the current cell, staged per warp.  The far-field loop
-// reads the first six fields (one 16-byte and one 8-byte shared load).
-struct __align__(16) LineC {
-  float dx, xc, A, qm;     // bytes  0-15: x = (j - jc) dx + xc; A = S y / (pi sqrt2 sigma) (scaled); qm = y^2 - 1/2
-  float q2, jcf, y, B;     // bytes 16-31: 2 y^2; jc as float (exact below 2^24); y; B = S / (sigma sqrt(2 pi))
-  int e0, e1, jlo, jhi;    // bytes 32-47: 8-point blocks [e0, e1] left to the fixup pass; cutoff window
-  int jc, klo, khi, pad;   // bytes 48-63: centre index; integer superset of the core |z| < 24
+// Per-line constants of the current cell, staged per warp in four 16-byte
+// groups (structure of arrays, so the staging stores are conflict free).
+struct __align__(16) LineG0 {   // every far-field loop
+  float dx;                     // dnu / (sigma sqrt 2)
+  float xc;                     // (nu_jc - nu0) / (sigma sqrt 2)
+  float A;                      // B y / sqrt(pi) (scaled)
+  float jcr;                    // jc - w0 (exact below 2^24)
 };
-static_assert(offsetof(LineC, q2) == 16 && offsetof(LineC, e0) == 32, "vector loads need these offsets");
+struct __align__(16) LineG1 {   // far-field denominators and the lane mask
+  float qm;                     // y^2 - 1/2  (one-pole form)
+  float q2;                     // 2 y^2      (one-pole form)
+  float qL;                     // y^2 - 3/2  (shifted Lorentz form)
+  unsigned take;                // lanes whose 16-point block joins the far-field sum
+};
+struct __align__(16) LineG2 {   // fixup range
+  int e0, e1;                   // 16-point blocks [e0, e1] left to the fixup pass
+  int jlo, jhi;                 // cutoff window
+};
+struct __align__(16) LineG3 {   // accurate branch
+  float y;
+  float B;                      // S / (sigma sqrt(2 pi)) (scaled): V = B Re w
+  int pad0, pad1;
+};
 
-// Each lane owns one 8-point block of the warp's 256-point span.  For a line,
-// a block goes through the branch-free far-field loop if it lies entirely in
+// Far-field classes of a (line, span) pair.  "L": every point of the span
+// has x^2 + y^2 large enough for the shifted Lorentz form
+//   Re w = (y/sqrt pi) / (x^2 + y^2 - 3/2)
+// (the asymptotic series w ~ (i/sqrt pi)(1/z + 1/(2 z^3) + ...) to second
+// order: relative error <= (2 y^2 + 3/2) / (x^2 + y^2)^2, required <= EPS_L);
+// "P": the one-pole form.  "F": the window covers the whole span and no block
+// is left to the fixup (no per-lane weight); "M": the lane weight is taken
+// from the line's lane mask.
+constexpr int CLS_LF = 0, CLS_LM = 1, CLS_PF = 2, CLS_PM = 3;
+constexpr float EPS_L = 2e-6f;
+constexpr float U_CORE = CORE_S - 0.5f;   // one-pole form where u = x^2 + y^2 - 1/2 >= U_CORE
+constexpr int CORE_CAP = 384;             // deferred accurate points per warp before a flush
+constexpr int ENT_SHIFT = 9;              // list entry: point in span (9 bits) | line slot << 9
+static_assert(OP_SPAN <= (1 << ENT_SHIFT), "list entries hold a point of the span");
+
+// Warp-private shared memory of the opacity kernel (dynamic: above the 48 KB
+// static limit).  Line constants are structure-of-arrays so the staging
+// stores are conflict free; the compensated pair is [point r][lane].
+struct OpShared {
+  float4 g0[OP_WARPS][32];
+  float4 g1[OP_WARPS][32];
+  int4 g2[OP_WARPS][32];
+  float2 g3[OP_WARPS][32];
+  float fix[OP_WARPS][OP_SPAN];
+  float hi[OP_WARPS][OP_R][32];
+  float lo[OP_WARPS][OP_R][32];
+  unsigned list[OP_WARPS][CORE_CAP];
+};
+
+__device__ __forceinline__ unsigned lane_range_mask(int a, int b) {   // bits a..b, empty if a > b
+  a = max(a, 0);
+  b = min(b, 31);
+  if (a > b) return 0u;
+  const unsigned hi = (b == 31) ? 0xffffffffu : ((1u << (b + 1)) - 1u);
+  return hi & ~((1u << a) - 1u);
+}
+
+// Each lane owns one 16-point block of the warp's 512-point span.  For a line,
+// a block goes through a branch-free far-field loop if it lies entirely in
 // the cutoff window and outside the line's core window; the remaining blocks
 // with points in the window (the block holding a window edge, the blocks the
 // core touches, and any blocks between them) form one interval [e0, e1] that
 // the fixup pass evaluates point by point: the one-pole form where
-// u = x^2 + y^2 - 1/2 >= 575.5, the accurate branch below.  Each (line, point)
-// is therefore counted once.
-constexpr float U_CORE = CORE_S - 0.5f;
-
+// u >= U_CORE at once, the accurate branch (Taylor table for |z| < 5,
+// continued fraction below |z| = 24) deferred into two per-warp lists that are
+// evaluated 32 points at a time.  Each (line, point) is counted once.
 __global__ void __launch_bounds__(OP_THREADS, 3)
 opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
                const SpanRange* __restrict__ spans, const CellConst* __restrict__ cells, double dnu,
                int64_t n_nu, float* __restrict__ out, const float2* __restrict__ wtab) {
-  __shared__ LineC s_line[OP_WARPS][32];
-  __shared__ float s_core[OP_WARPS][OP_SPAN];
+  extern __shared__ __align__(16) unsigned char op_smem[];
+  OpShared& sh = *reinterpret_cast<OpShared*>(op_smem);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w0l = ((int64_t)blockIdx.x * OP_WARPS + warp) * OP_SPAN;
   if (w0l >= n_nu) return;                  // warps are independent: no CTA barrier below
   const int w0 = (int)w0l, w1 = w0 + OP_SPAN - 1;
   const int j0 = w0 + lane * OP_R;          // first point of this lane
-  const float j0f = (float)j0;
+  const float j0r = (float)(lane * OP_R);   // its offset in the span
   const int cell = blockIdx.y;
   const CellConst cc = cells[cell];
   const SpanRange rg = spans[blockIdx.x * OP_WARPS + warp];
   const int last = (int)min((int64_t)w1, n_nu - 1);
+  const unsigned lt_mask = (1u << lane) - 1u;
 
-  float* fix = s_core[warp];
+  float* fix = sh.fix[warp];
+  unsigned* list = sh.list[warp];
+  float4* g0 = sh.g0[warp];
+  float4* g1 = sh.g1[warp];
+  int4* g2 = sh.g2[warp];
+  float2* g3 = sh.g3[warp];
 #pragma unroll
   for (int r = 0; r < OP_R; ++r) fix[lane * OP_R + r] = 0.0f;
 
-  float acc[OP_R], hi[OP_R], lo[OP_R];
+  float (*hi)[32] = sh.hi[warp];
+  float (*lo)[32] = sh.lo[warp];
+  float acc[OP_R];
 #pragma unroll
-  for (int r = 0; r < OP_R; ++r) { acc[r] = 0.f; hi[r] = 0.f; lo[r] = 0.f; }
+  for (int r = 0; r < OP_R; ++r) { acc[r] = 0.f; hi[r][lane] = 0.f; lo[r][lane] = 0.f; }
 
   const float dnuf = (float)dnu;
-  LineC* sl = s_line[warp];
   int chunks = 0;
+  int nT = 0, nC = 0;                       // deferred Taylor / continued-fraction points
+
+  // Evaluates the deferred accurate points and adds them to the fixup
+  // accumulator.  Entries are in (line, point) order; one line never repeats
+  // a point, so a group of 32 is added in rounds of equal line (ascending):
+  // deterministic.
+  auto flush = [&]() {
+    __syncwarp();            // immediate fixup adds are visible to every lane
+    for (int pass = 0; pass < 2; ++pass) {
+      const int n = pass == 0 ? nT : nC;
+      for (int g = 0; g < n; g += 32) {
+        const int k = g + lane;
+        const bool act = k < n;
+        const unsigned e = act ? list[pass == 0 ? k : CORE_CAP - 1 - k] : 0u;
+        const int l = (int)(e >> ENT_SHIFT), p = (int)(e & (OP_SPAN - 1));
+        const float4 c0 = g0[l];
+        const float2 c3 = g3[l];
+        // idle lanes evaluate a harmless point (|z| = 6) and add nothing
+        const float x = act ? fabsf(fmaf((float)p - c0.w, c0.x, c0.y)) : 6.0f;
+        const float y = act ? c3.x : 0.0f;
+        float v;
+        if (pass == 0) {
+          v = bartw::taylor_re<1>(x, y, wtab);
+        } else {
+          v = bartw::cf_re(x, y, 6);
+          // exponentially small Gaussian term the asymptotic fraction misses
+          const float gx = fmaf(y, y, -x * x);
+          const float gt = __expf(gx) * __cosf(2.0f * x * y);
+          v += (y < 1.0f && gx > -87.0f) ? gt : 0.0f;
+        }
+        v *= c3.y;
+        const int lp = __shfl_up_sync(0xffffffffu, l, 1);
+        unsigned seg = __ballot_sync(0xffffffffu, act && (lane == 0 || l != lp));
+        while (seg) {
+          const int s0 = __ffs(seg) - 1;
+          seg &= seg - 1;
+          const int s1 = seg ? __ffs(seg) - 1 : 32;
+          if (act && lane >= s0 && lane < s1) fix[p] += v;
+          __syncwarp();
+        }
+      }
+    }
+    nT = 0;
+    nC = 0;
+  };
 
   for (int64_t base = rg.i_lo; base < rg.i_hi; base += 32) {
     const int nl = (int)min((int64_t)32, rg.i_hi - base);
-    // ---- stage: one line's cell-dependent constants per lane, plus its class
-    bool fast = false, needs_fix = false;
+    // ---- stage: one line's cell-dependent constants per lane, its class,
+    // and its slot (lines sorted by class)
+    int cls = -1;
+    bool needs_fix = false, has_core = false;
+    float4 c0, c1;
+    int4 c2;
+    float2 c3;
     if (lane < nl) {
       const int64_t i = base + lane;
       const LineWin w = win[i];
@@ -213,102 +329,164 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       const float stim = 1.0f - ex2f_approx(-w.c2nu * cc.inv_t * LOG2EF);
       const float ln_s = w.ln_s0 + cc.ln_q - w.c2e * cc.inv_t + LN2F_ * lg2f_approx(stim);
       const float B = ex2f_approx((ln_s + LN_SCALE) * LOG2EF) * inv * bartw::INV_SQRTPI;
-      LineC c;
-      c.dx = dnuf * inv;
-      c.xc = w.delta * inv;
-      c.A = B * y * bartw::INV_SQRTPI;
-      c.qm = q - 0.5f;
-      c.q2 = 2.0f * q;
-      c.jcf = (float)w.jc;
-      c.y = y;
-      c.B = B;
-      c.jc = w.jc;
-      c.jlo = w.jlo;
-      c.jhi = w.jhi;
-      int klo = 0x7fffffff, khi = -0x7fffffff;            // empty core window
+      const float dx = dnuf * inv, xc = w.delta * inv;
+      const int jcr = w.jc - w0;
+      // integer superset of the core |z| < 24 (two extra points on each side)
+      int klo = 0x7fffffff, khi = -0x7fffffff;
       if (q < CORE_S) {
         const float X = sqrtf(CORE_S - q);
-        const float rdx = bartw::rcp_approx(c.dx);
-        // two extra points on each side: a generous superset of the core
-        const float lo_f = fmaxf(floorf((-X - c.xc) * rdx) - 2.0f, -1073741824.0f);
-        const float hi_f = fminf(ceilf((X - c.xc) * rdx) + 2.0f, 1073741824.0f);
+        const float rdx = bartw::rcp_approx(dx);
+        const float lo_f = fmaxf(floorf((-X - xc) * rdx) - 2.0f, -1073741824.0f);
+        const float hi_f = fminf(ceilf((X - xc) * rdx) + 2.0f, 1073741824.0f);
         klo = (int)max((long long)w.jc + (long long)lo_f, -1073741824LL);
         khi = (int)min((long long)w.jc + (long long)hi_f, 1073741824LL);
       }
-      c.klo = klo;
-      c.khi = khi;
-      c.pad = 0;
       // blocks for the fixup pass: window edges inside the span, core blocks
-      const int a = max(c.jlo, w0), b = min(c.jhi, last);
+      const int a = max(w.jlo, w0), b = min(w.jhi, last);
       int e0 = 32, e1 = -1;
       if (a <= b) {
-        if (a > w0 && ((a - w0) & (OP_R - 1))) { e0 = min(e0, (a - w0) >> 3); e1 = max(e1, (a - w0) >> 3); }
+        if (a > w0 && ((a - w0) & (OP_R - 1))) { e0 = min(e0, (a - w0) >> OP_R_LOG); e1 = max(e1, (a - w0) >> OP_R_LOG); }
         if ((b < w1) && (((b - w0) & (OP_R - 1)) != OP_R - 1)) {
-          e0 = min(e0, (b - w0) >> 3);
-          e1 = max(e1, (b - w0) >> 3);
+          e0 = min(e0, (b - w0) >> OP_R_LOG);
+          e1 = max(e1, (b - w0) >> OP_R_LOG);
         }
         const int ca = max(klo, a), cb = min(khi, b);
-        if (ca <= cb) { e0 = min(e0, (ca - w0) >> 3); e1 = max(e1, (cb - w0) >> 3); }
+        if (ca <= cb) { e0 = min(e0, (ca - w0) >> OP_R_LOG); e1 = max(e1, (cb - w0) >> OP_R_LOG); }
       }
-      c.e0 = e0;
-      c.e1 = e1;
-      sl[lane] = c;
       needs_fix = e0 <= e1;
-      fast = !needs_fix && (c.jlo <= w0) && (c.jhi >= w1);
+      has_core = needs_fix && max(klo, a) <= min(khi, b);
+      // lanes whose block lies in the window: jlo <= w0 + 8k and w0 + 8k + 7 <= jhi
+      unsigned take = lane_range_mask((w.jlo - w0 + OP_R - 1) >> OP_R_LOG, (w.jhi - w0 - (OP_R - 1)) >> OP_R_LOG);
+      if (needs_fix) take &= ~lane_range_mask(e0, e1);
+      // smallest x^2 + y^2 over the span decides the shifted Lorentz class
+      const float xa = fmaf((float)(w0 - w.jc), dx, xc), xb = fmaf((float)(w1 - w.jc), dx, xc);
+      const float xm = xa > 0.0f ? xa : (xb < 0.0f ? -xb : 0.0f);
+      const float smin = fmaf(xm, xm, q);
+      const bool lor = smin * smin * (EPS_L * 0.999f) >= fmaf(2.0f, q, 1.5f);
+      const bool full = take == 0xffffffffu;
+      cls = lor ? (full ? CLS_LF : CLS_LM) : (full ? CLS_PF : CLS_PM);
+      c0 = make_float4(dx, xc, B * y * bartw::INV_SQRTPI, (float)jcr);
+      c1 = make_float4(q - 0.5f, 2.0f * q, q - 1.5f, __uint_as_float(take));
+      c2 = make_int4(e0, e1, w.jlo, w.jhi);
+      c3 = make_float2(y, B);
     }
-    const unsigned fast_mask = __ballot_sync(0xffffffffu, fast);
-    const unsigned fix_mask = __ballot_sync(0xffffffffu, needs_fix);
+    const unsigned bLF = __ballot_sync(0xffffffffu, cls == CLS_LF);
+    const unsigned bLM = __ballot_sync(0xffffffffu, cls == CLS_LM);
+    const unsigned bPF = __ballot_sync(0xffffffffu, cls == CLS_PF);
+    const unsigned bPM = __ballot_sync(0xffffffffu, cls == CLS_PM);
+    const int nLF = __popc(bLF), nLM = __popc(bLM), nPF = __popc(bPF), nPM = __popc(bPM);
+    int slot = -1;
+    if (cls == CLS_LF) slot = __popc(bLF & lt_mask);
+    else if (cls == CLS_LM) slot = nLF + __popc(bLM & lt_mask);
+    else if (cls == CLS_PF) slot = nLF + nLM + __popc(bPF & lt_mask);
+    else if (cls == CLS_PM) slot = nLF + nLM + nPF + __popc(bPM & lt_mask);
+    if (slot >= 0) {
+      g0[slot] = c0;
+      g1[slot] = c1;
+      g2[slot] = c2;
+      g3[slot] = c3;
+    }
+    const unsigned fix_slots = __reduce_or_sync(0xffffffffu, (slot >= 0 && needs_fix) ? (1u << slot) : 0u);
+    const unsigned core_slots = __reduce_or_sync(0xffffffffu, (slot >= 0 && has_core) ? (1u << slot) : 0u);
     __syncwarp();
 
-    // ---- far field: one-pole form over the lane's 8 points
-    for (int l = 0; l < nl; ++l) {
-      const float4 c4 = *reinterpret_cast<const float4*>(&sl[l].dx);
-      const float2 c2 = *reinterpret_cast<const float2*>(&sl[l].q2);
-      const float dx = c4.x, qm = c4.w, q2 = c2.x;
-      const float x0 = fmaf(j0f - c2.y, dx, c4.y);
-      if ((fast_mask >> l) & 1u) {
+    // ---- far field
+    int l = 0;
+#pragma unroll 2
+    for (; l < nLF; ++l) {                  // shifted Lorentz, whole span
+      const float4 a = g0[l];
+      const float qL = g1[l].z;
+      const float x0 = fmaf(j0r - a.w, a.x, a.y);
 #pragma unroll
-        for (int r = 0; r < OP_R; ++r) {
-          const float x = fmaf((float)r, dx, x0);
-          const float u = fmaf(x, x, qm);
-          const float num = fmaf(c4.z, u, c4.z);
-          acc[r] = fmaf(num, bartw::rcp_approx(fmaf(u, u, q2)), acc[r]);
-        }
-      } else {
-        // this lane's block joins the far-field sum only if it is whole in the
-        // window and outside the fixup interval; otherwise its weight is 0
-        const int4 ew = *reinterpret_cast<const int4*>(&sl[l].e0);   // e0, e1, jlo, jhi
-        const bool take = (lane < ew.x || lane > ew.y) && (ew.z <= j0) && (ew.w >= j0 + OP_R - 1);
-        const float A = take ? c4.z : 0.0f;
+      for (int r = 0; r < OP_R; ++r) {
+        const float x = fmaf((float)r, a.x, x0);
+        acc[r] = fmaf(a.z, bartw::rcp_approx(fmaf(x, x, qL)), acc[r]);
+      }
+    }
+    const int eLM = nLF + nLM;
+#pragma unroll 2
+    for (; l < eLM; ++l) {                  // shifted Lorentz, lane weight
+      const float4 a = g0[l];
+      const float4 b = g1[l];
+      const float A = ((__float_as_uint(b.w) >> lane) & 1u) ? a.z : 0.0f;
+      const float x0 = fmaf(j0r - a.w, a.x, a.y);
 #pragma unroll
-        for (int r = 0; r < OP_R; ++r) {
-          const float x = fmaf((float)r, dx, x0);
-          const float u = fmaf(x, x, qm);
-          const float num = fmaf(A, u, A);
-          // the clamp keeps 0 * (1/d) finite where a skipped block holds a pole
-          acc[r] = fmaf(num, bartw::rcp_approx(fmaxf(fmaf(u, u, q2), 1e-30f)), acc[r]);
-        }
+      for (int r = 0; r < OP_R; ++r) {
+        const float x = fmaf((float)r, a.x, x0);
+        acc[r] = fmaf(A, bartw::rcp_approx(fmaf(x, x, b.z)), acc[r]);
+      }
+    }
+    const int ePF = eLM + nPF;
+#pragma unroll 2
+    for (; l < ePF; ++l) {                  // one-pole, whole span
+      const float4 a = g0[l];
+      const float4 b = g1[l];
+      const float x0 = fmaf(j0r - a.w, a.x, a.y);
+#pragma unroll
+      for (int r = 0; r < OP_R; ++r) {
+        const float x = fmaf((float)r, a.x, x0);
+        const float u = fmaf(x, x, b.x);
+        const float num = fmaf(a.z, u, a.z);
+        acc[r] = fmaf(num, bartw::rcp_approx(fmaf(u, u, b.y)), acc[r]);
+      }
+    }
+    const int ePM = ePF + nPM;
+    for (; l < ePM; ++l) {                  // one-pole, lane weight
+      const float4 a = g0[l];
+      const float4 b = g1[l];
+      const float A = ((__float_as_uint(b.w) >> lane) & 1u) ? a.z : 0.0f;
+      const float x0 = fmaf(j0r - a.w, a.x, a.y);
+#pragma unroll
+      for (int r = 0; r < OP_R; ++r) {
+        const float x = fmaf((float)r, a.x, x0);
+        const float u = fmaf(x, x, b.x);
+        const float num = fmaf(A, u, A);
+        // the clamp keeps 0 * (1/d) finite where a skipped block holds a pole
+        acc[r] = fmaf(num, bartw::rcp_approx(fmaxf(fmaf(u, u, b.y), 1e-30f)), acc[r]);
       }
     }
 
     // ---- fixup: the excluded blocks of each line, lanes take consecutive points
-    unsigned m = fix_mask;
+    unsigned m = fix_slots;
     while (m) {
-      const int l = __ffs(m) - 1;
+      const int fl = __ffs(m) - 1;
       m &= m - 1;
-      const LineC c = sl[l];
-      const int a = max(w0 + c.e0 * OP_R, c.jlo);
-      const int b = min(min(w0 + c.e1 * OP_R + OP_R - 1, c.jhi), last);
-      for (int p = a + lane; p <= b; p += 32) {
-        const float x = fmaf((float)(p - c.jc), c.dx, c.xc);
-        const float u = fmaf(x, x, c.qm);
-        float v;
-        if (u >= U_CORE) v = fmaf(c.A, u, c.A) * bartw::rcp_approx(fmaf(u, u, c.q2));
-        else v = c.B * bartw::core_re(x, c.y, wtab);
-        fix[p - w0] += v;
+      const float4 a = g0[fl];
+      const float4 b = g1[fl];
+      const int4 e = g2[fl];
+      const int pa = max(w0 + e.x * OP_R, e.z);
+      const int pb = min(min(w0 + e.y * OP_R + OP_R - 1, e.w), last);
+      if (!((core_slots >> fl) & 1u)) {
+        // window edges only: every point is outside the core (one-pole form)
+        for (int p = pa + lane; p <= pb; p += 32) {
+          const float x = fmaf((float)(p - w0) - a.w, a.x, a.y);
+          const float u = fmaf(x, x, b.x);
+          fix[p - w0] += fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
+        }
+        __syncwarp();
+        continue;
+      }
+      for (int p0 = pa; p0 <= pb; p0 += 32) {
+        if (nT + nC + 32 > CORE_CAP) flush();
+        const int p = p0 + lane;
+        const bool act = p <= pb;
+        const float x = fmaf((float)(p - w0) - a.w, a.x, a.y);
+        const float u = fmaf(x, x, b.x);
+        const bool far = act && u >= U_CORE;
+        if (far) fix[p - w0] += fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
+        const bool tay = act && u < 24.5f;                 // |z| < 5
+        const bool cfr = act && !far && !tay;
+        const unsigned bt = __ballot_sync(0xffffffffu, tay);
+        const unsigned bc = __ballot_sync(0xffffffffu, cfr);
+        const unsigned ent = (unsigned)(p - w0) | ((unsigned)fl << ENT_SHIFT);
+        if (tay) list[nT + __popc(bt & lt_mask)] = ent;
+        if (cfr) list[CORE_CAP - 1 - (nC + __popc(bc & lt_mask))] = ent;
+        nT += __popc(bt);
+        nC += __popc(bc);
       }
       __syncwarp();          // the next line's lanes may touch the same points
     }
+    if (nT + nC) flush();
     __syncwarp();            // staged constants are reused by the next chunk
 
     // fold partial sums into the compensated pair every 4 chunks (TwoSum)
@@ -316,10 +494,11 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       chunks = 0;
 #pragma unroll
       for (int r = 0; r < OP_R; ++r) {
-        const float s = hi[r] + acc[r];
-        const float bp = s - hi[r];
-        lo[r] += (hi[r] - (s - bp)) + (acc[r] - bp);
-        hi[r] = s;
+        const float h = hi[r][lane];
+        const float s = h + acc[r];
+        const float bp = s - h;
+        lo[r][lane] += (h - (s - bp)) + (acc[r] - bp);
+        hi[r][lane] = s;
         acc[r] = 0.f;
       }
     }
@@ -330,7 +509,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
 #pragma unroll
   for (int r = 0; r < OP_R; ++r) {
     const int64_t j = (int64_t)j0 + r;
-    if (j < n_nu) out[(int64_t)cell * n_nu + j] = ((hi[r] + lo[r]) + fix[lane * OP_R + r]) * INV_SCALE;
+    if (j < n_nu) out[(int64_t)cell * n_nu + j] = ((hi[r][lane] + lo[r][lane]) + fix[lane * OP_R + r]) * INV_SCALE;
   }
 }
 
@@ -391,6 +570,8 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
     }
   if ((st = bart_upload_const(ctx, "op_cells", hc.data(), hc.size() * sizeof(CellConst), &p_cells)) != BART_OK)
     return st;
+  BART_CUDA(ctx, cudaFuncSetAttribute(opacity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(OpShared)));
 
   for (int s = 0; s < n_species; ++s) {
     const bart_linelist& L = species[s];
@@ -405,7 +586,7 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
                                                                       L.n_lines, n_spans, (SpanRange*)p_spans);
     if ((st = bart_check_launch(ctx, "span_range_kernel")) != BART_OK) return st;
     dim3 grid((unsigned)n_tiles, (unsigned)n_cells);
-    opacity_kernel<<<grid, OP_THREADS, 0, ctx->stream>>>(
+    opacity_kernel<<<grid, OP_THREADS, sizeof(OpShared), ctx->stream>>>(
         (const LineWin*)p_win, L.gamma_ref_cm, (const SpanRange*)p_spans,
         (const CellConst*)p_cells + (size_t)s * n_cells, nu.dnu_cm, nu.n_nu, o, ctx->d_wtable);
     if ((st = bart_check_launch(ctx, "opacity_kernel")) != BART_OK) return st;

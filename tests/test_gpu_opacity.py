@@ -87,6 +87,27 @@ def test_opacity_cores_ragged_tail_and_edges(ctx, torch):
     assert np.all(got[ref == 0.0] == 0.0)
 
 
+def test_opacity_wide_cores(ctx, torch):
+    # A grid much finer than the Doppler width of a light, hot absorber: every
+    # line's core (|z| < 24) covers several 256-point spans, so one chunk of 32
+    # lines defers thousands of accurate points (several list flushes per
+    # chunk).  Pressures from the Doppler regime to y ~ 50.
+    import paper_2104_12522_gb300 as bart
+    rng = np.random.default_rng(12)
+    n_nu, dnu, start, cut = 3000, 0.0005, 2000.0, 1.0
+    nu0 = np.sort(rng.uniform(start + 0.2, start + n_nu * dnu - 0.2, 40))
+    ll = W.LineList(nu0, rng.uniform(-22, -20, nu0.size).astype(np.float32),
+                    rng.uniform(0, 2000, nu0.size).astype(np.float32),
+                    rng.uniform(0.05, 0.1, nu0.size).astype(np.float32), 2.0)
+    p = np.array([1e-6, 0.05, 3.0])
+    t = np.array([2500.0, 1800.0, 2900.0])
+    ref = O.opacity_cells([ll], p, t, start, dnu, n_nu, cut)
+    got = ctx.opacity_cells([bart.device_lines(ll)], p, t, bart.NuGrid(start, dnu, n_nu), cut).cpu().numpy()
+    rel, l2 = opacity_errors(got, ref)
+    print(f"opacity wide cores: max rel {rel:.2e}, row L2 {l2:.2e}")
+    assert rel < RTOL_OPACITY and l2 < RTOL_ROW_L2
+
+
 def test_single_line_and_empty_list(ctx, torch):
     import paper_2104_12522_gb300 as bart
     one = W.LineList(np.array([1000.37]), np.array([-20.0], np.float32), np.array([500.0], np.float32),
