@@ -590,10 +590,10 @@ def screen_false_rejections(ctx, bart, torch, dev, grid, ax, nu, filt, cfg, S, n
 
 
 def run_profile_case(args):
-    """Small launches of the two hot kernels for ncu captures: one opacity
-    launch (species 0, 5e6-line list, 3 layers x 20 temperatures on the full
-    100,000-point grid) and one emission generation (2,048 proposals) on a
-    4,096-point slice of the grid."""
+    """Small launches of the hot kernels for ncu captures: one opacity launch
+    (species 0, 5e6-line list, 3 layers x 20 temperatures on the full
+    100,000-point grid), one emission generation (2,048 proposals) and one
+    transmission batch (256 instances) on a 4,096-point slice of the grid."""
     import torch
     from paper_2104_12522_gb300 import build
     build.build()
@@ -617,8 +617,18 @@ def run_profile_case(args):
                x0=[W.BASE_VMR] * 3, t_int=W.T_INT_K, t_star=W.HD189_TSTAR_K, r_star_tp=W.HD189_RSTAR_CM,
                a_orbit=W.HD189_A_CM, t_min=float(ax.t_K[0]), t_max=float(ax.t_K[-1]))
     ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu_s, cfg, theta=theta, filters=filt, bands=bands)
+    # one transmission batch: 256 uneven instances (40..150 levels, 1,000..4,096 points) on the slice
+    inst = W.instances(256, nsub, span_lo=1000, span_hi=nsub)
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    tspec = torch.empty(int(inst.offsets[-1]), dtype=torch.float32, device="cuda")
+    tb = torch.empty((256, N_BANDS), dtype=torch.float32, device="cuda")
+    tcfg = dict(cfg, geometry=1, p_ref=W.HD189_PREF_BAR, p_top=1e-8, p_bot=100.0)
+    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu_s, tcfg, theta=d(inst.theta[:, :8]),
+                              n_levels=d(inst.n_levels), nu_lo=d(inst.nu_lo), nu_hi=d(inst.nu_hi),
+                              spec_offsets=d(inst.offsets), r_planet=d(inst.r_planet), r_star=d(inst.r_star),
+                              spectra=tspec, filters=filt, bands=tb)
     ctx.sync()
-    assert torch.isfinite(out).all() and torch.isfinite(bands).all()
+    assert torch.isfinite(out).all() and torch.isfinite(bands).all() and torch.isfinite(tspec).all()
     print("profile case done")
     return 0
 

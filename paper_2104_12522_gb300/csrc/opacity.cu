@@ -179,21 +179,33 @@ struct __align__(16) LineG2 {   // fixup range
 struct __align__(16) LineG3 {   // accurate branch
   float y;
   float B;                      // S / (sigma sqrt(2 pi)) (scaled): V = B Re w
-  int pad0, pad1;
+  int klo, khi;                 // integer superset of the core |z| < 24
 };
 
-// Far-field classes of a (line, span) pair.  "L": every point of the span
-// has x^2 + y^2 large enough for the shifted Lorentz form
+// Far-field classes of a (line, span) pair.  "L": every far-field point of
+// the span (points too close to the line go to the fixup when there are at
+// most LFIX_MAX of them) has x^2 + y^2 large enough for the shifted Lorentz form
 //   Re w = (y/sqrt pi) / (x^2 + y^2 - 3/2)
 // (the asymptotic series w ~ (i/sqrt pi)(1/z + 1/(2 z^3) + ...) to second
 // order: relative error <= (2 y^2 + 3/2) / (x^2 + y^2)^2, required <= EPS_L);
 // "P": the one-pole form.  "F": the window covers the whole span and no block
 // is left to the fixup (no per-lane weight); "M": the lane weight is taken
 // from the line's lane mask.
-constexpr int CLS_LF = 0, CLS_LM = 1, CLS_PF = 2, CLS_PM = 3;
+constexpr int CLS_FF = 4, CLS_LF = 0, CLS_LM = 1, CLS_PF = 2, CLS_PM = 3;
+// "FF": every point of the span lies at |x| >= FF_RATIO dx from the line (and
+// the shifted Lorentz form holds there): the line's contribution to a lane's
+// 16 points is expanded to degree FF_DEG in the point offset t about the
+// block centre, f(t) = (A/s) sum_n P_n t^n with s = xc^2 + y^2 - 3/2,
+// alpha = 2 xc dx / s, beta = dx^2 / s, P_0 = 1, P_1 = -alpha,
+// P_n = -alpha P_{n-1} - beta P_{n-2}; truncation error <= 2.5e-6 relative for
+// |xc| >= 12 h (h = 7.5 dx, half a block), i.e. |x| >= 11 h on the block.
+// The lane sums the coefficients over lines and expands them once per chunk.
+constexpr int FF_DEG = 5;
+constexpr float FF_RATIO = 11.0f * 0.5f * (OP_R - 1);
 constexpr float EPS_L = 2e-6f;
-constexpr float U_CORE = CORE_S - 0.5f;   // one-pole form where u = x^2 + y^2 - 1/2 >= U_CORE
-constexpr int CORE_CAP = 384;             // deferred accurate points per warp before a flush
+constexpr int LFIX_MAX = 64;              // longest stretch of one-pole points moved to the fixup
+constexpr float FAR_X = 1.0e4f;           // x of lanes with weight 0 in the lane-mask Lorentz loop
+constexpr int CORE_CAP = 320;             // deferred accurate points per warp before a flush
 constexpr int ENT_SHIFT = 9;              // list entry: point in span (9 bits) | line slot << 9
 static_assert(OP_SPAN <= (1 << ENT_SHIFT), "list entries hold a point of the span");
 
@@ -204,7 +216,7 @@ struct OpShared {
   float4 g0[OP_WARPS][32];
   float4 g1[OP_WARPS][32];
   int4 g2[OP_WARPS][32];
-  float2 g3[OP_WARPS][32];
+  float4 g3[OP_WARPS][32];
   float fix[OP_WARPS][OP_SPAN];
   float hi[OP_WARPS][OP_R][32];
   float lo[OP_WARPS][OP_R][32];
@@ -221,13 +233,14 @@ __device__ __forceinline__ unsigned lane_range_mask(int a, int b) {   // bits a.
 
 // Each lane owns one 16-point block of the warp's 512-point span.  For a line,
 // a block goes through a branch-free far-field loop if it lies entirely in
-// the cutoff window and outside the line's core window; the remaining blocks
+// the cutoff window and outside the line's fixup stretch; the remaining blocks
 // with points in the window (the block holding a window edge, the blocks the
-// core touches, and any blocks between them) form one interval [e0, e1] that
-// the fixup pass evaluates point by point: the one-pole form where
-// u >= U_CORE at once, the accurate branch (Taylor table for |z| < 5,
-// continued fraction below |z| = 24) deferred into two per-warp lists that are
-// evaluated 32 points at a time.  Each (line, point) is counted once.
+// stretch touches, and any blocks between them) form one interval [e0, e1]
+// that the fixup pass evaluates point by point, lanes = points: the one-pole
+// form outside the core window [klo, khi], the continued fraction to depth 3
+// for |z| >= 8 inside it, and the rest deferred into two per-warp lists
+// (Taylor table for |z| < 5, continued fraction to depth 6 for 5 <= |z| < 8)
+// that are evaluated 32 points at a time.  Each (line, point) is counted once.
 __global__ void __launch_bounds__(OP_THREADS, 3)
 opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
                const SpanRange* __restrict__ spans, const CellConst* __restrict__ cells, double dnu,
@@ -241,6 +254,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
   const int w0 = (int)w0l, w1 = w0 + OP_SPAN - 1;
   const int j0 = w0 + lane * OP_R;          // first point of this lane
   const float j0r = (float)(lane * OP_R);   // its offset in the span
+  const float tc = j0r + 0.5f * (OP_R - 1);  // offset of its block centre
   const int cell = blockIdx.y;
   const CellConst cc = cells[cell];
   const SpanRange rg = spans[blockIdx.x * OP_WARPS + warp];
@@ -252,7 +266,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
   float4* g0 = sh.g0[warp];
   float4* g1 = sh.g1[warp];
   int4* g2 = sh.g2[warp];
-  float2* g3 = sh.g3[warp];
+  float4* g3 = sh.g3[warp];
 #pragma unroll
   for (int r = 0; r < OP_R; ++r) fix[lane * OP_R + r] = 0.0f;
 
@@ -280,7 +294,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
         const unsigned e = act ? list[pass == 0 ? k : CORE_CAP - 1 - k] : 0u;
         const int l = (int)(e >> ENT_SHIFT), p = (int)(e & (OP_SPAN - 1));
         const float4 c0 = g0[l];
-        const float2 c3 = g3[l];
+        const float4 c3 = g3[l];
         // idle lanes evaluate a harmless point (|z| = 6) and add nothing
         const float x = act ? fabsf(fmaf((float)p - c0.w, c0.x, c0.y)) : 6.0f;
         const float y = act ? c3.x : 0.0f;
@@ -288,11 +302,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
         if (pass == 0) {
           v = bartw::taylor_re<1>(x, y, wtab);
         } else {
-          v = bartw::cf_re(x, y, 6);
-          // exponentially small Gaussian term the asymptotic fraction misses
-          const float gx = fmaf(y, y, -x * x);
-          const float gt = __expf(gx) * __cosf(2.0f * x * y);
-          v += (y < 1.0f && gx > -87.0f) ? gt : 0.0f;
+          v = bartw::cf_gauss_re(x, y, 6);
         }
         v *= c3.y;
         const int lp = __shfl_up_sync(0xffffffffu, l, 1);
@@ -318,7 +328,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
     bool needs_fix = false, has_core = false;
     float4 c0, c1;
     int4 c2;
-    float2 c3;
+    float4 c3;
     if (lane < nl) {
       const int64_t i = base + lane;
       const LineWin w = win[i];
@@ -331,18 +341,33 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       const float B = ex2f_approx((ln_s + LN_SCALE) * LOG2EF) * inv * bartw::INV_SQRTPI;
       const float dx = dnuf * inv, xc = w.delta * inv;
       const int jcr = w.jc - w0;
-      // integer superset of the core |z| < 24 (two extra points on each side)
-      int klo = 0x7fffffff, khi = -0x7fffffff;
-      if (q < CORE_S) {
-        const float X = sqrtf(CORE_S - q);
-        const float rdx = bartw::rcp_approx(dx);
-        const float lo_f = fmaxf(floorf((-X - xc) * rdx) - 2.0f, -1073741824.0f);
-        const float hi_f = fminf(ceilf((X - xc) * rdx) + 2.0f, 1073741824.0f);
-        klo = (int)max((long long)w.jc + (long long)lo_f, -1073741824LL);
-        khi = (int)min((long long)w.jc + (long long)hi_f, 1073741824LL);
-      }
-      // blocks for the fixup pass: window edges inside the span, core blocks
+      // Integer supersets (two extra points on each side) of the points with
+      // x^2 + y^2 < R2 on the grid, for R2 = 576 (the core) and for
+      // R2 = S_L = sqrt((2 y^2 + 3/2) / EPS_L), where the shifted Lorentz form
+      // is not accurate enough (S_L >= 866 > 576: it contains the core).
+      const float rdx = bartw::rcp_approx(dx);
+      auto window = [&](float R2, int& lo, int& hi) {
+        lo = 0x7fffffff;
+        hi = -0x7fffffff;
+        if (q < R2) {
+          const float X = sqrtf(R2 - q);
+          const float lo_f = fmaxf(floorf((-X - xc) * rdx) - 2.0f, -1073741824.0f);
+          const float hi_f = fminf(ceilf((X - xc) * rdx) + 2.0f, 1073741824.0f);
+          lo = (int)max((long long)w.jc + (long long)lo_f, -1073741824LL);
+          hi = (int)min((long long)w.jc + (long long)hi_f, 1073741824LL);
+        }
+      };
       const int a = max(w.jlo, w0), b = min(w.jhi, last);
+      int klo, khi, ilo, ihi;
+      window(CORE_S, klo, khi);
+      has_core = max(klo, a) <= min(khi, b);
+      window(sqrtf(fmaf(2.0f, q, 1.5f) * (1.0f / EPS_L)) * 1.001f, ilo, ihi);
+      // A short stretch of such points in the span joins the fixup (one-pole
+      // form there) and the rest of the span takes the shifted Lorentz form;
+      // a long one makes the whole span one-pole, with only the core fixed up.
+      const bool lor = min(ihi, b) - max(ilo, a) < LFIX_MAX;
+      const int flo = lor ? ilo : klo, fhi = lor ? ihi : khi;
+      // blocks for the fixup pass: window edges inside the span, the stretch above
       int e0 = 32, e1 = -1;
       if (a <= b) {
         if (a > w0 && ((a - w0) & (OP_R - 1))) { e0 = min(e0, (a - w0) >> OP_R_LOG); e1 = max(e1, (a - w0) >> OP_R_LOG); }
@@ -350,36 +375,42 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
           e0 = min(e0, (b - w0) >> OP_R_LOG);
           e1 = max(e1, (b - w0) >> OP_R_LOG);
         }
-        const int ca = max(klo, a), cb = min(khi, b);
+        const int ca = max(flo, a), cb = min(fhi, b);
         if (ca <= cb) { e0 = min(e0, (ca - w0) >> OP_R_LOG); e1 = max(e1, (cb - w0) >> OP_R_LOG); }
       }
       needs_fix = e0 <= e1;
-      has_core = needs_fix && max(klo, a) <= min(khi, b);
-      // lanes whose block lies in the window: jlo <= w0 + 8k and w0 + 8k + 7 <= jhi
+      has_core = has_core && needs_fix;
+      // lanes whose block lies in the window: jlo <= w0 + 16k and w0 + 16k + 15 <= jhi
       unsigned take = lane_range_mask((w.jlo - w0 + OP_R - 1) >> OP_R_LOG, (w.jhi - w0 - (OP_R - 1)) >> OP_R_LOG);
       if (needs_fix) take &= ~lane_range_mask(e0, e1);
-      // smallest x^2 + y^2 over the span decides the shifted Lorentz class
+      const bool full = take == 0xffffffffu;
+      // the whole span far from the line: expansion class (needs the shifted
+      // Lorentz bound at the span's closest point as well)
       const float xa = fmaf((float)(w0 - w.jc), dx, xc), xb = fmaf((float)(w1 - w.jc), dx, xc);
       const float xm = xa > 0.0f ? xa : (xb < 0.0f ? -xb : 0.0f);
       const float smin = fmaf(xm, xm, q);
-      const bool lor = smin * smin * (EPS_L * 0.999f) >= fmaf(2.0f, q, 1.5f);
-      const bool full = take == 0xffffffffu;
-      cls = lor ? (full ? CLS_LF : CLS_LM) : (full ? CLS_PF : CLS_PM);
+      const bool ff = !has_core && xm >= FF_RATIO * dx && smin * smin * (EPS_L * 0.999f) >= fmaf(2.0f, q, 1.5f);
+      cls = ff ? CLS_FF : lor ? (full ? CLS_LF : CLS_LM) : (full ? CLS_PF : CLS_PM);
       c0 = make_float4(dx, xc, B * y * bartw::INV_SQRTPI, (float)jcr);
       c1 = make_float4(q - 0.5f, 2.0f * q, q - 1.5f, __uint_as_float(take));
       c2 = make_int4(e0, e1, w.jlo, w.jhi);
-      c3 = make_float2(y, B);
+      // expansion lines have no core in the span: their slot of the
+      // accurate-branch group holds -2 dx and dx^2 instead
+      c3 = ff ? make_float4(-2.0f * dx, dx * dx, 0.0f, 0.0f)
+              : make_float4(y, B, __int_as_float(klo), __int_as_float(khi));
     }
+    const unsigned bFF = __ballot_sync(0xffffffffu, cls == CLS_FF);
     const unsigned bLF = __ballot_sync(0xffffffffu, cls == CLS_LF);
     const unsigned bLM = __ballot_sync(0xffffffffu, cls == CLS_LM);
     const unsigned bPF = __ballot_sync(0xffffffffu, cls == CLS_PF);
     const unsigned bPM = __ballot_sync(0xffffffffu, cls == CLS_PM);
-    const int nLF = __popc(bLF), nLM = __popc(bLM), nPF = __popc(bPF), nPM = __popc(bPM);
+    const int nFF = __popc(bFF), nLF = __popc(bLF), nLM = __popc(bLM), nPF = __popc(bPF), nPM = __popc(bPM);
     int slot = -1;
-    if (cls == CLS_LF) slot = __popc(bLF & lt_mask);
-    else if (cls == CLS_LM) slot = nLF + __popc(bLM & lt_mask);
-    else if (cls == CLS_PF) slot = nLF + nLM + __popc(bPF & lt_mask);
-    else if (cls == CLS_PM) slot = nLF + nLM + nPF + __popc(bPM & lt_mask);
+    if (cls == CLS_FF) slot = __popc(bFF & lt_mask);
+    else if (cls == CLS_LF) slot = nFF + __popc(bLF & lt_mask);
+    else if (cls == CLS_LM) slot = nFF + nLF + __popc(bLM & lt_mask);
+    else if (cls == CLS_PF) slot = nFF + nLF + nLM + __popc(bPF & lt_mask);
+    else if (cls == CLS_PM) slot = nFF + nLF + nLM + nPF + __popc(bPM & lt_mask);
     if (slot >= 0) {
       g0[slot] = c0;
       g1[slot] = c1;
@@ -390,10 +421,59 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
     const unsigned core_slots = __reduce_or_sync(0xffffffffu, (slot >= 0 && has_core) ? (1u << slot) : 0u);
     __syncwarp();
 
-    // ---- far field
+    // ---- far field.  The shifted Lorentz classes take two lines per
+    // reciprocal, A1/s1 + A2/s2 = (A1 s2 + A2 s1) / (s1 s2): the MUFU pipe
+    // (a quarter of the issue rate) would otherwise bind at one reciprocal
+    // in four instructions.  s >= 866 here, so s1 s2 stays far inside the
+    // FP32 range at the 2^100 scale.
     int l = 0;
-#pragma unroll 2
-    for (; l < nLF; ++l) {                  // shifted Lorentz, whole span
+    if (nFF > 0) {                          // expansion class: coefficient sums
+      float C[FF_DEG + 1];
+#pragma unroll
+      for (int k = 0; k <= FF_DEG; ++k) C[k] = 0.0f;
+      for (; l < nFF; ++l) {
+        const float4 a = g0[l];
+        const float4 b = g1[l];
+        const float4 d = g3[l];             // -2 dx, dx^2
+        const float A = ((__float_as_uint(b.w) >> lane) & 1u) ? a.z : 0.0f;
+        const float xc = fmaf(tc - a.w, a.x, a.y);
+        const float g = bartw::rcp_approx(fmaf(xc, xc, b.z));
+        const float al = xc * g * d.x;      // -alpha
+        const float be = d.y * g;           // beta
+        const float Ag = A * g;
+        float pm1 = 1.0f, pn = al;          // P_0, P_1
+        C[0] += Ag;
+        C[1] = fmaf(Ag, pn, C[1]);
+#pragma unroll
+        for (int k = 2; k <= FF_DEG; ++k) {
+          const float pk = fmaf(al, pn, -be * pm1);
+          pm1 = pn;
+          pn = pk;
+          C[k] = fmaf(Ag, pk, C[k]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < OP_R; ++r) {      // expand at the lane's 16 points
+        const float t = (float)r - 0.5f * (OP_R - 1);
+        float v = C[FF_DEG];
+#pragma unroll
+        for (int k = FF_DEG - 1; k >= 0; --k) v = fmaf(v, t, C[k]);
+        acc[r] += v;
+      }
+    }
+    const int eLF = nFF + nLF;
+    for (; l + 1 < eLF; l += 2) {           // shifted Lorentz, whole span
+      const float4 a = g0[l], a2 = g0[l + 1];
+      const float qL = g1[l].z, qL2 = g1[l + 1].z;
+      const float x0 = fmaf(j0r - a.w, a.x, a.y), x02 = fmaf(j0r - a2.w, a2.x, a2.y);
+#pragma unroll
+      for (int r = 0; r < OP_R; ++r) {
+        const float x = fmaf((float)r, a.x, x0), x2 = fmaf((float)r, a2.x, x02);
+        const float s1 = fmaf(x, x, qL), s2 = fmaf(x2, x2, qL2);
+        acc[r] = fmaf(fmaf(a2.z, s1, a.z * s2), bartw::rcp_approx(s1 * s2), acc[r]);
+      }
+    }
+    if (l < eLF) {                          // odd line out
       const float4 a = g0[l];
       const float qL = g1[l].z;
       const float x0 = fmaf(j0r - a.w, a.x, a.y);
@@ -402,19 +482,37 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
         const float x = fmaf((float)r, a.x, x0);
         acc[r] = fmaf(a.z, bartw::rcp_approx(fmaf(x, x, qL)), acc[r]);
       }
+      ++l;
     }
-    const int eLM = nLF + nLM;
-#pragma unroll 2
-    for (; l < eLM; ++l) {                  // shifted Lorentz, lane weight
+    const int eLM = eLF + nLM;
+    for (; l + 1 < eLM; l += 2) {           // shifted Lorentz, lane weight
+      const float4 a = g0[l], a2 = g0[l + 1];
+      const float4 b = g1[l], b2 = g1[l + 1];
+      const bool t1 = (__float_as_uint(b.w) >> lane) & 1u, t2 = (__float_as_uint(b2.w) >> lane) & 1u;
+      const float A = t1 ? a.z : 0.0f, A2 = t2 ? a2.z : 0.0f;
+      // a lane with weight 0 may hold points of the fixup stretch (small s):
+      // it evaluates far-away points instead
+      const float x0 = t1 ? fmaf(j0r - a.w, a.x, a.y) : FAR_X;
+      const float x02 = t2 ? fmaf(j0r - a2.w, a2.x, a2.y) : FAR_X;
+#pragma unroll
+      for (int r = 0; r < OP_R; ++r) {
+        const float x = fmaf((float)r, a.x, x0), x2 = fmaf((float)r, a2.x, x02);
+        const float s1 = fmaf(x, x, b.z), s2 = fmaf(x2, x2, b2.z);
+        acc[r] = fmaf(fmaf(A2, s1, A * s2), bartw::rcp_approx(s1 * s2), acc[r]);
+      }
+    }
+    if (l < eLM) {
       const float4 a = g0[l];
       const float4 b = g1[l];
-      const float A = ((__float_as_uint(b.w) >> lane) & 1u) ? a.z : 0.0f;
-      const float x0 = fmaf(j0r - a.w, a.x, a.y);
+      const bool t1 = (__float_as_uint(b.w) >> lane) & 1u;
+      const float A = t1 ? a.z : 0.0f;
+      const float x0 = t1 ? fmaf(j0r - a.w, a.x, a.y) : FAR_X;
 #pragma unroll
       for (int r = 0; r < OP_R; ++r) {
         const float x = fmaf((float)r, a.x, x0);
         acc[r] = fmaf(A, bartw::rcp_approx(fmaf(x, x, b.z)), acc[r]);
       }
+      ++l;
     }
     const int ePF = eLM + nPF;
 #pragma unroll 2
@@ -466,16 +564,28 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
         __syncwarp();
         continue;
       }
-      for (int p0 = pa; p0 <= pb; p0 += 32) {
-        if (nT + nC + 32 > CORE_CAP) flush();
-        const int p = p0 + lane;
-        const bool act = p <= pb;
+      // one-pole points on both sides of the core window [klo, khi]
+      const float4 c = g3[fl];
+      const int ka = max(pa, __float_as_int(c.z)), kb = min(pb, __float_as_int(c.w));
+      const int n_left = max(ka - pa, 0), n_far = n_left + max(pb - kb, 0);
+      for (int k = lane; k < n_far; k += 32) {
+        const int p = k < n_left ? pa + k : kb + 1 + (k - n_left);
         const float x = fmaf((float)(p - w0) - a.w, a.x, a.y);
         const float u = fmaf(x, x, b.x);
-        const bool far = act && u >= U_CORE;
-        if (far) fix[p - w0] += fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
+        fix[p - w0] += fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
+      }
+      // the core window: |z| >= 8 at once (continued fraction to depth 3),
+      // |z| < 8 deferred to the lists
+      for (int p0 = ka; p0 <= kb; p0 += 32) {
+        if (nT + nC + 32 > CORE_CAP) flush();
+        const int p = p0 + lane;
+        const bool act = p <= kb;
+        const float x = fmaf((float)(p - w0) - a.w, a.x, a.y);
+        const float u = fmaf(x, x, b.x);
+        const bool mid = act && u >= 63.5f;                // |z| >= 8
+        if (mid) fix[p - w0] += c.y * bartw::cf_gauss_re(fabsf(x), c.x, 3);
         const bool tay = act && u < 24.5f;                 // |z| < 5
-        const bool cfr = act && !far && !tay;
+        const bool cfr = act && !mid && !tay;
         const unsigned bt = __ballot_sync(0xffffffffu, tay);
         const unsigned bc = __ballot_sync(0xffffffffu, cfr);
         const unsigned ent = (unsigned)(p - w0) | ((unsigned)fl << ENT_SHIFT);

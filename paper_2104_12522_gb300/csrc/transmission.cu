@@ -370,8 +370,12 @@ void launch_trans(int grid_dim, size_t smem, cudaStream_t st, const float* grid,
 }
 
 template <int S>
-cudaError_t set_smem(size_t smem) {
-  return cudaFuncSetAttribute(trans_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t set_smem(size_t smem, int* per_sm) {
+  // opt in to the dynamic shared memory, then ask how many CTAs of this
+  // instantiation fit on an SM with it (the persistent grid size)
+  cudaError_t e = cudaFuncSetAttribute(trans_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, trans_kernel<S>, TR_THREADS, smem);
 }
 
 }  // namespace
@@ -391,12 +395,13 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
 
   TrLauncher launch = nullptr;
   cudaError_t ce = cudaSuccess;
+  int per_sm = 0;
   const size_t smem = (size_t)(TR_LMAX * TR_THREADS + TR_LMAX * TR_RB) * sizeof(float);
   switch (S) {
-    case 1: launch = launch_trans<1>; ce = set_smem<1>(smem); break;
-    case 2: launch = launch_trans<2>; ce = set_smem<2>(smem); break;
-    case 3: launch = launch_trans<3>; ce = set_smem<3>(smem); break;
-    case 4: launch = launch_trans<4>; ce = set_smem<4>(smem); break;
+    case 1: launch = launch_trans<1>; ce = set_smem<1>(smem, &per_sm); break;
+    case 2: launch = launch_trans<2>; ce = set_smem<2>(smem, &per_sm); break;
+    case 3: launch = launch_trans<3>; ce = set_smem<3>(smem, &per_sm); break;
+    case 4: launch = launch_trans<4>; ce = set_smem<4>(smem, &per_sm); break;
   }
   if (ce != cudaSuccess) return bart_fail(ctx, BART_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(ce));
 
@@ -426,8 +431,6 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
       (TrInst*)p_inst, b->active, ctx->d_status);
   if ((st = bart_check_launch(ctx, "trans_prologue")) != BART_OK) return st;
   const unsigned long long n_units = (unsigned long long)n_gtiles * (unsigned long long)n;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trans_kernel<1>, TR_THREADS, smem);
   if (per_sm < 1) per_sm = 1;
   int grid_dim = ctx->sm_count * per_sm;
   if ((unsigned long long)grid_dim > n_units) grid_dim = (int)n_units;
