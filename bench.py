@@ -43,7 +43,10 @@ N_PROPOSALS = 2048
 N_ANGLES = 8
 N_BANDS = 10
 OPACITY_LAUNCHES_PER_STEP = 3     # one opacity kernel launch per species
-KERNELS_PER_STEP = 3 * 2 + 3      # per species: window prologue + opacity; tp, emission, band reduce
+KERNELS_PER_STEP = 3 * 3 + 3      # per species: window and span prologues + opacity; tp, emission, band reduce
+# sources the opacity kernel is compiled from (the committed traffic figure is tied to them)
+OPACITY_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
+                   for f in ("opacity.cu", "faddeeva.cuh", "bart_internal.cuh")]
 
 
 def workload_desc():
@@ -101,22 +104,30 @@ def fp32_peak_tflops(n_sm: int, mhz: float) -> float:
     return n_sm * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def source_sha(path):
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def source_sha(paths):
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel_src, name):
-    """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{name}.traffic.json")
+def committed_traffic(kernel_srcs, name):
+    """DRAM bytes of one launch (read + write) from the committed ncu summary
+    profiles/<name>_traffic.txt (key = value lines), if it was taken on the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{name}_traffic.txt")
     if not os.path.exists(path):
         return None
+    kv = {}
     with open(path) as fh:
-        d = json.load(fh)
-    if d.get("source_sha") != source_sha(kernel_src):
+        for line in fh:
+            if "=" in line and not line.lstrip().startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != source_sha(kernel_srcs):
         return None
-    return d.get("dram_bytes_per_launch")
+    return float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])
 
 
 # ---------------------------------------------------------------- clocks
@@ -372,8 +383,7 @@ def run_native(args):
         op_launch_ms = op_avg / OPACITY_LAUNCHES_PER_STEP
         achieved = FLOPS_PER_EVAL * evals / OPACITY_LAUNCHES_PER_STEP / (op_launch_ms / 1e3) / 1e12
         peak = fp32_peak_tflops(n_sm, max_mhz)
-        src = os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", "opacity.cu")
-        traffic = committed_traffic(src, "opacity_kernel")
+        traffic = committed_traffic(OPACITY_SOURCES, "opacity_kernel")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": N, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

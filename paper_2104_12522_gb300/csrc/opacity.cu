@@ -173,13 +173,12 @@ struct __align__(16) LineG1 {   // far-field denominators and the lane mask
   unsigned take;                // lanes whose 16-point block joins the far-field sum
 };
 struct __align__(16) LineG2 {   // fixup range
-  int e0, e1;                   // 16-point blocks [e0, e1] left to the fixup pass
-  int jlo, jhi;                 // cutoff window
+  int pa, pb;                   // points [pa, pb] left to the fixup pass (blocks [e0, e1] in the window)
+  int ka, kb;                   // their part inside the core window (lines with a core in the span)
 };
-struct __align__(16) LineG3 {   // accurate branch
+struct __align__(8) LineG3 {    // accurate branch (expansion lines: -2 dx, dx^2)
   float y;
   float B;                      // S / (sigma sqrt(2 pi)) (scaled): V = B Re w
-  int klo, khi;                 // integer superset of the core |z| < 24
 };
 
 // Far-field classes of a (line, span) pair.  "L": every far-field point of
@@ -205,7 +204,7 @@ constexpr float FF_RATIO = 11.0f * 0.5f * (OP_R - 1);
 constexpr float EPS_L = 2e-6f;
 constexpr int LFIX_MAX = 64;              // longest stretch of one-pole points moved to the fixup
 constexpr float FAR_X = 1.0e4f;           // x of lanes with weight 0 in the lane-mask Lorentz loop
-constexpr int CORE_CAP = 320;             // deferred accurate points per warp before a flush
+constexpr int CORE_CAP = 352;             // deferred accurate points per warp before a flush
 constexpr int ENT_SHIFT = 9;              // list entry: point in span (9 bits) | line slot << 9
 static_assert(OP_SPAN <= (1 << ENT_SHIFT), "list entries hold a point of the span");
 
@@ -216,11 +215,12 @@ struct OpShared {
   float4 g0[OP_WARPS][32];
   float4 g1[OP_WARPS][32];
   int4 g2[OP_WARPS][32];
-  float4 g3[OP_WARPS][32];
+  float2 g3[OP_WARPS][32];
   float fix[OP_WARPS][OP_SPAN];
   float hi[OP_WARPS][OP_R][32];
   float lo[OP_WARPS][OP_R][32];
   unsigned list[OP_WARPS][CORE_CAP];
+  int eidx[OP_WARPS][32];             // packed edge-only fixups: (first entry << 5) | slot
 };
 
 __device__ __forceinline__ unsigned lane_range_mask(int a, int b) {   // bits a..b, empty if a > b
@@ -263,10 +263,11 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
 
   float* fix = sh.fix[warp];
   unsigned* list = sh.list[warp];
+  int* eidx = sh.eidx[warp];
   float4* g0 = sh.g0[warp];
   float4* g1 = sh.g1[warp];
   int4* g2 = sh.g2[warp];
-  float4* g3 = sh.g3[warp];
+  float2* g3 = sh.g3[warp];
 #pragma unroll
   for (int r = 0; r < OP_R; ++r) fix[lane * OP_R + r] = 0.0f;
 
@@ -294,7 +295,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
         const unsigned e = act ? list[pass == 0 ? k : CORE_CAP - 1 - k] : 0u;
         const int l = (int)(e >> ENT_SHIFT), p = (int)(e & (OP_SPAN - 1));
         const float4 c0 = g0[l];
-        const float4 c3 = g3[l];
+        const float2 c3 = g3[l];
         // idle lanes evaluate a harmless point (|z| = 6) and add nothing
         const float x = act ? fabsf(fmaf((float)p - c0.w, c0.x, c0.y)) : 6.0f;
         const float y = act ? c3.x : 0.0f;
@@ -328,7 +329,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
     bool needs_fix = false, has_core = false;
     float4 c0, c1;
     int4 c2;
-    float4 c3;
+    float2 c3;
     if (lane < nl) {
       const int64_t i = base + lane;
       const LineWin w = win[i];
@@ -393,11 +394,15 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       cls = ff ? CLS_FF : lor ? (full ? CLS_LF : CLS_LM) : (full ? CLS_PF : CLS_PM);
       c0 = make_float4(dx, xc, B * y * bartw::INV_SQRTPI, (float)jcr);
       c1 = make_float4(q - 0.5f, 2.0f * q, q - 1.5f, __uint_as_float(take));
-      c2 = make_int4(e0, e1, w.jlo, w.jhi);
+      {
+        // the fixup ranges, once per line here rather than per line in the fixup
+        const int pa = max(w0 + e0 * OP_R, w.jlo);
+        const int pb = min(min(w0 + e1 * OP_R + OP_R - 1, w.jhi), last);
+        c2 = make_int4(pa, pb, max(pa, klo), min(pb, khi));
+      }
       // expansion lines have no core in the span: their slot of the
       // accurate-branch group holds -2 dx and dx^2 instead
-      c3 = ff ? make_float4(-2.0f * dx, dx * dx, 0.0f, 0.0f)
-              : make_float4(y, B, __int_as_float(klo), __int_as_float(khi));
+      c3 = ff ? make_float2(-2.0f * dx, dx * dx) : make_float2(y, B);
     }
     const unsigned bFF = __ballot_sync(0xffffffffu, cls == CLS_FF);
     const unsigned bLF = __ballot_sync(0xffffffffu, cls == CLS_LF);
@@ -419,6 +424,20 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
     }
     const unsigned fix_slots = __reduce_or_sync(0xffffffffu, (slot >= 0 && needs_fix) ? (1u << slot) : 0u);
     const unsigned core_slots = __reduce_or_sync(0xffffffffu, (slot >= 0 && has_core) ? (1u << slot) : 0u);
+    // lines whose fixup holds window edges only (one-pole points): their
+    // ranges are concatenated and evaluated 32 points at a time below
+    const bool edge_only = slot >= 0 && needs_fix && !has_core;
+    const int elen = edge_only ? c2.y - c2.x + 1 : 0;
+    int eincl = elen;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, eincl, o);
+      if (lane >= o) eincl += v;
+    }
+    const int e_total = __shfl_sync(0xffffffffu, eincl, 31);
+    const unsigned b_edge = __ballot_sync(0xffffffffu, edge_only);
+    const int n_edge = __popc(b_edge);
+    if (edge_only) eidx[__popc(b_edge & lt_mask)] = ((eincl - elen) << 5) | slot;
     __syncwarp();
 
     // ---- far field.  The shifted Lorentz classes take two lines per
@@ -434,7 +453,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       for (; l < nFF; ++l) {
         const float4 a = g0[l];
         const float4 b = g1[l];
-        const float4 d = g3[l];             // -2 dx, dx^2
+        const float2 d = g3[l];             // -2 dx, dx^2
         const float A = ((__float_as_uint(b.w) >> lane) & 1u) ? a.z : 0.0f;
         const float xc = fmaf(tc - a.w, a.x, a.y);
         const float g = bartw::rcp_approx(fmaf(xc, xc, b.z));
@@ -545,28 +564,48 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
     }
 
     // ---- fixup: the excluded blocks of each line, lanes take consecutive points
-    unsigned m = fix_slots;
+    // edge-only lines, packed: entry t of the concatenated ranges belongs to
+    // the last edge line whose first entry is <= t (binary search); the
+    // values are added in rounds of equal line (ascending): deterministic
+    for (int g = 0; g < e_total; g += 32) {
+      const int t = g + lane;
+      const bool act = t < e_total;
+      int k = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cnd = k + step;
+        if (cnd < n_edge && (eidx[cnd] >> 5) <= t) k = cnd;
+      }
+      const int ek = eidx[k];
+      const int sl = ek & 31;
+      const float4 a = g0[sl];
+      const float4 b = g1[sl];
+      const int p = g2[sl].x + (t - (ek >> 5));
+      const float x = fmaf((float)(p - w0) - a.w, a.x, a.y);
+      const float u = fmaf(x, x, b.x);
+      const float v = fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
+      const int kp = __shfl_up_sync(0xffffffffu, k, 1);
+      unsigned seg = __ballot_sync(0xffffffffu, act && (lane == 0 || k != kp));
+      while (seg) {
+        const int s0 = __ffs(seg) - 1;
+        seg &= seg - 1;
+        const int s1 = seg ? __ffs(seg) - 1 : 32;
+        if (act && lane >= s0 && lane < s1) fix[p - w0] += v;
+        __syncwarp();
+      }
+    }
+    // lines with a core in the span
+    unsigned m = core_slots;
     while (m) {
       const int fl = __ffs(m) - 1;
       m &= m - 1;
       const float4 a = g0[fl];
       const float4 b = g1[fl];
       const int4 e = g2[fl];
-      const int pa = max(w0 + e.x * OP_R, e.z);
-      const int pb = min(min(w0 + e.y * OP_R + OP_R - 1, e.w), last);
-      if (!((core_slots >> fl) & 1u)) {
-        // window edges only: every point is outside the core (one-pole form)
-        for (int p = pa + lane; p <= pb; p += 32) {
-          const float x = fmaf((float)(p - w0) - a.w, a.x, a.y);
-          const float u = fmaf(x, x, b.x);
-          fix[p - w0] += fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
-        }
-        __syncwarp();
-        continue;
-      }
+      const int pa = e.x, pb = e.y;
       // one-pole points on both sides of the core window [klo, khi]
-      const float4 c = g3[fl];
-      const int ka = max(pa, __float_as_int(c.z)), kb = min(pb, __float_as_int(c.w));
+      const float2 c = g3[fl];
+      const int ka = e.z, kb = e.w;
       const int n_left = max(ka - pa, 0), n_far = n_left + max(pb - kb, 0);
       for (int k = lane; k < n_far; k += 32) {
         const int p = k < n_left ? pa + k : kb + 1 + (k - n_left);
