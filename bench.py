@@ -370,7 +370,7 @@ def run_native(args):
 
     aux = {}
     if not args.no_aux:
-        aux = run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args)
+        aux = run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_lines, theta)
 
     if rank == 0:
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -401,6 +401,7 @@ def run_native(args):
                               "proposals": N_PROPOSALS, "angles": N_ANGLES, "bands": N_BANDS,
                               "species": S},
             "opacity_build_ms": op_avg,
+            "opacity_build_ms_per_step": [round(v, 2) for v in op_ms],
             "cpu_baseline": cpu,
             "e2e": {"value": N * evals / (e2e_ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
@@ -426,8 +427,9 @@ def _event_ms(torch, stream, fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args):
+def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_lines, theta):
     """Measurements beside the timed step, on the grid the step built:
+    the paper's two approximations (line-strength bound, optical-depth limit),
     transmission batch, surrogate training and accuracy, screened vs plain
     retrieval.  Times are CUDA events on the library's stream."""
     S = int(grid.shape[0])
@@ -451,11 +453,63 @@ def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args):
     ctx.sync()
     out["transmission"] = {"spectra_per_s": 1024 / (ms / 1e3), "ms_per_batch": ms, "instances": 1024,
                            "level_sum": int(inst.n_levels.sum()), "points": int(offs[-1]), "bands": 12}
+    out["paper_approximations"] = paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta)
     net, out["surrogate"] = train_surrogate(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S,
                                             args.train_steps)
     out["retrieval"] = run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net,
                                      args.generations, args.burn, args.screen_beta, args.screen_margin)
     return out
+
+
+def _max_rel(torch, got, ref, floor_frac=1e-6):
+    """max |got/ref - 1| over points above floor_frac of their row maximum."""
+    ref2 = ref.reshape(-1, ref.shape[-1])
+    got2 = got.reshape(-1, ref.shape[-1])
+    big = ref2 > floor_frac * ref2.amax(dim=1, keepdim=True)
+    rel = ((got2 - ref2).abs() / ref2.clamp_min(1e-38))[big]
+    return float(rel.max()) if rel.numel() else 0.0
+
+
+def paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta):
+    """Speed-up against accuracy lost of Sec. 4 items 6 and 7 on the bench's
+    workload.  (a) The line-strength bound: time of the species-0 launch of
+    the grid build (2,000 cells) against the same launch without it; the grid
+    error against the step's grid (relative L2 and max relative error over
+    points above 1e-3 of their row maximum); and the error of the emission
+    spectra of the 2,048 proposals computed from the thresholded 3-species
+    grid.  (b) The optical-depth limit on the 2,048-proposal generation."""
+    res = {"line_threshold": [], "tau_limit": []}
+    n = theta.shape[0]
+    spec_ref = torch.empty((n, ax.n_nu), dtype=torch.float32, device=grid.device)
+    spec = torch.empty_like(spec_ref)
+    run = lambda g, c, o: ctx.forward_spectra_batch(g, ax.p_bar, ax.t_K, nu, c, theta=theta, spectra=o)
+    run(grid, cfg, spec_ref)
+    out = torch.empty((1,) + tuple(grid.shape[1:]), dtype=torch.float32, device=grid.device)
+    full = torch.empty_like(grid)
+    build0 = lambda: ctx.build_opacity_grid(d_lines[:1], ax.p_bar, ax.t_K, nu, ax.cutoff, out=out)
+    ms0 = _event_ms(torch, stream, build0)
+    ref0 = grid[0].reshape(-1, ax.n_nu)
+    for rel in (1e-6, 1e-4, 1e-2):
+        ctx.set_line_threshold(rel)
+        ms = _event_ms(torch, stream, build0)
+        ctx.build_opacity_grid(d_lines, ax.p_bar, ax.t_K, nu, ax.cutoff, out=full)
+        ctx.set_line_threshold(0.0)
+        run(full, cfg, spec)
+        got0 = out[0].reshape(-1, ax.n_nu)
+        l2 = float(torch.linalg.vector_norm(got0 - ref0) / torch.linalg.vector_norm(ref0))
+        res["line_threshold"].append({"rel": rel, "ms": ms, "ms_without": ms0, "speedup": ms0 / ms,
+                                      "grid_rel_l2": l2, "grid_max_rel_err_1e-3": _max_rel(torch, got0, ref0, 1e-3),
+                                      "spectra_max_rel_err": _max_rel(torch, spec, spec_ref, 0.0)})
+    del full
+    ms0 = _event_ms(torch, stream, lambda: run(grid, cfg, spec_ref))
+    for tau_max in (30.0, 10.0, 3.0):
+        c = dict(cfg, tau_max=tau_max)
+        run(grid, c, spec)
+        ms = _event_ms(torch, stream, lambda: run(grid, c, spec))
+        res["tau_limit"].append({"tau_max": tau_max, "ms": ms, "ms_without": ms0, "speedup": ms0 / ms,
+                                 "spectra_max_rel_err": _max_rel(torch, spec, spec_ref, 0.0)})
+    ctx.sync()
+    return res
 
 
 def train_surrogate(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, n_steps):

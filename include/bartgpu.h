@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define BART_ABI_VERSION 1
+#define BART_ABI_VERSION 2
 
 typedef enum {
   BART_OK = 0,
@@ -113,7 +113,7 @@ typedef struct {
 
 /* ---------------------------------------------------------- opacity build */
 
-/* Line-by-line opacity at explicit (P, T) cells ("on the spot", Sec. 3):
+/* Line-by-line opacity computed directly at explicit (P, T) cells (Sec. 3):
  *   out[s][c][j] = sum_i S_i(T_c) V(nu_j - nu0_i; sigma_i(T_c), gamma_i(P_c, T_c))
  * in cm^2 molecule^-1, for species s < n_species, cell c < n_cells.
  * V is the Voigt profile of Sec. 5.1.1 (Eqs. 2-9), evaluated through the
@@ -123,9 +123,9 @@ typedef struct {
  * Eq. 2).  gamma = gamma_ref (P/1 bar) (296/T)^0.5.  A line contributes at
  * grid points with |nu_j - nu0| <= cutoff_cm, the difference taken in FP64 as
  * (nu_start + j*dnu) - nu0.  Lines are summed in FP32 with compensation
- * (per-block partial sums folded with TwoSum); the Doppler cores
- * (|z| < 24) are added through shared-memory atomics, so the last bit may
- * vary between runs.
+ * (partial sums over 128 lines folded with TwoSum) in a fixed order: the
+ * result does not vary between runs.  With a line-strength threshold set
+ * (bart_set_line_threshold) lines below it are left out.
  *   species  host array [n_species] of line lists (device arrays inside)
  *   p_bar    host [n_cells] pressures, bar, > 0
  *   t_K      host [n_cells] temperatures, K, > 0
@@ -149,6 +149,14 @@ bart_status bart_build_opacity_grid(bart_ctx* ctx, const bart_linelist* species,
                                     const double* p_bar, int n_layers,
                                     const double* t_K, int n_temps,
                                     bart_nugrid nu, double cutoff_cm, float* grid);
+
+/* Line-strength lower bound of Sec. 4 item 6 for the following
+ * bart_opacity_cells / bart_build_opacity_grid calls on this context: at each
+ * (P, T) cell, a line whose strength S_i(T) is below rel times the strongest
+ * line of its species at that cell is left out of the sum (the comparison is
+ * made on ln S in FP32).  rel <= 0 turns the bound off (the default).
+ * Returns BART_EINVAL for NULL ctx or a non-finite rel. */
+bart_status bart_set_line_threshold(bart_ctx* ctx, double rel);
 
 /* Re w(x + i y) of the Faddeeva function (Sec. 5.1.1, Eqs. 4-9) as the
  * opacity kernels evaluate it, for y >= 0.  x, y, out: device [n] FP32.
@@ -183,7 +191,12 @@ enum { BART_EMISSION = 0, BART_TRANSMISSION = 1 };
  *   p_ref_bar     transmission: pressure at r_planet
  *   p_top_bar, p_bot_bar  transmission: instance levels are log-spaced
  *                 between these (n_levels[i] of them)
- *   x0            host [n_species] base volume mixing ratios X0_s */
+ *   x0            host [n_species] base volume mixing ratios X0_s
+ *   tau_max       emission: Sec. 4 item 7, stop the layer integration at a
+ *                 wavenumber once the vertical optical depth from the top
+ *                 exceeds tau_max; the level reached is then the bottom
+ *                 (blackbody) boundary.  <= 0 turns it off.
+ * (tau_max was added in ABI version 2, at the end of the struct.) */
 typedef struct {
   int32_t geometry;
   int32_t n_angles;
@@ -192,6 +205,7 @@ typedef struct {
   double t_min_K, t_max_K;
   double p_ref_bar, p_top_bar, p_bot_bar;
   const double* x0;
+  double tau_max;
 } bart_fwd_cfg;
 
 /* A batch of proposals (emission) or instances (transmission).

@@ -82,7 +82,7 @@ def emission_spectrum(grid, p_axis, t_axis, nu, theta, cfg, T=None):
     X = profile.abundances(theta, cfg["x0"])
     sig = layer_opacity(grid, t_axis, T)
     chi = mass_opacity(sig, X, cfg["mu"])
-    return radiation.emission_flux(chi, p_axis, T, nu, cfg["g"], cfg["n_angles"])
+    return radiation.emission_flux(chi, p_axis, T, nu, cfg["g"], cfg["n_angles"], tau_max=cfg.get("tau_max"))
 
 
 def instance_levels(n_levels, p_top, p_bot):

@@ -1,7 +1,7 @@
 """Line-by-line opacity, point-sampled on the output wavenumber grid.
 
-The paper's opacity grid (Sec. 3, "Transit accepts an atmospheric
-description..."; Sec. 4 items 3-4) holds, per molecule, the opacity on the
+The paper's opacity grid (Sec. 3, the radiative-transfer module's table;
+Sec. 4 items 3-4) holds, per molecule, the opacity on the
 output wavenumber grid over the layer pressures and a grid of temperatures.
 Lines are sampled at the grid wavenumbers, not bin-averaged (Sec. 4, text after
 the list of optimisations).  The line-strength and width formulas live in the
@@ -15,7 +15,10 @@ companion paper and are not printed; the readings used here are:
 * Lorentz half width: gamma = gamma_ref (P / 1 bar) (T_ref / T)^0.5;
 * profile cutoff: hard and inclusive, |nu_j - nu0| <= cutoff, with
   nu_j = nu_start + j*dnu and nu_j - nu0 evaluated in FP64 in that order;
-* no renormalisation of the truncated profile and no line-strength threshold.
+* no renormalisation of the truncated profile; by default no line-strength
+  threshold.  With rel_threshold > 0 (Sec. 4 item 6) a line whose S(T) is
+  below rel_threshold times the strongest line of the list at that T (and P)
+  is left out.
 
 The opacity of species s at grid point j is the plain sum
 sigma_s(nu_j) = sum_i S_i V(nu_j - nu0_i; sigma_i, gamma_i)   [cm^2 molecule^-1],
@@ -52,12 +55,13 @@ def grid_nu(nu_start, dnu, n_nu):
     return nu_start + np.arange(n_nu, dtype=np.float64) * dnu
 
 
-def opacity_cell(lines, p_bar, T, nu_start, dnu, n_nu, cutoff, j_lo=0, j_hi=None):
+def opacity_cell(lines, p_bar, T, nu_start, dnu, n_nu, cutoff, j_lo=0, j_hi=None, rel_threshold=0.0):
     """Opacity of one species at one (P, T) on grid points j in [j_lo, j_hi).
 
     `lines` carries nu0, log10_s296, elow, gamma_ref, mass_amu.  For every grid
-    point the contributions of all lines within the cutoff are evaluated and
-    added with math.fsum.  Returns an FP64 array of length j_hi - j_lo.
+    point the contributions of all lines within the cutoff (and, with
+    rel_threshold > 0, at or above the strength bound) are evaluated and added
+    with math.fsum.  Returns an FP64 array of length j_hi - j_lo.
     """
     if j_hi is None:
         j_hi = n_nu
@@ -65,6 +69,9 @@ def opacity_cell(lines, p_bar, T, nu_start, dnu, n_nu, cutoff, j_lo=0, j_hi=None
     out = np.zeros(max(n, 0))
     if n <= 0:
         return out
+    s_floor = 0.0
+    if rel_threshold > 0 and len(lines.nu0):
+        s_floor = rel_threshold * float(np.max(line_strength(lines.log10_s296, lines.nu0, lines.elow, T)))
     # Points are processed in chunks narrow against the cutoff so that the
     # (point x candidate line) matrix stays small.
     chunk = max(1, int(cutoff / (4.0 * dnu)))
@@ -81,22 +88,23 @@ def opacity_cell(lines, p_bar, T, nu_start, dnu, n_nu, cutoff, j_lo=0, j_hi=None
         sig = doppler_sigma(nu0, T, lines.mass_amu)
         gam = lorentz_gamma(lines.gamma_ref[lo:hi], p_bar, T)
         d = nu[:, None] - nu0[None, :]
-        inside = np.abs(d) <= cutoff
+        inside = (np.abs(d) <= cutoff) & (S[None, :] >= s_floor)
         v = S[None, :] * voigt(d, sig[None, :], gam[None, :])
         for r in range(j.size):
             out[c0 - j_lo + r] = math.fsum(v[r][inside[r]])
     return out
 
 
-def opacity_cells(species, p_bar, t_K, nu_start, dnu, n_nu, cutoff):
-    """Direct ("on the spot") opacity at each cell's own (P, T).
+def opacity_cells(species, p_bar, t_K, nu_start, dnu, n_nu, cutoff, rel_threshold=0.0):
+    """Direct opacity at each cell's own (P, T), computed for the cell (Sec. 3).
 
     Returns FP64 [n_species][n_cells][n_nu].
     """
     out = np.zeros((len(species), len(p_bar), n_nu))
     for s, ll in enumerate(species):
         for c in range(len(p_bar)):
-            out[s, c] = opacity_cell(ll, p_bar[c], t_K[c], nu_start, dnu, n_nu, cutoff)
+            out[s, c] = opacity_cell(ll, p_bar[c], t_K[c], nu_start, dnu, n_nu, cutoff,
+                                     rel_threshold=rel_threshold)
     return out
 
 

@@ -54,14 +54,27 @@ def intensity(tau, B, mu):
     return np.sum(Bbar * (t[..., :-1] - t[..., 1:]), axis=-1) + B[..., -1] * t[..., -1]
 
 
-def emission_flux(chi, p_bar, T, nu, g, n_angles):
-    """Planetary flux F(nu) for chi[L][n_nu], T[L]; returns FP64 [n_nu]."""
+def emission_flux(chi, p_bar, T, nu, g, n_angles, tau_max=None):
+    """Planetary flux F(nu) for chi[L][n_nu], T[L]; returns FP64 [n_nu].
+
+    tau_max (Sec. 4 item 7, the integration goes down to a chosen optical depth):
+    at each wavenumber the integration stops at the first level whose vertical
+    optical depth exceeds tau_max, and that level is the bottom boundary (its
+    blackbody seen through the layers above)."""
     tau = optical_depth(np.asarray(chi).T, p_bar, g)           # [n_nu][L]
     B = planck(np.asarray(nu)[:, None], np.asarray(T)[None, :])  # [n_nu][L]
     mu, w = gauss_legendre_mu(n_angles)
     F = np.zeros(len(nu))
-    for i in range(n_angles):
-        F += w[i] * mu[i] * intensity(tau, B, mu[i])
+    if tau_max is None:
+        for i in range(n_angles):
+            F += w[i] * mu[i] * intensity(tau, B, mu[i])
+        return 2.0 * math.pi * F
+    L = tau.shape[1]
+    for r in range(len(nu)):
+        over = np.nonzero(tau[r, 1:] > tau_max)[0]
+        k = over[0] + 1 if over.size else L - 1
+        for i in range(n_angles):
+            F[r] += w[i] * mu[i] * intensity(tau[r, :k + 1], B[r, :k + 1], mu[i])
     return 2.0 * math.pi * F
 
 

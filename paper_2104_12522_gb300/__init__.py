@@ -88,7 +88,7 @@ def _grid_cfg(grid, p_bar, t_K, nu, cfg):
                         float(cfg.get("r_star_tp", 0.0)), float(cfg.get("a_orbit", 0.0)),
                         float(cfg.get("t_min", 0.0)), float(cfg.get("t_max", 1e30)),
                         float(cfg.get("p_ref", 0.1)), float(cfg.get("p_top", 1e-8)),
-                        float(cfg.get("p_bot", 100.0)), C.cast(x0, C.c_void_p))
+                        float(cfg.get("p_bot", 100.0)), C.cast(x0, C.c_void_p), float(cfg.get("tau_max", 0.0)))
     return gd, fc, (pb, tk, x0)
 
 
@@ -133,6 +133,11 @@ class Context:
 
     def set_autotune(self, enable: bool):
         self._check(self.lib.bart_set_autotune(self.h, int(bool(enable))))
+
+    def set_line_threshold(self, rel: float):
+        """Line-strength lower bound for later opacity builds (relative to the
+        strongest line of each species at each cell; <= 0 turns it off)."""
+        self._check(self.lib.bart_set_line_threshold(self.h, float(rel)))
 
     def autotune_report(self) -> dict:
         """Autotuned tile width per launch shape."""

@@ -38,7 +38,7 @@ class FwdCfg(C.Structure):
                 ("t_int_K", c_double), ("t_star_K", c_double), ("r_star_tp_cm", c_double),
                 ("a_orbit_cm", c_double), ("t_min_K", c_double), ("t_max_K", c_double),
                 ("p_ref_bar", c_double), ("p_top_bar", c_double), ("p_bot_bar", c_double),
-                ("x0", c_void_p)]
+                ("x0", c_void_p), ("tau_max", c_double)]
 
 
 class Batch(C.Structure):
@@ -66,6 +66,7 @@ SIGNATURES = {
     "bart_last_error": (C.c_char_p, [c_void_p]),
     "bart_sync": (c_int, [c_void_p]),
     "bart_set_autotune": (c_int, [c_void_p, c_int]),
+    "bart_set_line_threshold": (c_int, [c_void_p, c_double]),
     "bart_autotune_report": (c_int, [c_void_p, C.c_char_p, c_int]),
     "bart_opacity_cells": (c_int, [c_void_p, P(LineList), c_int, P(c_double), P(c_double), c_int, NuGrid,
                                    c_double, c_void_p]),

@@ -1,5 +1,6 @@
 // Context management of the C ABI: creation, streams, errors, status word and
 // scratch memory.
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 
@@ -126,6 +127,13 @@ extern "C" bart_status bart_set_autotune(bart_ctx* ctx, int enable) {
   if (!ctx) return BART_EINVAL;
   ctx->autotune = enable ? 1 : 0;
   if (!enable) ctx->tiles.clear();
+  return BART_OK;
+}
+
+extern "C" bart_status bart_set_line_threshold(bart_ctx* ctx, double rel) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, std::isfinite(rel), "line threshold must be finite");
+  ctx->line_rel = rel;
   return BART_OK;
 }
 

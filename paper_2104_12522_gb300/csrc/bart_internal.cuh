@@ -26,6 +26,7 @@ struct bart_ctx {
   std::map<std::string, std::vector<unsigned char>> uploaded;   // host copy of each constant buffer
   std::map<std::string, int> tiles;  // autotuned tile width per launch shape
   int autotune = 1;
+  double line_rel = 0.0;            // line-strength lower bound (<= 0: off)
   int* d_status = nullptr;          // device status word
   float2* d_wtable = nullptr;       // Faddeeva Taylor-coefficient table
   bool wtable_ready = false;

@@ -136,7 +136,10 @@ __device__ __forceinline__ float planck(float c1nu3, float x) {
   return c1nu3 * bartf::rcp_approx(e - 1.0f);
 }
 
-template <int S, int NA, int TW, bool WIDE_X>
+// MODE bit 0: the FP64 Planck branch (c2 nu / T may exceed 20); bit 1: the
+// optical-depth limit (an early exit from the layer loop; without it the loop
+// has a fixed trip count the compiler can pipeline).
+template <int S, int NA, int TW, int MODE>
 __global__ void __launch_bounds__(TW)
 emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const LayerTW* __restrict__ tw,
                 const float* __restrict__ coef, const float* __restrict__ dpg,
@@ -144,7 +147,7 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
                 double dnu, const int64_t* __restrict__ nu_lo, const int64_t* __restrict__ nu_hi,
                 const int64_t* __restrict__ offs, float* __restrict__ spectra,
                 const float* __restrict__ filt, int n_bands, float2* __restrict__ partial, int n_tiles,
-                const int32_t* __restrict__ act_mask, int* __restrict__ status) {
+                const int32_t* __restrict__ act_mask, int* __restrict__ status, float tau_cut) {
   const int p = blockIdx.x;
   const int tile = blockIdx.y;
   const int tid = threadIdx.x;
@@ -204,7 +207,9 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
 
   LayerTW r = twp[0];
   float chi_prev = chi_at(r);
+  constexpr bool WIDE_X = (MODE & 1) != 0, TAU_LIM = (MODE & 2) != 0;
   float B_prev = planck<WIDE_X>(c1nu3, nuf * r.c2_t);
+  float tau_v = 0.0f;                            // vertical optical depth from the top
   for (int k = 1; k < L; ++k) {
     r = twp[k];
     const float chi = chi_at(r);
@@ -220,6 +225,12 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
     }
     chi_prev = chi;
     B_prev = B;
+    if (TAU_LIM) {
+      // Sec. 4 item 7: stop at the caller's optical-depth limit; the level
+      // reached is then the bottom boundary (its blackbody below)
+      tau_v += dtau;
+      if (tau_v > tau_cut) break;
+    }
   }
   float F = 0.0f;
 #pragma unroll
@@ -313,48 +324,59 @@ __global__ void band_integrate_kernel(const float* __restrict__ spectra, const i
   }
 }
 
-template <int S, int NA, int TW, bool WIDE_X>
+template <int S, int NA, int TW, int MODE>
 void launch_emission(dim3 g, cudaStream_t st, const float* grid, int L, int M, int64_t N, const LayerTW* tw,
                      const float* coef, const float* dpg, const float* ang, double nu_start, double dnu,
                      const int64_t* lo, const int64_t* hi, const int64_t* offs, float* spectra,
-                     const float* filt, int nb, float2* partial, int n_tiles, const int32_t* active, int* status) {
-  emission_kernel<S, NA, TW, WIDE_X><<<g, TW, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi, offs,
-                                               spectra, filt, nb, partial, n_tiles, active, status);
+                     const float* filt, int nb, float2* partial, int n_tiles, const int32_t* active, int* status,
+                     float tau_cut) {
+  emission_kernel<S, NA, TW, MODE><<<g, TW, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi, offs,
+                                               spectra, filt, nb, partial, n_tiles, active, status, tau_cut);
 }
 
 using EmLauncher = void (*)(dim3, cudaStream_t, const float*, int, int, int64_t, const LayerTW*, const float*,
                             const float*, const float*, double, double, const int64_t*, const int64_t*,
-                            const int64_t*, float*, const float*, int, float2*, int, const int32_t*, int*);
+                            const int64_t*, float*, const float*, int, float2*, int, const int32_t*, int*, float);
 
 // Wavenumber-tile widths the autotuner chooses from (threads per CTA).
 constexpr int TILE_CHOICES[3] = {64, 128, 256};
 constexpr int MIN_TILE = 64;
 
-template <int S, int NA, bool WIDE_X>
+template <int S, int NA, int MODE>
 EmLauncher pick_tile(int tw) {
   switch (tw) {
-    case 64: return launch_emission<S, NA, 64, WIDE_X>;
-    case 128: return launch_emission<S, NA, 128, WIDE_X>;
-    case 256: return launch_emission<S, NA, 256, WIDE_X>;
+    case 64: return launch_emission<S, NA, 64, MODE>;
+    case 128: return launch_emission<S, NA, 128, MODE>;
+    case 256: return launch_emission<S, NA, 256, MODE>;
     default: return nullptr;
   }
 }
 
-template <int S, bool WIDE_X>
+template <int S, int MODE>
 EmLauncher pick_na(int na, int tw) {
   switch (na) {
-    case 1: return pick_tile<S, 1, WIDE_X>(tw);
-    case 2: return pick_tile<S, 2, WIDE_X>(tw);
-    case 4: return pick_tile<S, 4, WIDE_X>(tw);
-    case 8: return pick_tile<S, 8, WIDE_X>(tw);
-    case 16: return pick_tile<S, 16, WIDE_X>(tw);
+    case 1: return pick_tile<S, 1, MODE>(tw);
+    case 2: return pick_tile<S, 2, MODE>(tw);
+    case 4: return pick_tile<S, 4, MODE>(tw);
+    case 8: return pick_tile<S, 8, MODE>(tw);
+    case 16: return pick_tile<S, 16, MODE>(tw);
     default: return nullptr;
   }
 }
 
 template <int S>
-EmLauncher pick_wide(int na, int tw, bool wide) {
-  return wide ? pick_na<S, true>(na, tw) : pick_na<S, false>(na, tw);
+EmLauncher pick_mode(int na, int tw, int mode) {
+  switch (mode) {
+    case 0: return pick_na<S, 0>(na, tw);
+    case 1: return pick_na<S, 1>(na, tw);
+    case 2: return pick_na<S, 2>(na, tw);
+    default: return pick_na<S, 3>(na, tw);
+  }
+}
+
+// The layer loop's optical-depth limit (cfg tau_max; <= 0: off).
+float tau_cut_of(const bart_fwd_cfg* c) {
+  return (c->tau_max > 0.0 && std::isfinite(c->tau_max)) ? (float)c->tau_max : 3.0e38f;
 }
 
 // True where x = c2 nu / T can exceed 20 on the grid: T is clamped to
@@ -365,14 +387,19 @@ bool planck_wide(const bart_nugrid& nu, double t_min) {
   return bartc::C2 * nu_max / t_min > 19.9;
 }
 
-EmLauncher pick_emission(int S, int na, int tw = EM_THREADS, bool wide = true) {
+// mode: bit 0 the FP64 Planck branch, bit 1 the optical-depth limit
+EmLauncher pick_emission(int S, int na, int tw = EM_THREADS, int mode = 1) {
   switch (S) {
-    case 1: return pick_wide<1>(na, tw, wide);
-    case 2: return pick_wide<2>(na, tw, wide);
-    case 3: return pick_wide<3>(na, tw, wide);
-    case 4: return pick_wide<4>(na, tw, wide);
+    case 1: return pick_mode<1>(na, tw, mode);
+    case 2: return pick_mode<2>(na, tw, mode);
+    case 3: return pick_mode<3>(na, tw, mode);
+    case 4: return pick_mode<4>(na, tw, mode);
     default: return nullptr;
   }
+}
+
+int emission_mode(const bart_grid_desc* g, const bart_fwd_cfg* c) {
+  return (planck_wide(g->nu, c->t_min_K) ? 1 : 0) | ((c->tau_max > 0.0 && std::isfinite(c->tau_max)) ? 2 : 0);
 }
 
 }  // namespace
@@ -450,21 +477,22 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
                                         (float)std::min(c->t_max_K, 1e30), dc + off_x0, (LayerTW*)p_tw,
                                         (float*)p_coef, b->active, ctx->d_status);
   if ((st = bart_check_launch(ctx, "tp_kernel")) != BART_OK) return st;
-  const bool wide = planck_wide(g->nu, c->t_min_K);
+  const int mode = emission_mode(g, c);
+  const float tau_cut = tau_cut_of(c);
   auto run = [&](int tw) {
     const int n_tiles = (int)((N + tw - 1) / tw);
-    pick_emission(S, c->n_angles, tw, wide)(dim3((unsigned)n, (unsigned)n_tiles), ctx->stream, g->grid, L, M, N,
+    pick_emission(S, c->n_angles, tw, mode)(dim3((unsigned)n, (unsigned)n_tiles), ctx->stream, g->grid, L, M, N,
                                       (const LayerTW*)p_tw, (const float*)p_coef, dc + off_dpg, dc + off_ang,
                                       g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
                                       nb ? f->weights : nullptr, nb, (float2*)p_part, n_tiles, b->active,
-                                      ctx->d_status);
+                                      ctx->d_status, tau_cut);
     return n_tiles;
   };
   // Tile width: cached per shape; measured once (each candidate timed with
   // CUDA events on the stream) unless the stream is being captured.
   char key[160];
-  snprintf(key, sizeof(key), "em S%d A%d L%d M%d N%lld n%d b%d span%d w%d", S, NA, L, M, (long long)N, n, nb,
-           b->nu_lo ? 1 : 0, wide ? 1 : 0);
+  snprintf(key, sizeof(key), "em S%d A%d L%d M%d N%lld n%d b%d span%d m%d", S, NA, L, M, (long long)N, n, nb,
+           b->nu_lo ? 1 : 0, mode);
   int tw = EM_THREADS;
   auto it = ctx->tiles.find(key);
   if (it != ctx->tiles.end()) {
@@ -585,7 +613,7 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
     if (!(g->p_bar[k] > 0) || (k > 0 && !(g->p_bar[k] > g->p_bar[k - 1]))) return BART_EINVAL;
   for (int m = 0; m < M; ++m)
     if (!(g->t_K[m] > 0) || (m > 0 && !(g->t_K[m] > g->t_K[m - 1]))) return BART_EINVAL;
-  EmLauncher launch = pick_emission(S, c->n_angles, EM_THREADS, planck_wide(g->nu, c->t_min_K));
+  EmLauncher launch = pick_emission(S, c->n_angles, EM_THREADS, emission_mode(g, c));
   if (!launch) return BART_EUNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return BART_ECUDA;
@@ -636,7 +664,7 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
   const int n_tiles = (int)((N + EM_THREADS - 1) / EM_THREADS);
   launch(dim3((unsigned)n, (unsigned)n_tiles), st, g->grid, L, M, N, a.tw, a.coef, a.cst + off_dpg,
          a.cst + off_ang, g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
-         nb ? f->weights : nullptr, nb, a.part, n_tiles, b->active, a.status);
+         nb ? f->weights : nullptr, nb, a.part, n_tiles, b->active, a.status, tau_cut_of(c));
   if (nb > 0) {
     const int64_t tot = (int64_t)n * nb;
     band_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a.part, n, n_tiles, nb, b->active, bands);

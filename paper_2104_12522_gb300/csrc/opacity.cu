@@ -35,6 +35,7 @@
 //  * All arithmetic runs at a 2^100 scale so far-wing terms of weak lines stay
 //    normal FP32 numbers (and products of two denominators stay in range);
 //    the result is scaled back on the store.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 
@@ -126,6 +127,43 @@ __global__ void line_window_kernel(const double* __restrict__ nu0, const float* 
   w.c2nu = (float)c2nu;
   w.nu0f = (float)c;
   win[i] = w;
+}
+
+// ln S(T) = ln_s0 + 1.5 ln(T_ref/T) - c2 E''/T + ln(1 - exp(-c2 nu0/T)), in FP32
+// (the staging of the opacity kernel and the threshold prologue share it).
+__device__ __forceinline__ float line_ln_s(const LineWin& w, const CellConst& cc) {
+  const float stim = 1.0f - ex2f_approx(-w.c2nu * cc.inv_t * LOG2EF);
+  return w.ln_s0 + cc.ln_q - w.c2e * cc.inv_t + LN2F_ * lg2f_approx(stim);
+}
+
+// Order-preserving map of floats to ints (for atomicMax on floats).
+__device__ __forceinline__ int ordered_int(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ordered_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// Largest ln S(T) of a species' lines at each temperature (Sec. 4 item 6:
+// the line-strength bound is relative to the strongest line at each cell; S
+// depends on T only).  smax[blockIdx.y] must start at a very negative
+// ordered value.
+__global__ void line_smax_kernel(const LineWin* __restrict__ win, int64_t n_lines,
+                                 const CellConst* __restrict__ cells, int* __restrict__ smax) {
+  const CellConst cc = cells[blockIdx.y];
+  float m = -3.0e38f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_lines; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, line_ln_s(win[i], cc));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float s_m[32];
+  if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? s_m[threadIdx.x] : -3.0e38f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(&smax[blockIdx.y], ordered_int(m));
+  }
 }
 
 // First index in [lo, hi) with key[i] >= v (key nondecreasing).
@@ -244,7 +282,8 @@ __device__ __forceinline__ unsigned lane_range_mask(int a, int b) {   // bits a.
 __global__ void __launch_bounds__(OP_THREADS, 3)
 opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
                const SpanRange* __restrict__ spans, const CellConst* __restrict__ cells, double dnu,
-               int64_t n_nu, float* __restrict__ out, const float2* __restrict__ wtab) {
+               int64_t n_nu, float* __restrict__ out, const float2* __restrict__ wtab,
+               const int* __restrict__ smax, const int* __restrict__ tmap, float ln_rel) {
   extern __shared__ __align__(16) unsigned char op_smem[];
   OpShared& sh = *reinterpret_cast<OpShared*>(op_smem);
 
@@ -257,6 +296,8 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
   const float tc = j0r + 0.5f * (OP_R - 1);  // offset of its block centre
   const int cell = blockIdx.y;
   const CellConst cc = cells[cell];
+  // line-strength bound: lines with ln S below this are left out
+  const float ln_thr = smax ? ordered_float(smax[tmap[cell]]) + ln_rel : -3.0e38f;
   const SpanRange rg = spans[blockIdx.x * OP_WARPS + warp];
   const int last = (int)min((int64_t)w1, n_nu - 1);
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -336,9 +377,8 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       const float inv = bartw::rcp_approx(w.nu0f * cc.dfac);   // 1 / (sigma sqrt 2)
       const float y = gref[i] * cc.gfac * inv;
       const float q = y * y;
-      // ln S(T) = ln_s0 + 1.5 ln(T_ref/T) - c2 E''/T + ln(1 - exp(-c2 nu0/T))
-      const float stim = 1.0f - ex2f_approx(-w.c2nu * cc.inv_t * LOG2EF);
-      const float ln_s = w.ln_s0 + cc.ln_q - w.c2e * cc.inv_t + LN2F_ * lg2f_approx(stim);
+      const float ln_s = line_ln_s(w, cc);
+      const bool keep = ln_s >= ln_thr;
       const float B = ex2f_approx((ln_s + LN_SCALE) * LOG2EF) * inv * bartw::INV_SQRTPI;
       const float dx = dnuf * inv, xc = w.delta * inv;
       const int jcr = w.jc - w0;
@@ -392,6 +432,11 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       const float smin = fmaf(xm, xm, q);
       const bool ff = !has_core && xm >= FF_RATIO * dx && smin * smin * (EPS_L * 0.999f) >= fmaf(2.0f, q, 1.5f);
       cls = ff ? CLS_FF : lor ? (full ? CLS_LF : CLS_LM) : (full ? CLS_PF : CLS_PM);
+      if (!keep) {                          // below the line-strength bound: no slot
+        cls = -1;
+        needs_fix = false;
+        has_core = false;
+      }
       c0 = make_float4(dx, xc, B * y * bartw::INV_SQRTPI, (float)jcr);
       c1 = make_float4(q - 0.5f, 2.0f * q, q - 1.5f, __uint_as_float(take));
       {
@@ -722,6 +767,33 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
   BART_CUDA(ctx, cudaFuncSetAttribute(opacity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sizeof(OpShared)));
 
+  // line-strength bound (Sec. 4 item 6): the strongest line per cell first.
+  // S depends on T only, so it is found once per distinct temperature.
+  const bool thr = ctx->line_rel > 0.0;
+  void *p_smax = nullptr, *p_tmap = nullptr, *p_tcells = nullptr;
+  std::vector<double> tu;                   // distinct temperatures
+  std::vector<int> tmap(n_cells);           // cell -> index in tu
+  if (thr) {
+    std::vector<int> first;                 // first cell of each distinct temperature
+    for (int c = 0; c < n_cells; ++c) {
+      auto it = std::find(tu.begin(), tu.end(), t[c]);
+      tmap[c] = (int)(it - tu.begin());
+      if (it == tu.end()) {
+        tu.push_back(t[c]);
+        first.push_back(c);
+      }
+    }
+    std::vector<CellConst> hu((size_t)n_species * tu.size());
+    for (int s = 0; s < n_species; ++s)
+      for (size_t u = 0; u < tu.size(); ++u) hu[(size_t)s * tu.size() + u] = hc[(size_t)s * n_cells + first[u]];
+    if ((st = bart_scratch(ctx, "op_smax", tu.size() * sizeof(int), &p_smax)) != BART_OK) return st;
+    if ((st = bart_upload_const(ctx, "op_tmap", tmap.data(), tmap.size() * sizeof(int), &p_tmap)) != BART_OK)
+      return st;
+    if ((st = bart_upload_const(ctx, "op_tcells", hu.data(), hu.size() * sizeof(CellConst), &p_tcells)) != BART_OK)
+      return st;
+  }
+  const float ln_rel = thr ? (float)std::log(ctx->line_rel) : 0.0f;
+
   for (int s = 0; s < n_species; ++s) {
     const bart_linelist& L = species[s];
     float* o = out + (int64_t)s * n_cells * nu.n_nu;
@@ -734,10 +806,21 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
     span_range_kernel<<<(n_spans + 127) / 128, 128, 0, ctx->stream>>>((const int*)p_jlo, (const int*)p_jhi,
                                                                       L.n_lines, n_spans, (SpanRange*)p_spans);
     if ((st = bart_check_launch(ctx, "span_range_kernel")) != BART_OK) return st;
+    if (thr) {
+      // 0x80 bytes: an ordered value below every finite ln S
+      BART_CUDA(ctx, cudaMemsetAsync(p_smax, 0x80, tu.size() * sizeof(int), ctx->stream));
+      if (L.n_lines > 0) {
+        const unsigned gx = (unsigned)std::min<int64_t>((L.n_lines + 255) / 256, 1024);
+        line_smax_kernel<<<dim3(gx, (unsigned)tu.size()), 256, 0, ctx->stream>>>(
+            (const LineWin*)p_win, L.n_lines, (const CellConst*)p_tcells + (size_t)s * tu.size(), (int*)p_smax);
+        if ((st = bart_check_launch(ctx, "line_smax_kernel")) != BART_OK) return st;
+      }
+    }
     dim3 grid((unsigned)n_tiles, (unsigned)n_cells);
     opacity_kernel<<<grid, OP_THREADS, sizeof(OpShared), ctx->stream>>>(
         (const LineWin*)p_win, L.gamma_ref_cm, (const SpanRange*)p_spans,
-        (const CellConst*)p_cells + (size_t)s * n_cells, nu.dnu_cm, nu.n_nu, o, ctx->d_wtable);
+        (const CellConst*)p_cells + (size_t)s * n_cells, nu.dnu_cm, nu.n_nu, o, ctx->d_wtable,
+        thr ? (const int*)p_smax : nullptr, (const int*)p_tmap, ln_rel);
     if ((st = bart_check_launch(ctx, "opacity_kernel")) != BART_OK) return st;
   }
   return BART_OK;

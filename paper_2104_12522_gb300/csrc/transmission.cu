@@ -234,6 +234,7 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
     const int64_t jj = active ? j : lo;
     // extinction at every level, then shell means into shared memory
     float a_prev = 0.f;
+#pragma unroll 2
     for (int k = 0; k < L; ++k) {
       const TrLevel lv = s_lev[k];
       const float* base = grid + ((int64_t)lv.a * M + lv.m) * N + jj;
@@ -278,6 +279,7 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
       float tau[TR_RB];
 #pragma unroll
       for (int r = 0; r < TR_RB; ++r) tau[r] = 0.f;
+#pragma unroll 4
       for (int k = 0; k < kmax; ++k) {
         const float a = s_alpha[k * TR_THREADS + tid];
         const float4 d0 = *reinterpret_cast<const float4*>(s_ds + k * TR_RB);

@@ -171,3 +171,28 @@ def test_autotuned_tiles_give_the_same_spectra(ctx, torch, grid_case):
     for s_, b_ in outs[1:]:
         assert np.array_equal(s_, outs[0][0])
         assert np.allclose(b_, outs[0][1], rtol=1e-6)
+
+
+def test_tau_limit(ctx, torch, grid_case):
+    """Sec. 4 item 7: the layer integration stops where the vertical optical
+    depth exceeds tau_max; parity with the oracle's truncated integration on
+    the batched grid case, and an isothermal atmosphere still gives pi B."""
+    species, p, t, N, dnu, nu, g_dev, g_ora = grid_case
+    theta = W.proposals(7, generation=9, n_species=2)
+    cfg = _cfg(4, [W.BASE_VMR] * 2)
+    cfg["tau_max"] = 3.0
+    spec = torch.empty((7, N), dtype=torch.float32, device="cuda")
+    ctx.forward_spectra_batch(g_dev, p, t, nu, cfg, theta=torch.tensor(theta, device="cuda"), spectra=spec)
+    spec = spec.cpu().numpy()
+    ocfg = dict(g=cfg["g"], t_int=cfg["t_int"], t_star=cfg["t_star"], r_star_tp=cfg["r_star_tp"],
+                a_orbit=cfg["a_orbit"], t_min=500.0, t_max=3000.0, x0=cfg["x0"], mu=cfg["mu"], n_angles=4,
+                tau_max=3.0)
+    nu_ax = W.nu_axis(1000.0, dnu, N)
+    es = max(max_rel(spec[i], Fw.emission_spectrum(g_ora, p, t, nu_ax, theta[i], ocfg)) for i in range(7))
+    print(f"emission with tau_max = 3, FP32 vs FP64: spectra {es:.2e}")
+    assert es < RTOL
+    T = torch.full((2, len(p)), 1500.0, dtype=torch.float32, device="cuda")
+    iso = torch.empty((2, N), dtype=torch.float32, device="cuda")
+    icfg = dict(cfg, t_min=1.0, t_max=1e5)
+    ctx.forward_spectra_batch(g_dev, p, t, nu, icfg, t_profile=T, spectra=iso, n=2)
+    assert max_rel(iso.cpu().numpy(), np.pi * R.planck(nu_ax, 1500.0)[None]) < 1e-5

@@ -176,3 +176,25 @@ def test_opacity_grid_full_size_sampled(ctx, torch):
     assert worst[0] < RTOL_OPACITY and worst[1] < RTOL_ROW_L2
     del grid
     torch.cuda.empty_cache()
+
+
+def test_line_strength_threshold(ctx, torch):
+    """Sec. 4 item 6: lines below rel x the strongest line at each cell are
+    left out; parity with the oracle's thresholded sum, and rel just below 1
+    keeps only the strongest line."""
+    import paper_2104_12522_gb300 as bart
+    w = W.emission_small()
+    dl = [bart.device_lines(s) for s in w.species]
+    nu = bart.NuGrid(w.nu_start, w.dnu, w.n_nu)
+    try:
+        for rel in (1e-3, 0.999):
+            ctx.set_line_threshold(rel)
+            got = ctx.opacity_cells(dl, w.p_bar[::10], w.t_K[::10], nu, w.cutoff).cpu().numpy()
+            ref = O.opacity_cells(w.species, w.p_bar[::10], w.t_K[::10], w.nu_start, w.dnu, w.n_nu, w.cutoff,
+                                  rel_threshold=rel)
+            rel_err, l2 = opacity_errors(got, ref)
+            print(f"opacity with line threshold {rel:g}: max rel {rel_err:.2e}, row L2 {l2:.2e}")
+            assert rel_err < RTOL_OPACITY and l2 < RTOL_ROW_L2
+            assert np.all(got[ref == 0.0] == 0.0)
+    finally:
+        ctx.set_line_threshold(0.0)

@@ -24,7 +24,15 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_abi_version(lib):
-    assert lib.bart_abi_version() == 1
+    import ctypes as C
+    import re
+    from paper_2104_12522_gb300 import _native
+    with open(os.path.join(ROOT, "include", "bartgpu.h")) as fh:
+        version = int(re.search(r"#define BART_ABI_VERSION (\d+)", fh.read()).group(1))
+    assert lib.bart_abi_version() == version == 2
+    # version 2 appended tau_max to bart_fwd_cfg: the binding's struct must match
+    assert C.sizeof(_native.FwdCfg) == 2 * 4 + 11 * 8 + 8 + 8
+    assert _native.FwdCfg.tau_max.offset == C.sizeof(_native.FwdCfg) - 8
 
 
 def test_null_context_is_rejected(lib):

@@ -113,3 +113,49 @@ def test_translation_by_grid_steps():
     S0 = O.line_strength(ll.log10_s296, ll.nu0, ll.elow, T)[0]
     S1 = O.line_strength(sh.log10_s296, sh.nu0, sh.elow, T)[0]
     assert np.max(np.abs(s[k:] / S1 - o[:-k] / S0)) <= 1e-8 * np.max(o / S0)
+
+
+# ---- line-strength bound (Sec. 4 item 6)
+
+def _random_lines(n, seed, lo=1500.0, hi=1510.0):
+    rng = np.random.default_rng(seed)
+    return _lines(np.sort(rng.uniform(lo, hi, n)), rng.uniform(-25, -19, n), rng.uniform(0, 4000, n),
+                  rng.uniform(0.05, 0.1, n))
+
+
+def test_threshold_zero_or_tiny_changes_nothing():
+    ll = _random_lines(40, 31)
+    args = (ll, 0.01, 900.0, 1499.0, 0.01, 1200, 2.0)
+    ref = O.opacity_cell(*args)
+    assert np.array_equal(O.opacity_cell(*args, rel_threshold=0.0), ref)
+    assert np.array_equal(O.opacity_cell(*args, rel_threshold=1e-30), ref)
+
+
+def test_threshold_above_one_leaves_nothing():
+    ll = _random_lines(40, 32)
+    assert np.all(O.opacity_cell(ll, 0.01, 900.0, 1499.0, 0.01, 1200, 2.0, rel_threshold=1.0001) == 0.0)
+
+
+def test_threshold_near_one_keeps_only_the_strongest_line():
+    # The strongest line at this T, found independently of the oracle's own
+    # selection: one-line list through the same point-sampled sum.
+    ll = _random_lines(40, 33)
+    T = 1300.0
+    S = [O.line_strength(ll.log10_s296[i], ll.nu0[i], ll.elow[i], T) for i in range(40)]
+    i = int(np.argmax(S))
+    one = _lines(ll.nu0[i:i + 1], ll.log10_s296[i:i + 1], ll.elow[i:i + 1], ll.gamma_ref[i:i + 1])
+    got = O.opacity_cell(ll, 0.3, T, 1499.0, 0.01, 1200, 2.0, rel_threshold=0.999)
+    exp = O.opacity_cell(one, 0.3, T, 1499.0, 0.01, 1200, 2.0)
+    assert np.array_equal(got, exp)
+
+
+def test_threshold_is_relative_to_each_temperature():
+    # Scaling every strength by the same factor leaves the selection (and the
+    # shape) unchanged: the bound is relative.
+    ll = _random_lines(40, 34)
+    scaled = _lines(ll.nu0, ll.log10_s296 + np.float32(2.0), ll.elow, ll.gamma_ref)
+    a = O.opacity_cell(ll, 0.1, 800.0, 1499.0, 0.01, 1200, 2.0, rel_threshold=1e-3)
+    b = O.opacity_cell(scaled, 0.1, 800.0, 1499.0, 0.01, 1200, 2.0, rel_threshold=1e-3)
+    ok = a > 0
+    assert np.array_equal(ok, b > 0)
+    assert np.allclose(b[ok] / a[ok], 100.0, rtol=1e-12)

@@ -115,3 +115,43 @@ def test_band_on_span_with_no_overlap_is_zero():
     W = np.zeros((1, 100), np.float32)
     W[0, 80:] = 1.0
     assert R.band_integrate(np.ones(30), W, nu_lo=10)[0] == 0.0
+
+
+# ---- optical-depth limit (Sec. 4 item 7)
+
+def test_tau_limit_keeps_isothermal_planck():
+    # The level where the integration stops becomes the blackbody bottom:
+    # an isothermal atmosphere still emits pi B(T) exactly.
+    rng = np.random.default_rng(4)
+    p = np.logspace(-6, 2, 60)
+    nu = np.linspace(1000, 3000, 23)
+    chi = 10 ** rng.uniform(-2, 4, (60, 23))
+    for tau_max in (0.5, 3.0, 20.0):
+        F = R.emission_flux(chi, p, np.full(60, 987.0), nu, 2182.73, 4, tau_max=tau_max)
+        assert np.max(np.abs(F / (np.pi * R.planck(nu, 987.0)) - 1)) < 1e-12
+
+
+def test_tau_limit_equals_truncated_atmosphere():
+    # Opacity constant across wavenumbers: every column stops at the same
+    # level k, and the result is the untruncated flux of levels 0..k.
+    p = np.logspace(-6, 2, 40)
+    T = np.linspace(700, 1600, 40)
+    nu = np.linspace(1000, 3000, 9)
+    chi = np.repeat(np.logspace(-1, 1, 40)[:, None], 9, axis=1)
+    tau = R.optical_depth(chi[:, 0], p, 2182.73)
+    tau_max = 7.0
+    k = int(np.nonzero(tau[1:] > tau_max)[0][0]) + 1
+    got = R.emission_flux(chi, p, T, nu, 2182.73, 8, tau_max=tau_max)
+    exp = R.emission_flux(chi[:k + 1], p[:k + 1], T[:k + 1], nu, 2182.73, 8)
+    assert np.max(np.abs(got / exp - 1)) < 1e-14
+
+
+def test_tau_limit_beyond_the_column_changes_nothing():
+    rng = np.random.default_rng(5)
+    p = np.logspace(-6, 2, 30)
+    T = rng.uniform(600, 1800, 30)
+    nu = np.linspace(1000, 3000, 13)
+    chi = 10 ** rng.uniform(-3, 1, (30, 13))
+    a = R.emission_flux(chi, p, T, nu, 2182.73, 4)
+    b = R.emission_flux(chi, p, T, nu, 2182.73, 4, tau_max=1e300)
+    assert np.max(np.abs(a / b - 1)) < 1e-15
