@@ -470,6 +470,37 @@ def _max_rel(torch, got, ref, floor_frac=1e-6):
     return float(rel.max()) if rel.numel() else 0.0
 
 
+def voigt_table_leg(ctx, torch, stream, grid, ax, nu, d_lines, build0, out, n_w=60, oversample=256):
+    """The paper's Voigt-table scheme (Sec. 4 items 4-5) on the species-0 launch:
+    a table of n_w x n_w widths spanning the workload's Doppler and Lorentz
+    widths, sampled `oversample` times per grid interval; time against the
+    direct launch and error against the direct grid."""
+    import paper_2104_12522_gb300 as bart
+    k, amu, c = 1.380649e-16, 1.66053906660e-24, 2.99792458e10
+    m_lo, m_hi = min(W.SPECIES_MASS_AMU[:grid.shape[0]]), max(W.SPECIES_MASS_AMU[:grid.shape[0]])
+    gref_lo, gref_hi = 0.05, 0.1           # the synthetic line lists' gamma_ref range, cm^-1
+    s_lo = ax.nu_start / c * np.sqrt(k * ax.t_K[0] / (m_hi * amu))
+    s_hi = (ax.nu_start + ax.n_nu * ax.dnu) / c * np.sqrt(k * ax.t_K[-1] / (m_lo * amu))
+    g_lo = gref_lo * ax.p_bar[0] * np.sqrt(296.0 / ax.t_K[-1])
+    g_hi = gref_hi * ax.p_bar[-1] * np.sqrt(296.0 / ax.t_K[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tab = bart.VoigtTable(ctx, n_w, s_lo, s_hi, n_w, g_lo, g_hi, oversample, ax.dnu, ax.cutoff)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fill_ms = e0.elapsed_time(e1)
+    ms0 = _event_ms(torch, stream, build0)
+    ms = _event_ms(torch, stream, lambda: ctx.build_opacity_grid_table(tab, d_lines[:1], ax.p_bar, ax.t_K, nu,
+                                                                      ax.cutoff, out=out))
+    got0, ref0 = out[0].reshape(-1, ax.n_nu), grid[0].reshape(-1, ax.n_nu)
+    l2 = float(torch.linalg.vector_norm(got0 - ref0) / torch.linalg.vector_norm(ref0))
+    res = {"n_sigma": n_w, "n_gamma": n_w, "oversample": oversample, "table_bytes": tab.nbytes,
+           "fill_ms": fill_ms, "ms": ms, "ms_direct": ms0, "speed_vs_direct": ms0 / ms, "grid_rel_l2": l2,
+           "grid_max_rel_err_1e-3": _max_rel(torch, got0, ref0, 1e-3)}
+    tab.close()
+    return res
+
+
 def paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta):
     """Speed-up against accuracy lost of Sec. 4 items 6 and 7 on the bench's
     workload.  (a) The line-strength bound: time of the species-0 launch of
@@ -501,6 +532,7 @@ def paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta):
                                       "grid_rel_l2": l2, "grid_max_rel_err_1e-3": _max_rel(torch, got0, ref0, 1e-3),
                                       "spectra_max_rel_err": _max_rel(torch, spec, spec_ref, 0.0)})
     del full
+    res["voigt_table"] = voigt_table_leg(ctx, torch, stream, grid, ax, nu, d_lines, build0, out)
     ms0 = _event_ms(torch, stream, lambda: run(grid, cfg, spec_ref))
     for tau_max in (30.0, 10.0, 3.0):
         c = dict(cfg, tau_max=tau_max)

@@ -150,6 +150,45 @@ bart_status bart_build_opacity_grid(bart_ctx* ctx, const bart_linelist* species,
                                     const double* t_K, int n_temps,
                                     bart_nugrid nu, double cutoff_cm, float* grid);
 
+/* ------------------------------------------- the paper's Voigt-table scheme */
+
+/* The opacity scheme of Sec. 4 items 4-5 and Sec. 5.1.1 (test f04broadening):
+ * Voigt profiles tabulated once for a grid of widths and read by every line.
+ *   n_sigma Doppler widths (Gaussian standard deviations, cm^-1) log-spaced
+ *   from sigma_lo to sigma_hi, n_gamma Lorentz half widths (cm^-1) log-spaced
+ *   from gamma_lo to gamma_hi; each profile sampled `oversample` times per grid
+ *   interval dnu_cm, aligned to the grid, out to cutoff_cm (plus one interval).
+ * A line at a cell uses the profile of the nearest widths in ln sigma and
+ * ln gamma (clamped to the bounds), its centre rounded to the nearest fine
+ * sample, read at the grid points within |nu_j - nu0| <= cutoff of its exact
+ * centre; strengths as in bart_opacity_cells.  The profile values come from
+ * the same FP32 Faddeeva evaluation as the direct sum.  The table occupies
+ * n_sigma n_gamma oversample (2 ceil(cutoff/dnu) + 3) x 4 bytes of device
+ * memory on the context's device, owned by the table until
+ * bart_voigt_table_destroy.  The line-strength bound is not applied on this
+ * path.  Returns BART_EINVAL for non-positive or inverted bounds, counts < 1
+ * or a table above 200 GB, BART_ENOMEM if the device memory is missing. */
+typedef struct bart_voigt_table bart_voigt_table;
+bart_status bart_voigt_table_create(bart_ctx* ctx, int n_sigma, double sigma_lo, double sigma_hi,
+                                    int n_gamma, double gamma_lo, double gamma_hi, int oversample,
+                                    double dnu_cm, double cutoff_cm, bart_voigt_table** out);
+void bart_voigt_table_destroy(bart_voigt_table* table);
+/* Device bytes held by the table (-1 for NULL). */
+int64_t bart_voigt_table_bytes(const bart_voigt_table* table);
+
+/* bart_opacity_cells and bart_build_opacity_grid with the table scheme; same
+ * arguments and layouts plus the table, which must have been built on this
+ * context's device for the same dnu and a cutoff >= cutoff_cm (else
+ * BART_EINVAL). */
+bart_status bart_opacity_cells_table(bart_ctx* ctx, const bart_voigt_table* table,
+                                     const bart_linelist* species, int n_species, const double* p_bar,
+                                     const double* t_K, int n_cells, bart_nugrid nu, double cutoff_cm,
+                                     float* out);
+bart_status bart_build_opacity_grid_table(bart_ctx* ctx, const bart_voigt_table* table,
+                                          const bart_linelist* species, int n_species,
+                                          const double* p_bar, int n_layers, const double* t_K, int n_temps,
+                                          bart_nugrid nu, double cutoff_cm, float* grid);
+
 /* Line-strength lower bound of Sec. 4 item 6 for the following
  * bart_opacity_cells / bart_build_opacity_grid calls on this context: at each
  * (P, T) cell, a line whose strength S_i(T) is below rel times the strongest

@@ -191,6 +191,35 @@ class Context:
                                                      p.size, _dbl(t), t.size, nu, float(cutoff), _ptr(out)))
         return out
 
+    def opacity_cells_table(self, table, species, p_bar, t_K, nu, cutoff, out=None):
+        """bart_opacity_cells_table: the paper's Voigt-table scheme."""
+        import torch
+        p = np.asarray(p_bar, np.float64)
+        t = np.asarray(t_K, np.float64)
+        if p.shape != t.shape or p.ndim != 1:
+            raise ValueError("p_bar and t_K must be 1-D of equal length")
+        shape = (len(species), p.size, int(nu.n_nu))
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=species[0].nu0.device)
+        _check_tensor(out, "float32", int(np.prod(shape)))
+        self._check(self.lib.bart_opacity_cells_table(self.h, table.h, self._lists(species), len(species), _dbl(p),
+                                                      _dbl(t), p.size, nu, float(cutoff), _ptr(out)))
+        return out
+
+    def build_opacity_grid_table(self, table, species, p_bar, t_K, nu, cutoff, out=None):
+        """bart_build_opacity_grid_table: the grid with the paper's Voigt-table scheme."""
+        import torch
+        p = np.asarray(p_bar, np.float64)
+        t = np.asarray(t_K, np.float64)
+        shape = (len(species), p.size, t.size, int(nu.n_nu))
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=species[0].nu0.device)
+        _check_tensor(out, "float32", int(np.prod(shape)))
+        self._check(self.lib.bart_build_opacity_grid_table(self.h, table.h, self._lists(species), len(species),
+                                                           _dbl(p), p.size, _dbl(t), t.size, nu, float(cutoff),
+                                                           _ptr(out)))
+        return out
+
     # ------------------------------------------------------------ forward model
     def forward_spectra_batch(self, grid, p_bar, t_K, nu, cfg: dict, theta=None, t_profile=None,
                               n_levels=None, nu_lo=None, nu_hi=None, spec_offsets=None, r_planet=None,
@@ -339,6 +368,38 @@ class Mlp:
         self.ctx._check(self.lib.bart_mlp_train_step(self.h, _ptr(x), _ptr(t), int(x.shape[0]), float(lr),
                                                      _ptr(loss)))
         return loss
+
+
+class VoigtTable:
+    """Precomputed Voigt profiles of the paper's table scheme (bart_voigt_table_*)
+    on a context's device; widths in cm^-1, log-spaced between the bounds."""
+
+    def __init__(self, ctx: Context, n_sigma, sigma_lo, sigma_hi, n_gamma, gamma_lo, gamma_hi, oversample, dnu,
+                 cutoff):
+        self.ctx, self.lib = ctx, ctx.lib
+        h = C.c_void_p()
+        ctx._check(self.lib.bart_voigt_table_create(ctx.h, int(n_sigma), float(sigma_lo), float(sigma_hi),
+                                                    int(n_gamma), float(gamma_lo), float(gamma_hi), int(oversample),
+                                                    float(dnu), float(cutoff), C.byref(h)))
+        self.h = h
+        self.spec = dict(n_sigma=int(n_sigma), sigma_lo=float(sigma_lo), sigma_hi=float(sigma_hi),
+                         n_gamma=int(n_gamma), gamma_lo=float(gamma_lo), gamma_hi=float(gamma_hi),
+                         oversample=int(oversample))
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.lib.bart_voigt_table_bytes(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bart_voigt_table_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Demc:

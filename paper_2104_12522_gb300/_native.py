@@ -67,6 +67,14 @@ SIGNATURES = {
     "bart_sync": (c_int, [c_void_p]),
     "bart_set_autotune": (c_int, [c_void_p, c_int]),
     "bart_set_line_threshold": (c_int, [c_void_p, c_double]),
+    "bart_voigt_table_create": (c_int, [c_void_p, c_int, c_double, c_double, c_int, c_double, c_double, c_int,
+                                        c_double, c_double, c_void_p]),
+    "bart_voigt_table_destroy": (None, [c_void_p]),
+    "bart_voigt_table_bytes": (c_int64, [c_void_p]),
+    "bart_opacity_cells_table": (c_int, [c_void_p, c_void_p, P(LineList), c_int, P(c_double), P(c_double), c_int,
+                                         NuGrid, c_double, c_void_p]),
+    "bart_build_opacity_grid_table": (c_int, [c_void_p, c_void_p, P(LineList), c_int, P(c_double), c_int,
+                                              P(c_double), c_int, NuGrid, c_double, c_void_p]),
     "bart_autotune_report": (c_int, [c_void_p, C.c_char_p, c_int]),
     "bart_opacity_cells": (c_int, [c_void_p, P(LineList), c_int, P(c_double), P(c_double), c_int, NuGrid,
                                    c_double, c_void_p]),

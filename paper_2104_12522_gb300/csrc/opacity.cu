@@ -826,6 +826,244 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
   return BART_OK;
 }
 
+// ------------------------------------------------------------------------
+// The paper's own scheme (Sec. 4 items 4-5, Sec. 5.1.1): a precomputed table
+// of Voigt profiles on a grid of Doppler and Lorentz widths, each sampled
+// `oversample` times per grid interval and aligned to the grid; a line takes
+// the profile of the nearest widths (in ln sigma and ln gamma), with its
+// centre rounded to the nearest fine sample, and reads it at the grid points
+// inside the same cutoff window as the direct sum.
+//
+// Layout: data[is][ig][r][k], r = 0 .. O-1 the fine offset, k = 0 .. 2 KK the
+// grid offset, value V(((k - KK) + r / O) dnu; sigma_is, gamma_ig).  A line
+// whose quantised centre is s fine samples from nu_start (s = jc O - r,
+// 0 <= r < O) reads data[is][ig][r][j - jc + KK] at grid point j: a warp's
+// consecutive points are consecutive floats.
+
+__global__ void table_fill_kernel(float* __restrict__ data, int n_sigma, double ln_slo, double sstep, int n_gamma,
+                                  double ln_glo, double gstep, int O, int kk, double dnu,
+                                  const float2* __restrict__ wtab) {
+  const int nk = 2 * kk + 1;
+  const int64_t total = (int64_t)n_sigma * n_gamma * O * nk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % nk);
+    int64_t rest = e / nk;
+    const int r = (int)(rest % O);
+    rest /= O;
+    const int ig = (int)(rest % n_gamma);
+    const int is = (int)(rest / n_gamma);
+    const double sigma = exp(ln_slo + is * sstep), gamma = exp(ln_glo + ig * gstep);
+    const double d = ((double)(k - kk) + (double)r / O) * dnu;
+    const double inv = 1.0 / (sigma * 1.4142135623730951);
+    const float v = bartw::faddeeva_re((float)(d * inv), (float)(gamma * inv), wtab);
+    data[e] = (float)(v * inv * 0.56418958354775628695);   // Re w / (sigma sqrt(2 pi))
+  }
+}
+
+struct TabLine {            // per line, cell independent
+  double ln_nu0, ln_gref;   // for the nearest-width choice (FP64)
+  int jc, r;                // quantised centre s = jc O - r
+};
+
+__global__ void table_line_kernel(const double* __restrict__ nu0, const float* __restrict__ gref, int64_t n_lines,
+                                  double nu_start, double dnu, int O, TabLine* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_lines) return;
+  const double c = nu0[i];
+  const double big = 1073741824.0;
+  const double s = fmin(fmax(floor((c - nu_start) * O / dnu + 0.5), -big * O), big * O);
+  const double jc = ceil(s / O);
+  TabLine t;
+  t.ln_nu0 = log(c);
+  t.ln_gref = log((double)gref[i]);
+  t.jc = (int)jc;
+  t.r = (int)(jc * O - s);
+  out[i] = t;
+}
+
+struct TabCell {            // per (species, cell), FP64
+  double ln_sfac;           // ln(sigma / nu0) = ln(sqrt(k T / m) / c)
+  double ln_gfac;           // ln(gamma / gamma_ref) = ln(P sqrt(296 / T))
+};
+
+struct TabSpec {
+  int n_sigma, n_gamma, O, kk;
+  double ln_slo, inv_sstep, ln_glo, inv_gstep;
+};
+
+__device__ __forceinline__ int nearest_index(double v, double lo, double inv_step, int n) {
+  if (n == 1) return 0;
+  const double k = floor((v - lo) * inv_step + 0.5);
+  return (int)fmin(fmax(k, 0.0), (double)(n - 1));
+}
+
+// One warp per (cell, 512-point span), lane l owns points w0 + 32 q + l
+// (q = 0 .. 15, coalesced table reads); partial sums over 4 chunks of 32
+// lines folded into a TwoSum pair; terms at the 2^100 scale as in the direct
+// kernel.
+__global__ void __launch_bounds__(OP_THREADS)
+table_opacity_kernel(const LineWin* __restrict__ win, const TabLine* __restrict__ tl,
+                     const SpanRange* __restrict__ spans, const CellConst* __restrict__ cells,
+                     const TabCell* __restrict__ tcells, TabSpec ts, const float* __restrict__ data, int64_t n_nu,
+                     float* __restrict__ out) {
+  __shared__ long long s_row[OP_WARPS][32];
+  __shared__ float s_S[OP_WARPS][32];
+  __shared__ int2 s_win[OP_WARPS][32];
+  __shared__ int s_kofs[OP_WARPS][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w0l = ((int64_t)blockIdx.x * OP_WARPS + warp) * OP_SPAN;
+  if (w0l >= n_nu) return;
+  const int w0 = (int)w0l;
+  const int cell = blockIdx.y;
+  const CellConst cc = cells[cell];
+  const TabCell tc = tcells[cell];
+  const SpanRange rg = spans[blockIdx.x * OP_WARPS + warp];
+  const int64_t nk = 2 * ts.kk + 1;
+  float acc[OP_R], hi[OP_R], lo[OP_R];
+#pragma unroll
+  for (int q = 0; q < OP_R; ++q) { acc[q] = 0.f; hi[q] = 0.f; lo[q] = 0.f; }
+  int chunks = 0;
+  for (int64_t base = rg.i_lo; base < rg.i_hi; base += 32) {
+    const int nl = (int)min((int64_t)32, rg.i_hi - base);
+    if (lane < nl) {
+      const int64_t i = base + lane;
+      const LineWin w = win[i];
+      const TabLine t = tl[i];
+      const int is = nearest_index(t.ln_nu0 + tc.ln_sfac, ts.ln_slo, ts.inv_sstep, ts.n_sigma);
+      const int ig = nearest_index(t.ln_gref + tc.ln_gfac, ts.ln_glo, ts.inv_gstep, ts.n_gamma);
+      // element read at grid point j: row + (j - jc + kk), the grid offset
+      // kept inside the profile row [0, 2 kk] (it is by construction)
+      s_row[warp][lane] = (((long long)is * ts.n_gamma + ig) * ts.O + t.r) * nk;
+      s_kofs[warp][lane] = ts.kk - t.jc;
+      s_S[warp][lane] = ex2f_approx((line_ln_s(w, cc) + LN_SCALE) * LOG2EF);
+      s_win[warp][lane] = make_int2(w.jlo, w.jhi);
+    }
+    __syncwarp();
+    for (int l = 0; l < nl; ++l) {
+      const long long row = s_row[warp][l];
+      const float S = s_S[warp][l];
+      const int2 wn = s_win[warp][l];
+      const int kofs = s_kofs[warp][l];
+#pragma unroll
+      for (int q = 0; q < OP_R; ++q) {
+        const int j = w0 + 32 * q + lane;
+        const int k = min(max(j + kofs, 0), (int)nk - 1);
+        if (j >= wn.x && j <= wn.y) acc[q] = fmaf(S, __ldg(data + (row + k)), acc[q]);
+      }
+    }
+    __syncwarp();
+    if (++chunks == 4 || base + 32 >= rg.i_hi) {
+      chunks = 0;
+#pragma unroll
+      for (int q = 0; q < OP_R; ++q) {
+        const float sum = hi[q] + acc[q];
+        const float bp = sum - hi[q];
+        lo[q] += (hi[q] - (sum - bp)) + (acc[q] - bp);
+        hi[q] = sum;
+        acc[q] = 0.f;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < OP_R; ++q) {
+    const int64_t j = (int64_t)w0 + 32 * q + lane;
+    if (j < n_nu) out[(int64_t)cell * n_nu + j] = (hi[q] + lo[q]) * INV_SCALE;
+  }
+}
+
+}  // namespace
+
+struct bart_voigt_table {
+  int device = 0;
+  int n_sigma = 0, n_gamma = 0, oversample = 0, kk = 0;
+  double sigma_lo = 0, sigma_hi = 0, gamma_lo = 0, gamma_hi = 0, dnu = 0, cutoff = 0;
+  float* data = nullptr;
+  size_t bytes = 0;
+};
+
+namespace {
+
+TabSpec table_spec(const bart_voigt_table* t) {
+  TabSpec ts;
+  ts.n_sigma = t->n_sigma;
+  ts.n_gamma = t->n_gamma;
+  ts.O = t->oversample;
+  ts.kk = t->kk;
+  ts.ln_slo = std::log(t->sigma_lo);
+  ts.ln_glo = std::log(t->gamma_lo);
+  ts.inv_sstep = t->n_sigma > 1 ? (t->n_sigma - 1) / (std::log(t->sigma_hi) - std::log(t->sigma_lo)) : 0.0;
+  ts.inv_gstep = t->n_gamma > 1 ? (t->n_gamma - 1) / (std::log(t->gamma_hi) - std::log(t->gamma_lo)) : 0.0;
+  return ts;
+}
+
+bart_status run_cells_table(bart_ctx* ctx, const bart_voigt_table* tab, const bart_linelist* species,
+                            int n_species, const std::vector<double>& p, const std::vector<double>& t,
+                            bart_nugrid nu, double cutoff, float* out) {
+  const int n_cells = (int)p.size();
+  BART_REQUIRE(ctx, n_cells >= 1 && n_cells <= 65535, "n_cells must be in [1, 65535]");
+  BART_REQUIRE(ctx, tab->device == ctx->device, "the table lives on another device");
+  BART_REQUIRE(ctx, std::fabs(tab->dnu - nu.dnu_cm) <= 1e-12 * nu.dnu_cm && tab->cutoff >= cutoff,
+               "the table was built for another grid spacing or a smaller cutoff");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  int64_t max_lines = 0;
+  for (int s = 0; s < n_species; ++s) max_lines = std::max(max_lines, species[s].n_lines);
+  const size_t nl = (size_t)std::max<int64_t>(max_lines, 1);
+  const int64_t n_tiles = (nu.n_nu + OP_TILE - 1) / OP_TILE;
+  const int n_spans = (int)(n_tiles * OP_WARPS);
+  void *p_jlo, *p_jhi, *p_win, *p_spans, *p_tl, *p_cells, *p_tcells;
+  bart_status st;
+  if ((st = bart_scratch(ctx, "op_jlo", nl * sizeof(int), &p_jlo)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "op_jhi", nl * sizeof(int), &p_jhi)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "op_win", nl * sizeof(LineWin), &p_win)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "op_spans", (size_t)n_spans * sizeof(SpanRange), &p_spans)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "tb_lines", nl * sizeof(TabLine), &p_tl)) != BART_OK) return st;
+  std::vector<CellConst> hc((size_t)n_species * n_cells);
+  std::vector<TabCell> ht((size_t)n_species * n_cells);
+  for (int s = 0; s < n_species; ++s)
+    for (int c = 0; c < n_cells; ++c) {
+      const double T = t[c], P = p[c];
+      CellConst k;
+      k.inv_t = (float)(1.0 / T);
+      k.ln_q = (float)(1.5 * std::log(bartc::TREF / T));
+      k.gfac = (float)(P * std::sqrt(bartc::TREF / T));
+      k.dfac = (float)(std::sqrt(2.0 * bartc::KB * T / (species[s].mass_amu * bartc::AMU)) / bartc::C);
+      k.c2_t = (float)(bartc::C2 / T);
+      hc[(size_t)s * n_cells + c] = k;
+      TabCell q;
+      q.ln_sfac = std::log(std::sqrt(bartc::KB * T / (species[s].mass_amu * bartc::AMU)) / bartc::C);
+      q.ln_gfac = std::log(P * std::sqrt(bartc::TREF / T));
+      ht[(size_t)s * n_cells + c] = q;
+    }
+  if ((st = bart_upload_const(ctx, "tb_cells", hc.data(), hc.size() * sizeof(CellConst), &p_cells)) != BART_OK)
+    return st;
+  if ((st = bart_upload_const(ctx, "tb_tcells", ht.data(), ht.size() * sizeof(TabCell), &p_tcells)) != BART_OK)
+    return st;
+  const TabSpec ts = table_spec(tab);
+  for (int s = 0; s < n_species; ++s) {
+    const bart_linelist& L = species[s];
+    float* o = out + (int64_t)s * n_cells * nu.n_nu;
+    if (L.n_lines > 0) {
+      const unsigned gl = (unsigned)((L.n_lines + 255) / 256);
+      line_window_kernel<<<gl, 256, 0, ctx->stream>>>(L.nu0_cm, L.log10_s296, L.elow_cm, L.n_lines, nu.nu_start_cm,
+                                                      nu.dnu_cm, nu.n_nu, cutoff, (int*)p_jlo, (int*)p_jhi,
+                                                      (LineWin*)p_win);
+      if ((st = bart_check_launch(ctx, "line_window_kernel")) != BART_OK) return st;
+      table_line_kernel<<<gl, 256, 0, ctx->stream>>>(L.nu0_cm, L.gamma_ref_cm, L.n_lines, nu.nu_start_cm,
+                                                     nu.dnu_cm, tab->oversample, (TabLine*)p_tl);
+      if ((st = bart_check_launch(ctx, "table_line_kernel")) != BART_OK) return st;
+    }
+    span_range_kernel<<<(n_spans + 127) / 128, 128, 0, ctx->stream>>>((const int*)p_jlo, (const int*)p_jhi,
+                                                                      L.n_lines, n_spans, (SpanRange*)p_spans);
+    if ((st = bart_check_launch(ctx, "span_range_kernel")) != BART_OK) return st;
+    table_opacity_kernel<<<dim3((unsigned)n_tiles, (unsigned)n_cells), OP_THREADS, 0, ctx->stream>>>(
+        (const LineWin*)p_win, (const TabLine*)p_tl, (const SpanRange*)p_spans,
+        (const CellConst*)p_cells + (size_t)s * n_cells, (const TabCell*)p_tcells + (size_t)s * n_cells, ts,
+        tab->data, nu.n_nu, o);
+    if ((st = bart_check_launch(ctx, "table_opacity_kernel")) != BART_OK) return st;
+  }
+  return BART_OK;
+}
+
 }  // namespace
 
 extern "C" bart_status bart_opacity_cells(bart_ctx* ctx, const bart_linelist* species, int n_species,
@@ -870,4 +1108,109 @@ extern "C" bart_status bart_build_opacity_grid(bart_ctx* ctx, const bart_linelis
       t.push_back(t_K[m]);
     }
   return run_cells(ctx, species, n_species, p, t, nu, cutoff_cm, grid);
+}
+
+extern "C" bart_status bart_voigt_table_create(bart_ctx* ctx, int n_sigma, double sigma_lo, double sigma_hi,
+                                               int n_gamma, double gamma_lo, double gamma_hi, int oversample,
+                                               double dnu_cm, double cutoff_cm, bart_voigt_table** out) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, out != nullptr, "out is NULL");
+  *out = nullptr;
+  BART_REQUIRE(ctx, n_sigma >= 1 && n_gamma >= 1 && oversample >= 1, "n_sigma, n_gamma, oversample must be >= 1");
+  BART_REQUIRE(ctx, sigma_lo > 0 && sigma_hi >= sigma_lo && gamma_lo > 0 && gamma_hi >= gamma_lo &&
+                        std::isfinite(sigma_hi) && std::isfinite(gamma_hi),
+               "need 0 < sigma_lo <= sigma_hi and 0 < gamma_lo <= gamma_hi");
+  BART_REQUIRE(ctx, dnu_cm > 0 && cutoff_cm > 0 && std::isfinite(dnu_cm) && std::isfinite(cutoff_cm),
+               "dnu and cutoff must be > 0");
+  const double kkd = std::ceil(cutoff_cm / dnu_cm) + 1.0;
+  BART_REQUIRE(ctx, kkd < 1e8, "cutoff / dnu is too large");
+  const int kk = (int)kkd;
+  const double n_el = (double)n_sigma * n_gamma * oversample * (2.0 * kk + 1.0);
+  BART_REQUIRE(ctx, n_el * 4.0 < 2.0e11, "the table would exceed 200 GB");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  bart_status st = bart_ensure_wtable(ctx);
+  if (st != BART_OK) return st;
+  auto* t = new bart_voigt_table;
+  t->device = ctx->device;
+  t->n_sigma = n_sigma;
+  t->n_gamma = n_gamma;
+  t->oversample = oversample;
+  t->kk = kk;
+  t->sigma_lo = sigma_lo;
+  t->sigma_hi = sigma_hi;
+  t->gamma_lo = gamma_lo;
+  t->gamma_hi = gamma_hi;
+  t->dnu = dnu_cm;
+  t->cutoff = cutoff_cm;
+  t->bytes = (size_t)n_el * sizeof(float);
+  cudaError_t e = cudaMalloc(&t->data, t->bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete t;
+    return bart_fail(ctx, BART_ENOMEM, "cudaMalloc of %zu bytes for the Voigt table failed", (size_t)n_el * 4);
+  }
+  const TabSpec ts = table_spec(t);
+  table_fill_kernel<<<(unsigned)std::min<double>(std::ceil(n_el / 256.0), 152.0 * 64.0), 256, 0, ctx->stream>>>(
+      t->data, n_sigma, ts.ln_slo, n_sigma > 1 ? 1.0 / ts.inv_sstep : 0.0, n_gamma, ts.ln_glo,
+      n_gamma > 1 ? 1.0 / ts.inv_gstep : 0.0, oversample, kk, dnu_cm, ctx->d_wtable);
+  if ((st = bart_check_launch(ctx, "table_fill_kernel")) != BART_OK) {
+    cudaFree(t->data);
+    delete t;
+    return st;
+  }
+  *out = t;
+  return BART_OK;
+}
+
+extern "C" void bart_voigt_table_destroy(bart_voigt_table* t) {
+  if (!t) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(t->device);
+  cudaFree(t->data);
+  cudaSetDevice(cur);
+  delete t;
+}
+
+extern "C" int64_t bart_voigt_table_bytes(const bart_voigt_table* t) { return t ? (int64_t)t->bytes : -1; }
+
+extern "C" bart_status bart_opacity_cells_table(bart_ctx* ctx, const bart_voigt_table* table,
+                                                const bart_linelist* species, int n_species, const double* p_bar,
+                                                const double* t_K, int n_cells, bart_nugrid nu, double cutoff_cm,
+                                                float* out) {
+  if (!ctx) return BART_EINVAL;
+  bart_status st;
+  BART_REQUIRE(ctx, table != nullptr, "table is NULL");
+  if ((st = validate_lists(ctx, species, n_species)) != BART_OK) return st;
+  if ((st = validate_grid(ctx, nu, cutoff_cm)) != BART_OK) return st;
+  BART_REQUIRE(ctx, p_bar && t_K && out, "NULL p_bar, t_K or out");
+  BART_REQUIRE(ctx, n_cells >= 1, "n_cells must be >= 1");
+  std::vector<double> p(p_bar, p_bar + n_cells), t(t_K, t_K + n_cells);
+  for (int c = 0; c < n_cells; ++c)
+    BART_REQUIRE(ctx, p[c] > 0 && t[c] > 0 && std::isfinite(p[c]) && std::isfinite(t[c]),
+                 "cell %d: P and T must be > 0 and finite", c);
+  for (int s = 0; s < n_species; ++s)
+    BART_REQUIRE(ctx, species[s].gamma_ref_cm || species[s].n_lines == 0, "species %d: NULL widths", s);
+  return run_cells_table(ctx, table, species, n_species, p, t, nu, cutoff_cm, out);
+}
+
+extern "C" bart_status bart_build_opacity_grid_table(bart_ctx* ctx, const bart_voigt_table* table,
+                                                     const bart_linelist* species, int n_species,
+                                                     const double* p_bar, int n_layers, const double* t_K,
+                                                     int n_temps, bart_nugrid nu, double cutoff_cm, float* grid) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, p_bar && t_K && grid, "NULL p_bar, t_K or grid");
+  BART_REQUIRE(ctx, n_layers >= 1 && n_temps >= 1, "n_layers and n_temps must be >= 1");
+  for (int k = 0; k < n_layers; ++k)
+    BART_REQUIRE(ctx, p_bar[k] > 0 && (k == 0 || p_bar[k] > p_bar[k - 1]), "p_bar must be > 0 and increasing");
+  for (int m = 0; m < n_temps; ++m)
+    BART_REQUIRE(ctx, t_K[m] > 0 && (m == 0 || t_K[m] > t_K[m - 1]), "t_K must be > 0 and increasing");
+  std::vector<double> p, t;
+  for (int k = 0; k < n_layers; ++k)
+    for (int m = 0; m < n_temps; ++m) {
+      p.push_back(p_bar[k]);
+      t.push_back(t_K[m]);
+    }
+  return bart_opacity_cells_table(ctx, table, species, n_species, p.data(), t.data(), (int)p.size(), nu, cutoff_cm,
+                                  grid);
 }

@@ -198,3 +198,29 @@ def test_line_strength_threshold(ctx, torch):
             assert np.all(got[ref == 0.0] == 0.0)
     finally:
         ctx.set_line_threshold(0.0)
+
+
+def test_voigt_table_scheme(ctx, torch):
+    """Sec. 4 items 4-5: the paper's table of Voigt profiles (nearest widths,
+    centre on the nearest fine sample); parity with the oracle's statement of
+    the same scheme, on the small emission workload's lines at three cells."""
+    import paper_2104_12522_gb300 as bart
+    from oracle import voigt_table as VT
+    w = W.emission_small()
+    cells = [0, 30, 59]
+    p, t = w.p_bar[cells], w.t_K[cells]
+    sig = np.concatenate([O.doppler_sigma(s.nu0, T, s.mass_amu) for s in w.species for T in t])
+    gam = np.concatenate([O.lorentz_gamma(s.gamma_ref, P, T) for s in w.species for P, T in zip(p, t)])
+    tab = bart.VoigtTable(ctx, 20, sig.min(), sig.max(), 20, gam.min(), gam.max(), 16, w.dnu, w.cutoff)
+    nu = bart.NuGrid(w.nu_start, w.dnu, w.n_nu)
+    got = ctx.opacity_cells_table(tab, [bart.device_lines(s) for s in w.species], p, t, nu, w.cutoff)
+    got = got.cpu().numpy()
+    ref = VT.opacity_cells_table(w.species, p, t, w.nu_start, w.dnu, w.n_nu, w.cutoff, tab.spec)
+    rel, l2 = opacity_errors(got, ref)
+    exact = O.opacity_cells(w.species, p, t, w.nu_start, w.dnu, w.n_nu, w.cutoff)
+    scheme, _ = opacity_errors(ref, exact)
+    print(f"Voigt-table scheme: GPU vs oracle max rel {rel:.2e}, row L2 {l2:.2e}; "
+          f"the scheme itself vs the exact sum (20 x 20 widths, 16 samples per interval): {scheme:.2e}")
+    assert rel < RTOL_OPACITY and l2 < RTOL_ROW_L2
+    assert tab.nbytes == 20 * 20 * 16 * (2 * (int(np.ceil(w.cutoff / w.dnu)) + 1) + 1) * 4
+    tab.close()
