@@ -363,7 +363,8 @@ bart_status bart_mlp_train_step(bart_mlp* net, const float* x, const float* t, i
  * bart_demc_set_screen), stage 2 accepts a survivor with probability
  * min(1, exp(L_y - L_x) a1(y -> x) / a1(x -> y)) from the exact
  * log-likelihood, which keeps the exact posterior as the target.
- * 6 <= n_chains <= 65536, 1 <= n_params <= 32. */
+ * 3 <= n_chains <= 65536 (DE-MC proposals need >= 6, DEMCzs >= 3),
+ * 1 <= n_params <= 32. */
 typedef struct bart_demc bart_demc;
 bart_status bart_demc_create(bart_ctx* ctx, int n_chains, int n_params, const float* lo, const float* hi,
                              double gamma, int jump_every, double eps, uint64_t seed, bart_demc** out);
@@ -391,6 +392,38 @@ bart_status bart_demc_screen(bart_demc* s, int64_t half_step, const int32_t* inb
  * accepted device [n_chains] or NULL. */
 bart_status bart_demc_accept(bart_demc* s, int64_t half_step, const float* y, const int32_t* pass,
                              const double* L_y, const double* ls_y, int32_t* accepted);
+/* Switches the sampler to DEMCzs (Sec. 4; ter Braak & Vrugt 2008): every
+ * chain proposes from an archive Z of past states, so all chains move at each
+ * half_step.  With probability p_snooker the move is a snooker update, z, z1,
+ * z2 drawn from Z, y = x + g ((z1 - z2) . e) e with e the unit vector from z
+ * to x and g uniform in [1.2, 2.2), accepted with the extra factor
+ * (|y - z| / |x - z|)^(d - 1) (also inside the screen's two stages);
+ * otherwise y = x + gamma (z1 - z2) + eps (hi - lo) N(0, 1).  Every `thin`
+ * half_steps bart_demc_accept appends all chains' states to Z while it holds
+ * fewer than `capacity` states (then it stops growing).
+ *   z0  device [n0][n_params], the initial archive (copied), 3 <= n0 <= capacity
+ * The archive (capacity x n_params x 4 bytes) is device memory owned by the
+ * sampler.  Returns BART_EINVAL for bad sizes or p_snooker outside [0, 1],
+ * BART_ENOMEM if the archive cannot be allocated. */
+bart_status bart_demc_set_archive(bart_demc* s, const float* z0, int64_t n0, int64_t capacity, int thin,
+                                  double p_snooker);
+/* Number of states in the DEMCzs archive (0 for a DE-MC sampler); waits for
+ * the stream. */
+bart_status bart_demc_archive_size(bart_demc* s, int64_t* n);
+
+/* Convergence and sample-size statistics of Sec. 4 and App. C on a chain
+ * history chain[t][c][q] (device, n x n_chains x n_params FP32):
+ *   speis  device [n_chains][n_params] or NULL: steps per effectively
+ *          independent sample, 1 + 2 sum_k rho_k over lags k >= 1 until the
+ *          autocorrelation rho_k first falls below `threshold` (lags < n/2);
+ *          ESS = n n_chains / (largest over parameters of the mean over chains)
+ *   gr     device [n_params] or NULL: Gelman-Rubin R, sqrt(V / W) with W the
+ *          mean within-chain variance, B = n x the variance of the chain
+ *          means, V = (n - 1)/n W + B/n (needs n_chains >= 2).
+ * Returns BART_EINVAL for n < 4 or empty shapes. */
+bart_status bart_chain_stats(bart_ctx* ctx, const float* chain, int n, int n_chains, int n_params,
+                             double threshold, double* speis, double* gr);
+
 /* Gaussian log-likelihood of band values (Sec. 3: model bands compared to
  * data): out[i] = -1/2 sum_b ((model[i][b] - data[b]) / sigma[b])^2 in FP64,
  * -inf where mask[i] == 0 (mask may be NULL).  model device [n][n_bands];

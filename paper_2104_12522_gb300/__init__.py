@@ -274,6 +274,17 @@ class Context:
                                                 _ptr(chain), C.byref(st)))
         return {k: getattr(st, k) for k, _ in _native.RetrievalStats._fields_}
 
+    def chain_stats(self, chain, threshold=0.01, speis=True, gr=True):
+        """SPEIS [C][d], Gelman-Rubin R [d] and ESS of chain [n][C][d] (device)."""
+        import torch
+        n, Cn, d = (int(v) for v in chain.shape)
+        _check_tensor(chain, "float32", n * Cn * d)
+        sp = torch.empty((Cn, d), dtype=torch.float64, device=chain.device) if speis else None
+        g = torch.empty(d, dtype=torch.float64, device=chain.device) if gr else None
+        self._check(self.lib.bart_chain_stats(self.h, _ptr(chain), n, Cn, d, float(threshold), _ptr(sp), _ptr(g)))
+        ess = n * Cn / float(sp.mean(0).max()) if speis else None
+        return sp, g, ess
+
     def loglike_bands(self, model, data, sigma, out, mask=None):
         """out[i] = -1/2 sum_b ((model[i][b] - data[b]) / sigma[b])^2 (FP64)."""
         n, nb = (int(v) for v in model.shape)
@@ -433,6 +444,18 @@ class Demc:
     def get_state(self, x=None, loglike=None, loglike_s=None):
         self.ctx._check(self.lib.bart_demc_get_state(self.h, _ptr(x), _ptr(loglike), _ptr(loglike_s)))
         return x, loglike, loglike_s
+
+    def set_archive(self, z0, capacity, thin=10, p_snooker=0.1):
+        """Switch to DEMCzs with the initial archive z0 (device [n0][d])."""
+        n0 = int(z0.shape[0])
+        _check_tensor(z0, "float32", n0 * self.d)
+        self.ctx._check(self.lib.bart_demc_set_archive(self.h, _ptr(z0), n0, int(capacity), int(thin),
+                                                       float(p_snooker)))
+
+    def archive_size(self) -> int:
+        n = C.c_int64()
+        self.ctx._check(self.lib.bart_demc_archive_size(self.h, C.byref(n)))
+        return int(n.value)
 
     def set_screen(self, beta=1.0, margin=0.0):
         self.ctx._check(self.lib.bart_demc_set_screen(self.h, float(beta), float(margin)))

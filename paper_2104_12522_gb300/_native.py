@@ -67,6 +67,9 @@ SIGNATURES = {
     "bart_sync": (c_int, [c_void_p]),
     "bart_set_autotune": (c_int, [c_void_p, c_int]),
     "bart_set_line_threshold": (c_int, [c_void_p, c_double]),
+    "bart_demc_set_archive": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_double]),
+    "bart_demc_archive_size": (c_int, [c_void_p, P(c_int64)]),
+    "bart_chain_stats": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_double, c_void_p, c_void_p]),
     "bart_voigt_table_create": (c_int, [c_void_p, c_int, c_double, c_double, c_int, c_double, c_double, c_int,
                                         c_double, c_double, c_void_p]),
     "bart_voigt_table_destroy": (None, [c_void_p]),

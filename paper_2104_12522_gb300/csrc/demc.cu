@@ -17,6 +17,16 @@
 //             probability min(1, exp((L_y - L_x) - (ls_y - ls_x))) from the
 //             exact model.  Rejected proposals never reach the exact model;
 //             every accepted sample has its exact log-likelihood.
+// DEMCzs (Sec. 4; ter Braak & Vrugt 2008), set by bart_demc_set_archive:
+// every chain proposes from an archive Z of past states, so all chains move
+// in one step.  With probability p_snooker a snooker move: z, z1, z2 from Z,
+// y = x + g_s ((z1 - z2) . e) e, e the unit vector from z to x, g_s in
+// [1.2, 2.2), and the factor q = (|y - z| / |x - z|)^(d - 1) in the
+// Metropolis ratio; otherwise y = x + gamma (z1 - z2) + noise (q = 1).  The
+// screen's stage 1 is min(1, exp(beta (ls_y - ls_x) + margin) q) and stage 2
+// min(1, exp(L_y - L_x) q a1(y -> x) / a1(x -> y)).  Every `thin` steps the
+// chains' states are appended to Z while it has room; the count lives on the
+// device so a replayed graph keeps appending.
 // Random numbers come from a counter-based generator (SplitMix64 finaliser
 // of seed, generation, chain and draw index), so a generation's draws do not
 // depend on launch order and the loop can be captured in a CUDA graph.
@@ -40,6 +50,14 @@ struct bart_demc {
   const int64_t* hs_dev = nullptr;   // if set, kernels read the half-step index here
   double beta = 1.0;        // stage-1 temperature of the surrogate log-likelihood
   double margin = 0.0;      // stage-1 margin
+  // DEMCzs archive (zs mode)
+  bool zs = false;
+  float* Z = nullptr;       // device [cap][d]
+  int64_t cap = 0;
+  long long* zc = nullptr;  // device: states in Z
+  int thin = 10;
+  double p_snooker = 0.1;
+  double* logq = nullptr;   // device [C] log proposal factor of the last proposal
 };
 
 namespace {
@@ -107,21 +125,91 @@ __global__ void propose_kernel(int C, int d, const float* __restrict__ x, const 
   inbox[i] = ok;
 }
 
-// log of the stage-1 acceptance a1(x -> y) = min(1, exp(beta (ls_y - ls_x) + margin))
-__device__ __forceinline__ double log_a1(double d, double beta, double margin) {
-  return fmin(0.0, beta * d + margin);
+// DEMCzs proposals: all chains, from the archive.
+__global__ void propose_zs_kernel(int C, int d, const float* __restrict__ x, const float* __restrict__ lo,
+                                  const float* __restrict__ hi, int64_t gen_arg, const int64_t* __restrict__ gen_dev,
+                                  uint64_t seed, double gamma, int jump_every, double eps, const float* __restrict__ Z,
+                                  const long long* __restrict__ zc, double p_snooker, float* __restrict__ y,
+                                  int32_t* __restrict__ inbox, double* __restrict__ logq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C) return;
+  const int64_t gen = gen_dev ? *gen_dev : gen_arg;
+  const int m = (int)*zc;
+  const int a = min((int)(uniform(seed, gen, i, 51) * m), m - 1);
+  int b = min((int)(uniform(seed, gen, i, 52) * (m - 1)), m - 2);
+  if (b >= a) ++b;
+  const float* xi = x + (int64_t)i * d;
+  const float* za = Z + (int64_t)a * d;
+  const float* zb = Z + (int64_t)b * d;
+  double lq = 0.0;
+  int ok = 1;
+  if (uniform(seed, gen, i, 50) < p_snooker) {
+    const int c = min((int)(uniform(seed, gen, i, 53) * m), m - 1);
+    const float* zz = Z + (int64_t)c * d;
+    double nn = 0.0, proj = 0.0;
+    for (int q = 0; q < d; ++q) {
+      const double e = (double)xi[q] - zz[q];
+      nn += e * e;
+      proj += ((double)za[q] - zb[q]) * e;
+    }
+    if (nn == 0.0) {                          // x on an archive state: no move
+      ok = 0;
+      for (int q = 0; q < d; ++q) y[(int64_t)i * d + q] = xi[q];
+    } else {
+      const double gs = 1.2 + uniform(seed, gen, i, 54);
+      const double f = gs * proj / nn;
+      double ny = 0.0;
+      for (int q = 0; q < d; ++q) {
+        const double e = (double)xi[q] - zz[q];
+        const float vf = (float)((double)xi[q] + f * e);
+        y[(int64_t)i * d + q] = vf;
+        ok &= (vf >= lo[q]) && (vf <= hi[q]);
+        const double dy = (double)vf - zz[q];
+        ny += dy * dy;
+      }
+      lq = (d - 1) * 0.5 * (log(ny) - log(nn));
+    }
+  } else {
+    const double gm = (jump_every > 0 && (gen % jump_every) == jump_every - 1) ? 1.0 : gamma;
+    for (int q = 0; q < d; ++q) {
+      const double w = (double)hi[q] - (double)lo[q];
+      const float vf = (float)((double)xi[q] + gm * ((double)za[q] - zb[q]) + eps * w * normal(seed, gen, i, 8 + q));
+      y[(int64_t)i * d + q] = vf;
+      ok &= (vf >= lo[q]) && (vf <= hi[q]);
+    }
+  }
+  inbox[i] = ok;
+  logq[i] = lq;
+}
+
+// Appends the chains' states to the archive every `thin` steps while it has room.
+__global__ void archive_kernel(int C, int d, const float* __restrict__ x, int64_t gen_arg,
+                               const int64_t* __restrict__ gen_dev, int thin, float* __restrict__ Z, int64_t cap,
+                               long long* __restrict__ zc) {
+  const int64_t gen = gen_dev ? *gen_dev : gen_arg;
+  const long long m = *zc;
+  if ((gen + 1) % thin != 0 || m + C > cap) return;
+  for (int64_t e = threadIdx.x; e < (int64_t)C * d; e += blockDim.x) Z[m * d + e] = x[e];
+  __syncthreads();
+  if (threadIdx.x == 0) *zc = m + C;
+}
+
+// log of the stage-1 acceptance a1(x -> y) = min(1, exp(beta (ls_y - ls_x) + margin) q)
+__device__ __forceinline__ double log_a1(double d, double beta, double margin, double lq = 0.0) {
+  return fmin(0.0, beta * d + margin + lq);
 }
 
 __global__ void screen_kernel(int C, const int32_t* __restrict__ inbox, const double* __restrict__ ls_y,
                               const double* __restrict__ ls_x, int64_t gen_arg, const int64_t* __restrict__ gen_dev,
-                              uint64_t seed, double beta, double margin, int32_t* __restrict__ pass) {
+                              uint64_t seed, double beta, double margin, const double* __restrict__ logq,
+                              int32_t* __restrict__ pass) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C) return;
   const int64_t gen = gen_dev ? *gen_dev : gen_arg;
   int p = inbox[i];
   if (p && ls_y) {
     const double lu = log(uniform(seed, gen, i, 100));
-    p = lu < log_a1(ls_y[i] - ls_x[i], beta, margin);
+    p = lu < log_a1(ls_y[i] - ls_x[i], beta, margin, logq ? logq[i] : 0.0);
   }
   pass[i] = p;
 }
@@ -130,19 +218,20 @@ __global__ void accept_kernel(int C, int d, float* __restrict__ x, double* __res
                               const float* __restrict__ y, const int32_t* __restrict__ pass,
                               const double* __restrict__ L_y, const double* __restrict__ ls_y, int64_t gen_arg,
                               const int64_t* __restrict__ gen_dev, uint64_t seed, double beta, double margin,
-                              int32_t* __restrict__ accepted) {
+                              const double* __restrict__ logq, int32_t* __restrict__ accepted) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= C) return;
   const int64_t gen = gen_dev ? *gen_dev : gen_arg;
   int a = 0;
   if (pass[i]) {
-    double r = L_y[i] - L[i];
+    const double lq = logq ? logq[i] : 0.0;   // proposal factor (DEMCzs snooker moves)
+    double r = L_y[i] - L[i] + lq;
     if (ls_y) {
       // delayed acceptance: the stage-1 probabilities of the reverse and the
-      // forward move enter the stage-2 ratio (for beta = 1, margin = 0 this is
-      // -(ls_y - ls_x))
+      // forward move enter the stage-2 ratio (for beta = 1, margin = 0 and a
+      // symmetric proposal this is -(ls_y - ls_x))
       const double d = ls_y[i] - Ls[i];
-      r += log_a1(-d, beta, margin) - log_a1(d, beta, margin);
+      r += log_a1(-d, beta, margin, -lq) - log_a1(d, beta, margin, lq);
     }
     const double lu = log(uniform(seed, gen, i, 101));
     a = (r >= 0.0) || (lu < r);
@@ -183,7 +272,7 @@ extern "C" bart_status bart_demc_create(bart_ctx* ctx, int n_chains, int n_param
   if (!ctx) return BART_EINVAL;
   BART_REQUIRE(ctx, out && lo && hi, "NULL out, lo or hi");
   *out = nullptr;
-  BART_REQUIRE(ctx, n_chains >= 6 && n_chains <= 65536, "n_chains must be in [6, 65536]");
+  BART_REQUIRE(ctx, n_chains >= 3 && n_chains <= 65536, "n_chains must be in [3, 65536]");
   BART_REQUIRE(ctx, n_params >= 1 && n_params <= DEMC_MAX_PARAMS, "n_params must be in [1, %d]", DEMC_MAX_PARAMS);
   for (int q = 0; q < n_params; ++q)
     BART_REQUIRE(ctx, std::isfinite(lo[q]) && std::isfinite(hi[q]) && hi[q] > lo[q], "bad prior box");
@@ -218,7 +307,8 @@ extern "C" void bart_demc_destroy(bart_demc* s) {
   if (!s) return;
   cudaSetDevice(s->ctx->device);
   cudaStreamSynchronize(s->ctx->stream);
-  for (void* p : {(void*)s->lo, (void*)s->hi, (void*)s->x, (void*)s->L, (void*)s->Ls})
+  for (void* p : {(void*)s->lo, (void*)s->hi, (void*)s->x, (void*)s->L, (void*)s->Ls, (void*)s->Z, (void*)s->zc,
+                  (void*)s->logq})
     if (p) cudaFree(p);
   delete s;
 }
@@ -251,6 +341,13 @@ extern "C" bart_status bart_demc_propose(bart_demc* s, int64_t half_step, float*
   if (!s) return BART_EINVAL;
   BART_REQUIRE(s->ctx, y && inbox, "NULL y or inbox");
   BART_REQUIRE(s->ctx, half_step >= 0, "half_step must be >= 0");
+  if (s->zs) {
+    propose_zs_kernel<<<nblk(s->C), 128, 0, s->ctx->stream>>>(s->C, s->d, s->x, s->lo, s->hi, half_step, s->hs_dev,
+                                                              s->seed, s->gamma, s->jump_every, s->eps, s->Z, s->zc,
+                                                              s->p_snooker, y, inbox, s->logq);
+    return bart_check_launch(s->ctx, "propose_zs_kernel");
+  }
+  BART_REQUIRE(s->ctx, s->C >= 6, "DE-MC needs at least 6 chains (3 per half); DEMCzs needs 3");
   propose_kernel<<<nblk(s->C), 128, 0, s->ctx->stream>>>(s->C, s->d, s->x, s->lo, s->hi, half_step, s->hs_dev,
                                                          s->seed, s->gamma, s->jump_every, s->eps, y, inbox);
   return bart_check_launch(s->ctx, "propose_kernel");
@@ -261,7 +358,7 @@ extern "C" bart_status bart_demc_screen(bart_demc* s, int64_t half_step, const i
   if (!s) return BART_EINVAL;
   BART_REQUIRE(s->ctx, inbox && pass, "NULL inbox or pass");
   screen_kernel<<<nblk(s->C), 128, 0, s->ctx->stream>>>(s->C, inbox, ls_y, s->Ls, half_step, s->hs_dev, s->seed,
-                                                        s->beta, s->margin, pass);
+                                                        s->beta, s->margin, s->zs ? s->logq : nullptr, pass);
   return bart_check_launch(s->ctx, "screen_kernel");
 }
 
@@ -271,8 +368,12 @@ extern "C" bart_status bart_demc_accept(bart_demc* s, int64_t half_step, const f
   BART_REQUIRE(s->ctx, y && pass && L_y, "NULL y, pass or L_y");
   accept_kernel<<<nblk(s->C), 128, 0, s->ctx->stream>>>(s->C, s->d, s->x, s->L, s->Ls, y, pass, L_y, ls_y,
                                                         half_step, s->hs_dev, s->seed, s->beta, s->margin,
-                                                        accepted);
-  return bart_check_launch(s->ctx, "accept_kernel");
+                                                        s->zs ? s->logq : nullptr, accepted);
+  bart_status st = bart_check_launch(s->ctx, "accept_kernel");
+  if (st != BART_OK || !s->zs) return st;
+  archive_kernel<<<1, 256, 0, s->ctx->stream>>>(s->C, s->d, s->x, half_step, s->hs_dev, s->thin, s->Z, s->cap,
+                                                s->zc);
+  return bart_check_launch(s->ctx, "archive_kernel");
 }
 
 extern "C" bart_status bart_loglike_bands(bart_ctx* ctx, const float* model, int n, int n_bands, const float* data,
@@ -297,3 +398,139 @@ void bart_demc_use_counter(bart_demc* s, const int64_t* hs_dev) { s->hs_dev = hs
 int bart_demc_chains(const bart_demc* s) { return s->C; }
 int bart_demc_params(const bart_demc* s) { return s->d; }
 const float* bart_demc_states(const bart_demc* s) { return s->x; }
+
+extern "C" bart_status bart_demc_set_archive(bart_demc* s, const float* z0, int64_t n0, int64_t capacity, int thin,
+                                             double p_snooker) {
+  if (!s) return BART_EINVAL;
+  bart_ctx* ctx = s->ctx;
+  BART_REQUIRE(ctx, z0 != nullptr, "z0 is NULL");
+  BART_REQUIRE(ctx, n0 >= 3 && capacity >= n0 && capacity <= ((int64_t)1 << 31), "need 3 <= n0 <= capacity <= 2^31");
+  BART_REQUIRE(ctx, thin >= 1, "thin must be >= 1");
+  BART_REQUIRE(ctx, p_snooker >= 0 && p_snooker <= 1, "p_snooker must be in [0, 1]");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (s->Z) cudaFree(s->Z);
+  s->Z = nullptr;
+  if (!s->zc && cudaMalloc(&s->zc, sizeof(long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return bart_fail(ctx, BART_ENOMEM, "DEMCzs counter allocation failed");
+  }
+  if (!s->logq && cudaMalloc(&s->logq, (size_t)s->C * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return bart_fail(ctx, BART_ENOMEM, "DEMCzs buffer allocation failed");
+  }
+  if (cudaMalloc(&s->Z, (size_t)capacity * s->d * 4) != cudaSuccess) {
+    cudaGetLastError();
+    s->Z = nullptr;
+    return bart_fail(ctx, BART_ENOMEM, "DEMCzs archive of %lld states failed", (long long)capacity);
+  }
+  const long long n0ll = n0;
+  BART_CUDA(ctx, cudaMemcpyAsync(s->Z, z0, (size_t)n0 * s->d * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  BART_CUDA(ctx, cudaMemcpy(s->zc, &n0ll, sizeof(long long), cudaMemcpyHostToDevice));
+  BART_CUDA(ctx, cudaMemsetAsync(s->logq, 0, (size_t)s->C * 8, ctx->stream));
+  s->cap = capacity;
+  s->thin = thin;
+  s->p_snooker = p_snooker;
+  s->zs = true;
+  return BART_OK;
+}
+
+extern "C" bart_status bart_demc_archive_size(bart_demc* s, int64_t* n) {
+  if (!s) return BART_EINVAL;
+  BART_REQUIRE(s->ctx, n != nullptr, "n is NULL");
+  long long v = 0;
+  if (s->zs) {
+    BART_CUDA(s->ctx, cudaMemcpyAsync(&v, s->zc, sizeof(long long), cudaMemcpyDeviceToHost, s->ctx->stream));
+    BART_CUDA(s->ctx, cudaStreamSynchronize(s->ctx->stream));
+  }
+  *n = v;
+  return BART_OK;
+}
+
+// ---------------------------------------------------------------- chain statistics
+
+namespace {
+
+__device__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();                           // sh is reused by consecutive calls
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;
+}
+
+// SPEIS of one (chain, parameter) series per block: 1 + 2 sum of the
+// autocorrelation from lag 1 until it first falls below `threshold` (Sec. 4).
+__global__ void speis_kernel(const float* __restrict__ chain, int n, int C, int d, double threshold,
+                             double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int c = blockIdx.x / d, q = blockIdx.x % d;
+  auto at = [&](int t) { return (double)chain[((int64_t)t * C + c) * d + q]; };
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) s += at(t);
+  const double mean = block_sum(s, sh) / n;
+  double v = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) v += (at(t) - mean) * (at(t) - mean);
+  const double var = block_sum(v, sh) / n;
+  double speis = 1.0;
+  if (var > 0.0) {
+    for (int k = 1; k < n / 2; ++k) {
+      double a = 0.0;
+      for (int t = threadIdx.x; t + k < n; t += blockDim.x) a += (at(t) - mean) * (at(t + k) - mean);
+      const double rho = block_sum(a, sh) / (n * var);
+      if (rho < threshold) break;            // the same value in every thread
+      speis += 2.0 * rho;
+    }
+  }
+  if (threadIdx.x == 0) out[(int64_t)c * d + q] = speis;
+}
+
+// Gelman-Rubin R of one parameter per block over C chains of length n.
+__global__ void gr_kernel(const float* __restrict__ chain, int n, int C, int d, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int q = blockIdx.x;
+  double sw = 0.0, sm = 0.0, sm2 = 0.0;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double m = 0.0;
+    for (int t = 0; t < n; ++t) m += chain[((int64_t)t * C + c) * d + q];
+    m /= n;
+    double v = 0.0;
+    for (int t = 0; t < n; ++t) {
+      const double e = chain[((int64_t)t * C + c) * d + q] - m;
+      v += e * e;
+    }
+    sw += v / (n - 1);
+    sm += m;
+    sm2 += m * m;
+  }
+  const double W = block_sum(sw, sh) / C;
+  const double M = block_sum(sm, sh) / C;
+  const double M2 = block_sum(sm2, sh);
+  const double B = n * (M2 - C * M * M) / (C - 1);
+  const double V = (n - 1.0) / n * W + B / n;
+  if (threadIdx.x == 0) out[q] = W > 0.0 ? sqrt(V / W) : 1.0;
+}
+
+}  // namespace
+
+extern "C" bart_status bart_chain_stats(bart_ctx* ctx, const float* chain, int n, int n_chains, int n_params,
+                                        double threshold, double* speis, double* gr) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, chain != nullptr, "chain is NULL");
+  BART_REQUIRE(ctx, n >= 4 && n_chains >= 1 && n_params >= 1, "need n >= 4, n_chains >= 1, n_params >= 1");
+  BART_REQUIRE(ctx, (int64_t)n_chains * n_params <= 0x7fffffff, "too many series");
+  BART_REQUIRE(ctx, !gr || n_chains >= 2, "the Gelman-Rubin statistic needs at least 2 chains");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (speis) {
+    speis_kernel<<<n_chains * n_params, 256, 0, ctx->stream>>>(chain, n, n_chains, n_params, threshold, speis);
+    bart_status st = bart_check_launch(ctx, "speis_kernel");
+    if (st != BART_OK) return st;
+  }
+  if (gr) {
+    gr_kernel<<<n_params, 256, 0, ctx->stream>>>(chain, n, n_chains, n_params, gr);
+    return bart_check_launch(ctx, "gr_kernel");
+  }
+  return BART_OK;
+}

@@ -120,3 +120,73 @@ def test_loglike_bands(ctx, torch):
     got = out.cpu().numpy()
     assert np.all(np.isneginf(got[mask == 0]))
     assert np.allclose(got[mask == 1], ref[mask == 1], rtol=1e-12)
+
+
+# ---- DEMCzs and the chain statistics (Sec. 4, App. C)
+
+def _run_zs(ctx, torch, n_steps, C, p_snooker, screened=False, seed=6020):
+    import paper_2104_12522_gb300 as bart
+    mu, cov, lo, hi = target()
+    d = 9
+    sd = np.sqrt(np.diag(cov))
+    inv = torch.tensor(np.linalg.inv(cov), device="cuda")
+    mu_t = torch.tensor(mu, device="cuda")
+    def L(y):
+        r = y.double() - mu_t
+        return -0.5 * torch.einsum("ij,jk,ik->i", r, inv, r)
+    s = bart.Demc(ctx, C, lo.astype(np.float32), hi.astype(np.float32), jump_every=10, eps=1e-4, seed=seed)
+    rng = np.random.default_rng(seed)
+    z0 = torch.tensor((mu + rng.normal(size=(90, d)) * sd * 2.0).astype(np.float32), device="cuda")
+    s.set_archive(z0, capacity=90 + C * (n_steps // 10), thin=10, p_snooker=p_snooker)
+    x0 = torch.tensor((mu + rng.normal(size=(C, d)) * sd).astype(np.float32), device="cuda")
+    ls0 = 0.7 * L(x0) if screened else None
+    s.set_state(x0, L(x0).contiguous(), ls0.contiguous() if screened else None)
+    y = torch.empty((C, d), dtype=torch.float32, device="cuda")
+    inbox = torch.empty(C, dtype=torch.int32, device="cuda")
+    passed = torch.empty(C, dtype=torch.int32, device="cuda")
+    hist = torch.empty((n_steps, C, d), dtype=torch.float32, device="cuda")
+    for st in range(n_steps):
+        s.propose(st, y, inbox)
+        ly = L(y).contiguous()
+        ls = (0.7 * ly).contiguous() if screened else None
+        s.screen(st, inbox, ls, passed)
+        s.accept(st, y, passed, ly, ls)
+        s.get_state(hist[st])
+    return s, hist, mu, cov
+
+
+@pytest.mark.parametrize("C,p_snooker,screened", [(3, 0.1, False), (4, 1.0, False), (4, 0.1, True)])
+def test_gpu_demczs_recovers_gaussian(ctx, torch, C, p_snooker, screened):
+    n = 12000
+    s, hist, mu, cov = _run_zs(ctx, torch, n, C, p_snooker, screened)
+    assert s.archive_size() == 90 + C * (n // 10)
+    sm = hist.cpu().numpy().astype(np.float64)[2000:]
+    flat = sm.reshape(-1, 9)
+    e = D.ess(sm)
+    sd = np.sqrt(np.diag(cov))
+    z = np.abs(flat.mean(0) - mu) / (sd / np.sqrt(e))
+    var_ratio = flat.var(0) / sd ** 2
+    print(f"GPU DEMCzs (C={C}, p_snooker={p_snooker}, screened={screened}): ESS {e:.0f}, "
+          f"max |z| {z.max():.2f}, var ratio {var_ratio.min():.3f}..{var_ratio.max():.3f}")
+    assert e > 100
+    assert np.all(z < 4.5)
+    assert np.all(np.abs(var_ratio - 1) < 4.5 * np.sqrt(2.0 / e))
+
+
+def test_chain_stats_match_the_oracle(ctx, torch):
+    rng = np.random.default_rng(21)
+    n, C, d = 3000, 4, 3
+    x = np.zeros((n, C, d))
+    phi = np.array([0.0, 0.5, 0.9])
+    for t in range(1, n):
+        x[t] = phi * x[t - 1] + rng.normal(size=(C, d))
+    x += np.array([0.0, 0.1, 0.0, -0.1])[None, :, None]
+    x32 = x.astype(np.float32)
+    sp, gr, ess = ctx.chain_stats(torch.tensor(x32, device="cuda"))
+    sp, gr = sp.cpu().numpy(), gr.cpu().numpy()
+    ref_sp = np.array([[D.speis(x32[:, c, q].astype(np.float64)) for q in range(d)] for c in range(C)])
+    ref_gr = D.gelman_rubin(x32.astype(np.float64))
+    print(f"SPEIS GPU vs oracle: max rel {np.max(np.abs(sp / ref_sp - 1)):.2e}; GR {gr} vs {ref_gr}")
+    assert np.allclose(sp, ref_sp, rtol=1e-9)
+    assert np.allclose(gr, ref_gr, rtol=1e-9)
+    assert abs(ess - D.ess(x32.astype(np.float64))) < 1e-6 * ess
