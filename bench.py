@@ -622,23 +622,34 @@ def run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net
     xb_, Lb_ = torch.empty_like(x0), torch.empty_like(L0)
     burn.get_state(xb_, Lb_)
     res["burn_in"] = {"generations": n_burn, "ms": burn_ms}
-    for mode in ("plain", "screened"):
-        s = bart.Demc(ctx, C, lo, hi, jump_every=10, eps=1e-4, seed=6000)
+    for mode in ("plain", "screened", "demczs"):
+        # DEMCzs (Sec. 4): 4 chains from the burnt-in state, its 16 states as the
+        # initial archive, every chain moving at each of a generation's two steps
+        Cm = 4 if mode == "demczs" else C
+        s = bart.Demc(ctx, Cm, lo, hi, jump_every=10, eps=1e-4, seed=6000)
         s.set_screen(beta, margin)
+        if mode == "demczs":
+            s.set_archive(xb_, capacity=C + Cm * (2 * generations // 10 + 1), thin=10, p_snooker=0.1)
         Ls0 = None
         if mode == "screened":
             Ls0 = torch.empty(C, dtype=torch.float64, device=dev)
             ctx.loglike_bands(net.forward(xb_), data, sigma, Ls0)
-        s.set_state(xb_, Lb_, Ls0)
+        s.set_state(xb_[:Cm].contiguous(), Lb_[:Cm].contiguous(), Ls0)
+        chain = torch.empty((generations, Cm, 5 + S), dtype=torch.float32, device=dev)
         st = {}
         def run():
             st.update(ctx.retrieval_run(s, net if mode == "screened" else None, grid, ax.p_bar, ax.t_K, nu, cfg,
-                                        filt, data, sigma, generations, use_graph=True))
+                                        filt, data, sigma, generations, use_graph=True, chain=chain))
         ms = _event_ms(torch, stream, run)
         ctx.sync()
         st["accepted_samples_per_s"] = st["accepted"] / (ms / 1e3)
         st["proposals_per_s"] = st["proposals"] / (ms / 1e3)
         st["generations"] = generations
+        st["chains"] = Cm
+        _, gr, ess = ctx.chain_stats(chain)
+        st["ess"] = ess
+        st["ess_per_s"] = ess / (ms / 1e3)
+        st["gelman_rubin_max"] = float(gr.max())
         if mode == "screened":
             st["screen"] = {"beta": beta, "margin": margin}
         st["ms"] = ms
