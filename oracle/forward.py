@@ -11,12 +11,15 @@ transmission RT, then the spectrum integrator (Sec. 3).  Readings:
   a node hits weight 0 on its upper neighbour;
 * instances whose levels differ from the grid's layers interpolate bilinearly
   in (log10 P, T), with the same bracket rule in log10 P;
-* chi = sum_s X_s sigma_s / (mu m_u) in cm^2 g^-1.
+* chi = sum_s X_s sigma_s / (mu m_u) in cm^2 g^-1, plus the Rayleigh term and
+  with the gray cloud deck of ``cloud_rayleigh`` when cfg sets rayleigh_coef
+  or p_cloud.
 """
 import numpy as np
 
 from .constants import AMU
 from . import profile, radiation, transmission
+from .cloud_rayleigh import deck_levels, rayleigh_chi
 
 
 def bracket(axis, v):
@@ -81,8 +84,10 @@ def emission_spectrum(grid, p_axis, t_axis, nu, theta, cfg, T=None):
         T = tp_of(theta, p_axis, cfg)
     X = profile.abundances(theta, cfg["x0"])
     sig = layer_opacity(grid, t_axis, T)
-    chi = mass_opacity(sig, X, cfg["mu"])
-    return radiation.emission_flux(chi, p_axis, T, nu, cfg["g"], cfg["n_angles"], tau_max=cfg.get("tau_max"))
+    chi = mass_opacity(sig, X, cfg["mu"]) + rayleigh_chi(nu, cfg.get("rayleigh_coef", 0.0), cfg["mu"])[None, :]
+    Le = deck_levels(p_axis, cfg.get("p_cloud"))
+    return radiation.emission_flux(chi[:Le], np.asarray(p_axis)[:Le], np.asarray(T)[:Le], nu, cfg["g"],
+                                   cfg["n_angles"], tau_max=cfg.get("tau_max"))
 
 
 def instance_levels(n_levels, p_top, p_bot):
@@ -95,8 +100,13 @@ def transmission_spectrum(grid, p_axis, t_axis, nu_start, dnu, inst, i, cfg):
     th = inst.theta[i]
     T = tp_of(th, P, cfg)
     X = profile.abundances(th, cfg["x0"])
-    sub = grid[..., int(inst.nu_lo[i]):int(inst.nu_hi[i])]
+    lo, hi = int(inst.nu_lo[i]), int(inst.nu_hi[i])
+    sub = grid[..., lo:hi]
     sig = level_opacity_bilinear(sub, p_axis, t_axis, P, T)
+    nu = nu_start + np.arange(lo, hi, dtype=np.float64) * dnu
     chi = mass_opacity(sig, X, cfg["mu"])
+    if cfg.get("rayleigh_coef", 0.0):
+        chi = chi + rayleigh_chi(nu, cfg["rayleigh_coef"], cfg["mu"])[None, :]
     r = transmission.radii(P, T, float(inst.r_planet[i]), cfg["p_ref"], cfg["g"], cfg["mu"])
-    return transmission.transit_depth(chi, P, T, r, float(inst.r_star[i]), cfg["mu"])
+    Le = deck_levels(P, cfg.get("p_cloud"))
+    return transmission.transit_depth(chi[:Le], P[:Le], T[:Le], r[:Le], float(inst.r_star[i]), cfg["mu"])
