@@ -90,6 +90,23 @@ def emission_spectrum(grid, p_axis, t_axis, nu, theta, cfg, T=None):
                                    cfg["n_angles"], tau_max=cfg.get("tau_max"))
 
 
+def emission_contributions(grid, p_axis, t_axis, nu, theta, cfg, T=None):
+    """Per-layer contributions C[L][n_nu] of one proposal's emission spectrum
+    (``radiation.emission_contributions``), with the Rayleigh term and the
+    gray cloud deck as in ``emission_spectrum``; levels below the deck are 0."""
+    if T is None:
+        T = tp_of(theta, p_axis, cfg)
+    X = profile.abundances(theta, cfg["x0"])
+    sig = layer_opacity(grid, t_axis, T)
+    chi = mass_opacity(sig, X, cfg["mu"]) + rayleigh_chi(nu, cfg.get("rayleigh_coef", 0.0), cfg["mu"])[None, :]
+    L = len(p_axis)
+    Le = deck_levels(p_axis, cfg.get("p_cloud"))
+    C = np.zeros((L, len(nu)))
+    C[:Le] = radiation.emission_contributions(chi[:Le], np.asarray(p_axis)[:Le], np.asarray(T)[:Le], nu, cfg["g"],
+                                              cfg["n_angles"], tau_max=cfg.get("tau_max"))
+    return C
+
+
 def instance_levels(n_levels, p_top, p_bot):
     return np.logspace(np.log10(p_top), np.log10(p_bot), int(n_levels))
 

@@ -100,3 +100,31 @@ def band_integrate(spec, filters, nu_lo=0):
     num = np.array([math.fsum(W[b] * spec * dw) for b in range(W.shape[0])])
     den = np.array([math.fsum(W[b] * dw) for b in range(W.shape[0])])
     return np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+
+
+def emission_contributions(chi, p_bar, T, nu, g, n_angles, tau_max=None):
+    """Contribution functions of the emission spectrum (post-processing, Sec. 3),
+    FP64 [L][n_nu].
+
+    Reading: the flux is a sum of one term per layer plus the bottom boundary,
+    F = sum_{k < kb} C_k + C_kb, with
+    C_k = 2 pi sum_i w_i mu_i (B_k + B_{k+1}) / 2 (t_k(mu_i) - t_{k+1}(mu_i))
+    the emission of the layer between levels k and k+1 that reaches the top,
+    and C_kb = 2 pi sum_i w_i mu_i B_kb t_kb(mu_i) the bottom level's blackbody
+    seen through the column; kb is the last level integrated (L - 1, or the
+    level where the optical-depth limit stops).  Entries after kb are 0."""
+    tau = optical_depth(np.asarray(chi).T, p_bar, g)           # [n_nu][L]
+    B = planck(np.asarray(nu)[:, None], np.asarray(T)[None, :])  # [n_nu][L]
+    mu, w = gauss_legendre_mu(n_angles)
+    n_nu, L = tau.shape
+    C = np.zeros((L, n_nu))
+    for r in range(n_nu):
+        kb = L - 1
+        if tau_max is not None:
+            over = np.nonzero(tau[r, 1:] > tau_max)[0]
+            kb = over[0] + 1 if over.size else L - 1
+        for i in range(n_angles):
+            t = np.exp(-tau[r, :kb + 1] / mu[i])
+            C[:kb, r] += w[i] * mu[i] * 0.5 * (B[r, :kb] + B[r, 1:kb + 1]) * (t[:-1] - t[1:])
+            C[kb, r] += w[i] * mu[i] * B[r, kb] * t[kb]
+    return 2.0 * math.pi * C
