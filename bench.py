@@ -453,6 +453,8 @@ def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_line
     ctx.sync()
     out["transmission"] = {"spectra_per_s": 1024 / (ms / 1e3), "ms_per_batch": ms, "instances": 1024,
                            "level_sum": int(inst.n_levels.sum()), "points": int(offs[-1]), "bands": 12}
+    out["cloud_rayleigh"] = cloud_rayleigh_leg(ctx, torch, stream, grid, ax, nu, cfg, theta, run_t, ms, tcfg, targs,
+                                               spec)
     out["paper_approximations"] = paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta)
     net, out["surrogate"] = train_surrogate(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S,
                                             args.train_steps)
@@ -498,6 +500,42 @@ def voigt_table_leg(ctx, torch, stream, grid, ax, nu, d_lines, build0, out, n_w=
            "fill_ms": fill_ms, "ms": ms, "ms_direct": ms0, "speed_vs_direct": ms0 / ms, "grid_rel_l2": l2,
            "grid_max_rel_err_1e-3": _max_rel(torch, got0, ref0, 1e-3)}
     tab.close()
+    return res
+
+
+H2_RAYLEIGH = 8.4e-45        # cm^2 (cm^-1)^-4: H2 cross-section per molecule a nu^4
+
+
+def cloud_rayleigh_leg(ctx, torch, stream, grid, ax, nu, cfg, theta, run_t, ms_t, tcfg, targs, spec_t):
+    """Cost of the Sec. 3 gray cloud deck (0.1 bar, at the reference radius)
+    and H2 Rayleigh scattering on the bench's two forward-model workloads:
+    the 2,048-proposal emission generation and the 1,024-instance transmission
+    batch, each timed with and without the options, with the largest relative
+    change of the spectra they cause."""
+    res = {}
+    n = theta.shape[0]
+    ref = torch.empty((n, ax.n_nu), dtype=torch.float32, device=grid.device)
+    out = torch.empty_like(ref)
+    run = lambda c, o: ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, c, theta=theta, spectra=o)
+    run(cfg, ref)
+    ms0 = _event_ms(torch, stream, lambda: run(cfg, ref))
+    t_ref = spec_t.clone()
+    for name, extra in (("rayleigh", {"rayleigh_coef": H2_RAYLEIGH}), ("deck_0.1bar", {"p_cloud": 0.1}),
+                        ("both", {"rayleigh_coef": H2_RAYLEIGH, "p_cloud": 0.1})):
+        c = dict(cfg, **extra)
+        run(c, out)
+        ms = _event_ms(torch, stream, lambda: run(c, out))
+        tc = dict(tcfg, **extra)
+        run_tc = lambda: ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, tc, **targs)
+        run_tc()
+        mst = _event_ms(torch, stream, run_tc, reps=2)
+        res[name] = {"emission_ms": ms, "emission_ms_without": ms0,
+                     "emission_spectra_per_s": n / (ms / 1e3),
+                     "emission_max_rel_change": _max_rel(torch, out, ref, 0.0),
+                     "transmission_ms": mst, "transmission_ms_without": ms_t,
+                     "transmission_spectra_per_s": 1024 / (mst / 1e3),
+                     "transmission_max_rel_change": _max_rel(torch, spec_t, t_ref, 0.0)}
+    ctx.sync()
     return res
 
 

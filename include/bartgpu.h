@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define BART_ABI_VERSION 2
+#define BART_ABI_VERSION 3
 
 typedef enum {
   BART_OK = 0,
@@ -235,7 +235,20 @@ enum { BART_EMISSION = 0, BART_TRANSMISSION = 1 };
  *                 wavenumber once the vertical optical depth from the top
  *                 exceeds tau_max; the level reached is then the bottom
  *                 (blackbody) boundary.  <= 0 turns it off.
- * (tau_max was added in ABI version 2, at the end of the struct.) */
+ *   p_cloud_bar   gray cloud deck (Sec. 3): an opaque surface on the first
+ *                 level with P >= p_cloud_bar (grid layers for emission, the
+ *                 instance's levels for transmission; a deck between levels
+ *                 acts at the deeper one, at least two levels remain).
+ *                 Emission takes that level's blackbody as the bottom
+ *                 boundary; transmission takes the planet as opaque below it
+ *                 (altitudes stay those of the whole column).  <= 0: no deck.
+ *   rayleigh_coef Rayleigh scattering (Sec. 3) by the bulk gas: cross-section
+ *                 per molecule a nu^4 in cm^2, a in cm^2 (cm^-1)^-4 (about
+ *                 8.4e-45 for H2), added to every level as extinction
+ *                 (mass opacity a nu^4 / (mu m_u)).  0: off; must be finite
+ *                 and >= 0 (BART_EINVAL otherwise).
+ * (tau_max was added in ABI version 2, p_cloud_bar and rayleigh_coef in
+ * version 3, each at the end of the struct.) */
 typedef struct {
   int32_t geometry;
   int32_t n_angles;
@@ -245,6 +258,8 @@ typedef struct {
   double p_ref_bar, p_top_bar, p_bot_bar;
   const double* x0;
   double tau_max;
+  double p_cloud_bar;
+  double rayleigh_coef;
 } bart_fwd_cfg;
 
 /* A batch of proposals (emission) or instances (transmission).
@@ -309,6 +324,32 @@ bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid_desc* grid
 bart_status bart_band_integrate(bart_ctx* ctx, const float* spectra, const int64_t* spec_offsets,
                                 const int64_t* nu_lo, const int64_t* nu_hi, int n_spec,
                                 bart_nugrid nu, const bart_filters* filters, float* out);
+
+/* Contribution functions of emission spectra (the post-processing of Sec. 3
+ * computes them per bandpass).  Each proposal's flux is split into one term
+ * per layer plus the bottom boundary, with the layer-averaged source of
+ * bart_forward_spectra_batch:
+ *   C_k(nu) = 2 pi sum_i w_i mu_i (B_k + B_{k+1})/2 (t_k(mu_i) - t_{k+1}(mu_i))
+ * for the layer between levels k and k+1 (t = exp(-tau/mu) from the top), and
+ * at the last level integrated, kb (L-1, the cloud deck's level, or where the
+ * optical-depth limit stops), C_kb = 2 pi sum_i w_i mu_i B_kb t_kb(mu_i);
+ * C_k = 0 for k > kb.  sum_k C_k(nu) is the emission spectrum.
+ *   grid, cfg, batch  as bart_forward_spectra_batch (cfg->geometry must be
+ *            BART_EMISSION; n_angles 1, 2, 4, 8 or 16; 1-4 species)
+ *   contrib  device [n][n_layers][nu.n_nu] or NULL: C_k at grid index j; only
+ *            j inside the entry's span are written
+ *   filters, bands  bands device [n][n_layers][filters->n_bands] or NULL: the
+ *            band mean of each C_k (trapezoid weights over the entry's span,
+ *            as bart_band_integrate); they add up over k to the band value of
+ *            the spectrum.
+ * At least one of contrib and bands.  Without contrib the rows go to context
+ * scratch (n x n_layers x n_nu floats).  Errors: BART_EINVAL for the checks
+ * of bart_forward_spectra_batch, transmission geometry, or nothing requested;
+ * an entry with an invalid span makes bart_sync() return BART_ERANGE. */
+bart_status bart_contribution_functions(bart_ctx* ctx, const bart_grid_desc* grid,
+                                        const bart_fwd_cfg* cfg, const bart_batch* batch,
+                                        float* contrib, const bart_filters* filters,
+                                        float* bands);
 
 /* -------------------------------------------------------- surrogate network */
 

@@ -88,7 +88,8 @@ def _grid_cfg(grid, p_bar, t_K, nu, cfg):
                         float(cfg.get("r_star_tp", 0.0)), float(cfg.get("a_orbit", 0.0)),
                         float(cfg.get("t_min", 0.0)), float(cfg.get("t_max", 1e30)),
                         float(cfg.get("p_ref", 0.1)), float(cfg.get("p_top", 1e-8)),
-                        float(cfg.get("p_bot", 100.0)), C.cast(x0, C.c_void_p), float(cfg.get("tau_max", 0.0)))
+                        float(cfg.get("p_bot", 100.0)), C.cast(x0, C.c_void_p), float(cfg.get("tau_max", 0.0)),
+                        float(cfg.get("p_cloud", 0.0) or 0.0), float(cfg.get("rayleigh_coef", 0.0)))
     return gd, fc, (pb, tk, x0)
 
 
@@ -258,6 +259,39 @@ class Context:
                                                         _ptr(spectra), C.byref(fl) if fl else None,
                                                         _ptr(bands)))
         return spectra, bands
+
+    def contribution_functions(self, grid, p_bar, t_K, nu, cfg: dict, theta=None, t_profile=None, nu_lo=None,
+                               nu_hi=None, contrib=None, filters=None, bands=None, n=None, active=None):
+        """Per-layer contribution functions of emission spectra; see
+        bart_contribution_functions.  contrib [n][L][n_nu] and/or bands
+        [n][L][n_bands] (device, float32)."""
+        S, L, M, N = (int(v) for v in grid.shape)
+        _check_tensor(grid, "float32")
+        for t, dt in ((theta, "float32"), (t_profile, "float32"), (nu_lo, "int64"), (nu_hi, "int64"),
+                      (contrib, "float32"), (filters, "float32"), (bands, "float32"), (active, "int32")):
+            _check_tensor(t, dt)
+        if n is None:
+            n = int(theta.shape[0]) if theta is not None else int(t_profile.shape[0])
+        if theta is not None and tuple(theta.shape) != (n, 5 + S):
+            raise ValueError(f"theta must be [{n}][{5 + S}]")
+        if t_profile is not None and tuple(t_profile.shape) != (n, L):
+            raise ValueError(f"t_profile must be [{n}][{L}]")
+        for t in (nu_lo, nu_hi, active):
+            if t is not None and t.numel() != n:
+                raise ValueError(f"per-entry array has {t.numel()} elements, expected {n}")
+        if contrib is not None and tuple(contrib.shape) != (n, L, N):
+            raise ValueError(f"contrib must be [{n}][{L}][{N}]")
+        if bands is not None and (filters is None or tuple(bands.shape) != (n, L, int(filters.shape[0]))):
+            raise ValueError("bands must be [n][n_layers][n_bands] and need filters")
+        if filters is not None and tuple(filters.shape[1:]) != (N,):
+            raise ValueError("filters must be [n_bands][n_nu]")
+        gd, fc, keep = _grid_cfg(grid, p_bar, t_K, nu, cfg)
+        b = _native.Batch(int(n), _ptr(theta), _ptr(t_profile), None, _ptr(nu_lo), _ptr(nu_hi), None, None, None,
+                          _ptr(active))
+        fl = _native.Filters(int(filters.shape[0]), _ptr(filters)) if filters is not None else None
+        self._check(self.lib.bart_contribution_functions(self.h, C.byref(gd), C.byref(fc), C.byref(b),
+                                                         _ptr(contrib), C.byref(fl) if fl else None, _ptr(bands)))
+        return contrib, bands
 
     def retrieval_run(self, demc, surrogate, grid, p_bar, t_K, nu, cfg, filters, data, sigma, n_generations,
                       first_half_step=0, use_graph=True, chain=None):

@@ -38,7 +38,8 @@ class FwdCfg(C.Structure):
                 ("t_int_K", c_double), ("t_star_K", c_double), ("r_star_tp_cm", c_double),
                 ("a_orbit_cm", c_double), ("t_min_K", c_double), ("t_max_K", c_double),
                 ("p_ref_bar", c_double), ("p_top_bar", c_double), ("p_bot_bar", c_double),
-                ("x0", c_void_p), ("tau_max", c_double)]
+                ("x0", c_void_p), ("tau_max", c_double), ("p_cloud_bar", c_double),
+                ("rayleigh_coef", c_double)]
 
 
 class Batch(C.Structure):
@@ -88,6 +89,8 @@ SIGNATURES = {
                                            c_void_p]),
     "bart_band_integrate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, NuGrid,
                                     P(Filters), c_void_p]),
+    "bart_contribution_functions": (c_int, [c_void_p, P(GridDesc), P(FwdCfg), P(Batch), c_void_p, P(Filters),
+                                            c_void_p]),
     "bart_mlp_create": (c_int, [c_void_p, P(c_int32), c_int, c_int, c_int, c_int, P(c_void_p)]),
     "bart_mlp_destroy": (None, [c_void_p]),
     "bart_mlp_num_params": (c_int64, [c_void_p]),

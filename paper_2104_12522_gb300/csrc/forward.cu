@@ -8,14 +8,15 @@
 //                    coefficients X_s / (mu m_u).
 //   emission_kernel  one thread per (proposal, wavenumber); layers top to
 //                    bottom: opacity interpolated in T and summed over species
-//                    (coalesced reads of grid rows), trapezoid optical depth,
-//                    Planck source, and per Gauss-Legendre angle the
-//                    multiplicative transmittance t_{k+1} = t_k exp(-dtau/mu)
-//                    with I += (B_k + B_{k+1})/2 (t_k - t_{k+1}).  The running
-//                    product replaces a cumulative tau sum (no FP64 needed:
-//                    the relative error of t grows like 1e-7 tau/mu).  Flux
-//                    F = 2 pi sum_i w_i mu_i I(mu_i).  Band numerators and
-//                    denominators are reduced per CTA (fused epilogue).
+//                    (coalesced reads of grid rows) plus the Rayleigh term
+//                    a nu^4 / (mu m_u), trapezoid optical depth, Planck
+//                    source, and per Gauss-Legendre angle the log2 of the
+//                    transmittance (a running sum of positive terms) with
+//                    I += (B_k + B_{k+1})/2 (t_k - t_{k+1}).  A gray cloud
+//                    deck ends the layer loop at its level (its blackbody is
+//                    the bottom boundary).  Flux F = 2 pi sum_i w_i mu_i
+//                    I(mu_i).  Band numerators and denominators are reduced
+//                    per CTA (fused epilogue).
 //   band_reduce      sums the per-CTA partials in a fixed order (FP64).
 // Proposals run along blockIdx.x, so CTAs in flight share wavenumber tiles and
 // the grid rows they read stay in L2.
@@ -39,6 +40,14 @@ struct LayerTW {
   int64_t row;  // offset of grid row (layer k, lower temperature bracket m): (k M + m) n_nu
   float w;      // weight of the upper bracket
   float c2_t;   // c2 / T
+};
+
+// Per-call options of the emission kernel (Sec. 3 cloud deck and Rayleigh
+// scattering, Sec. 4 item 7 optical-depth limit).
+struct EmExtra {
+  int L_run;      // levels integrated: a gray cloud deck on level L_run-1 ends the column
+  float tau_cut;  // vertical optical depth that ends the layer loop (MODE bit 1)
+  double ray;     // Rayleigh a / (mu m_u): chi_R = ray nu^4, cm^2 g^-1
 };
 
 // n-point Gauss-Legendre nodes/weights on [0, 1] (Newton on P_n).
@@ -147,7 +156,7 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
                 double dnu, const int64_t* __restrict__ nu_lo, const int64_t* __restrict__ nu_hi,
                 const int64_t* __restrict__ offs, float* __restrict__ spectra,
                 const float* __restrict__ filt, int n_bands, float2* __restrict__ partial, int n_tiles,
-                const int32_t* __restrict__ act_mask, int* __restrict__ status, float tau_cut) {
+                const int32_t* __restrict__ act_mask, int* __restrict__ status, EmExtra ex) {
   const int p = blockIdx.x;
   const int tile = blockIdx.y;
   const int tid = threadIdx.x;
@@ -175,6 +184,8 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
   const double nu = nu_start + (double)jj * dnu;
   const float nuf = (float)nu;
   const float c1nu3 = (float)(2.0 * bartc::H * bartc::C * bartc::C * nu * nu * nu);
+  // Rayleigh mass opacity a nu^4 / (mu m_u), the same at every level
+  const float chi_r = (float)(ex.ray * (nu * nu) * (nu * nu));
 
   // per angle: lt = log2 of the transmittance to the current level (a sum of
   // positive optical-depth terms times -log2(e)/mu), t = 2^lt, and the
@@ -195,7 +206,7 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
 
   auto chi_at = [&](const LayerTW& r) {
     const float* g0 = gj + r.row;
-    float chi = 0.0f;
+    float chi = chi_r;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const float a = __ldg(g0 + s * sstride);
@@ -210,7 +221,8 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
   constexpr bool WIDE_X = (MODE & 1) != 0, TAU_LIM = (MODE & 2) != 0;
   float B_prev = planck<WIDE_X>(c1nu3, nuf * r.c2_t);
   float tau_v = 0.0f;                            // vertical optical depth from the top
-  for (int k = 1; k < L; ++k) {
+  // levels 0 .. L_run-1: a gray cloud deck on level L_run-1 ends the column
+  for (int k = 1; k < ex.L_run; ++k) {
     r = twp[k];
     const float chi = chi_at(r);
     const float B = planck<WIDE_X>(c1nu3, nuf * r.c2_t);
@@ -229,7 +241,7 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
       // Sec. 4 item 7: stop at the caller's optical-depth limit; the level
       // reached is then the bottom boundary (its blackbody below)
       tau_v += dtau;
-      if (tau_v > tau_cut) break;
+      if (tau_v > ex.tau_cut) break;
     }
   }
   float F = 0.0f;
@@ -324,19 +336,180 @@ __global__ void band_integrate_kernel(const float* __restrict__ spectra, const i
   }
 }
 
+// Contribution functions of the emission spectrum (post-processing of
+// Sec. 3): the same layer loop as emission_kernel, one thread per (proposal,
+// wavenumber), but each layer's term of the intensity sum is stored instead
+// of accumulated: C_k = 2 pi sum_i w_i mu_i (B_k + B_{k+1})/2 (t_k - t_{k+1})
+// for the layer between levels k and k+1, then at the last level integrated
+// (kb: the deck, the optical-depth limit or L-1) its blackbody seen through
+// the column, and zeros below.  sum_k C_k is the flux of emission_kernel.
+// Species count and the Planck/limit options are runtime values here (a
+// post-processing pass over a few spectra), only the angle count is a
+// template parameter.
+constexpr int CF_THREADS = 128;
+
+template <int NA>
+__global__ void __launch_bounds__(CF_THREADS)
+contrib_kernel(const float* __restrict__ grid, int S, int L, int M, int64_t N, const LayerTW* __restrict__ tw,
+               const float* __restrict__ coef, const float* __restrict__ dpg, const float* __restrict__ ang,
+               double nu_start, double dnu, const int64_t* __restrict__ nu_lo, const int64_t* __restrict__ nu_hi,
+               float* __restrict__ contrib, const int32_t* __restrict__ act_mask, int* __restrict__ status,
+               EmExtra ex, int wide_x, int tau_lim) {
+  const int p = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (act_mask && !act_mask[p]) return;
+  const int64_t lo = nu_lo ? nu_lo[p] : 0;
+  const int64_t hi = nu_hi ? nu_hi[p] : N;
+  if (lo < 0 || hi > N || lo >= hi) {
+    if (tid == 0 && blockIdx.y == 0) atomicOr(status, BART_DEV_RANGE);
+    return;
+  }
+  const int64_t j = lo + (int64_t)blockIdx.y * CF_THREADS + tid;
+  if (j >= hi) return;                       // no block-level synchronisation below
+  float xs[4];
+  for (int s = 0; s < 4; ++s) xs[s] = s < S ? coef[(int64_t)p * S + s] : 0.0f;
+  const double nu = nu_start + (double)j * dnu;
+  const float nuf = (float)nu;
+  const float c1nu3 = (float)(2.0 * bartc::H * bartc::C * bartc::C * nu * nu * nu);
+  const float chi_r = (float)(ex.ray * (nu * nu) * (nu * nu));
+  float nl2mu[NA], wmu[NA], lt[NA], t[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) {
+    nl2mu[i] = ang[i];
+    wmu[i] = ang[NA + i];
+    lt[i] = 0.0f;
+    t[i] = 1.0f;
+  }
+  const LayerTW* twp = tw + (int64_t)p * L;
+  const int64_t sstride = (int64_t)L * M * N;
+  const int64_t dm = (M > 1) ? N : 0;
+  const float* gj = grid + j;
+  auto chi_at = [&](const LayerTW& r) {
+    float chi = chi_r;
+    for (int s = 0; s < S; ++s) {
+      const float a = __ldg(gj + r.row + s * sstride);
+      const float b = __ldg(gj + r.row + s * sstride + dm);
+      chi = fmaf(xs[s], fmaf(r.w, b - a, a), chi);
+    }
+    return chi;
+  };
+  auto planck_x = [&](float x) { return wide_x ? planck<true>(c1nu3, x) : planck<false>(c1nu3, x); };
+  float* out = contrib + (int64_t)p * L * N + j;
+  LayerTW r = twp[0];
+  float chi_prev = chi_at(r);
+  float B_prev = planck_x(nuf * r.c2_t);
+  float tau_v = 0.0f;
+  int k = 1;
+  for (; k < ex.L_run; ++k) {
+    r = twp[k];
+    const float chi = chi_at(r);
+    const float B = planck_x(nuf * r.c2_t);
+    const float dtau = (chi_prev + chi) * dpg[k - 1];
+    const float Bsum = B_prev + B;
+    float C = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      lt[i] = fmaf(dtau, nl2mu[i], lt[i]);
+      const float te = bartf::ex2_approx(lt[i]);
+      C = fmaf(wmu[i], Bsum * (t[i] - te), C);
+      t[i] = te;
+    }
+    out[(int64_t)(k - 1) * N] = C;
+    chi_prev = chi;
+    B_prev = B;
+    if (tau_lim) {
+      tau_v += dtau;
+      if (tau_v > ex.tau_cut) {
+        ++k;
+        break;
+      }
+    }
+  }
+  // k - 1 is now the last level integrated: its blackbody through the column
+  float Cb = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NA; ++i) Cb = fmaf(wmu[i], 2.0f * B_prev * t[i], Cb);
+  out[(int64_t)(k - 1) * N] = Cb;
+  for (int q = k; q < L; ++q) out[(int64_t)q * N] = 0.0f;
+}
+
+// Band means of contribution rows: one CTA per (row = proposal x level, band),
+// trapezoid weights over the proposal's span, FP64 sums (as
+// band_integrate_kernel).
+__global__ void contrib_band_kernel(const float* __restrict__ contrib, int L, int64_t N,
+                                    const int64_t* __restrict__ nu_lo, const int64_t* __restrict__ nu_hi,
+                                    const float* __restrict__ filt, int n_bands, const int32_t* __restrict__ act_mask,
+                                    float* __restrict__ out) {
+  const int row = blockIdx.x, b = blockIdx.y;
+  const int p = row / L;
+  if (act_mask && !act_mask[p]) return;
+  const int64_t lo = nu_lo ? nu_lo[p] : 0, hi = nu_hi ? nu_hi[p] : N;
+  if (lo < 0 || hi > N || lo >= hi) return;   // reported by contrib_kernel
+  const float* c = contrib + (int64_t)row * N;
+  double num = 0.0, den = 0.0;
+  for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+    const float dw = (hi - lo == 1) ? 1.0f : ((j == lo || j == hi - 1) ? 0.5f : 1.0f);
+    const float W = __ldg(filt + (int64_t)b * N + j) * dw;
+    num += (double)W * (double)c[j];
+    den += (double)W;
+  }
+  __shared__ double sn[32], sd[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sn[threadIdx.x >> 5] = num;
+    sd[threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, d = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += sn[w];
+      d += sd[w];
+    }
+    out[(int64_t)row * n_bands + b] = d > 0.0 ? (float)(a / d) : 0.0f;
+  }
+}
+
+using CfLauncher = void (*)(dim3, cudaStream_t, const float*, int, int, int, int64_t, const LayerTW*, const float*,
+                            const float*, const float*, double, double, const int64_t*, const int64_t*, float*,
+                            const int32_t*, int*, EmExtra, int, int);
+
+template <int NA>
+void launch_contrib(dim3 g, cudaStream_t st, const float* grid, int S, int L, int M, int64_t N, const LayerTW* tw,
+                    const float* coef, const float* dpg, const float* ang, double nu_start, double dnu,
+                    const int64_t* lo, const int64_t* hi, float* contrib, const int32_t* active, int* status,
+                    EmExtra ex, int wide_x, int tau_lim) {
+  contrib_kernel<NA><<<g, CF_THREADS, 0, st>>>(grid, S, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi, contrib,
+                                               active, status, ex, wide_x, tau_lim);
+}
+
+CfLauncher pick_contrib(int na) {
+  switch (na) {
+    case 1: return launch_contrib<1>;
+    case 2: return launch_contrib<2>;
+    case 4: return launch_contrib<4>;
+    case 8: return launch_contrib<8>;
+    case 16: return launch_contrib<16>;
+    default: return nullptr;
+  }
+}
+
 template <int S, int NA, int TW, int MODE>
 void launch_emission(dim3 g, cudaStream_t st, const float* grid, int L, int M, int64_t N, const LayerTW* tw,
                      const float* coef, const float* dpg, const float* ang, double nu_start, double dnu,
                      const int64_t* lo, const int64_t* hi, const int64_t* offs, float* spectra,
                      const float* filt, int nb, float2* partial, int n_tiles, const int32_t* active, int* status,
-                     float tau_cut) {
+                     EmExtra ex) {
   emission_kernel<S, NA, TW, MODE><<<g, TW, 0, st>>>(grid, L, M, N, tw, coef, dpg, ang, nu_start, dnu, lo, hi, offs,
-                                               spectra, filt, nb, partial, n_tiles, active, status, tau_cut);
+                                               spectra, filt, nb, partial, n_tiles, active, status, ex);
 }
 
 using EmLauncher = void (*)(dim3, cudaStream_t, const float*, int, int, int64_t, const LayerTW*, const float*,
                             const float*, const float*, double, double, const int64_t*, const int64_t*,
-                            const int64_t*, float*, const float*, int, float2*, int, const int32_t*, int*, float);
+                            const int64_t*, float*, const float*, int, float2*, int, const int32_t*, int*, EmExtra);
 
 // Wavenumber-tile widths the autotuner chooses from (threads per CTA).
 constexpr int TILE_CHOICES[3] = {64, 128, 256};
@@ -379,6 +552,25 @@ float tau_cut_of(const bart_fwd_cfg* c) {
   return (c->tau_max > 0.0 && std::isfinite(c->tau_max)) ? (float)c->tau_max : 3.0e38f;
 }
 
+// Levels the emission integral keeps under a gray cloud deck at p_cloud_bar:
+// the deck sits on the first grid level with P >= p_cloud (at least the
+// second level); no such level, or p_cloud <= 0: all L levels.
+int deck_levels_of(const bart_grid_desc* g, const bart_fwd_cfg* c) {
+  const int L = g->n_layers;
+  if (!(c->p_cloud_bar > 0.0)) return L;
+  for (int k = 0; k < L; ++k)
+    if (g->p_bar[k] >= c->p_cloud_bar) return std::max(k + 1, 2);
+  return L;
+}
+
+EmExtra emission_extra(const bart_grid_desc* g, const bart_fwd_cfg* c) {
+  EmExtra ex;
+  ex.L_run = deck_levels_of(g, c);
+  ex.tau_cut = tau_cut_of(c);
+  ex.ray = c->rayleigh_coef / (c->mu_amu * bartc::AMU);
+  return ex;
+}
+
 // True where x = c2 nu / T can exceed 20 on the grid: T is clamped to
 // [t_min, t_max] by tp_kernel, so x <= c2 nu_max / t_min.
 bool planck_wide(const bart_nugrid& nu, double t_min) {
@@ -407,10 +599,11 @@ int emission_mode(const bart_grid_desc* g, const bart_fwd_cfg* c) {
 bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
                                     const bart_batch* b, float* spectra, const bart_filters* f, float* bands);
 
-extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
-                                                  const bart_batch* b, float* spectra, const bart_filters* f,
-                                                  float* bands) {
-  if (!ctx) return BART_EINVAL;
+namespace {
+
+// Checks shared by the batched forward model and the contribution functions.
+bart_status check_forward_request(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
+                                  const bart_batch* b) {
   BART_REQUIRE(ctx, g && c && b, "NULL grid, cfg or batch");
   BART_REQUIRE(ctx, g->grid, "grid->grid is NULL");
   BART_REQUIRE(ctx, g->n_species >= 1 && g->n_layers >= 2 && g->n_layers <= MAX_LAYERS && g->n_temps >= 1,
@@ -425,9 +618,70 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
     BART_REQUIRE(ctx, g->t_K[m] > 0 && (m == 0 || g->t_K[m] > g->t_K[m - 1]),
                  "t_K must be positive and strictly increasing");
   BART_REQUIRE(ctx, c->g_cgs > 0 && c->mu_amu > 0 && c->x0, "cfg: g, mu must be > 0 and x0 set");
+  BART_REQUIRE(ctx, c->rayleigh_coef >= 0 && std::isfinite(c->rayleigh_coef) && !std::isnan(c->p_cloud_bar),
+               "cfg: rayleigh_coef must be finite and >= 0, p_cloud_bar not NaN");
   BART_REQUIRE(ctx, b->n >= 1, "batch.n must be >= 1");
   BART_REQUIRE(ctx, b->theta || b->t_profile, "batch needs theta or t_profile");
   BART_REQUIRE(ctx, (b->nu_lo == nullptr) == (b->nu_hi == nullptr), "nu_lo and nu_hi go together");
+  return BART_OK;
+}
+
+// Constants, layer brackets and abundance coefficients of an emission batch:
+// uploads the constant table and launches tp_kernel on the context's stream.
+struct EmPrep {
+  const float* dc;      // [p_cgs L][t_axis M][dpg L-1][ang 2NA][x0 S]
+  size_t off_dpg, off_ang;
+  LayerTW* tw;
+  float* coef;
+};
+
+bart_status emission_prologue(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c, const bart_batch* b,
+                              EmPrep* out) {
+  const int S = g->n_species, L = g->n_layers, M = g->n_temps, n = b->n;
+  const int64_t N = g->nu.n_nu;
+  std::vector<double> mu, w;
+  gauss_legendre01(c->n_angles, mu, w);
+  const int NA = c->n_angles;
+  std::vector<float> hconst;
+  for (int k = 0; k < L; ++k) hconst.push_back((float)(g->p_bar[k] * bartc::BAR));
+  for (int m = 0; m < M; ++m) hconst.push_back((float)g->t_K[m]);
+  for (int k = 0; k + 1 < L; ++k)
+    hconst.push_back((float)((g->p_bar[k + 1] - g->p_bar[k]) * bartc::BAR / (2.0 * c->g_cgs)));
+  for (int i = 0; i < NA; ++i) hconst.push_back((float)(-1.4426950408889634 / mu[i]));
+  for (int i = 0; i < NA; ++i) hconst.push_back((float)(2.0 * bartc::PI * w[i] * mu[i] * 0.5));
+  for (int s = 0; s < S; ++s) hconst.push_back((float)(c->x0[s] / (c->mu_amu * bartc::AMU)));
+  const size_t off_t = L, off_dpg = off_t + M, off_ang = off_dpg + (L - 1), off_x0 = off_ang + 2 * NA;
+  void *p_const, *p_tw, *p_coef;
+  bart_status st;
+  if ((st = bart_upload_const(ctx, "fw_const", hconst.data(), hconst.size() * sizeof(float), &p_const)) != BART_OK)
+    return st;
+  if ((st = bart_scratch(ctx, "fw_tw", (size_t)n * L * sizeof(LayerTW), &p_tw)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "fw_coef", (size_t)n * S * sizeof(float), &p_coef)) != BART_OK) return st;
+  const float* dc = (const float*)p_const;
+  const double rs = c->r_star_tp_cm, a = c->a_orbit_cm;
+  const float tirr0 = (rs > 0 && a > 0) ? (float)(std::sqrt(rs / (2.0 * a)) * c->t_star_K) : 0.0f;
+  const float tint4 = (float)std::pow(c->t_int_K, 4.0);
+  tp_kernel<<<n, 128, 0, ctx->stream>>>(b->theta, 5 + S, b->t_profile, n, L, S, dc, dc + off_t, M, N,
+                                        (float)(1.0 / c->g_cgs), tint4, tirr0, (float)c->t_min_K,
+                                        (float)std::min(c->t_max_K, 1e30), dc + off_x0, (LayerTW*)p_tw,
+                                        (float*)p_coef, b->active, ctx->d_status);
+  if ((st = bart_check_launch(ctx, "tp_kernel")) != BART_OK) return st;
+  out->dc = dc;
+  out->off_dpg = off_dpg;
+  out->off_ang = off_ang;
+  out->tw = (LayerTW*)p_tw;
+  out->coef = (float*)p_coef;
+  return BART_OK;
+}
+
+}  // namespace
+
+extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
+                                                  const bart_batch* b, float* spectra, const bart_filters* f,
+                                                  float* bands) {
+  if (!ctx) return BART_EINVAL;
+  bart_status st;
+  if ((st = check_forward_request(ctx, g, c, b)) != BART_OK) return st;
   int nb = 0;
   if (bands) {
     BART_REQUIRE(ctx, f && f->weights, "bands requested without filters");
@@ -444,55 +698,30 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
                      "(species 1-4; angles 1, 2, 4, 8, 16)", S, c->n_angles);
   BART_CUDA(ctx, cudaSetDevice(ctx->device));
 
-  // host-side constants
-  std::vector<double> mu, w;
-  gauss_legendre01(c->n_angles, mu, w);
   const int NA = c->n_angles;
-  std::vector<float> hconst;                 // [p_cgs L][t_axis M][dpg L-1][ang 2NA][x0 S]
-  for (int k = 0; k < L; ++k) hconst.push_back((float)(g->p_bar[k] * bartc::BAR));
-  for (int m = 0; m < M; ++m) hconst.push_back((float)g->t_K[m]);
-  for (int k = 0; k + 1 < L; ++k)
-    hconst.push_back((float)((g->p_bar[k + 1] - g->p_bar[k]) * bartc::BAR / (2.0 * c->g_cgs)));
-  for (int i = 0; i < NA; ++i) hconst.push_back((float)(-1.4426950408889634 / mu[i]));
-  for (int i = 0; i < NA; ++i) hconst.push_back((float)(2.0 * bartc::PI * w[i] * mu[i] * 0.5));
-  for (int s = 0; s < S; ++s) hconst.push_back((float)(c->x0[s] / (c->mu_amu * bartc::AMU)));
-  const size_t off_t = L, off_dpg = off_t + M, off_ang = off_dpg + (L - 1), off_x0 = off_ang + 2 * NA;
-
+  EmPrep pr;
+  if ((st = emission_prologue(ctx, g, c, b, &pr)) != BART_OK) return st;
   const int max_tiles = (int)((N + MIN_TILE - 1) / MIN_TILE);   // partials sized for the smallest tile
-  void *p_const, *p_tw, *p_coef, *p_part = nullptr;
-  bart_status st;
-  if ((st = bart_upload_const(ctx, "fw_const", hconst.data(), hconst.size() * sizeof(float), &p_const)) != BART_OK)
-    return st;
-  if ((st = bart_scratch(ctx, "fw_tw", (size_t)n * L * sizeof(LayerTW), &p_tw)) != BART_OK) return st;
-  if ((st = bart_scratch(ctx, "fw_coef", (size_t)n * S * sizeof(float), &p_coef)) != BART_OK) return st;
+  void* p_part = nullptr;
   if (nb > 0 &&
       (st = bart_scratch(ctx, "fw_part", (size_t)n * max_tiles * nb * sizeof(float2), &p_part)) != BART_OK)
     return st;
-  const float* dc = (const float*)p_const;
-  const double rs = c->r_star_tp_cm, a = c->a_orbit_cm;
-  const float tirr0 = (rs > 0 && a > 0) ? (float)(std::sqrt(rs / (2.0 * a)) * c->t_star_K) : 0.0f;
-  const float tint4 = (float)std::pow(c->t_int_K, 4.0);
-  tp_kernel<<<n, 128, 0, ctx->stream>>>(b->theta, 5 + S, b->t_profile, n, L, S, dc, dc + off_t, M, N,
-                                        (float)(1.0 / c->g_cgs), tint4, tirr0, (float)c->t_min_K,
-                                        (float)std::min(c->t_max_K, 1e30), dc + off_x0, (LayerTW*)p_tw,
-                                        (float*)p_coef, b->active, ctx->d_status);
-  if ((st = bart_check_launch(ctx, "tp_kernel")) != BART_OK) return st;
   const int mode = emission_mode(g, c);
-  const float tau_cut = tau_cut_of(c);
+  const EmExtra ex = emission_extra(g, c);
   auto run = [&](int tw) {
     const int n_tiles = (int)((N + tw - 1) / tw);
     pick_emission(S, c->n_angles, tw, mode)(dim3((unsigned)n, (unsigned)n_tiles), ctx->stream, g->grid, L, M, N,
-                                      (const LayerTW*)p_tw, (const float*)p_coef, dc + off_dpg, dc + off_ang,
+                                      pr.tw, pr.coef, pr.dc + pr.off_dpg, pr.dc + pr.off_ang,
                                       g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
                                       nb ? f->weights : nullptr, nb, (float2*)p_part, n_tiles, b->active,
-                                      ctx->d_status, tau_cut);
+                                      ctx->d_status, ex);
     return n_tiles;
   };
   // Tile width: cached per shape; measured once (each candidate timed with
   // CUDA events on the stream) unless the stream is being captured.
   char key[160];
-  snprintf(key, sizeof(key), "em S%d A%d L%d M%d N%lld n%d b%d span%d m%d", S, NA, L, M, (long long)N, n, nb,
-           b->nu_lo ? 1 : 0, mode);
+  snprintf(key, sizeof(key), "em S%d A%d L%d/%d M%d N%lld n%d b%d span%d m%d", S, NA, L, ex.L_run, M, (long long)N,
+           n, nb, b->nu_lo ? 1 : 0, mode);
   int tw = EM_THREADS;
   auto it = ctx->tiles.find(key);
   if (it != ctx->tiles.end()) {
@@ -550,6 +779,49 @@ extern "C" bart_status bart_band_integrate(bart_ctx* ctx, const float* spectra, 
   return bart_check_launch(ctx, "band_integrate_kernel");
 }
 
+extern "C" bart_status bart_contribution_functions(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
+                                                   const bart_batch* b, float* contrib, const bart_filters* f,
+                                                   float* bands) {
+  if (!ctx) return BART_EINVAL;
+  bart_status st;
+  if ((st = check_forward_request(ctx, g, c, b)) != BART_OK) return st;
+  BART_REQUIRE(ctx, c->geometry == BART_EMISSION, "contribution functions are defined for emission only");
+  BART_REQUIRE(ctx, contrib || bands, "nothing requested: contrib and bands are both NULL");
+  int nb = 0;
+  if (bands) {
+    BART_REQUIRE(ctx, f && f->weights, "bands requested without filters");
+    nb = f->n_bands;
+    BART_REQUIRE(ctx, nb >= 1 && nb <= 65535, "n_bands must be in [1, 65535]");
+  }
+  CfLauncher launch = pick_contrib(c->n_angles);
+  BART_REQUIRE(ctx, launch != nullptr, "n_angles must be 1, 2, 4, 8 or 16");
+  BART_REQUIRE(ctx, g->n_species <= 4, "contribution functions support 1-4 species");
+  const int S = g->n_species, L = g->n_layers, M = g->n_temps, n = b->n;
+  const int64_t N = g->nu.n_nu;
+  BART_REQUIRE(ctx, (int64_t)n * L <= 2147483647LL, "n x n_layers too large");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  EmPrep pr;
+  if ((st = emission_prologue(ctx, g, c, b, &pr)) != BART_OK) return st;
+  float* out = contrib;
+  if (!out) {
+    void* p = nullptr;
+    if ((st = bart_scratch(ctx, "cf_rows", (size_t)n * L * N * sizeof(float), &p)) != BART_OK) return st;
+    out = (float*)p;
+  }
+  const int mode = emission_mode(g, c);
+  const int64_t n_tiles = (N + CF_THREADS - 1) / CF_THREADS;
+  launch(dim3((unsigned)n, (unsigned)n_tiles), ctx->stream, g->grid, S, L, M, N, pr.tw, pr.coef,
+         pr.dc + pr.off_dpg, pr.dc + pr.off_ang, g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, out, b->active,
+         ctx->d_status, emission_extra(g, c), mode & 1, (mode >> 1) & 1);
+  if ((st = bart_check_launch(ctx, "contrib_kernel")) != BART_OK) return st;
+  if (nb > 0) {
+    contrib_band_kernel<<<dim3((unsigned)(n * L), (unsigned)nb), 256, 0, ctx->stream>>>(
+        out, L, N, b->nu_lo, b->nu_hi, f->weights, nb, b->active, bands);
+    if ((st = bart_check_launch(ctx, "contrib_band_kernel")) != BART_OK) return st;
+  }
+  return BART_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Emission forward model that allocates nothing.
 //
@@ -604,6 +876,7 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
   if (c->geometry != BART_EMISSION) return BART_EUNSUPPORTED;
   if (S < 1 || L < 2 || M < 1 || n < 1 || N < 1 || nb < 0 || (nb > 0 && !f->weights) || !(g->nu.dnu_cm > 0) ||
       c->n_angles < 1 || !(c->g_cgs > 0) || !(c->mu_amu > 0) || (!b->theta && !b->t_profile) ||
+      !(c->rayleigh_coef >= 0 && std::isfinite(c->rayleigh_coef)) || std::isnan(c->p_cloud_bar) ||
       ((b->nu_lo == nullptr) != (b->nu_hi == nullptr)))
     return BART_EINVAL;   // malformed request
   if (S > NA_MAX_SPECIES || L > NA_MAX_LAYERS || M > NA_MAX_TEMPS || n > NA_MAX_ENTRIES || N > NA_MAX_NU ||
@@ -664,7 +937,7 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
   const int n_tiles = (int)((N + EM_THREADS - 1) / EM_THREADS);
   launch(dim3((unsigned)n, (unsigned)n_tiles), st, g->grid, L, M, N, a.tw, a.coef, a.cst + off_dpg,
          a.cst + off_ang, g->nu.nu_start_cm, g->nu.dnu_cm, b->nu_lo, b->nu_hi, b->spec_offsets, spectra,
-         nb ? f->weights : nullptr, nb, a.part, n_tiles, b->active, a.status, tau_cut_of(c));
+         nb ? f->weights : nullptr, nb, a.part, n_tiles, b->active, a.status, emission_extra(g, c));
   if (nb > 0) {
     const int64_t tot = (int64_t)n * nb;
     band_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(a.part, n, n_tiles, nb, b->active, bands);

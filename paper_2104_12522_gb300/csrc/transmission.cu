@@ -6,12 +6,14 @@
 //                   p_top and p_bot), T(P), hydrostatic altitudes in FP64
 //                   (g ~ r^-2, r = R_p at P_ref, trapezoid in ln P with P_ref as
 //                   a node), number densities and the bilinear (log10 P, T)
-//                   brackets on the grid.
+//                   brackets on the grid; a gray cloud deck cuts the
+//                   instance's level count at its level (opaque below).
 //   trans_kernel    persistent CTAs pulling (wavenumber tile, instance) units
 //                   from an atomic counter; tile-major order keeps the grid
 //                   slab of a tile in L2 while every instance covering it runs.
-//                   Per unit: shell extinction for 128 wavenumbers into shared
-//                   memory, then the ray optical depths
+//                   Per unit: shell extinction for 128 wavenumbers (lines
+//                   plus Rayleigh a nu^4 per molecule) into shared memory,
+//                   then the ray optical depths
 //                   tau_i = sum_{k<i} ds_ik (alpha_k + alpha_{k+1}) / 2,
 //                   register-blocked over 8 rays per pass, chords recomputed
 //                   per pass as 2 (A - B) / (sqrt A + sqrt B) from altitude
@@ -55,7 +57,7 @@ __global__ void trans_prologue(const float* __restrict__ theta, int n_theta, int
                                double p_ref, double g, double mu_amu, float inv_g_f, float tint4, float tirr0,
                                float t_min, float t_max, const float* __restrict__ x0, TrLevel* __restrict__ lev,
                                TrInst* __restrict__ inst, const int32_t* __restrict__ act_mask,
-                               int* __restrict__ status) {
+                               int* __restrict__ status, double p_cloud) {
   const int i = blockIdx.x;
   if (i >= n) return;
   if (act_mask && !act_mask[i]) return;      // skipped entry
@@ -154,8 +156,20 @@ __global__ void trans_prologue(const float* __restrict__ theta, int n_theta, int
       // r = 1/(1/R_p + C phi): altitude r - R_p written without cancellation
       lev[(int64_t)i * TR_LMAX + k].z = (float)(-cphi * rp * rp / (1.0 + cphi * rp));
     }
+    // gray cloud deck: the column ends on the first level with P >= p_cloud
+    // (at least two levels); altitudes above stay those of the whole column
+    int L_eff = L;
+    if (p_cloud > 0.0) {
+      for (int k = 0; k < L; ++k) {
+        const double lp = lt + (lb - lt) * (double)k / (double)(L - 1);
+        if (exp10(lp) >= p_cloud) {
+          L_eff = max(k + 1, 2);
+          break;
+        }
+      }
+    }
     TrInst in;
-    in.L = L;
+    in.L = L_eff;
     in.ok = 1;
     in.r_planet = r_planet[i];
     in.r_star = r_star[i];
@@ -186,7 +200,8 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
              const int64_t* __restrict__ nu_hi, const int64_t* __restrict__ offs, float* __restrict__ spectra,
              const float* __restrict__ filt, int n_bands, float2* __restrict__ partial, int n_gtiles,
              unsigned long long n_units, unsigned long long* __restrict__ counter,
-             const int32_t* __restrict__ active, int* __restrict__ status) {
+             const int32_t* __restrict__ active, int* __restrict__ status, double nu_start, double dnu,
+             double ray) {
   extern __shared__ float smem[];
   float* s_alpha = smem;                                  // [TR_LMAX][TR_THREADS] shell extinction
   float* s_ds = s_alpha + TR_LMAX * TR_THREADS;           // [TR_LMAX][TR_RB] chords of the ray block
@@ -232,6 +247,9 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
     const int64_t j = g0 + tid;
     const bool active = (j >= lo) && (j < hi);
     const int64_t jj = active ? j : lo;
+    // Rayleigh cross-section per molecule a nu^4, the same at every level
+    const double nu = nu_start + (double)jj * dnu;
+    const float sig_r = (float)(ray * (nu * nu) * (nu * nu));
     // extinction at every level, then shell means into shared memory
     float a_prev = 0.f;
 #pragma unroll 2
@@ -240,7 +258,7 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
       const float* base = grid + ((int64_t)lv.a * M + lv.m) * N + jj;
       const int64_t dl = (Lg > 1) ? (int64_t)M * N : 0;
       const int64_t dm = (M > 1) ? N : 0;
-      float sig = 0.f;
+      float sig = sig_r;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         const float* b = base + s * sstride;
@@ -360,15 +378,17 @@ __global__ void trans_band_reduce(const float2* __restrict__ partial, const int6
 using TrLauncher = void (*)(int, size_t, cudaStream_t, const float*, int, int, int64_t, const TrLevel*,
                             const TrInst*, int, const int64_t*, const int64_t*, const int64_t*, float*,
                             const float*, int, float2*, int, unsigned long long, unsigned long long*,
-                            const int32_t*, int*);
+                            const int32_t*, int*, double, double, double);
 
 template <int S>
 void launch_trans(int grid_dim, size_t smem, cudaStream_t st, const float* grid, int Lg, int M, int64_t N,
                   const TrLevel* lev, const TrInst* inst, int n, const int64_t* lo, const int64_t* hi,
                   const int64_t* offs, float* spectra, const float* filt, int nb, float2* partial, int ngt,
-                  unsigned long long nu, unsigned long long* counter, const int32_t* active, int* status) {
+                  unsigned long long nu, unsigned long long* counter, const int32_t* active, int* status,
+                  double nu_start, double dnu, double ray) {
   trans_kernel<S><<<grid_dim, TR_THREADS, smem, st>>>(grid, Lg, M, N, lev, inst, n, lo, hi, offs, spectra, filt,
-                                                      nb, partial, ngt, nu, counter, active, status);
+                                                      nb, partial, ngt, nu, counter, active, status, nu_start,
+                                                      dnu, ray);
 }
 
 template <int S>
@@ -430,7 +450,7 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
       b->theta, 5 + S, n, S, b->n_levels, b->r_planet_cm, b->r_star_cm, dc, Lg, dc + Lg, M, c->p_top_bar,
       c->p_bot_bar, c->p_ref_bar, c->g_cgs, c->mu_amu, (float)(1.0 / c->g_cgs), (float)std::pow(c->t_int_K, 4.0),
       tirr0, (float)c->t_min_K, (float)std::min(c->t_max_K, 1e30), dc + Lg + M, (TrLevel*)p_lev,
-      (TrInst*)p_inst, b->active, ctx->d_status);
+      (TrInst*)p_inst, b->active, ctx->d_status, c->p_cloud_bar);
   if ((st = bart_check_launch(ctx, "trans_prologue")) != BART_OK) return st;
   const unsigned long long n_units = (unsigned long long)n_gtiles * (unsigned long long)n;
   if (per_sm < 1) per_sm = 1;
@@ -438,7 +458,8 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
   if ((unsigned long long)grid_dim > n_units) grid_dim = (int)n_units;
   launch(grid_dim, smem, ctx->stream, g->grid, Lg, M, N, (const TrLevel*)p_lev, (const TrInst*)p_inst, n,
          b->nu_lo, b->nu_hi, b->spec_offsets, spectra, nb ? f->weights : nullptr, nb, (float2*)p_part, n_gtiles,
-         n_units, (unsigned long long*)p_counter, b->active, ctx->d_status);
+         n_units, (unsigned long long*)p_counter, b->active, ctx->d_status, g->nu.nu_start_cm, g->nu.dnu_cm,
+         c->rayleigh_coef);
   if ((st = bart_check_launch(ctx, "trans_kernel")) != BART_OK) return st;
   if (nb > 0) {
     const int64_t tot = (int64_t)n * nb;

@@ -196,3 +196,107 @@ def test_tau_limit(ctx, torch, grid_case):
     icfg = dict(cfg, t_min=1.0, t_max=1e5)
     ctx.forward_spectra_batch(g_dev, p, t, nu, icfg, t_profile=T, spectra=iso, n=2)
     assert max_rel(iso.cpu().numpy(), np.pi * R.planck(nu_ax, 1500.0)[None]) < 1e-5
+
+
+@pytest.mark.parametrize("deck,ray", [(True, 0.0), (False, 1e-34), (True, 1e-34)])
+def test_cloud_deck_and_rayleigh(ctx, torch, grid_case, deck, ray):
+    """Sec. 3 gray cloud deck and Rayleigh scattering: parity with the oracle
+    on the batched grid case.  The Rayleigh coefficient is raised to a haze
+    (vertical optical depth 1 near 1e-4 bar at 1000 cm^-1) so that it matters on
+    this grid; the deck sits between two grid layers."""
+    species, p, t, N, dnu, nu, g_dev, g_ora = grid_case
+    theta = W.proposals(6, generation=11, n_species=2)
+    cfg = _cfg(4, [W.BASE_VMR] * 2)
+    p_cloud = float(np.sqrt(p[8] * p[9])) if deck else 0.0
+    cfg.update(p_cloud=p_cloud, rayleigh_coef=ray)
+    spec = torch.empty((6, N), dtype=torch.float32, device="cuda")
+    ctx.forward_spectra_batch(g_dev, p, t, nu, cfg, theta=torch.tensor(theta, device="cuda"), spectra=spec)
+    spec = spec.cpu().numpy()
+    ocfg = dict(g=cfg["g"], t_int=cfg["t_int"], t_star=cfg["t_star"], r_star_tp=cfg["r_star_tp"],
+                a_orbit=cfg["a_orbit"], t_min=500.0, t_max=3000.0, x0=cfg["x0"], mu=cfg["mu"], n_angles=4,
+                p_cloud=p_cloud, rayleigh_coef=ray)
+    nu_ax = W.nu_axis(1000.0, dnu, N)
+    ref = [Fw.emission_spectrum(g_ora, p, t, nu_ax, theta[i], ocfg) for i in range(6)]
+    es = max(max_rel(spec[i], ref[i]) for i in range(6))
+    plain = [Fw.emission_spectrum(g_ora, p, t, nu_ax, theta[i], dict(ocfg, p_cloud=None, rayleigh_coef=0.0))
+             for i in range(6)]
+    change = max(max_rel(ref[i], plain[i]) for i in range(6))
+    print(f"emission, deck {deck}, Rayleigh {ray}: FP32 vs FP64 {es:.2e} (the options change the spectra by "
+          f"{change:.2e})")
+    assert change > 5e-3                       # the case exercises the option
+    assert es < RTOL
+
+
+def test_deck_seen_through_a_transparent_atmosphere(ctx, torch):
+    """No opacity above an opaque deck on layer k: F = pi B(T_k)."""
+    import paper_2104_12522_gb300 as bart
+    L, N = 30, 500
+    p = W.log_pressures(L, 1e-6, 100.0)
+    grid = torch.zeros((1, L, 1, N), dtype=torch.float32, device="cuda")
+    nu = bart.NuGrid(1500.0, 9.0, N)
+    T = np.linspace(900.0, 2100.0, L)
+    Tt = torch.tensor(T, dtype=torch.float32, device="cuda")[None].contiguous()
+    spec = torch.empty((1, N), dtype=torch.float32, device="cuda")
+    nu_ax = W.nu_axis(1500.0, 9.0, N)
+    for k in (1, 9, 22):
+        cfg = _cfg(8, [1e-4])
+        cfg.update(t_min=1.0, t_max=1e5, p_cloud=float(p[k] * 0.99))
+        ctx.forward_spectra_batch(grid, p, [1000.0], nu, cfg, t_profile=Tt, spectra=spec, n=1)
+        assert max_rel(spec.cpu().numpy()[0], np.pi * R.planck(nu_ax, np.float32(T[k]))) < 1e-5
+
+
+@pytest.mark.parametrize("deck", [False, True])
+def test_contribution_functions(ctx, torch, grid_case, deck):
+    """Per-layer contribution functions (post-processing of Sec. 3): parity
+    of the rows with the oracle on proposals with uneven spans (and with a
+    cloud deck), band values of the rows against the oracle's band means, and
+    the rows adding up to the forward model's own spectra and bands."""
+    species, p, t, N, dnu, nu, g_dev, g_ora = grid_case
+    n, L = 5, len(p)
+    theta = W.proposals(n, generation=13, n_species=2)
+    lo = np.array([0, 3, 100, 257, 640], np.int64)
+    hi = np.array([N, 700, 101, 612, N], np.int64)
+    cfg = _cfg(4, [W.BASE_VMR] * 2)
+    p_cloud = float(np.sqrt(p[15] * p[16])) if deck else 0.0
+    cfg.update(p_cloud=p_cloud)
+    filt = W.gaussian_filters(W.nu_axis(1000.0, dnu, N), 6, 1002.0, 1033.0, 1.0, 6.0)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    th, d_lo, d_hi, d_f = dev(theta), dev(lo), dev(hi), dev(filt)
+    contrib = torch.full((n, L, N), -1.0, dtype=torch.float32, device="cuda")
+    cb = torch.empty((n, L, 6), dtype=torch.float32, device="cuda")
+    ctx.contribution_functions(g_dev, p, t, nu, cfg, theta=th, nu_lo=d_lo, nu_hi=d_hi, contrib=contrib,
+                               filters=d_f, bands=cb)
+    offs = np.concatenate([[0], np.cumsum(hi - lo)]).astype(np.int64)
+    spec = torch.empty(int(offs[-1]), dtype=torch.float32, device="cuda")
+    sb = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+    ctx.forward_spectra_batch(g_dev, p, t, nu, cfg, theta=th, nu_lo=d_lo, nu_hi=d_hi, spec_offsets=dev(offs),
+                              spectra=spec, filters=d_f, bands=sb)
+    ctx.sync()
+    contrib, cb, spec, sb = (v.cpu().numpy() for v in (contrib, cb, spec, sb))
+    ocfg = dict(g=cfg["g"], t_int=cfg["t_int"], t_star=cfg["t_star"], r_star_tp=cfg["r_star_tp"],
+                a_orbit=cfg["a_orbit"], t_min=500.0, t_max=3000.0, x0=cfg["x0"], mu=cfg["mu"], n_angles=4,
+                p_cloud=p_cloud)
+    nu_ax = W.nu_axis(1000.0, dnu, N)
+    e_row, e_band, e_sum = 0.0, 0.0, 0.0
+    for i in range(n):
+        # the oracle's contributions over the entry's span
+        sub = g_ora[..., lo[i]:hi[i]]
+        Co = Fw.emission_contributions(sub, p, t, nu_ax[lo[i]:hi[i]], theta[i], ocfg)
+        got = contrib[i][:, lo[i]:hi[i]]
+        assert np.all(contrib[i][:, :lo[i]] == -1.0) and np.all(contrib[i][:, hi[i]:] == -1.0)
+        # each layer's term, relative to the spectrum at that wavenumber (a
+        # thin layer's term is a difference of two transmittances: its own
+        # relative error in FP32 grows as the layer thins, its share of the
+        # flux does not)
+        e_row = max(e_row, float(np.max(np.abs(got - Co) / Co.sum(axis=0)[None, :])))
+        Bo = np.array([R.band_integrate(Co[k], filt, nu_lo=int(lo[i])) for k in range(L)])
+        Bs = Bo.sum(axis=0)
+        ok = Bs > 0
+        if ok.any():
+            e_band = max(e_band, float(np.max(np.abs(cb[i][:, ok] - Bo[:, ok]) / Bs[None, ok])))
+        e_sum = max(e_sum, max_rel(got.sum(axis=0, dtype=np.float64), spec[offs[i]:offs[i + 1]]))
+        okb = sb[i] != 0
+        e_sum = max(e_sum, max_rel(cb[i].sum(axis=0, dtype=np.float64)[okb], sb[i][okb]))
+    print(f"contribution functions (deck {deck}) FP32 vs FP64: rows {e_row:.2e}, bands {e_band:.2e}; "
+          f"sum vs the forward model {e_sum:.2e}")
+    assert e_row < 1e-5 and e_band < 1e-5 and e_sum < 1e-5

@@ -113,3 +113,60 @@ def test_bad_level_count_sets_status(ctx, torch, case):
     with pytest.raises(bart.BartError, match="ERANGE"):
         ctx.sync()
     ctx.sync()                                  # status was cleared
+
+
+@pytest.mark.parametrize("p_cloud,ray", [(3.3e-5, 0.0), (0.0, 1e-34), (3.3e-5, 1e-34)])
+def test_cloud_deck_and_rayleigh(ctx, torch, case, p_cloud, ray):
+    """Sec. 3 gray cloud deck and Rayleigh scattering on uneven instances:
+    parity with the oracle (Rayleigh raised to a haze, vertical optical depth 1
+    near 1e-4 bar at 1000 cm^-1, so that it matters on this grid)."""
+    S, p, t, N, dnu, nu, g_dev, g_ora = case
+    inst = W.instances(10, N, lmin=40, lmax=150, span_lo=1, span_hi=N, seed=4300)
+    inst.n_levels[0] = 192
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    offs = inst.offsets
+    n = len(inst.n_levels)
+    spec = torch.empty(int(offs[-1]), dtype=torch.float32, device="cuda")
+    cfg = dict(_cfg(S), p_cloud=p_cloud, rayleigh_coef=ray)
+    ctx.forward_spectra_batch(g_dev, p, t, nu, cfg, theta=dev(inst.theta), n_levels=dev(inst.n_levels),
+                              nu_lo=dev(inst.nu_lo), nu_hi=dev(inst.nu_hi), spec_offsets=dev(offs),
+                              r_planet=dev(inst.r_planet), r_star=dev(inst.r_star), spectra=spec)
+    spec = spec.cpu().numpy()
+    ocfg = dict(g=cfg["g"], t_int=cfg["t_int"], t_star=cfg["t_star"], r_star_tp=cfg["r_star_tp"],
+                a_orbit=cfg["a_orbit"], t_min=500.0, t_max=3000.0, x0=cfg["x0"], mu=cfg["mu"],
+                p_ref=cfg["p_ref"], p_top=1e-8, p_bot=100.0, p_cloud=p_cloud, rayleigh_coef=ray)
+    es, change = 0.0, 0.0
+    for i in range(n):
+        d = Fw.transmission_spectrum(g_ora, p, t, 1000.0, dnu, inst, i, ocfg)
+        d0 = Fw.transmission_spectrum(g_ora, p, t, 1000.0, dnu, inst, i,
+                                      dict(ocfg, p_cloud=None, rayleigh_coef=0.0))
+        es = max(es, max_rel(spec[offs[i]:offs[i + 1]], d))
+        change = max(change, max_rel(d, d0))
+    print(f"transmission, deck {p_cloud}, Rayleigh {ray}: FP32 vs FP64 {es:.2e} (the options change the "
+          f"spectra by {change:.2e})")
+    assert change > 1e-3
+    assert es < RTOL
+
+
+def test_deck_radius_through_a_transparent_atmosphere(ctx, torch, case):
+    """No opacity above the deck: delta = r_deck^2 / R_star^2 with r from the
+    whole column's hydrostatic altitudes."""
+    S, p, t, N, dnu, nu, g_dev, g_ora = case
+    zero = torch.zeros_like(g_dev)
+    inst = W.instances(3, N, span_lo=1, seed=4400)
+    inst.nu_lo[:], inst.nu_hi[:] = 0, N
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    spec = torch.empty((3, N), dtype=torch.float32, device="cuda")
+    cfg = dict(_cfg(S), p_cloud=0.0123)
+    ctx.forward_spectra_batch(zero, p, t, nu, cfg, theta=dev(inst.theta), n_levels=dev(inst.n_levels),
+                              r_planet=dev(inst.r_planet), r_star=dev(inst.r_star), spectra=spec)
+    from oracle import transmission as Tr, forward as F2
+    ocfg = dict(g=cfg["g"], t_int=cfg["t_int"], t_star=cfg["t_star"], r_star_tp=cfg["r_star_tp"],
+                a_orbit=cfg["a_orbit"], t_min=500.0, t_max=3000.0)
+    for i in range(3):
+        P = F2.instance_levels(inst.n_levels[i], 1e-8, 100.0)
+        T = F2.tp_of(inst.theta[i], P, ocfg)
+        r = Tr.radii(P, T, float(inst.r_planet[i]), cfg["p_ref"], cfg["g"], cfg["mu"])
+        k = int(np.nonzero(P >= 0.0123)[0][0])
+        exp = r[k] ** 2 / float(inst.r_star[i]) ** 2
+        assert max_rel(spec[i].cpu().numpy(), np.full(N, exp)) < 1e-5
