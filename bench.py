@@ -456,6 +456,8 @@ def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_line
     out["cloud_rayleigh"] = cloud_rayleigh_leg(ctx, torch, stream, grid, ax, nu, cfg, theta, run_t, ms, tcfg, targs,
                                                spec)
     out["paper_approximations"] = paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta)
+    out["grid_spacing"] = grid_spacing_leg(ctx, bart, torch, stream, ax, cfg, d_lines, theta)
+    out["contribution_functions"] = contribution_leg(ctx, torch, stream, grid, ax, nu, filt, cfg, theta)
     net, out["surrogate"] = train_surrogate(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S,
                                             args.train_steps)
     out["retrieval"] = run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net,
@@ -537,6 +539,64 @@ def cloud_rayleigh_leg(ctx, torch, stream, grid, ax, nu, cfg, theta, run_t, ms_t
                      "transmission_max_rel_change": _max_rel(torch, spec_t, t_ref, 0.0)}
     ctx.sync()
     return res
+
+
+def grid_spacing_leg(ctx, bart, torch, stream, ax, cfg, d_lines, theta, n_prop=256):
+    """App. D: band values of the same proposals on wavenumber grids of
+    0.025, 0.1, 0.25 and 1.0 cm^-1 (each also shifted by 0.09 cm^-1) over
+    1900..2100 cm^-1, against the 0.025 cm^-1 grid: the discretisation error
+    the grid spacing puts into band-integrated values.  Eight Gaussian bands
+    (FWHM 5..30 cm^-1); each grid built by the library (time reported)."""
+    res = []
+    th = theta[:n_prop].contiguous()
+    ref = None
+    for dnu in (0.025, 0.1, 0.25, 1.0):
+        for shift in (0.0, 0.09):
+            if dnu == 0.025 and shift:
+                continue
+            n_nu = int(round(200.0 / dnu))
+            nu_g = bart.NuGrid(1900.0 + shift, dnu, n_nu)
+            filt = torch.tensor(W.gaussian_filters(W.nu_axis(1900.0 + shift, dnu, n_nu), 8, 1920.0, 2080.0, 5.0,
+                                                   30.0, seed=3100), device=theta.device)
+            g = torch.empty((len(d_lines), len(ax.p_bar), len(ax.t_K), n_nu), dtype=torch.float32,
+                            device=theta.device)
+            build = lambda: ctx.build_opacity_grid(d_lines, ax.p_bar, ax.t_K, nu_g, ax.cutoff, out=g)
+            build()                                  # scratch sized on the first call
+            ms_build = _event_ms(torch, stream, build, reps=1)
+            bands = torch.empty((n_prop, 8), dtype=torch.float32, device=theta.device)
+            ctx.forward_spectra_batch(g, ax.p_bar, ax.t_K, nu_g, cfg, theta=th, filters=filt, bands=bands)
+            ctx.sync()
+            b = bands.double()
+            entry = {"dnu": dnu, "shift": shift, "n_nu": n_nu, "build_ms": ms_build}
+            if ref is None:
+                ref = b
+            else:
+                rel = ((b - ref).abs() / ref.abs()).flatten()
+                entry["band_max_rel_diff"] = float(rel.max())
+                entry["band_median_rel_diff"] = float(rel.median())
+            res.append(entry)
+            del g
+    return res
+
+
+def contribution_leg(ctx, torch, stream, grid, ax, nu, filt, cfg, theta, n=4):
+    """Band contribution functions of n proposals on the full grid (the
+    post-processing of Sec. 3): time, and how closely the per-layer band
+    values add up to the forward model's band values."""
+    th = theta[:n].contiguous()
+    L, nb = len(ax.p_bar), int(filt.shape[0])
+    cb = torch.empty((n, L, nb), dtype=torch.float32, device=theta.device)
+    run = lambda: ctx.contribution_functions(grid, ax.p_bar, ax.t_K, nu, cfg, theta=th, filters=filt, bands=cb)
+    run()
+    ms = _event_ms(torch, stream, run, reps=3)
+    bands = torch.empty((n, nb), dtype=torch.float32, device=theta.device)
+    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=th, filters=filt, bands=bands)
+    ctx.sync()
+    tot = cb.double().sum(dim=1)
+    rel = float(((tot - bands.double()).abs() / bands.double().abs()).max())
+    peak = cb.double().argmax(dim=1).float()
+    return {"proposals": n, "layers": L, "bands": nb, "ms": ms, "sum_vs_band_values_max_rel": rel,
+            "peak_layer_median": float(peak.median())}
 
 
 def paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta):

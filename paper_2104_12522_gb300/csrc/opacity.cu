@@ -19,16 +19,23 @@
 //    registers.  The offset x = (j - jc) dnu / (sigma sqrt 2) + delta /
 //    (sigma sqrt 2) is formed from exact integer differences, so it stays
 //    relatively accurate near the core.
-//  * Far field: where every point of the span has x^2 + y^2 large enough,
-//    the shifted Lorentz form (three FFMA and one MUFU reciprocal per
-//    line-point); elsewhere outside the core the one-pole form (five FFMA and
-//    one reciprocal).  Lines covering the whole span run without any
-//    per-lane weight; the others take a per-lane weight from a lane mask.
-//  * Blocks of 16 points holding a window edge or a line's core (|z| < 24) are
-//    evaluated point by point in a fixup pass; core points are gathered into
-//    two per-warp lists (Taylor table, continued fraction) and evaluated 32
-//    at a time, so lanes do not diverge across the branches.  All fixup sums
-//    go to a warp-private accumulator in a fixed order: deterministic.
+//  * Far field: lines far from the whole span by a degree-5 expansion of
+//    their shifted Lorentz term about each lane's block centre (coefficients
+//    summed over lines, expanded once per chunk); otherwise, where x^2 + y^2
+//    is large enough, the shifted Lorentz form with two lines per reciprocal;
+//    elsewhere outside the core the one-pole form.  These loops work on two
+//    points at a time with the packed FP32 instructions of sm_100+
+//    (__ffma2_rn, __fmul2_rn, __fadd2_rn: two lanes of arithmetic per issue).
+//    Lines covering the whole span run without any per-lane weight; the
+//    others take a per-lane weight from a lane mask.
+//  * Blocks of 16 points holding a window edge, a short stretch where the
+//    far-field forms are not accurate enough, or a line's core (|z| < 24) go
+//    to a fixup pass.  Lines with one-pole points only: lanes take the points
+//    of their blocks and sum over the lines in registers (one add per point).
+//    Lines with a core: point by point, core points gathered into two
+//    per-warp lists (Taylor table, continued fraction) and evaluated 32 at a
+//    time, so lanes do not diverge across the branches.  All fixup sums go to
+//    a warp-private accumulator in a fixed order: deterministic.
 //  * Partial sums are plain FP32 over 4 chunks of 32 lines and folded into a
 //    TwoSum (hi, lo) pair per point kept in shared memory: compensated
 //    accumulation.
@@ -258,7 +265,7 @@ struct OpShared {
   float hi[OP_WARPS][OP_R][32];
   float lo[OP_WARPS][OP_R][32];
   unsigned list[OP_WARPS][CORE_CAP];
-  int eidx[OP_WARPS][32];             // packed edge-only fixups: (first entry << 5) | slot
+  int eidx[OP_WARPS][32];             // one-pole-only fixups: slot | first block << 5 | last block << 10
 };
 
 __device__ __forceinline__ unsigned lane_range_mask(int a, int b) {   // bits a..b, empty if a > b
@@ -267,6 +274,71 @@ __device__ __forceinline__ unsigned lane_range_mask(int a, int b) {   // bits a.
   if (a > b) return 0u;
   const unsigned hi = (b == 31) ? 0xffffffffu : ((1u << (b + 1)) - 1u);
   return hi & ~((1u << a) - 1u);
+}
+
+// Far-field loops over the lane's 16 points, two points per packed FP32
+// instruction (__ffma2_rn and friends: sm_100+).  x advances by 2 dx per
+// pair (x_{r+2} = x_r + 2 dx): with |x| below 50 across a block the rounding
+// this adds to s = x^2 + y^2 - 3/2 stays below 1e-6 relative where s >= 866.
+// far != 0 moves the line to x = FAR_X (a lane that takes no weight).
+__device__ __forceinline__ float2 pair_x0(float j0r, const float4& a, float far) {
+  const float x0 = far != 0.0f ? FAR_X : fmaf(j0r - a.w, a.x, a.y);
+  const float dx = far != 0.0f ? 0.0f : a.x;
+  return make_float2(x0, x0 + dx);
+}
+
+// Two shifted-Lorentz lines per reciprocal: A1/s1 + A2/s2 = (A1 s2 + A2 s1) / (s1 s2).
+__device__ __forceinline__ void lorentz_pair(float2 (&acc)[OP_R / 2], float j0r, const float4& a, const float4& a2,
+                                             float A, float A2, float q, float q2, float far, float far2) {
+  float2 X = pair_x0(j0r, a, far), X2 = pair_x0(j0r, a2, far2);
+  const float2 D = make_float2(far != 0.0f ? 0.0f : 2.0f * a.x, far != 0.0f ? 0.0f : 2.0f * a.x);
+  const float2 D2 = make_float2(far2 != 0.0f ? 0.0f : 2.0f * a2.x, far2 != 0.0f ? 0.0f : 2.0f * a2.x);
+  const float2 Q = make_float2(q, q), Q2 = make_float2(q2, q2);
+  const float2 AA = make_float2(A, A), AA2 = make_float2(A2, A2);
+#pragma unroll
+  for (int r = 0; r < OP_R / 2; ++r) {
+    const float2 s1 = __ffma2_rn(X, X, Q), s2 = __ffma2_rn(X2, X2, Q2);
+    const float2 num = __ffma2_rn(AA2, s1, __fmul2_rn(AA, s2));
+    const float2 den = __fmul2_rn(s1, s2);
+    const float2 inv = make_float2(bartw::rcp_approx(den.x), bartw::rcp_approx(den.y));
+    acc[r] = __ffma2_rn(num, inv, acc[r]);
+    X = __fadd2_rn(X, D);
+    X2 = __fadd2_rn(X2, D2);
+  }
+}
+
+__device__ __forceinline__ void lorentz_one(float2 (&acc)[OP_R / 2], float j0r, const float4& a, float A, float q,
+                                            float far) {
+  float2 X = pair_x0(j0r, a, far);
+  const float2 D = make_float2(far != 0.0f ? 0.0f : 2.0f * a.x, far != 0.0f ? 0.0f : 2.0f * a.x);
+  const float2 Q = make_float2(q, q), AA = make_float2(A, A);
+#pragma unroll
+  for (int r = 0; r < OP_R / 2; ++r) {
+    const float2 s = __ffma2_rn(X, X, Q);
+    const float2 inv = make_float2(bartw::rcp_approx(s.x), bartw::rcp_approx(s.y));
+    acc[r] = __ffma2_rn(AA, inv, acc[r]);
+    X = __fadd2_rn(X, D);
+  }
+}
+
+// One-pole form A (u + 1) / (u^2 + 2 y^2), u = x^2 + y^2 - 1/2; CLAMP keeps
+// the denominator >= 1e-30.
+template <bool CLAMP>
+__device__ __forceinline__ void one_pole(float2 (&acc)[OP_R / 2], float j0r, const float4& a, float A, float qm,
+                                         float q2) {
+  float2 X = pair_x0(j0r, a, 0.0f);
+  const float2 D = make_float2(2.0f * a.x, 2.0f * a.x);
+  const float2 QM = make_float2(qm, qm), Q2 = make_float2(q2, q2), AA = make_float2(A, A);
+#pragma unroll
+  for (int r = 0; r < OP_R / 2; ++r) {
+    const float2 u = __ffma2_rn(X, X, QM);
+    const float2 num = __ffma2_rn(AA, u, AA);
+    const float2 den = __ffma2_rn(u, u, Q2);
+    const float2 inv = CLAMP ? make_float2(bartw::rcp_approx(fmaxf(den.x, 1e-30f)), bartw::rcp_approx(fmaxf(den.y, 1e-30f)))
+                             : make_float2(bartw::rcp_approx(den.x), bartw::rcp_approx(den.y));
+    acc[r] = __ffma2_rn(num, inv, acc[r]);
+    X = __fadd2_rn(X, D);
+  }
 }
 
 // Each lane owns one 16-point block of the warp's 512-point span.  For a line,
@@ -314,9 +386,13 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
 
   float (*hi)[32] = sh.hi[warp];
   float (*lo)[32] = sh.lo[warp];
-  float acc[OP_R];
+  // far-field sums of the lane's points, as pairs (r, r+1) for the packed
+  // FP32 instructions of sm_100+ (two lanes of arithmetic per issue)
+  float2 acc[OP_R / 2];
 #pragma unroll
-  for (int r = 0; r < OP_R; ++r) { acc[r] = 0.f; hi[r][lane] = 0.f; lo[r][lane] = 0.f; }
+  for (int r = 0; r < OP_R; ++r) { hi[r][lane] = 0.f; lo[r][lane] = 0.f; }
+#pragma unroll
+  for (int r = 0; r < OP_R / 2; ++r) acc[r] = make_float2(0.f, 0.f);
 
   const float dnuf = (float)dnu;
   int chunks = 0;
@@ -368,6 +444,7 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
     // and its slot (lines sorted by class)
     int cls = -1;
     bool needs_fix = false, has_core = false;
+    int eb0 = 0, eb1 = 0;                   // blocks [eb0, eb1] of the line's fixup range
     float4 c0, c1;
     int4 c2;
     float2 c3;
@@ -421,6 +498,8 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       }
       needs_fix = e0 <= e1;
       has_core = has_core && needs_fix;
+      eb0 = e0;
+      eb1 = e1;
       // lanes whose block lies in the window: jlo <= w0 + 16k and w0 + 16k + 15 <= jhi
       unsigned take = lane_range_mask((w.jlo - w0 + OP_R - 1) >> OP_R_LOG, (w.jhi - w0 - (OP_R - 1)) >> OP_R_LOG);
       if (needs_fix) take &= ~lane_range_mask(e0, e1);
@@ -469,20 +548,14 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
     }
     const unsigned fix_slots = __reduce_or_sync(0xffffffffu, (slot >= 0 && needs_fix) ? (1u << slot) : 0u);
     const unsigned core_slots = __reduce_or_sync(0xffffffffu, (slot >= 0 && has_core) ? (1u << slot) : 0u);
-    // lines whose fixup holds window edges only (one-pole points): their
-    // ranges are concatenated and evaluated 32 points at a time below
+    // lines whose fixup holds one-pole points only (window edges, short
+    // stretches): their slots and fixup blocks, in line order, and the blocks
+    // they touch
     const bool edge_only = slot >= 0 && needs_fix && !has_core;
-    const int elen = edge_only ? c2.y - c2.x + 1 : 0;
-    int eincl = elen;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, eincl, o);
-      if (lane >= o) eincl += v;
-    }
-    const int e_total = __shfl_sync(0xffffffffu, eincl, 31);
     const unsigned b_edge = __ballot_sync(0xffffffffu, edge_only);
     const int n_edge = __popc(b_edge);
-    if (edge_only) eidx[__popc(b_edge & lt_mask)] = ((eincl - elen) << 5) | slot;
+    if (edge_only) eidx[__popc(b_edge & lt_mask)] = slot | (eb0 << 5) | (eb1 << 10);
+    const unsigned e_blocks = __reduce_or_sync(0xffffffffu, edge_only ? lane_range_mask(eb0, eb1) : 0u);
     __syncwarp();
 
     // ---- far field.  The shifted Lorentz classes take two lines per
@@ -517,35 +590,24 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
         }
       }
 #pragma unroll
-      for (int r = 0; r < OP_R; ++r) {      // expand at the lane's 16 points
-        const float t = (float)r - 0.5f * (OP_R - 1);
-        float v = C[FF_DEG];
+      for (int r = 0; r < OP_R; r += 2) {   // expand at the lane's 16 points, two at a time
+        const float2 t = make_float2((float)r - 0.5f * (OP_R - 1), (float)(r + 1) - 0.5f * (OP_R - 1));
+        float2 v = make_float2(C[FF_DEG], C[FF_DEG]);
 #pragma unroll
-        for (int k = FF_DEG - 1; k >= 0; --k) v = fmaf(v, t, C[k]);
-        acc[r] += v;
+        for (int k = FF_DEG - 1; k >= 0; --k) v = __ffma2_rn(v, t, make_float2(C[k], C[k]));
+        acc[r >> 1] = __fadd2_rn(acc[r >> 1], v);
       }
     }
     const int eLF = nFF + nLF;
     for (; l + 1 < eLF; l += 2) {           // shifted Lorentz, whole span
       const float4 a = g0[l], a2 = g0[l + 1];
       const float qL = g1[l].z, qL2 = g1[l + 1].z;
-      const float x0 = fmaf(j0r - a.w, a.x, a.y), x02 = fmaf(j0r - a2.w, a2.x, a2.y);
-#pragma unroll
-      for (int r = 0; r < OP_R; ++r) {
-        const float x = fmaf((float)r, a.x, x0), x2 = fmaf((float)r, a2.x, x02);
-        const float s1 = fmaf(x, x, qL), s2 = fmaf(x2, x2, qL2);
-        acc[r] = fmaf(fmaf(a2.z, s1, a.z * s2), bartw::rcp_approx(s1 * s2), acc[r]);
-      }
+      lorentz_pair(acc, j0r, a, a2, a.z, a2.z, qL, qL2, 0.0f, 0.0f);
     }
     if (l < eLF) {                          // odd line out
       const float4 a = g0[l];
       const float qL = g1[l].z;
-      const float x0 = fmaf(j0r - a.w, a.x, a.y);
-#pragma unroll
-      for (int r = 0; r < OP_R; ++r) {
-        const float x = fmaf((float)r, a.x, x0);
-        acc[r] = fmaf(a.z, bartw::rcp_approx(fmaf(x, x, qL)), acc[r]);
-      }
+      lorentz_one(acc, j0r, a, a.z, qL, 0.0f);
       ++l;
     }
     const int eLM = eLF + nLM;
@@ -555,27 +617,15 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       const bool t1 = (__float_as_uint(b.w) >> lane) & 1u, t2 = (__float_as_uint(b2.w) >> lane) & 1u;
       const float A = t1 ? a.z : 0.0f, A2 = t2 ? a2.z : 0.0f;
       // a lane with weight 0 may hold points of the fixup stretch (small s):
-      // it evaluates far-away points instead
-      const float x0 = t1 ? fmaf(j0r - a.w, a.x, a.y) : FAR_X;
-      const float x02 = t2 ? fmaf(j0r - a2.w, a2.x, a2.y) : FAR_X;
-#pragma unroll
-      for (int r = 0; r < OP_R; ++r) {
-        const float x = fmaf((float)r, a.x, x0), x2 = fmaf((float)r, a2.x, x02);
-        const float s1 = fmaf(x, x, b.z), s2 = fmaf(x2, x2, b2.z);
-        acc[r] = fmaf(fmaf(A2, s1, A * s2), bartw::rcp_approx(s1 * s2), acc[r]);
-      }
+      // it evaluates far-away points instead (x = FAR_X)
+      lorentz_pair(acc, j0r, a, a2, A, A2, b.z, b2.z, t1 ? 0.0f : 1.0f, t2 ? 0.0f : 1.0f);
     }
     if (l < eLM) {
       const float4 a = g0[l];
       const float4 b = g1[l];
       const bool t1 = (__float_as_uint(b.w) >> lane) & 1u;
       const float A = t1 ? a.z : 0.0f;
-      const float x0 = t1 ? fmaf(j0r - a.w, a.x, a.y) : FAR_X;
-#pragma unroll
-      for (int r = 0; r < OP_R; ++r) {
-        const float x = fmaf((float)r, a.x, x0);
-        acc[r] = fmaf(A, bartw::rcp_approx(fmaf(x, x, b.z)), acc[r]);
-      }
+      lorentz_one(acc, j0r, a, A, b.z, t1 ? 0.0f : 1.0f);
       ++l;
     }
     const int ePF = eLM + nPF;
@@ -583,59 +633,62 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
     for (; l < ePF; ++l) {                  // one-pole, whole span
       const float4 a = g0[l];
       const float4 b = g1[l];
-      const float x0 = fmaf(j0r - a.w, a.x, a.y);
-#pragma unroll
-      for (int r = 0; r < OP_R; ++r) {
-        const float x = fmaf((float)r, a.x, x0);
-        const float u = fmaf(x, x, b.x);
-        const float num = fmaf(a.z, u, a.z);
-        acc[r] = fmaf(num, bartw::rcp_approx(fmaf(u, u, b.y)), acc[r]);
-      }
+      one_pole<false>(acc, j0r, a, a.z, b.x, b.y);
     }
     const int ePM = ePF + nPM;
     for (; l < ePM; ++l) {                  // one-pole, lane weight
       const float4 a = g0[l];
       const float4 b = g1[l];
       const float A = ((__float_as_uint(b.w) >> lane) & 1u) ? a.z : 0.0f;
-      const float x0 = fmaf(j0r - a.w, a.x, a.y);
-#pragma unroll
-      for (int r = 0; r < OP_R; ++r) {
-        const float x = fmaf((float)r, a.x, x0);
-        const float u = fmaf(x, x, b.x);
-        const float num = fmaf(A, u, A);
-        // the clamp keeps 0 * (1/d) finite where a skipped block holds a pole
-        acc[r] = fmaf(num, bartw::rcp_approx(fmaxf(fmaf(u, u, b.y), 1e-30f)), acc[r]);
-      }
+      // the clamp keeps 0 * (1/d) finite where a skipped block holds a pole
+      one_pole<true>(acc, j0r, a, A, b.x, b.y);
     }
 
-    // ---- fixup: the excluded blocks of each line, lanes take consecutive points
-    // edge-only lines, packed: entry t of the concatenated ranges belongs to
-    // the last edge line whose first entry is <= t (binary search); the
-    // values are added in rounds of equal line (ascending): deterministic
-    for (int g = 0; g < e_total; g += 32) {
-      const int t = g + lane;
-      const bool act = t < e_total;
-      int k = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cnd = k + step;
-        if (cnd < n_edge && (eidx[cnd] >> 5) <= t) k = cnd;
-      }
-      const int ek = eidx[k];
-      const int sl = ek & 31;
-      const float4 a = g0[sl];
-      const float4 b = g1[sl];
-      const int p = g2[sl].x + (t - (ek >> 5));
-      const float x = fmaf((float)(p - w0) - a.w, a.x, a.y);
-      const float u = fmaf(x, x, b.x);
-      const float v = fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
-      const int kp = __shfl_up_sync(0xffffffffu, k, 1);
-      unsigned seg = __ballot_sync(0xffffffffu, act && (lane == 0 || k != kp));
-      while (seg) {
-        const int s0 = __ffs(seg) - 1;
-        seg &= seg - 1;
-        const int s1 = seg ? __ffs(seg) - 1 : 32;
-        if (act && lane >= s0 && lane < s1) fix[p - w0] += v;
+    // ---- fixup: the excluded blocks of each line.  One-pole-only lines:
+    // lanes take the 16 points of two touched blocks (or of one block, the
+    // halves taking alternate lines), loop over the lines touching them and
+    // keep the sum in a register (points outside a line's range add 0); each
+    // point is then added once: deterministic, no conflicting adds
+    if (e_blocks) {
+      const int ek = lane < n_edge ? eidx[lane] : -1;
+      const int ke0 = ek < 0 ? 64 : (ek >> 5) & 31, ke1 = ek < 0 ? -1 : (ek >> 10) & 31;
+      const int half = lane >> 4;
+      unsigned bm = e_blocks;
+      while (bm) {
+        const int b0 = __ffs(bm) - 1;
+        bm &= bm - 1;
+        int b1 = -1;
+        if (bm) {
+          b1 = __ffs(bm) - 1;
+          bm &= bm - 1;
+        }
+        const bool split = b1 < 0;
+        unsigned lm = __ballot_sync(0xffffffffu, (ke0 <= b0 && b0 <= ke1) || (ke0 <= b1 && b1 <= ke1));
+        const int pr = ((split || half == 0) ? b0 : b1) * OP_R + (lane & (OP_R - 1));   // point in span
+        const float pf = (float)pr;
+        float v = 0.0f;
+        while (lm) {
+          int k = __ffs(lm) - 1;
+          lm &= lm - 1;
+          if (split) {
+            const int k2 = lm ? __ffs(lm) - 1 : -1;
+            if (lm) lm &= lm - 1;
+            if (half) k = k2;
+          }
+          if (k >= 0) {
+            const int sl = eidx[k] & 31;
+            const float4 a = g0[sl];
+            const float4 b = g1[sl];
+            const int4 e = g2[sl];
+            const float x = fmaf(pf - a.w, a.x, a.y);
+            const float u = fmaf(x, x, b.x);
+            const float t = fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
+            const int p = w0 + pr;
+            v += (p >= e.x && p <= e.y) ? t : 0.0f;
+          }
+        }
+        if (split) v += __shfl_down_sync(0xffffffffu, v, 16);
+        if (!split || half == 0) fix[pr] += v;
         __syncwarp();
       }
     }
@@ -688,13 +741,15 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       chunks = 0;
 #pragma unroll
       for (int r = 0; r < OP_R; ++r) {
+        const float ar = (r & 1) ? acc[r >> 1].y : acc[r >> 1].x;
         const float h = hi[r][lane];
-        const float s = h + acc[r];
+        const float s = h + ar;
         const float bp = s - h;
-        lo[r][lane] += (h - (s - bp)) + (acc[r] - bp);
+        lo[r][lane] += (h - (s - bp)) + (ar - bp);
         hi[r][lane] = s;
-        acc[r] = 0.f;
       }
+#pragma unroll
+      for (int r = 0; r < OP_R / 2; ++r) acc[r] = make_float2(0.f, 0.f);
     }
   }
   __syncwarp();

@@ -295,8 +295,10 @@ def test_contribution_functions(ctx, torch, grid_case, deck):
         if ok.any():
             e_band = max(e_band, float(np.max(np.abs(cb[i][:, ok] - Bo[:, ok]) / Bs[None, ok])))
         e_sum = max(e_sum, max_rel(got.sum(axis=0, dtype=np.float64), spec[offs[i]:offs[i + 1]]))
-        okb = sb[i] != 0
-        e_sum = max(e_sum, max_rel(cb[i].sum(axis=0, dtype=np.float64)[okb], sb[i][okb]))
+        okb = sb[i] != 0                    # a band with no weight on the span is 0 on both sides
+        assert np.all(cb[i][:, ~okb] == 0.0)
+        if okb.any():
+            e_sum = max(e_sum, max_rel(cb[i].sum(axis=0, dtype=np.float64)[okb], sb[i][okb]))
     print(f"contribution functions (deck {deck}) FP32 vs FP64: rows {e_row:.2e}, bands {e_band:.2e}; "
           f"sum vs the forward model {e_sum:.2e}")
     assert e_row < 1e-5 and e_band < 1e-5 and e_sum < 1e-5

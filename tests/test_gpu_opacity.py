@@ -218,9 +218,11 @@ def test_voigt_table_scheme(ctx, torch):
     ref = VT.opacity_cells_table(w.species, p, t, w.nu_start, w.dnu, w.n_nu, w.cutoff, tab.spec)
     rel, l2 = opacity_errors(got, ref)
     exact = O.opacity_cells(w.species, p, t, w.nu_start, w.dnu, w.n_nu, w.cutoff)
-    scheme, _ = opacity_errors(ref, exact)
-    print(f"Voigt-table scheme: GPU vs oracle max rel {rel:.2e}, row L2 {l2:.2e}; "
-          f"the scheme itself vs the exact sum (20 x 20 widths, 16 samples per interval): {scheme:.2e}")
+    # the scheme's own error: row L2 (its quantised centres move the steep
+    # Doppler wings, so pointwise relative errors there are not meaningful)
+    _, scheme_l2 = opacity_errors(ref, exact)
+    print(f"Voigt-table scheme: GPU vs oracle max rel {rel:.2e}, row L2 {l2:.2e}; the scheme itself vs the "
+          f"exact sum (20 x 20 widths, 16 samples per interval): row L2 {scheme_l2:.2e}")
     assert rel < RTOL_OPACITY and l2 < RTOL_ROW_L2
     assert tab.nbytes == 20 * 20 * 16 * (2 * (int(np.ceil(w.cutoff / w.dnu)) + 1) + 1) * 4
     tab.close()
