@@ -497,7 +497,7 @@ def voigt_table_leg(ctx, torch, stream, grid, ax, nu, d_lines, build0, out, n_w=
     ms = _event_ms(torch, stream, lambda: ctx.build_opacity_grid_table(tab, d_lines[:1], ax.p_bar, ax.t_K, nu,
                                                                       ax.cutoff, out=out))
     got0, ref0 = out[0].reshape(-1, ax.n_nu), grid[0].reshape(-1, ax.n_nu)
-    l2 = float(torch.linalg.vector_norm(got0 - ref0) / torch.linalg.vector_norm(ref0))
+    l2 = float(torch.linalg.vector_norm(got0.double() - ref0.double()) / torch.linalg.vector_norm(ref0.double()))
     res = {"n_sigma": n_w, "n_gamma": n_w, "oversample": oversample, "table_bytes": tab.nbytes,
            "fill_ms": fill_ms, "ms": ms, "ms_direct": ms0, "speed_vs_direct": ms0 / ms, "grid_rel_l2": l2,
            "grid_max_rel_err_1e-3": _max_rel(torch, got0, ref0, 1e-3)}
@@ -625,7 +625,8 @@ def paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta):
         ctx.set_line_threshold(0.0)
         run(full, cfg, spec)
         got0 = out[0].reshape(-1, ax.n_nu)
-        l2 = float(torch.linalg.vector_norm(got0 - ref0) / torch.linalg.vector_norm(ref0))
+        # FP64: squares of FP32 opacities (1e-13 .. 1e-30 cm^2) underflow
+        l2 = float(torch.linalg.vector_norm(got0.double() - ref0.double()) / torch.linalg.vector_norm(ref0.double()))
         res["line_threshold"].append({"rel": rel, "ms": ms, "ms_without": ms0, "speedup": ms0 / ms,
                                       "grid_rel_l2": l2, "grid_max_rel_err_1e-3": _max_rel(torch, got0, ref0, 1e-3),
                                       "spectra_max_rel_err": _max_rel(torch, spec, spec_ref, 0.0)})

@@ -71,13 +71,23 @@ class LineList:
         return int(self.nu0.shape[0])
 
 
+# second radiation constant h c / k_B (cm K), for the lower-state population
+# of the synthetic line strengths at 296 K
+_C2_CM_K = 1.438776877
+
+
 def line_list(species: int, n_lines: int, nu_lo: float = 1000.0, nu_hi: float = 3000.0) -> LineList:
-    """Seeded synthetic line list: centres U[nu_lo, nu_hi], log10 S U[-25,-19],
-    E'' U[0, 5000] cm^-1, gamma_ref U[0.05, 0.1] cm^-1; sorted by centre."""
+    """Seeded synthetic line list, sorted by centre: centres U[nu_lo, nu_hi],
+    E'' U[0, 5000] cm^-1, gamma_ref U[0.05, 0.1] cm^-1, and strengths at 296 K
+    S = S_int exp(-c2 E'' / 296 K) with log10 S_int U[-25, -19]: a line from a
+    highly excited lower state is weak at 296 K (its population), as in real
+    line lists, so that hot layers are not made opaque by lines that are
+    strong at every temperature."""
     g = _rng(1000 + species)
     nu0 = g.uniform(nu_lo, nu_hi, n_lines)
     logs = g.uniform(-25.0, -19.0, n_lines)
     elow = g.uniform(0.0, 5000.0, n_lines)
+    logs = logs - _C2_CM_K * elow / (296.0 * np.log(10.0))
     gam = g.uniform(0.05, 0.1, n_lines)
     order = np.argsort(nu0, kind="stable")
     return LineList(nu0=nu0[order].astype(np.float64),
