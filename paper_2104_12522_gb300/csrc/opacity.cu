@@ -236,6 +236,7 @@ struct __align__(8) LineG3 {    // accurate branch (expansion lines: -2 dx, dx^2
 // is left to the fixup (no per-lane weight); "M": the lane weight is taken
 // from the line's lane mask.
 constexpr int CLS_FF = 4, CLS_LF = 0, CLS_LM = 1, CLS_PF = 2, CLS_PM = 3;
+constexpr int CLS_F2 = 5, CLS_F4 = 6, CLS_F8 = 7;   // expansion about a block of G = 2, 4, 8 lanes
 // "FF": every point of the span lies at |x| >= FF_RATIO dx from the line (and
 // the shifted Lorentz form holds there): the line's contribution to a lane's
 // 16 points is expanded to degree FF_DEG in the point offset t about the
@@ -244,8 +245,15 @@ constexpr int CLS_FF = 4, CLS_LF = 0, CLS_LM = 1, CLS_PF = 2, CLS_PM = 3;
 // P_n = -alpha P_{n-1} - beta P_{n-2}; truncation error <= 2.5e-6 relative for
 // |xc| >= 12 h (h = 7.5 dx, half a block), i.e. |x| >= 11 h on the block.
 // The lane sums the coefficients over lines and expands them once per chunk.
+// Lines farther away are expanded about the centre of a group of G = 2, 4 or
+// 8 lanes (h = (16 G - 1) dx / 2, the same bound with |x| >= 11 h on the
+// group's points) when their lane mask is uniform over each group: each lane
+// of a group takes every G-th such line, the group adds its coefficients by
+// shuffles, and each lane moves the polynomial to its own block centre
+// (Taylor shift), so one line costs 1/G of a lane's work.
 constexpr int FF_DEG = 5;
 constexpr float FF_RATIO = 11.0f * 0.5f * (OP_R - 1);
+__host__ __device__ constexpr float ff_ratio(int G) { return 11.0f * 0.5f * (G * OP_R - 1); }
 constexpr float EPS_L = 2e-6f;
 constexpr int LFIX_MAX = 64;              // longest stretch of one-pole points moved to the fixup
 constexpr float FAR_X = 1.0e4f;           // x of lanes with weight 0 in the lane-mask Lorentz loop
@@ -274,6 +282,55 @@ __device__ __forceinline__ unsigned lane_range_mask(int a, int b) {   // bits a.
   if (a > b) return 0u;
   const unsigned hi = (b == 31) ? 0xffffffffu : ((1u << (b + 1)) - 1u);
   return hi & ~((1u << a) - 1u);
+}
+
+// Expansion coefficients of lines [l0, l0 + n) about the centre of the lane's
+// group of G lanes (16 G points); lane u of a group takes lines l0 + u,
+// l0 + u + G, ...  Lines of this group size have a lane mask that is uniform
+// over the group.
+template <int G>
+__device__ __forceinline__ void ff_lines(float (&C)[FF_DEG + 1], const float4* g0, const float4* g1,
+                                         const float2* g3, int l0, int n, int lane) {
+  const float tcg = (float)((lane & ~(G - 1)) * OP_R) + 0.5f * (G * OP_R - 1);
+  for (int i = l0 + (lane & (G - 1)); i < l0 + n; i += G) {
+    const float4 a = g0[i];
+    const float4 b = g1[i];
+    const float2 d = g3[i];                 // -2 dx, dx^2
+    const float A = ((__float_as_uint(b.w) >> lane) & 1u) ? a.z : 0.0f;
+    const float xc = fmaf(tcg - a.w, a.x, a.y);
+    const float g = bartw::rcp_approx(fmaf(xc, xc, b.z));
+    const float al = xc * g * d.x;          // -alpha
+    const float be = d.y * g;               // beta
+    const float Ag = A * g;
+    float pm1 = 1.0f, pn = al;              // P_0, P_1
+    C[0] += Ag;
+    C[1] = fmaf(Ag, pn, C[1]);
+#pragma unroll
+    for (int k = 2; k <= FF_DEG; ++k) {
+      const float pk = fmaf(al, pn, -be * pm1);
+      pm1 = pn;
+      pn = pk;
+      C[k] = fmaf(Ag, pk, C[k]);
+    }
+  }
+}
+
+// Adds the partial sums over lane bit G/2 (the two halves of a group of G)
+// and moves the polynomial from the group's centre to the centre of the
+// lane's half: p(t) -> p(t + delta), delta = centre(G/2) - centre(G), by the
+// Horner form of the Taylor shift.
+template <int G>
+__device__ __forceinline__ void ff_fold(float (&C)[FF_DEG + 1], int lane) {
+#pragma unroll
+  for (int k = 0; k <= FF_DEG; ++k) C[k] += __shfl_xor_sync(0xffffffffu, C[k], G / 2);
+  const float c_g = (float)((lane & ~(G - 1)) * OP_R) + 0.5f * (G * OP_R - 1);
+  const float c_h = (float)((lane & ~(G / 2 - 1)) * OP_R) + 0.5f * ((G / 2) * OP_R - 1);
+  const float delta = c_h - c_g;
+#pragma unroll
+  for (int i = 0; i < FF_DEG; ++i) {
+#pragma unroll
+    for (int j = FF_DEG - 1; j >= i; --j) C[j] = fmaf(delta, C[j + 1], C[j]);
+  }
 }
 
 // Far-field loops over the lane's 16 points, two points per packed FP32
@@ -510,7 +567,17 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       const float xm = xa > 0.0f ? xa : (xb < 0.0f ? -xb : 0.0f);
       const float smin = fmaf(xm, xm, q);
       const bool ff = !has_core && xm >= FF_RATIO * dx && smin * smin * (EPS_L * 0.999f) >= fmaf(2.0f, q, 1.5f);
-      cls = ff ? CLS_FF : lor ? (full ? CLS_LF : CLS_LM) : (full ? CLS_PF : CLS_PM);
+      int ffc = CLS_FF;
+      if (ff) {
+        // largest group with a uniform lane mask within each group of G lanes
+        const bool u2 = (((take >> 1) ^ take) & 0x55555555u) == 0u;
+        const bool u4 = u2 && (((take >> 2) ^ take) & 0x33333333u) == 0u;
+        const bool u8 = u4 && (((take >> 4) ^ take) & 0x0f0f0f0fu) == 0u;
+        if (u8 && xm >= ff_ratio(8) * dx) ffc = CLS_F8;
+        else if (u4 && xm >= ff_ratio(4) * dx) ffc = CLS_F4;
+        else if (u2 && xm >= ff_ratio(2) * dx) ffc = CLS_F2;
+      }
+      cls = ff ? ffc : lor ? (full ? CLS_LF : CLS_LM) : (full ? CLS_PF : CLS_PM);
       if (!keep) {                          // below the line-strength bound: no slot
         cls = -1;
         needs_fix = false;
@@ -528,14 +595,22 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       // accurate-branch group holds -2 dx and dx^2 instead
       c3 = ff ? make_float2(-2.0f * dx, dx * dx) : make_float2(y, B);
     }
-    const unsigned bFF = __ballot_sync(0xffffffffu, cls == CLS_FF);
+    const unsigned bF8 = __ballot_sync(0xffffffffu, cls == CLS_F8);
+    const unsigned bF4 = __ballot_sync(0xffffffffu, cls == CLS_F4);
+    const unsigned bF2 = __ballot_sync(0xffffffffu, cls == CLS_F2);
+    const unsigned bF1 = __ballot_sync(0xffffffffu, cls == CLS_FF);
     const unsigned bLF = __ballot_sync(0xffffffffu, cls == CLS_LF);
     const unsigned bLM = __ballot_sync(0xffffffffu, cls == CLS_LM);
     const unsigned bPF = __ballot_sync(0xffffffffu, cls == CLS_PF);
     const unsigned bPM = __ballot_sync(0xffffffffu, cls == CLS_PM);
-    const int nFF = __popc(bFF), nLF = __popc(bLF), nLM = __popc(bLM), nPF = __popc(bPF), nPM = __popc(bPM);
+    const int n8 = __popc(bF8), n4 = __popc(bF4), n2 = __popc(bF2), n1 = __popc(bF1);
+    const int nFF = n8 + n4 + n2 + n1;      // all expansion lines (slots [0, nFF))
+    const int nLF = __popc(bLF), nLM = __popc(bLM), nPF = __popc(bPF), nPM = __popc(bPM);
     int slot = -1;
-    if (cls == CLS_FF) slot = __popc(bFF & lt_mask);
+    if (cls == CLS_F8) slot = __popc(bF8 & lt_mask);
+    else if (cls == CLS_F4) slot = n8 + __popc(bF4 & lt_mask);
+    else if (cls == CLS_F2) slot = n8 + n4 + __popc(bF2 & lt_mask);
+    else if (cls == CLS_FF) slot = n8 + n4 + n2 + __popc(bF1 & lt_mask);
     else if (cls == CLS_LF) slot = nFF + __popc(bLF & lt_mask);
     else if (cls == CLS_LM) slot = nFF + nLF + __popc(bLM & lt_mask);
     else if (cls == CLS_PF) slot = nFF + nLF + nLM + __popc(bPF & lt_mask);
@@ -568,27 +643,18 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       float C[FF_DEG + 1];
 #pragma unroll
       for (int k = 0; k <= FF_DEG; ++k) C[k] = 0.0f;
-      for (; l < nFF; ++l) {
-        const float4 a = g0[l];
-        const float4 b = g1[l];
-        const float2 d = g3[l];             // -2 dx, dx^2
-        const float A = ((__float_as_uint(b.w) >> lane) & 1u) ? a.z : 0.0f;
-        const float xc = fmaf(tc - a.w, a.x, a.y);
-        const float g = bartw::rcp_approx(fmaf(xc, xc, b.z));
-        const float al = xc * g * d.x;      // -alpha
-        const float be = d.y * g;           // beta
-        const float Ag = A * g;
-        float pm1 = 1.0f, pn = al;          // P_0, P_1
-        C[0] += Ag;
-        C[1] = fmaf(Ag, pn, C[1]);
-#pragma unroll
-        for (int k = 2; k <= FF_DEG; ++k) {
-          const float pk = fmaf(al, pn, -be * pm1);
-          pm1 = pn;
-          pn = pk;
-          C[k] = fmaf(Ag, pk, C[k]);
-        }
-      }
+      // groups of 8, 4, 2 lanes, then single lanes: after a group size's lines,
+      // the partial sums are added over the next lane bit and moved to the
+      // centre of the next smaller group, so every group's sum is complete and
+      // centred on the lane's own block at the end
+      if (n8 > 0) ff_lines<8>(C, g0, g1, g3, 0, n8, lane);
+      if (n8 > 0) ff_fold<8>(C, lane);
+      if (n4 > 0) ff_lines<4>(C, g0, g1, g3, n8, n4, lane);
+      if (n8 + n4 > 0) ff_fold<4>(C, lane);
+      if (n2 > 0) ff_lines<2>(C, g0, g1, g3, n8 + n4, n2, lane);
+      if (n8 + n4 + n2 > 0) ff_fold<2>(C, lane);
+      ff_lines<1>(C, g0, g1, g3, n8 + n4 + n2, n1, lane);
+      l = nFF;
 #pragma unroll
       for (int r = 0; r < OP_R; r += 2) {   // expand at the lane's 16 points, two at a time
         const float2 t = make_float2((float)r - 0.5f * (OP_R - 1), (float)(r + 1) - 0.5f * (OP_R - 1));
