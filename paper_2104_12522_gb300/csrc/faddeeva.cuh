@@ -67,6 +67,25 @@ __device__ __forceinline__ float cf_re(float x, float y, int depth) {
   return INV_SQRTPI * ti * rcp_approx(fmaf(tr, tr, ti * ti));
 }
 
+// The continued fraction to depth 2, w = (i/sqrt(pi)) (z^2 - 1) / (z (z^2 - 3/2)),
+// in closed real form.  With u = x^2 - y^2 and v = 2xy,
+//   Re w = y (x^2 + v^2 + (u - 1)(u - 3/2)) / (sqrt(pi) (x^2 + y^2) ((u - 3/2)^2 + v^2)),
+// where every term of the numerator carries the factor y (no cancellation near
+// the real axis; (u - 1)(u - 3/2) > -1/16 is negligible against x^2 for
+// |z| >= 14).  Relative error of Re w against the Faddeeva function (FP64):
+// <= 7.2e-7 for 14 <= |z| < 24 (the truncation is ~5.25 / x^6 near the real
+// axis), plus the FP32 rounding of about ten operations.  The Gaussian term
+// exp(-x^2) is below the FP32 range there.
+__device__ __forceinline__ float cf2_re(float x, float y) {
+  const float x2 = x * x, y2 = y * y;
+  const float u = x2 - y2;
+  const float v2 = 4.0f * x2 * y2;
+  const float um = u - 1.5f;
+  const float num = y * (x2 + v2 + (u - 1.0f) * um);
+  const float den = (x2 + y2) * fmaf(um, um, v2);
+  return INV_SQRTPI * num * rcp_approx(den);
+}
+
 // Continued fraction plus the exponentially small Gaussian term
 // exp(y^2 - x^2) cos(2xy) that the asymptotic fraction misses near the real
 // axis (y < 1), branch free.  Relative error of Re w for |z| >= 8: <= 1e-6 at

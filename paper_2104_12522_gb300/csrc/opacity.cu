@@ -404,10 +404,11 @@ __device__ __forceinline__ void one_pole(float2 (&acc)[OP_R / 2], float j0r, con
 // with points in the window (the block holding a window edge, the blocks the
 // stretch touches, and any blocks between them) form one interval [e0, e1]
 // that the fixup pass evaluates point by point, lanes = points: the one-pole
-// form outside the core window [klo, khi], the continued fraction to depth 3
-// for |z| >= 8 inside it, and the rest deferred into two per-warp lists
-// (Taylor table for |z| < 5, continued fraction to depth 6 for 5 <= |z| < 8)
-// that are evaluated 32 points at a time.  Each (line, point) is counted once.
+// form outside the core window [klo, khi], the closed form of the continued
+// fraction to depth 2 for |z| >= 14 inside it, and the rest deferred into two
+// per-warp lists (Taylor table for |z| < 5, continued fraction to depth 6 for
+// 5 <= |z| < 14) that are evaluated 32 points at a time.  Each (line, point)
+// is counted once.
 __global__ void __launch_bounds__(OP_THREADS, 3)
 opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
                const SpanRange* __restrict__ spans, const CellConst* __restrict__ cells, double dnu,
@@ -777,16 +778,16 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
         const float u = fmaf(x, x, b.x);
         fix[p - w0] += fmaf(a.z, u, a.z) * bartw::rcp_approx(fmaf(u, u, b.y));
       }
-      // the core window: |z| >= 8 at once (continued fraction to depth 3),
-      // |z| < 8 deferred to the lists
+      // the core window: |z| >= 14 at once (closed form of the continued
+      // fraction to depth 2), |z| < 14 deferred to the lists
       for (int p0 = ka; p0 <= kb; p0 += 32) {
         if (nT + nC + 32 > CORE_CAP) flush();
         const int p = p0 + lane;
         const bool act = p <= kb;
         const float x = fmaf((float)(p - w0) - a.w, a.x, a.y);
         const float u = fmaf(x, x, b.x);
-        const bool mid = act && u >= 63.5f;                // |z| >= 8
-        if (mid) fix[p - w0] += c.y * bartw::cf_gauss_re(fabsf(x), c.x, 3);
+        const bool mid = act && u >= 195.5f;               // |z| >= 14
+        if (mid) fix[p - w0] += c.y * bartw::cf2_re(fabsf(x), c.x);
         const bool tay = act && u < 24.5f;                 // |z| < 5
         const bool cfr = act && !mid && !tay;
         const unsigned bt = __ballot_sync(0xffffffffu, tay);
