@@ -347,20 +347,31 @@ def run_native(args):
         h_theta.numel() * 4 + h_filt.numel() * 4
     d2h = h_grid.numel() * 4 + h_bands.numel() * 4
     e2e_steps = max(1, min(args.steps, 2))
+    # the grid comes back one species at a time on a second stream, each slab
+    # while the next species is built (one library call per species)
+    copy_stream = torch.cuda.Stream(dev)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
+        stream.wait_stream(copy_stream)          # the previous step's slabs are home
         for hd, dd in zip(h_lines, d_lines):
             for h, d in zip(hd, (dd.nu0, dd.log10_s296, dd.elow, dd.gamma_ref)):
                 d.copy_(h, non_blocking=True)
         theta.copy_(h_theta, non_blocking=True)
         filt.copy_(h_filt, non_blocking=True)
-        step()
-        h_grid.copy_(grid, non_blocking=True)
+        for s_ in range(S):
+            ctx.build_opacity_grid(d_lines[s_:s_ + 1], ax.p_bar, ax.t_K, nu, ax.cutoff, out=grid[s_:s_ + 1])
+            built = torch.cuda.Event()
+            built.record(stream)
+            copy_stream.wait_event(built)
+            with torch.cuda.stream(copy_stream):
+                h_grid[s_].copy_(grid[s_], non_blocking=True)
+        ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=theta, filters=filt, bands=bands)
         h_bands.copy_(bands, non_blocking=True)
+        stream.wait_stream(copy_stream)
         flush.fill_(1.0)
     e1.record(stream)
     torch.cuda.synchronize()
