@@ -47,6 +47,9 @@ KERNELS_PER_STEP = 3 * 3 + 3      # per species: window and span prologues + opa
 # sources the opacity kernel is compiled from (the committed traffic figure is tied to them)
 OPACITY_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
                    for f in ("opacity.cu", "faddeeva.cuh", "bart_internal.cuh")]
+FORWARD_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
+                   for f in ("forward.cu", "forward.cuh", "bart_internal.cuh")]
+MUFU_PER_CLK = 16                 # MUFU (ex2, rcp) results per clock per SM
 
 
 def workload_desc():
@@ -392,11 +395,16 @@ def run_native(args):
                 peaks = json.load(fh)
         max_mhz = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
         op_launch_ms = op_avg / OPACITY_LAUNCHES_PER_STEP
-        # forward model against HBM: every (proposal, layer, wavenumber) reads
-        # the 2 S grid values of its temperature bracket, counted as if streamed
+        # forward model: the proposals of a wavenumber tile share the grid rows
+        # through L2, so the binding unit is the MUFU (NA ex2 of the angles, ex2
+        # and reciprocal of the Planck function per (proposal, layer,
+        # wavenumber)); DRAM traffic from the committed ncu capture
         hbm = float(peaks.get("hbm_gbs") or 6800.0)
-        fw_bytes = N_PROPOSALS * L * NU * 2 * S * 4
-        fw_gbs = fw_bytes / (fw_avg / 1e3) / 1e9
+        fw_units = N_PROPOSALS * L * NU
+        mufu = fw_units * (N_ANGLES + 2) / (fw_avg / 1e3) / 1e12
+        mufu_peak = n_sm * MUFU_PER_CLK * max_mhz * 1e6 / 1e12
+        fw_dram = committed_traffic(FORWARD_SOURCES, "emission_kernel")
+        fw_dram_frac = fw_dram / (fw_avg / 1e3) / (hbm * 1e9) if fw_dram else None
         achieved = FLOPS_PER_EVAL * evals / OPACITY_LAUNCHES_PER_STEP / (op_launch_ms / 1e3) / 1e12
         peak = fp32_peak_tflops(n_sm, max_mhz)
         traffic = committed_traffic(OPACITY_SOURCES, "opacity_kernel")
@@ -416,16 +424,16 @@ def run_native(args):
             "forward_model": {"spectra_per_s": N * N_PROPOSALS / (fw_avg / 1e3), "ms_per_generation": fw_avg,
                               "proposals": N_PROPOSALS, "angles": N_ANGLES, "bands": N_BANDS,
                               "species": S,
-                              "roofline": {"bound": "hbm", "achieved": fw_gbs, "peak": hbm, "unit": "GB/s",
-                                           "frac": fw_gbs / hbm, "traffic": None, "kernel": "emission_kernel",
-                                           "note": ("algorithmic bytes: 2 S FP32 grid values per (proposal, layer, "
-                                                    "wavenumber) as if streamed from HBM, "
-                                                    f"{fw_bytes / 1e9:.0f} GB per generation; peak = "
-                                                    f"{'measured' if peaks.get('hbm_gbs') else 'fallback'} copy "
-                                                    "bandwidth.  The proposals of a wavenumber tile run together "
-                                                    "and share the rows through L2 (98% hit rate, DRAM moves about "
-                                                    "the grid once), so the fraction can exceed 1: the kernel is "
-                                                    "bound by instruction issue, not by HBM")}},
+                              "roofline": {"bound": "mufu", "achieved": mufu, "peak": mufu_peak, "unit": "Tops/s",
+                                           "frac": mufu / mufu_peak, "traffic": fw_dram,
+                                           "dram_frac": fw_dram_frac, "kernel": "emission_kernel",
+                                           "note": (f"{N_ANGLES + 2} MUFU ops per (proposal, layer, wavenumber): "
+                                                    f"{N_ANGLES} ex2 of the angles, ex2 and reciprocal of the Planck "
+                                                    f"function; peak = {n_sm} SMs x {MUFU_PER_CLK} MUFU results per "
+                                                    f"clock x {max_mhz:.0f} MHz.  The proposals of a wavenumber tile "
+                                                    "share the grid rows through L2, so DRAM moves about the grid "
+                                                    "once per generation: dram_frac = DRAM bytes per generation "
+                                                    "(ncu) / time / measured HBM copy bandwidth")}},
             "opacity_build_ms": op_avg,
             "opacity_build_ms_per_step": [round(v, 2) for v in op_ms],
             "cpu_baseline": cpu,
