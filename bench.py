@@ -461,20 +461,48 @@ def _event_ms(torch, stream, fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_lines, theta):
-    """Measurements beside the timed step, on the grid the step built:
-    the paper's two approximations (line-strength bound, optical-depth limit),
-    transmission batch, surrogate training and accuracy, screened vs plain
-    retrieval.  Times are CUDA events on the library's stream."""
-    S = int(grid.shape[0])
-    out = {}
-    # --- transmission: 1,024 uneven instances (40..150 levels, 1e4..1e5 points)
-    inst = W.instances(1024, ax.n_nu)
+TRANS_INSTANCES = 1024
+TRANSMISSION_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
+                        for f in ("transmission.cu", "forward.cuh", "bart_internal.cuh")]
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth from MEASURED_PEAKS.json (fallback 6,800 GB/s) and its source."""
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as fh:
+            v = json.load(fh).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    return 6800.0, "fallback"
+
+
+def committed_kv(kernel_srcs, name):
+    """key = value lines of profiles/<name>.txt if taken on the current sources, else None."""
+    path = os.path.join(ROOT, "profiles", f"{name}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as fh:
+        for line in fh:
+            if "=" in line and not line.lstrip().startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+    return kv if kv.get("kernel_source_sha") == source_sha(kernel_srcs) else None
+
+
+def transmission_leg(ctx, torch, dev, stream, grid, ax, nu, cfg, S):
+    """The 1,024-instance transmission batch (40..150 levels, 1e4..1e5 points,
+    12 bands) on the step's grid: time, spectra/s and the fraction of HBM its
+    algorithmic bilinear reads (4 corners x S x 4 B per (level, wavenumber))
+    would take if streamed."""
+    n = TRANS_INSTANCES
+    inst = W.instances(n, ax.n_nu)
     th = torch.tensor(inst.theta[:, :5 + S].copy(), device=dev)
     d = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
     offs = inst.offsets
     spec = torch.empty(int(offs[-1]), dtype=torch.float32, device=dev)
-    tb = torch.empty((1024, 12), dtype=torch.float32, device=dev)
+    tb = torch.empty((n, 12), dtype=torch.float32, device=dev)
     tfilt = torch.tensor(W.gaussian_filters(W.nu_axis(ax.nu_start, ax.dnu, ax.n_nu), 12, 1100.0, 2900.0,
                                             100.0, 400.0, seed=3001), device=dev)
     tcfg = dict(cfg, geometry=1, p_ref=W.HD189_PREF_BAR, p_top=1e-8, p_bot=100.0)
@@ -485,8 +513,31 @@ def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_line
     run_t()
     ms = _event_ms(torch, stream, run_t, reps=2)
     ctx.sync()
-    out["transmission"] = {"spectra_per_s": 1024 / (ms / 1e3), "ms_per_batch": ms, "instances": 1024,
-                           "level_sum": int(inst.n_levels.sum()), "points": int(offs[-1]), "bands": 12}
+    lnu = int(np.sum(inst.n_levels.astype(np.int64) * (inst.nu_hi - inst.nu_lo)))
+    alg = lnu * 4 * S * 4
+    hbm, src = measured_hbm_gbs()
+    res = {"spectra_per_s": n / (ms / 1e3), "ms_per_batch": ms, "instances": n,
+           "level_sum": int(inst.n_levels.sum()), "points": int(offs[-1]), "bands": 12,
+           "level_points": lnu, "algorithmic_bytes": alg, "algorithmic_gbs": alg / (ms / 1e3) / 1e9,
+           "hbm_frac_algorithmic": alg / (ms / 1e3) / 1e9 / hbm, "hbm_peak": f"{hbm:.0f} GB/s ({src})"}
+    lb = committed_kv(TRANSMISSION_SOURCES, "trans_kernel_load_balance")
+    if lb:
+        # busiest / average SM active cycles of one launch (ncu)
+        res["load_balance"] = {"sm_cycles_active_max": float(lb["sm_cycles_active_max"]),
+                               "sm_cycles_active_avg": float(lb["sm_cycles_active_avg"]),
+                               "efficiency": float(lb["sm_cycles_active_avg"]) / float(lb["sm_cycles_active_max"])}
+    return run_t, tcfg, targs, spec, ms, res
+
+
+def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_lines, theta):
+    """Measurements beside the timed step, on the grid the step built:
+    the paper's two approximations (line-strength bound, optical-depth limit),
+    transmission batch, surrogate training and accuracy, screened vs plain
+    retrieval.  Times are CUDA events on the library's stream."""
+    S = int(grid.shape[0])
+    out = {}
+    run_t, tcfg, targs, spec, ms, out["transmission"] = transmission_leg(ctx, torch, dev, stream, grid, ax, nu,
+                                                                         cfg, S)
     out["cloud_rayleigh"] = cloud_rayleigh_leg(ctx, torch, stream, grid, ax, nu, cfg, theta, run_t, ms, tcfg, targs,
                                                spec)
     out["paper_approximations"] = paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta)
@@ -829,6 +880,28 @@ def screen_false_rejections(ctx, bart, torch, dev, grid, ax, nu, filt, cfg, S, n
             "exact_acceptance_in_box": float(np.mean(p_all)) if p_all else 0.0}
 
 
+def run_transmission_case(args):
+    """The bench's 1,024-instance transmission batch alone, on the full-size
+    grid: one JSON line (for ncu captures of its launch)."""
+    import torch
+    from paper_2104_12522_gb300 import build
+    build.build()
+    import paper_2104_12522_gb300 as bart
+    ax = W.grid_axes()
+    species = W.opacity_grid_species(3)
+    ctx = bart.Context(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    nu = bart.NuGrid(ax.nu_start, ax.dnu, ax.n_nu)
+    grid = ctx.build_opacity_grid([bart.device_lines(s) for s in species], ax.p_bar, ax.t_K, nu, ax.cutoff)
+    cfg = dict(geometry=0, n_angles=N_ANGLES, g=W.HD189_GRAV_CGS, mu=W.MEAN_MOLECULAR_MASS_AMU,
+               x0=[W.BASE_VMR] * 3, t_int=W.T_INT_K, t_star=W.HD189_TSTAR_K, r_star_tp=W.HD189_RSTAR_CM,
+               a_orbit=W.HD189_A_CM, t_min=float(ax.t_K[0]), t_max=float(ax.t_K[-1]))
+    *_, res = transmission_leg(ctx, torch, dev, stream, grid, ax, nu, cfg, 3)
+    print(json.dumps({"transmission": res}), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """Small launches of the hot kernels for ncu captures: one opacity launch
     (species 0, 5e6-line list, 3 layers x 20 temperatures on the full
@@ -888,11 +961,14 @@ def main():
     ap.add_argument("--burn", type=int, default=3000, help="exact-model burn-in generations before the retrieval legs")
     ap.add_argument("--screen-beta", type=float, default=1.0)
     ap.add_argument("--screen-margin", type=float, default=1.0)
-    ap.add_argument("--case", choices=["bench", "profile"], default="bench",
-                    help="profile: small launches of the hot kernels for ncu")
+    ap.add_argument("--case", choices=["bench", "profile", "transmission"], default="bench",
+                    help="profile: small launches of the hot kernels for ncu; transmission: the "
+                         "1,024-instance transmission batch alone")
     args = ap.parse_args()
     if args.case == "profile":
         return run_profile_case(args)
+    if args.case == "transmission":
+        return run_transmission_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
