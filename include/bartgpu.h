@@ -10,7 +10,7 @@
  *      spot ... or interpolates from a pre-calculated table"; Sec. 4 items 3-4),
  *   2. the per-proposal spectrum: temperature interpolation of the grid,
  *      abundance scaling, optical depth, emission at Gauss-Legendre angles or
- *      the transit ray geometry (Sec. 3, Sec. 5.1),
+ *      the transit ray geometry (Sec. 3, Sec. 6.1),
  *   3. integration over filter bandpasses (the spectrum integrator, Sec. 3).
  *
  * Conventions shared by every entry point:
@@ -116,7 +116,7 @@ typedef struct {
 /* Line-by-line opacity computed directly at explicit (P, T) cells (Sec. 3):
  *   out[s][c][j] = sum_i S_i(T_c) V(nu_j - nu0_i; sigma_i(T_c), gamma_i(P_c, T_c))
  * in cm^2 molecule^-1, for species s < n_species, cell c < n_cells.
- * V is the Voigt profile of Sec. 5.1.1 (Eqs. 2-9), evaluated through the
+ * V is the Voigt profile of Sec. 6.1.1 (Eqs. 2-11), evaluated through the
  * Faddeeva function in FP32 with region-dependent approximations (relative
  * error <= 1e-5).  S(T): HITRAN convention, T_ref = 296 K, partition ratio
  * (T/T_ref)^1.5.  sigma = (nu0/c) sqrt(kT/m) (Gaussian standard deviation of
@@ -152,7 +152,7 @@ bart_status bart_build_opacity_grid(bart_ctx* ctx, const bart_linelist* species,
 
 /* ------------------------------------------- the paper's Voigt-table scheme */
 
-/* The opacity scheme of Sec. 4 items 4-5 and Sec. 5.1.1 (test f04broadening):
+/* The opacity scheme of Sec. 4 items 4-5 and Sec. 6.1.1 (test f04broadening):
  * Voigt profiles tabulated once for a grid of widths and read by every line.
  *   n_sigma Doppler widths (Gaussian standard deviations, cm^-1) log-spaced
  *   from sigma_lo to sigma_hi, n_gamma Lorentz half widths (cm^-1) log-spaced
@@ -197,7 +197,7 @@ bart_status bart_build_opacity_grid_table(bart_ctx* ctx, const bart_voigt_table*
  * Returns BART_EINVAL for NULL ctx or a non-finite rel. */
 bart_status bart_set_line_threshold(bart_ctx* ctx, double rel);
 
-/* Re w(x + i y) of the Faddeeva function (Sec. 5.1.1, Eqs. 4-9) as the
+/* Re w(x + i y) of the Faddeeva function (Sec. 6.1.1, Eqs. 4-11) as the
  * opacity kernels evaluate it, for y >= 0.  x, y, out: device [n] FP32.
  * Exposed so the profile evaluation can be checked on its own. */
 bart_status bart_faddeeva_re(bart_ctx* ctx, const float* x, const float* y, int64_t n, float* out);
@@ -218,7 +218,7 @@ typedef struct {
 
 enum { BART_EMISSION = 0, BART_TRANSMISSION = 1 };
 
-/* Forward-model constants (Sec. 3; Sec. 5.2 for the HD 189733 b-like values).
+/* Forward-model constants (Sec. 3; Sec. 6.2 for the HD 189733 b-like values).
  *   geometry      BART_EMISSION or BART_TRANSMISSION
  *   n_angles      emission: Gauss-Legendre points on mu in [0, 1], 1..16
  *   g_cgs         gravity, cm s^-2 (at r_planet for transmission)
@@ -267,7 +267,7 @@ typedef struct {
  *   theta        device [n][5 + n_species]: log10 kappa, log10 gamma1,
  *                log10 gamma2, alpha, beta (the five T(P) parameters), then
  *                the log10 abundance scalings a_s (X_s = X0_s 10^a_s)
- *                (Sec. 7.1, nine free parameters)
+ *                (Sec. 7, nine free parameters)
  *   t_profile    device [n][n_layers] or NULL; if set, emission uses these
  *                layer temperatures instead of the T(P) profile of theta
  *   n_levels     transmission: device [n] level counts in [2, 192]
@@ -452,7 +452,7 @@ bart_status bart_demc_set_archive(bart_demc* s, const float* z0, int64_t n0, int
  * the stream. */
 bart_status bart_demc_archive_size(bart_demc* s, int64_t* n);
 
-/* Convergence and sample-size statistics of Sec. 4 and App. C on a chain
+/* Convergence and sample-size statistics of Sec. 5 and App. C on a chain
  * history chain[t][c][q] (device, n x n_chains x n_params FP32):
  *   speis  device [n_chains][n_params] or NULL: steps per effectively
  *          independent sample, 1 + 2 sum_k rho_k over lags k >= 1 until the

@@ -15,6 +15,8 @@ parameterisation), the oracle takes the reading stated in its docstring.
 
 Pins (tests/test_oracle_*.py) tie each function to something other than itself:
 closed forms, limits, invariants, brute-force quadrature and textbook constants.
-The MLP and DE-MC parts are pinned by finite differences and by sampling a
-known Gaussian target.  Nothing here is "parity unpinned".
+The steps between the grid and the radiative transfer (temperature
+interpolation, abundances, mass opacity) are pinned through the composed
+emission and transit paths (tests/test_oracle_composed.py).  The MLP and DE-MC
+parts are pinned by finite differences and by sampling a known Gaussian target.  Nothing here is "parity unpinned".
 """

@@ -25,13 +25,13 @@ delayed acceptance carries the proposal factor q in both stages:
 a1(x -> y) = min(1, exp(beta (ls_y - ls_x) + margin) q) and the stage-2
 ratio exp(L_y - L_x) q a1(y -> x) / a1(x -> y).
 
-Statistics (Sec. 4 "Bayesian samplers", App. C):
+Statistics (Sec. 5 "Bayesian samplers and convergence", App. C):
 * SPEIS by summing the autocorrelation from lag 0 until it first falls below a
   small positive threshold: SPEIS = 1 + 2 sum_{k>=1} rho_k; ESS = N / SPEIS;
 * standard error of a mean, s = sigma / sqrt(ESS) (App. C, Eq. C3 reading);
 * accuracy of a credible region's probability content,
-  s_C = sqrt(C (1 - C) / ESS) (Sec. 4, Eq. 12 solved for s_C);
-* the Gelman-Rubin statistic (Sec. 4, GR 1992) of m chains of length n:
+  s_C = sqrt(C (1 - C) / ESS) (Sec. 5, the ESS relation solved for s_C);
+* the Gelman-Rubin statistic (Sec. 5, GR 1992) of m chains of length n:
   W = mean within-chain variance, B = n x variance of the chain means,
   V = (n - 1)/n W + B/n, R = sqrt(V / W).
 """

@@ -1,7 +1,7 @@
 """Per-proposal forward model on a precomputed opacity grid.
 
 The retrieval interpolates the precomputed opacity table to the temperature of
-each layer (Sec. 4 items 3 and Sec. 5.1.1, "it interpolates in the opacity
+each layer (Sec. 4 items 3 and Sec. 6.1.1, "it interpolates in the opacity
 table ... to the temperature of each atmospheric layer"), scales by the
 abundances from the profile generator (Sec. 3), and runs the emission or
 transmission RT, then the spectrum integrator (Sec. 3).  Readings:

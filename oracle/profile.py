@@ -1,7 +1,7 @@
 """Temperature-pressure profile and abundances of a proposal.
 
 The retrieval model has nine free parameters: five for the T(p) profile of
-Line et al. (2013) and four log-abundance scalings (Sec. 7.1); the profile
+Line et al. (2013) and four log-abundance scalings (Sec. 7); the profile
 generator scales each abundance profile by a constant factor (Sec. 3).  The
 T(p) form is cited, not printed; the reading used is the two-stream
 three-channel form

@@ -2,8 +2,8 @@
 
 The paper implements the emergent-ray geometry of an eclipse observation
 (Sec. 3) and tests it against closed forms: the isothermal atmosphere emits the
-Planck function (test f08isothermal, Sec. 5.1.3) and the optically thin line
-depth scales with abundance (test f05abundance, Sec. 5.1.2, Eqs. 10-11).  The
+Planck function (test f08isothermal, Sec. 6.1.3) and the optically thin line
+depth scales with abundance (test f05abundance, Sec. 6.1.2, Eqs. 12-13).  The
 discretisation itself is in the companion paper (its Eqs. 14-18); the reading
 taken here makes the isothermal case exact:
 

@@ -1,7 +1,7 @@
 """Transmission (transit) geometry.
 
 The paper describes the transit calculation in words (test f01oneline,
-Sec. 5.1): compute the slant path of rays at several altitudes through the
+Sec. 6.1): compute the slant path of rays at several altitudes through the
 layers, the optical depth and transmission along each ray, multiply by 2 pi r
 and integrate over altitude.  The details are in the companion paper; the
 reading taken here:

@@ -1,9 +1,9 @@
-"""Voigt line profile (Sec. 5.1.1, test f04broadening, Eqs. 2-9).
+"""Voigt line profile (Sec. 6.1.1, test f04broadening, Eqs. 2-11).
 
 G(nu; sigma) = exp(-nu^2 / 2 sigma^2) / (sigma sqrt(2 pi))        (Eq. 2)
 L(nu; gamma) = gamma / (pi (nu^2 + gamma^2))                       (Eq. 3)
 V(nu; sigma, gamma) = Re w(z) / (sigma sqrt(2 pi)),
-z = (nu + i gamma) / (sigma sqrt 2)                                (Eqs. 4-9)
+z = (nu + i gamma) / (sigma sqrt 2)                                (Eqs. 4-11)
 
 w(z) is the Faddeeva function.  As in the paper's own test suite, its reference
 value is scipy.special.wofz.
@@ -21,7 +21,7 @@ def faddeeva_re(x, y):
 
 
 def voigt(dnu, sigma, gamma):
-    """V(dnu; sigma, gamma) in units of 1/cm^-1 (Eqs. 4-9)."""
+    """V(dnu; sigma, gamma) in units of 1/cm^-1 (Eqs. 4-11)."""
     dnu = np.asarray(dnu, np.float64)
     z = (dnu + 1j * gamma) / (sigma * SQRT2)
     return wofz(z).real / (sigma * SQRT2PI)

@@ -1,7 +1,7 @@
 """The paper's own opacity scheme: a precomputed table of Voigt profiles (FP64,
 test infrastructure).
 
-Sec. 4 items 4-5 and the sampling text after the list, Sec. 5.1.1 (test
+Sec. 4 items 4-5 and the sampling text after the list, Sec. 6.1.1 (test
 f04broadening): before the opacity grid is built, Voigt profiles are tabulated
 for a grid of Doppler and Lorentz widths, each sampled finely (several samples
 per output-grid interval) and aligned to the output grid.  A line then uses the

@@ -462,7 +462,7 @@ __device__ double block_sum(double v, double* sh) {
 }
 
 // SPEIS of one (chain, parameter) series per block: 1 + 2 sum of the
-// autocorrelation from lag 1 until it first falls below `threshold` (Sec. 4).
+// autocorrelation from lag 1 until it first falls below `threshold` (Sec. 5).
 __global__ void speis_kernel(const float* __restrict__ chain, int n, int C, int d, double threshold,
                              double* __restrict__ out) {
   __shared__ double sh[32];

@@ -1,7 +1,7 @@
 // Real part of the Faddeeva function, Re w(x + i y) for y >= 0, in FP32.
 //
-// The Voigt profile of Sec. 5.1.1 is V = Re w(z) / (sigma sqrt(2 pi)) with
-// z = (nu + i gamma) / (sigma sqrt 2) (Eqs. 4-9).  The paper's code uses a
+// The Voigt profile of Sec. 6.1.1 is V = Re w(z) / (sigma sqrt(2 pi)) with
+// z = (nu + i gamma) / (sigma sqrt 2) (Eqs. 4-11).  The paper's code uses a
 // tabulated Pierluissi approximation; this library evaluates w directly with
 // three regimes chosen so that Re w keeps a relative (not only absolute)
 // error bound, also close to the real axis where Re w << |w|:

@@ -58,7 +58,7 @@ __device__ inline float xi_channel(float g, float tau) {
 }
 
 // Temperature at pressure p_cgs (dyn cm^-2) of the five-parameter profile
-// (Sec. 7.1: five T(p) parameters of Line et al. 2013), read as
+// (Sec. 7: five T(p) parameters of Line et al. 2013), read as
 //   T^4 = 3/4 Tint^4 (2/3 + tau) + 3/4 Tirr^4 [(1-alpha) xi(g1, tau) + alpha xi(g2, tau)],
 //   tau = kappa p / g,  Tirr = beta sqrt(R_star / 2a) T_star.
 // th = (log10 kappa, log10 gamma1, log10 gamma2, alpha, beta).

@@ -949,7 +949,7 @@ bart_status run_cells(bart_ctx* ctx, const bart_linelist* species, int n_species
 }
 
 // ------------------------------------------------------------------------
-// The paper's own scheme (Sec. 4 items 4-5, Sec. 5.1.1): a precomputed table
+// The paper's own scheme (Sec. 4 items 4-5, Sec. 6.1.1): a precomputed table
 // of Voigt profiles on a grid of Doppler and Lorentz widths, each sampled
 // `oversample` times per grid interval and aligned to the grid; a line takes
 // the profile of the nearest widths (in ln sigma and ln gamma), with its

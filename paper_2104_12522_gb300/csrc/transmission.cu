@@ -1,4 +1,4 @@
-// Transmission (transit) geometry of the forward model (Sec. 5.1, the transit
+// Transmission (transit) geometry of the forward model (Sec. 6.1, the transit
 // case of test f01oneline: slant paths through the layers, optical depth and
 // transmission along each ray, times 2 pi r, integrated over altitude).
 //

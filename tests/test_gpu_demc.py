@@ -122,7 +122,7 @@ def test_loglike_bands(ctx, torch):
     assert np.allclose(got[mask == 1], ref[mask == 1], rtol=1e-12)
 
 
-# ---- DEMCzs and the chain statistics (Sec. 4, App. C)
+# ---- DEMCzs (Sec. 4) and the chain statistics (Sec. 5, App. C)
 
 def _run_zs(ctx, torch, n_steps, C, p_snooker, screened=False, seed=6020):
     import paper_2104_12522_gb300 as bart

@@ -1,5 +1,5 @@
 """GPU parity of the emission forward model and the spectrum integrator
-against the FP64 oracle (Sec. 3; f08isothermal Sec. 5.1.3)."""
+against the FP64 oracle (Sec. 3; f08isothermal Sec. 6.1.3)."""
 import numpy as np
 import pytest
 

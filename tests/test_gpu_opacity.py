@@ -1,5 +1,5 @@
 """GPU parity of the line-by-line opacity kernels against the FP64 oracle
-(Sec. 3, Sec. 4 items 3-4; Voigt profile Sec. 5.1.1 Eqs. 2-9)."""
+(Sec. 3, Sec. 4 items 3-4; Voigt profile Sec. 6.1.1 Eqs. 2-11)."""
 import numpy as np
 import pytest
 
@@ -26,7 +26,7 @@ def torch():
 
 
 def test_faddeeva_dense_grid(ctx, torch):
-    # Re w(x + iy) against scipy's wofz (the paper's own reference, Sec. 5.1.1)
+    # Re w(x + iy) against scipy's wofz (the paper's own reference, Sec. 6.1.1)
     xs = np.concatenate([np.linspace(-40, 40, 8001), np.linspace(-6, 6, 2401)])
     ys = np.array([1e-10, 1e-8, 1e-6, 1e-4, 1e-3, 1e-2, 0.05, 0.1, 0.2, 0.3, 0.5, 0.75, 1, 1.5, 2, 3, 4,
                    4.9, 5.1, 6, 8, 10, 15, 23.9, 24.1, 30, 100, 1e3, 1e4])

@@ -1,5 +1,5 @@
 """GPU parity of the transmission (transit) forward model against the FP64
-oracle (Sec. 5.1, transit case of f01oneline) on uneven instances."""
+oracle (Sec. 6.1, transit case of f01oneline) on uneven instances."""
 import numpy as np
 import pytest
 

@@ -51,7 +51,7 @@ def test_speis_of_white_noise_and_ar1():
     assert abs(D.speis(x) - 19.0) < 2.0
 
 
-# ---- DEMCzs and the Gelman-Rubin statistic (Sec. 4)
+# ---- DEMCzs (Sec. 4) and the Gelman-Rubin statistic (Sec. 5)
 
 def test_demczs_recovers_gaussian_with_three_chains():
     mu, cov, lo, hi = target()

@@ -1,6 +1,6 @@
 """Pins of the oracle's line strengths, widths and point-sampled opacity
 (Sec. 4 items 3-4 and the sampling text after them; tests f01-f03 ideas,
-Sec. 5.1 Table 1)."""
+Sec. 6.1 Table 1)."""
 import dataclasses
 import numpy as np
 

@@ -1,5 +1,5 @@
-"""Pins of the oracle's T(P) profile (Sec. 7.1, nine-parameter model), grid
-interpolation and transit geometry (test f01oneline transit text, Sec. 5.1)."""
+"""Pins of the oracle's T(P) profile (Sec. 7, nine-parameter model), grid
+interpolation and transit geometry (test f01oneline transit text, Sec. 6.1)."""
 import numpy as np
 import pytest
 from scipy import integrate

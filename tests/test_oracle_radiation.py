@@ -1,5 +1,5 @@
 """Pins of the oracle's emission RT, Planck function, quadrature and band
-integration: f08isothermal (Sec. 5.1.3), f05abundance (Sec. 5.1.2, Eqs. 10-11,
+integration: f08isothermal (Sec. 6.1.3), f05abundance (Sec. 6.1.2, Eqs. 12-13,
 Table 2), Stefan-Boltzmann and Wien laws."""
 import json
 import os

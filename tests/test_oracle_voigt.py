@@ -1,4 +1,4 @@
-"""Pins of the oracle's Voigt profile (Sec. 5.1.1, Eqs. 2-9) to its limits,
+"""Pins of the oracle's Voigt profile (Sec. 6.1.1, Eqs. 2-11) to its limits,
 its normalisation and a brute-force convolution integral."""
 import numpy as np
 import pytest
@@ -44,7 +44,7 @@ def test_truncated_lorentz_mass():
 
 
 def _convolution(nu, sig, gam):
-    # Eq. 8 written out: integral G(nu'; sigma) L(nu - nu'; gamma) dnu'
+    # Eq. 10 written out: integral G(nu'; sigma) L(nu - nu'; gamma) dnu'
     f = lambda t: V.gaussian(t, sig) * V.lorentzian(nu - t, gam)
     lim = 12 * sig
     val, _ = integrate.quad(f, -lim, lim, points=sorted({0.0, float(np.clip(nu, -lim, lim))}),

@@ -1,5 +1,5 @@
 """Pins of the oracle's version of the paper's Voigt-table opacity scheme
-(Sec. 4 items 4-5 and the sampling text; Sec. 5.1.1, test f04broadening)."""
+(Sec. 4 items 4-5 and the sampling text; Sec. 6.1.1, test f04broadening)."""
 import dataclasses
 import math
 
@@ -82,7 +82,7 @@ def test_quantised_centre_is_within_half_a_sample():
 
 
 def test_width_quantisation_error_converges_to_the_papers_bound():
-    # f04broadening-like layer (Sec. 5.1.1): 0.33516 bar and 1442.58 K, a table
+    # f04broadening-like layer (Sec. 6.1.1): 0.33516 bar and 1442.58 K, a table
     # spanning the list's widths at that layer, sampled 1,000 times per grid
     # interval (the paper samples its profiles thousands of times per
     # interval).  The error comes from the nearest-width choice and falls as

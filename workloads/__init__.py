@@ -6,7 +6,7 @@ instance shapes.  It holds none of the method's arithmetic (no line strengths,
 widths, profiles, optical depths or band integrals) so that neither side of a
 parity test depends on the other through it.
 
-Workloads (shapes follow the paper's retrieval setup, Sec. 7.1: 100 layers over
+Workloads (shapes follow the paper's retrieval setup, Sec. 7: 100 layers over
 1e-8..100 bar, nine free parameters; line statistics are synthetic):
 
 * ``emission_small``     2 species x 10,000 lines, 60 layers (1e-6..100 bar),
@@ -30,7 +30,7 @@ import dataclasses
 import numpy as np
 
 # Physical inputs quoted by the paper for its HD 189733 b-like test planet
-# (Sec. 5.2): stellar radius 0.756 R_sun, T_star 5000 K, planet radius
+# (Sec. 6.2): stellar radius 0.756 R_sun, T_star 5000 K, planet radius
 # 1.138 R_J, gravity 2182.73 cm s^-2, reference pressure 0.1 bar; orbit
 # 0.0312 AU (Sec. 7).  IAU nominal radii.
 R_SUN_CM = 6.957e10
