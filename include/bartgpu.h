@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define BART_ABI_VERSION 3
+#define BART_ABI_VERSION 4
 
 typedef enum {
   BART_OK = 0,
@@ -78,6 +78,48 @@ bart_status bart_sync(bart_ctx* ctx);
  * calls; during a stream capture only a cached or the default width is used.
  * enable = 0 turns it off and forgets the choices. */
 bart_status bart_set_autotune(bart_ctx* ctx, int enable);
+
+/* Wavenumber-tile width (threads per CTA) of the emission forward model:
+ * 64, 128 or 256 fixes it for later calls of this context; 0 (the default)
+ * leaves the choice to the autotuner (or the default width when autotuning is
+ * off).  Spectra do not depend on the width, band values only through the
+ * order of their partial sums.  Other values return BART_EINVAL. */
+bart_status bart_set_emission_tile(bart_ctx* ctx, int tile);
+
+/* Launch structure of an emission batch in bart_forward_spectra_batch.
+ *   BART_LAUNCH_FUSED (default): one persistent kernel per batch.  CTAs (as
+ *     many as fit on the SMs) take (wavenumber tile, proposal) units from a
+ *     device counter in tile-major order, so the CTAs in flight read the same
+ *     grid rows and share them through L2; each unit evaluates its proposal's
+ *     T(P) profile and abundances, the column and the band partial sums, and
+ *     the CTA finishing a proposal's last tile reduces its band values.  The
+ *     counters reset themselves at the end of the launch, so a captured graph
+ *     replays it unchanged.
+ *   BART_LAUNCH_SPLIT: three launches (per-proposal profile kernel, one CTA
+ *     per (proposal, tile) column kernel, band reduction), kept for
+ *     comparison.
+ * Results agree to FP32 rounding (band values through the order of partial
+ * sums).  Other values return BART_EINVAL. */
+#define BART_LAUNCH_FUSED 0
+#define BART_LAUNCH_SPLIT 1
+bart_status bart_set_emission_launch(bart_ctx* ctx, int mode);
+
+/* Graph capture of library calls.  bart_capture_begin starts capturing the
+ * work of later calls on this context (they run nothing until the graph is
+ * launched; the capture goes to a private stream ordered after the context's
+ * stream); bart_capture_end stops it and instantiates the graph into *out.
+ * bart_graph_launch replays it on the context's stream; bart_graph_destroy
+ * frees it.  Calls inside a capture must not need new scratch or changed
+ * constant tables: make one eager call of the same shape and arguments first
+ * (otherwise they return BART_EINVAL and bart_capture_end fails).  A graph
+ * keeps the device pointers it was captured with: replaying it recomputes
+ * from whatever those buffers hold then (CUDA Graphs; the paper's sampler
+ * calls the same forward model once per generation, Sec. 3). */
+typedef struct bart_graph bart_graph;
+bart_status bart_capture_begin(bart_ctx* ctx);
+bart_status bart_capture_end(bart_ctx* ctx, bart_graph** out);
+bart_status bart_graph_launch(bart_ctx* ctx, const bart_graph* graph);
+void bart_graph_destroy(bart_graph* graph);
 
 /* Writes "shape -> tile" lines of the autotuner's choices into buf (len bytes,
  * NUL-terminated, truncated if short); returns the full length, -1 for NULL. */
@@ -307,7 +349,9 @@ typedef struct {
  *   filters  bands to integrate, or NULL
  *   bands    device [n][filters->n_bands] or NULL (needs filters)
  * Band values are the trapezoid-weighted means of bart_band_integrate; a band
- * with no weight on an entry's span yields 0. */
+ * with no weight on an entry's span yields 0.  An entry whose span is invalid
+ * (lo < 0, hi > nu.n_nu or lo >= hi) keeps its spectrum untouched, gets band
+ * values 0 and makes bart_sync() return BART_ERANGE. */
 bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid_desc* grid,
                                        const bart_fwd_cfg* cfg, const bart_batch* batch,
                                        float* spectra, const bart_filters* filters,
@@ -515,16 +559,23 @@ bart_status bart_retrieval_run(bart_ctx* ctx, bart_demc* s, bart_mlp* surrogate,
  * the library holds until the process exits.
  *   Limits: n <= 64 entries, n_layers <= 256, n_species <= 4, n_temps <= 64,
  *   n_nu <= 131072, n_bands <= 16, emission geometry only.  Larger requests
- *   return BART_ERANGE before any work; malformed ones BART_EINVAL.
+ *   return BART_ERANGE before any work; malformed ones BART_EINVAL (among
+ *   them bands requested without filters, without weights or with
+ *   n_bands < 1).
  *   Arguments and results are those of bart_forward_spectra_batch; the work is
  *   issued on cuda_stream (a cudaStream_t, NULL = default stream) of the
  *   current device.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   (cudaGetSymbolAddress, under a lock, so first calls from several host
+ *   threads are safe); make that first call before any stream capture.  The
+ *   call's constant tables reach the device as a kernel argument, so no host
+ *   buffer has to outlive the call.
  *   All calls share the one array and reuse it without clearing it beyond
  *   what each call writes first: calls that overlap on the GPU (other streams,
  *   other host threads) race and must be serialised by the caller.
- *   Device-side range checks are not reported (there is no context). */
+ *   Device-side range checks are not reported (there is no context): an
+ *   entry whose nu_lo/nu_hi span is invalid keeps its spectrum untouched and
+ *   gets band values 0. */
 bart_status bart_forward_emission_noalloc(void* cuda_stream, const bart_grid_desc* grid, const bart_fwd_cfg* cfg,
                                           const bart_batch* batch, float* spectra, const bart_filters* filters,
                                           float* bands);

@@ -15,11 +15,11 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _native
-from ._native import BART_EMISSION, BART_TRANSMISSION  # noqa: F401
+from ._native import BART_EMISSION, BART_TRANSMISSION, BART_LAUNCH_FUSED, BART_LAUNCH_SPLIT  # noqa: F401
 
-__all__ = ["Context", "BartError", "DeviceLines", "device_lines", "NuGrid", "Mlp", "Demc",
+__all__ = ["Context", "Graph", "BartError", "DeviceLines", "device_lines", "NuGrid", "Mlp", "Demc",
            "forward_emission_noalloc", "BART_EMISSION",
-           "BART_TRANSMISSION"]
+           "BART_TRANSMISSION", "BART_LAUNCH_FUSED", "BART_LAUNCH_SPLIT"]
 
 
 class BartError(RuntimeError):
@@ -98,6 +98,28 @@ def _dbl(a) -> C.Array:
     return (C.c_double * a.size)(*a.tolist())
 
 
+class Graph:
+    """A captured sequence of library calls (bart_graph), replayed on its
+    context's stream by launch()."""
+
+    def __init__(self, ctx: "Context", handle: C.c_void_p):
+        self.ctx, self.h = ctx, handle
+
+    def launch(self):
+        self.ctx._check(self.ctx.lib.bart_graph_launch(self.ctx.h, self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.bart_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """A library context bound to one device and one CUDA stream."""
 
@@ -134,6 +156,31 @@ class Context:
 
     def set_autotune(self, enable: bool):
         self._check(self.lib.bart_set_autotune(self.h, int(bool(enable))))
+
+    def set_emission_tile(self, tile: int):
+        """Fix the emission wavenumber-tile width (64, 128, 256); 0 = autotuner."""
+        self._check(self.lib.bart_set_emission_tile(self.h, int(tile)))
+
+    def set_emission_launch(self, mode: int):
+        """BART_LAUNCH_FUSED (0, one persistent kernel) or BART_LAUNCH_SPLIT (1, three launches)."""
+        self._check(self.lib.bart_set_emission_launch(self.h, int(mode)))
+
+    def capture(self, fn) -> "Graph":
+        """Capture the library calls fn() makes on this context into a CUDA
+        graph (bart_capture_begin / bart_capture_end); fn must have run eagerly
+        once with the same shapes and arguments."""
+        self._check(self.lib.bart_capture_begin(self.h))
+        err = None
+        try:
+            fn()
+        except Exception as e:          # close the capture either way
+            err = e
+        g = C.c_void_p()
+        st = self.lib.bart_capture_end(self.h, C.byref(g))
+        if err is not None:
+            raise err
+        self._check(st)
+        return Graph(self, g)
 
     def set_line_threshold(self, rel: float):
         """Line-strength lower bound for later opacity builds (relative to the

@@ -17,6 +17,7 @@ BART_OK, BART_EINVAL, BART_ENOMEM, BART_ECUDA, BART_ETIMEOUT, BART_ERANGE, BART_
 STATUS_NAMES = {0: "BART_OK", 1: "BART_EINVAL", 2: "BART_ENOMEM", 3: "BART_ECUDA",
                 4: "BART_ETIMEOUT", 5: "BART_ERANGE", 6: "BART_EUNSUPPORTED"}
 BART_EMISSION, BART_TRANSMISSION = 0, 1
+BART_LAUNCH_FUSED, BART_LAUNCH_SPLIT = 0, 1
 
 
 class LineList(C.Structure):
@@ -67,6 +68,12 @@ SIGNATURES = {
     "bart_last_error": (C.c_char_p, [c_void_p]),
     "bart_sync": (c_int, [c_void_p]),
     "bart_set_autotune": (c_int, [c_void_p, c_int]),
+    "bart_set_emission_tile": (c_int, [c_void_p, c_int]),
+    "bart_set_emission_launch": (c_int, [c_void_p, c_int]),
+    "bart_capture_begin": (c_int, [c_void_p]),
+    "bart_capture_end": (c_int, [c_void_p, P(c_void_p)]),
+    "bart_graph_launch": (c_int, [c_void_p, c_void_p]),
+    "bart_graph_destroy": (None, [c_void_p]),
     "bart_set_line_threshold": (c_int, [c_void_p, c_double]),
     "bart_demc_set_archive": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int, c_double]),
     "bart_demc_archive_size": (c_int, [c_void_p, P(c_int64)]),

@@ -27,12 +27,25 @@ bart_status bart_check_launch(bart_ctx* ctx, const char* what) {
   return BART_OK;
 }
 
+// True while work issued on the context's stream is being captured.
+static bool stream_capturing(bart_ctx* ctx) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
 bart_status bart_scratch(bart_ctx* ctx, const char* name, size_t bytes, void** out) {
   auto it = ctx->scratch.find(name);
   if (it != ctx->scratch.end() && it->second.second >= bytes) {
     *out = it->second.first;
     return BART_OK;
   }
+  if (stream_capturing(ctx))
+    return bart_fail(ctx, BART_EINVAL, "scratch '%s' (%zu bytes) must be sized by an eager call of the same "
+                     "shape before a stream capture", name, bytes);
   if (it != ctx->scratch.end()) {
     // The old buffer may still be in use by queued work on this stream.
     BART_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -44,6 +57,12 @@ bart_status bart_scratch(bart_ctx* ctx, const char* name, size_t bytes, void** o
   if (cudaMalloc(&p, sz) != cudaSuccess) {
     cudaGetLastError();
     return bart_fail(ctx, BART_ENOMEM, "scratch '%s': cudaMalloc of %zu bytes failed", name, sz);
+  }
+  // zeroed once, so counters kept in scratch start at 0
+  if (cudaMemsetAsync(p, 0, sz, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p);
+    return bart_fail(ctx, BART_ECUDA, "scratch '%s': clearing %zu bytes failed", name, sz);
   }
   ctx->scratch[name] = {p, sz};
   *out = p;
@@ -59,6 +78,9 @@ bart_status bart_upload_const(bart_ctx* ctx, const char* name, const void* data,
   auto& host = ctx->uploaded[name];
   const unsigned char* src = static_cast<const unsigned char*>(data);
   if (*dev == before && host.size() == bytes && std::memcmp(host.data(), src, bytes) == 0) return BART_OK;
+  if (stream_capturing(ctx))
+    return bart_fail(ctx, BART_EINVAL, "constant table '%s' changed inside a stream capture: make an eager "
+                     "call with the same arguments first", name);
   host.assign(src, src + bytes);
   // from the retained host copy, which outlives the asynchronous copy
   BART_CUDA(ctx, cudaMemcpyAsync(*dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -128,6 +150,96 @@ extern "C" bart_status bart_set_autotune(bart_ctx* ctx, int enable) {
   ctx->autotune = enable ? 1 : 0;
   if (!enable) ctx->tiles.clear();
   return BART_OK;
+}
+
+extern "C" bart_status bart_set_emission_tile(bart_ctx* ctx, int tile) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, tile == 0 || tile == 64 || tile == 128 || tile == 256,
+               "emission tile must be 0 (autotuner), 64, 128 or 256, got %d", tile);
+  ctx->em_tile = tile;
+  return BART_OK;
+}
+
+extern "C" bart_status bart_set_emission_launch(bart_ctx* ctx, int mode) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, mode == BART_LAUNCH_FUSED || mode == BART_LAUNCH_SPLIT, "unknown emission launch mode %d", mode);
+  ctx->em_launch = mode;
+  return BART_OK;
+}
+
+struct bart_graph {
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" bart_status bart_capture_begin(bart_ctx* ctx) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, !ctx->capturing, "a capture is already open on this context");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  // capture on a private non-blocking stream ordered after the caller's (the
+  // legacy default stream cannot be captured); the graph replays on the caller's
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev = nullptr;
+  BART_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev, 0);
+  if (ev) cudaEventDestroy(ev);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(cap);
+    return bart_fail(ctx, BART_ECUDA, "could not begin the capture: %s", cudaGetErrorString(e));
+  }
+  ctx->user_stream = ctx->stream;
+  ctx->stream = cap;
+  ctx->capturing = true;
+  return BART_OK;
+}
+
+extern "C" bart_status bart_capture_end(bart_ctx* ctx, bart_graph** out) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, ctx->capturing, "no capture is open on this context");
+  if (out) *out = nullptr;
+  cudaStream_t cap = ctx->stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap, &graph);    // always ends the capture
+  ctx->stream = ctx->user_stream;
+  ctx->user_stream = nullptr;
+  ctx->capturing = false;
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return bart_fail(ctx, BART_ECUDA, "graph capture failed: %s (a library call inside it may have failed: "
+                     "see its status)", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bart_fail(ctx, BART_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  BART_REQUIRE(ctx, out != nullptr, "out is NULL");
+  bart_graph* g = new bart_graph();
+  g->exec = exec;
+  *out = g;
+  return BART_OK;
+}
+
+extern "C" bart_status bart_graph_launch(bart_ctx* ctx, const bart_graph* graph) {
+  if (!ctx) return BART_EINVAL;
+  BART_REQUIRE(ctx, graph && graph->exec, "NULL graph");
+  BART_REQUIRE(ctx, !ctx->capturing, "close the open capture first");
+  BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  BART_CUDA(ctx, cudaGraphLaunch(graph->exec, ctx->stream));
+  return BART_OK;
+}
+
+extern "C" void bart_graph_destroy(bart_graph* graph) {
+  if (!graph) return;
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  delete graph;
 }
 
 extern "C" bart_status bart_set_line_threshold(bart_ctx* ctx, double rel) {

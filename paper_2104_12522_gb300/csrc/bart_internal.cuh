@@ -27,6 +27,10 @@ struct bart_ctx {
   std::map<std::string, int> tiles;  // autotuned tile width per launch shape
   int autotune = 1;
   double line_rel = 0.0;            // line-strength lower bound (<= 0: off)
+  int em_tile = 0;                  // emission tile width fixed by the caller (0: autotuner)
+  int em_launch = BART_LAUNCH_FUSED; // emission launch structure (bart_set_emission_launch)
+  cudaStream_t user_stream = nullptr;  // the caller's stream while a capture is open
+  bool capturing = false;           // between bart_capture_begin and bart_capture_end
   int* d_status = nullptr;          // device status word
   float2* d_wtable = nullptr;       // Faddeeva Taylor-coefficient table
   bool wtable_ready = false;

@@ -21,67 +21,16 @@
 // Proposals run along blockIdx.x, so CTAs in flight share wavenumber tiles and
 // the grid rows they read stay in L2.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "bart_internal.cuh"
+#include "emission.cuh"
 #include "forward.cuh"
 
+using namespace bartem;
+
 namespace {
-
-constexpr int EM_THREADS = 128;
-constexpr int MAX_BANDS = 64;
-constexpr int MAX_ANGLES = 16;
-constexpr int MAX_LAYERS = 256;
-constexpr float LOG2E = 1.4426950408889634f;
-constexpr float LOG2E_LO = 1.925963033500011e-08f;   // log2(e) - (float)log2(e)
-constexpr float LN2F = 0.6931471805599453f;
-
-struct LayerTW {
-  int64_t row;  // offset of grid row (layer k, lower temperature bracket m): (k M + m) n_nu
-  float w;      // weight of the upper bracket
-  float c2_t;   // c2 / T
-};
-
-// Per-call options of the emission kernel (Sec. 3 cloud deck and Rayleigh
-// scattering, Sec. 4 item 7 optical-depth limit).
-struct EmExtra {
-  int L_run;      // levels integrated: a gray cloud deck on level L_run-1 ends the column
-  float tau_cut;  // vertical optical depth that ends the layer loop (MODE bit 1)
-  double ray;     // Rayleigh a / (mu m_u): chi_R = ray nu^4, cm^2 g^-1
-};
-
-// n-point Gauss-Legendre nodes/weights on [0, 1] (Newton on P_n).
-void gauss_legendre01(int n, std::vector<double>& mu, std::vector<double>& w) {
-  mu.assign(n, 0.0);
-  w.assign(n, 0.0);
-  for (int i = 0; i < n; ++i) {
-    double x = std::cos(bartc::PI * (i + 0.75) / (n + 0.5));
-    double dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = x;
-      for (int k = 2; k <= n; ++k) {
-        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      if (n == 1) { p1 = x; p0 = 1.0; }
-      dp = n * (x * p1 - p0) / (x * x - 1.0);
-      double dx = p1 / dp;
-      x -= dx;
-      if (std::fabs(dx) < 1e-16) break;
-    }
-    // recompute derivative at the converged root
-    double p0 = 1.0, p1 = x;
-    for (int k = 2; k <= n; ++k) {
-      double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-      p0 = p1;
-      p1 = p2;
-    }
-    dp = (n == 1) ? 1.0 : n * (x * p1 - p0) / (x * x - 1.0);
-    mu[i] = 0.5 * (x + 1.0);
-    w[i] = 0.5 * 2.0 / ((1.0 - x * x) * dp * dp);
-  }
-}
 
 __global__ void tp_kernel(const float* __restrict__ theta, int n_theta, const float* __restrict__ t_profile,
                           int n, int L, int S, const float* __restrict__ p_cgs, const float* __restrict__ t_axis,
@@ -101,48 +50,12 @@ __global__ void tp_kernel(const float* __restrict__ theta, int n_theta, const fl
       for (int i = 0; i < 5; ++i) th[i] = theta[(int64_t)p * n_theta + i];
       T = bartf::tp_temperature(th, p_cgs[k], inv_g, tint4, tirr0);
     }
-    if (!(T == T) || T <= 0.0f) {
-      atomicOr(status, BART_DEV_RANGE);
-      T = t_min > 0.0f ? t_min : 1.0f;
-    }
-    T = fminf(fmaxf(T, t_min), t_max);
-    int m = 0;
-    float w = 0.0f;
-    if (M > 1) {
-      // m = max{m : t_axis[m] <= T} limited to [0, M-2]
-      int lo = 0, hi = M;               // first index with t_axis > T
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (t_axis[mid] <= T) lo = mid + 1; else hi = mid;
-      }
-      m = min(max(lo - 1, 0), M - 2);
-      w = (T - t_axis[m]) / (t_axis[m + 1] - t_axis[m]);
-      w = fminf(fmaxf(w, 0.0f), 1.0f);
-    }
-    LayerTW r;
-    r.row = ((int64_t)k * M + m) * N;
-    r.w = w;
-    r.c2_t = (float)bartc::C2 / T;
-    tw[(int64_t)p * L + k] = r;
+    tw[(int64_t)p * L + k] = layer_state(T, k, t_axis, M, N, t_min, t_max, status);
   }
   if (threadIdx.x < S) {
     float a = theta ? theta[(int64_t)p * n_theta + 5 + threadIdx.x] : 0.0f;
     coef[(int64_t)p * S + threadIdx.x] = x0_over_mu[threadIdx.x] * exp10f(a);
   }
-}
-
-// Planck function per unit wavenumber, B = c1nu3 / (exp(x) - 1), x = c2 nu / T.
-// For x <= 20 exp(x) = 2^(x log2 e) in FP32: the rounding of the product
-// bounds the relative error of B by ~3e-6 for x >= 0.48 (the smallest
-// c2 nu / T of a 1000 cm^-1, 3000 K grid); larger x, where 2^(x log2 e) would
-// lose digits and eventually overflow, takes an FP64 exponential.
-// WIDE_X: instantiated only where c2 nu / T can exceed 20 on this grid (the
-// host bounds it by c2 nu_max / t_min), so the usual kernel has no branch.
-template <bool WIDE_X>
-__device__ __forceinline__ float planck(float c1nu3, float x) {
-  if (WIDE_X && x > 20.0f) return (float)((double)c1nu3 / expm1((double)x));
-  const float e = bartf::ex2_approx(x * LOG2E);
-  return c1nu3 * bartf::rcp_approx(e - 1.0f);
 }
 
 // MODE bit 0: the FP64 Planck branch (c2 nu / T may exceed 20); bit 1: the
@@ -163,8 +76,11 @@ emission_kernel(const float* __restrict__ grid, int L, int M, int64_t N, const L
   if (act_mask && !act_mask[p]) return;        // skipped entry: outputs untouched
   const int64_t lo = nu_lo ? nu_lo[p] : 0;
   const int64_t hi = nu_hi ? nu_hi[p] : N;
-  if (lo < 0 || hi > N || lo >= hi) {          // invalid span: report, touch nothing
+  if (lo < 0 || hi > N || lo >= hi) {
+    // invalid span: report it, leave the spectrum untouched and give the
+    // band reduction zero partials (band value 0, never a stale sum)
     if (tid == 0 && tile == 0) atomicOr(status, BART_DEV_RANGE);
+    if (tid < n_bands) partial[((int64_t)p * n_tiles + tile) * n_bands + tid] = make_float2(0.f, 0.f);
     return;
   }
   const int64_t j = lo + (int64_t)tile * TW + tid;
@@ -511,9 +427,6 @@ using EmLauncher = void (*)(dim3, cudaStream_t, const float*, int, int, int64_t,
                             const float*, const float*, double, double, const int64_t*, const int64_t*,
                             const int64_t*, float*, const float*, int, float2*, int, const int32_t*, int*, EmExtra);
 
-// Wavenumber-tile widths the autotuner chooses from (threads per CTA).
-constexpr int TILE_CHOICES[3] = {64, 128, 256};
-constexpr int MIN_TILE = 64;
 
 template <int S, int NA, int MODE>
 EmLauncher pick_tile(int tw) {
@@ -563,13 +476,6 @@ int deck_levels_of(const bart_grid_desc* g, const bart_fwd_cfg* c) {
   return L;
 }
 
-EmExtra emission_extra(const bart_grid_desc* g, const bart_fwd_cfg* c) {
-  EmExtra ex;
-  ex.L_run = deck_levels_of(g, c);
-  ex.tau_cut = tau_cut_of(c);
-  ex.ray = c->rayleigh_coef / (c->mu_amu * bartc::AMU);
-  return ex;
-}
 
 // True where x = c2 nu / T can exceed 20 on the grid: T is clamped to
 // [t_min, t_max] by tp_kernel, so x <= c2 nu_max / t_min.
@@ -590,11 +496,53 @@ EmLauncher pick_emission(int S, int na, int tw = EM_THREADS, int mode = 1) {
   }
 }
 
-int emission_mode(const bart_grid_desc* g, const bart_fwd_cfg* c) {
-  return (planck_wide(g->nu, c->t_min_K) ? 1 : 0) | ((c->tau_max > 0.0 && std::isfinite(c->tau_max)) ? 2 : 0);
-}
 
 }  // namespace
+
+// n-point Gauss-Legendre nodes/weights on [0, 1] (Newton on P_n).
+void bartem::gauss_legendre01(int n, std::vector<double>& mu, std::vector<double>& w) {
+  mu.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(bartc::PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = x; p0 = 1.0; }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    // recompute derivative at the converged root
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = (n == 1) ? 1.0 : n * (x * p1 - p0) / (x * x - 1.0);
+    mu[i] = 0.5 * (x + 1.0);
+    w[i] = 0.5 * 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+EmExtra bartem::emission_extra(const bart_grid_desc* g, const bart_fwd_cfg* c) {
+  EmExtra ex;
+  ex.L_run = deck_levels_of(g, c);
+  ex.tau_cut = tau_cut_of(c);
+  ex.ray = c->rayleigh_coef / (c->mu_amu * bartc::AMU);
+  return ex;
+}
+
+int bartem::emission_mode(const bart_grid_desc* g, const bart_fwd_cfg* c) {
+  return (planck_wide(g->nu, c->t_min_K) ? 1 : 0) | ((c->tau_max > 0.0 && std::isfinite(c->tau_max)) ? 2 : 0);
+}
 
 bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
                                     const bart_batch* b, float* spectra, const bart_filters* f, float* bands);
@@ -697,6 +645,7 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
     return bart_fail(ctx, BART_EUNSUPPORTED, "emission with %d species and %d angles is not instantiated "
                      "(species 1-4; angles 1, 2, 4, 8, 16)", S, c->n_angles);
   BART_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (ctx->em_launch == BART_LAUNCH_FUSED) return fused_emission(ctx, g, c, b, spectra, f, bands, nb);
 
   const int NA = c->n_angles;
   EmPrep pr;
@@ -722,9 +671,11 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
   char key[160];
   snprintf(key, sizeof(key), "em S%d A%d L%d/%d M%d N%lld n%d b%d span%d m%d", S, NA, L, ex.L_run, M, (long long)N,
            n, nb, b->nu_lo ? 1 : 0, mode);
-  int tw = EM_THREADS;
+  int tw = ctx->em_tile > 0 ? ctx->em_tile : EM_THREADS;
   auto it = ctx->tiles.find(key);
-  if (it != ctx->tiles.end()) {
+  if (ctx->em_tile > 0) {
+    // fixed by the caller
+  } else if (it != ctx->tiles.end()) {
     tw = it->second;
   } else if (ctx->autotune) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -863,6 +814,19 @@ struct NaAddrs {
 constexpr int NA_MAX_DEVICES = 64;
 NaAddrs g_na[NA_MAX_DEVICES];
 bool g_na_ready[NA_MAX_DEVICES];
+std::mutex g_na_mutex;             // guards the two tables above (first calls from several threads)
+
+// The call's constant table, passed by value as a kernel argument (2.4 KB,
+// inside the 4 KB parameter space), so no host buffer has to outlive the call.
+struct NaConstArg {
+  float v[NA_CONST];
+  int n;
+};
+
+__global__ void na_fill_kernel(NaConstArg c, float* __restrict__ dst, int* __restrict__ status) {
+  for (int i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.v[i];
+  if (threadIdx.x == 0) *status = 0;
+}
 
 }  // namespace
 
@@ -872,9 +836,10 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
   if (!g || !c || !b || !g->grid || !g->p_bar || !g->t_K || !c->x0) return BART_EINVAL;
   const int S = g->n_species, L = g->n_layers, M = g->n_temps, n = b->n;
   const int64_t N = g->nu.n_nu;
-  const int nb = bands ? (f ? f->n_bands : -1) : 0;
+  // bands need filters with at least one band and their weights
+  const int nb = bands ? ((f && f->weights && f->n_bands >= 1) ? f->n_bands : -1) : 0;
   if (c->geometry != BART_EMISSION) return BART_EUNSUPPORTED;
-  if (S < 1 || L < 2 || M < 1 || n < 1 || N < 1 || nb < 0 || (nb > 0 && !f->weights) || !(g->nu.dnu_cm > 0) ||
+  if (S < 1 || L < 2 || M < 1 || n < 1 || N < 1 || nb < 0 || !(g->nu.dnu_cm > 0) ||
       c->n_angles < 1 || !(c->g_cgs > 0) || !(c->mu_amu > 0) || (!b->theta && !b->t_profile) ||
       !(c->rayleigh_coef >= 0 && std::isfinite(c->rayleigh_coef)) || std::isnan(c->p_cloud_bar) ||
       ((b->nu_lo == nullptr) != (b->nu_hi == nullptr)))
@@ -890,26 +855,30 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
   if (!launch) return BART_EUNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return BART_ECUDA;
-  if (!g_na_ready[dev]) {   // set-up once per device, with that device current
-    NaAddrs a{};
-    if (cudaGetSymbolAddress((void**)&a.tw, na_tw) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&a.coef, na_coef) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&a.part, na_part) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&a.cst, na_const) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&a.status, na_status) != cudaSuccess) {
-      cudaGetLastError();
-      return BART_ECUDA;
+  NaAddrs a{};
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ready[dev]) {   // set-up once per device, with that device current
+      if (cudaGetSymbolAddress((void**)&a.tw, na_tw) != cudaSuccess ||
+          cudaGetSymbolAddress((void**)&a.coef, na_coef) != cudaSuccess ||
+          cudaGetSymbolAddress((void**)&a.part, na_part) != cudaSuccess ||
+          cudaGetSymbolAddress((void**)&a.cst, na_const) != cudaSuccess ||
+          cudaGetSymbolAddress((void**)&a.status, na_status) != cudaSuccess) {
+        cudaGetLastError();
+        return BART_ECUDA;
+      }
+      g_na[dev] = a;
+      g_na_ready[dev] = true;
     }
-    g_na[dev] = a;
-    g_na_ready[dev] = true;
+    a = g_na[dev];
   }
-  const NaAddrs& a = g_na[dev];
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
   std::vector<double> mu, w;
   gauss_legendre01(c->n_angles, mu, w);
   const int NA = c->n_angles;
-  float hconst[NA_CONST];
+  NaConstArg carg;
+  float* hconst = carg.v;
   int o = 0;
   for (int k = 0; k < L; ++k) hconst[o++] = (float)(g->p_bar[k] * bartc::BAR);
   const int off_t = o;
@@ -921,12 +890,9 @@ extern "C" bart_status bart_forward_emission_noalloc(void* cuda_stream, const ba
   for (int i = 0; i < NA; ++i) hconst[o++] = (float)(2.0 * bartc::PI * w[i] * mu[i] * 0.5);
   const int off_x0 = o;
   for (int s = 0; s < S; ++s) hconst[o++] = (float)(c->x0[s] / (c->mu_amu * bartc::AMU));
-  // pageable source: the copy is staged before cudaMemcpyAsync returns
-  if (cudaMemcpyAsync(a.cst, hconst, o * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(a.status, 0, sizeof(int), st) != cudaSuccess) {
-    cudaGetLastError();
-    return BART_ECUDA;
-  }
+  // the table travels as a kernel argument; the same launch clears the status word
+  carg.n = o;
+  na_fill_kernel<<<1, 256, 0, st>>>(carg, a.cst, a.status);
   const double rs = c->r_star_tp_cm, ao = c->a_orbit_cm;
   const float tirr0 = (rs > 0 && ao > 0) ? (float)(std::sqrt(rs / (2.0 * ao)) * c->t_star_K) : 0.0f;
   const float tint4 = (float)std::pow(c->t_int_K, 4.0);

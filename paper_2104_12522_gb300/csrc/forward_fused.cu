@@ -1,0 +1,435 @@
+// One persistent fused launch per emission batch: a whole sampler generation
+// of proposals (Sec. 3 forward model -- profile generator, transit and the
+// spectrum integrator -- for every proposal; Sec. 4 items 3 and 7; Sec. 7
+// nine-parameter model) in a single kernel.
+//
+// CTAs (as many as fit on the SMs) take units (wavenumber tile, proposal)
+// from a device counter in tile-major order: the CTAs in flight work on the
+// same tile for neighbouring proposals, so the grid rows they read (the same
+// rows for proposals whose layer temperatures fall in the same bracket) are
+// shared through L2.  For its unit a CTA
+//   1. evaluates the proposal's five-parameter T(P) profile at every layer
+//      (one thread per layer) and keeps each layer's temperature bracket,
+//      weight and c2/T in shared memory, with the abundance coefficients
+//      X_s / (mu m_u) = X0_s 10^{a_s} / (mu m_u);
+//   2. runs one thread per wavenumber down the column: opacity interpolated
+//      in T and summed over species (coalesced grid-row reads, the next
+//      layer's rows requested before the current layer is computed), the
+//      trapezoid optical depth, the Planck source and per Gauss-Legendre angle
+//      the log2 transmittance and the intensity sum (the arithmetic of the
+//      three-launch path in forward.cu);
+//   3. writes the spectrum and the tile's band partial sums; the CTA that
+//      finishes a proposal's last tile sums its partials in a fixed order
+//      (FP64) into the band values.
+// Nothing waits on another CTA: the last-tile test is an atomic count, and
+// the last CTA to leave resets the counters, so the launch can be replayed
+// from a CUDA graph unchanged.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "bart_internal.cuh"
+#include "emission.cuh"
+#include "forward.cuh"
+
+using namespace bartem;
+
+namespace {
+
+constexpr int FUSED_MAX_SPECIES = 4;
+
+struct FusedArgs {
+  const float* grid;                 // [S][L][M][N]
+  int L, M;
+  int64_t N;
+  const float* theta;                // [n][n_theta] or NULL
+  int n_theta;
+  const float* t_profile;            // [n][L] or NULL
+  int n;
+  const int64_t* nu_lo;
+  const int64_t* nu_hi;
+  const int64_t* offs;
+  const int32_t* active;
+  const float* p_cgs;                // [L] level pressures, dyn cm^-2
+  const float* t_axis;               // [M]
+  const float* dpg;                  // [L-1] (P_{k+1} - P_k) / (2 g)
+  float x0mu[FUSED_MAX_SPECIES];     // X0_s / (mu m_u)
+  float ang[2 * MAX_ANGLES];         // -log2(e) / mu_i, then 2 pi w_i mu_i / 2
+  float inv_g, tint4, tirr0, t_min, t_max;
+  double nu_start, dnu;
+  float* spectra;
+  const float* filt;
+  int n_bands;
+  float2* partial;                   // [n][n_tiles][n_bands]
+  float* bands;
+  int n_tiles;                       // tiles per proposal over the whole grid
+  unsigned long long n_units;        // n_tiles x n
+  unsigned long long* work;          // [0] next unit, [1] CTAs finished
+  unsigned int* p_done;              // [n] tiles finished per proposal
+  int* status;
+  EmExtra ex;
+};
+
+template <int S, int NA, int TW, int MODE>
+__global__ void __launch_bounds__(TW) emission_fused_kernel(const __grid_constant__ FusedArgs a) {
+  __shared__ LayerTW s_tw[MAX_LAYERS];
+  __shared__ float s_dpg[MAX_LAYERS];
+  __shared__ float s_xs[S];
+  __shared__ float2 s_red[TW / 32][MAX_BANDS];
+  __shared__ unsigned long long s_unit;
+  __shared__ int s_last;
+  constexpr bool WIDE_X = (MODE & 1) != 0, TAU_LIM = (MODE & 2) != 0;
+  const int tid = threadIdx.x;
+  const int L = a.L, nb = a.n_bands;
+  for (int k = tid; k + 1 < L; k += TW) s_dpg[k] = a.dpg[k];
+  const int64_t sstride = (int64_t)L * a.M * a.N;
+  const int64_t dm = (a.M > 1) ? a.N : 0;          // offset of the upper temperature bracket
+
+  for (;;) {
+    if (tid == 0) s_unit = atomicAdd(a.work, 1ULL);
+    __syncthreads();
+    const unsigned long long u = s_unit;
+    if (u >= a.n_units) break;
+    const int p = (int)(u % (unsigned long long)a.n);
+    const int tile = (int)(u / (unsigned long long)a.n);
+    // every value below is uniform over the CTA
+    bool skip = a.active && !a.active[p];
+    int64_t lo = 0, hi = a.N;
+    if (!skip) {
+      lo = a.nu_lo ? a.nu_lo[p] : 0;
+      hi = a.nu_hi ? a.nu_hi[p] : a.N;
+      if (lo < 0 || hi > a.N || lo >= hi) {
+        // invalid span: report it once, band values 0, spectrum untouched
+        if (tile == 0) {
+          if (tid == 0) atomicOr(a.status, BART_DEV_RANGE);
+          if (a.bands && tid < nb) a.bands[(int64_t)p * nb + tid] = 0.0f;
+        }
+        skip = true;
+      }
+    }
+    const int n_tiles_p = skip ? 0 : (int)((hi - lo + TW - 1) / TW);
+    if (!skip && tile < n_tiles_p) {
+      // 1. the proposal's layers: T(P) (or the given profile), bracket, c2/T
+      for (int k = tid; k < L; k += TW) {
+        float T;
+        if (a.t_profile) {
+          T = a.t_profile[(int64_t)p * L + k];
+        } else {
+          float th[5];
+#pragma unroll
+          for (int i = 0; i < 5; ++i) th[i] = a.theta[(int64_t)p * a.n_theta + i];
+          T = bartf::tp_temperature(th, a.p_cgs[k], a.inv_g, a.tint4, a.tirr0);
+        }
+        s_tw[k] = layer_state(T, k, a.t_axis, a.M, a.N, a.t_min, a.t_max, a.status);
+      }
+      if (tid < S) {
+        const float ab = a.theta ? a.theta[(int64_t)p * a.n_theta + 5 + tid] : 0.0f;
+        s_xs[tid] = a.x0mu[tid] * exp10f(ab);
+      }
+      __syncthreads();
+
+      // 2. the column of wavenumber j
+      const int64_t j = lo + (int64_t)tile * TW + tid;
+      const bool act = j < hi;
+      const int64_t jj = act ? j : lo;             // idle lanes compute on a valid index
+      float xs[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) xs[s] = s_xs[s];
+      const double nu = a.nu_start + (double)jj * a.dnu;
+      const float nuf = (float)nu;
+      const float c1nu3 = (float)(2.0 * bartc::H * bartc::C * bartc::C * nu * nu * nu);
+      const float chi_r = (float)(a.ex.ray * (nu * nu) * (nu * nu));   // Rayleigh a nu^4 / (mu m_u)
+      float lt[NA], t[NA], I[NA];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        lt[i] = 0.0f;
+        t[i] = 1.0f;
+        I[i] = 0.0f;
+      }
+      const float* gj = a.grid + jj;
+      const int L_run = a.ex.L_run;
+      // grid values of a layer: lower (x) and upper (y) temperature bracket per species
+      auto fetch = [&](int k, float* x, float* y) {
+        const float* g0 = gj + s_tw[k].row;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          x[s] = __ldg(g0 + s * sstride);
+          y[s] = __ldg(g0 + s * sstride + dm);
+        }
+      };
+      auto chi_of = [&](int k, const float* x, const float* y) {
+        const float w = s_tw[k].w;
+        float chi = chi_r;
+#pragma unroll
+        for (int s = 0; s < S; ++s) chi = fmaf(xs[s], fmaf(w, y[s] - x[s], x[s]), chi);
+        return chi;
+      };
+      float cx[S], cy[S], nx[S], ny[S];
+      fetch(0, cx, cy);
+      fetch(min(1, L_run - 1), nx, ny);
+      float chi_prev = chi_of(0, cx, cy);
+      float B_prev = planck<WIDE_X>(c1nu3, nuf * s_tw[0].c2_t);
+      float tau_v = 0.0f;                          // vertical optical depth from the top
+#pragma unroll 2
+      for (int k = 1; k < L_run; ++k) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          cx[s] = nx[s];
+          cy[s] = ny[s];
+        }
+        fetch(min(k + 1, L_run - 1), nx, ny);      // the next layer's rows are in flight meanwhile
+        const float chi = chi_of(k, cx, cy);
+        const float B = planck<WIDE_X>(c1nu3, nuf * s_tw[k].c2_t);
+        const float dtau = (chi_prev + chi) * s_dpg[k - 1];
+        const float Bsum = B_prev + B;
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+          lt[i] = fmaf(dtau, a.ang[i], lt[i]);
+          const float te = bartf::ex2_approx(lt[i]);
+          I[i] = fmaf(Bsum, t[i] - te, I[i]);
+          t[i] = te;
+        }
+        chi_prev = chi;
+        B_prev = B;
+        if (TAU_LIM) {
+          // Sec. 4 item 7: stop at the caller's optical-depth limit; the level
+          // reached is the bottom boundary (its blackbody below)
+          tau_v += dtau;
+          if (tau_v > a.ex.tau_cut) break;
+        }
+      }
+      float F = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NA; ++i) F = fmaf(a.ang[NA + i], fmaf(2.0f * B_prev, t[i], I[i]), F);
+      if (act && a.spectra) {
+        const int64_t base = a.offs ? a.offs[p] : (int64_t)p * a.N;
+        a.spectra[base + (j - lo)] = F;
+      }
+
+      // 3. band partial sums of the tile; the proposal's last tile reduces them
+      if (nb > 0) {
+        float dw = 0.0f;
+        if (act) dw = (hi - lo == 1) ? 1.0f : ((j == lo || j == hi - 1) ? 0.5f : 1.0f);
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int b = 0; b < nb; ++b) {
+          const float W = act ? __ldg(a.filt + (int64_t)b * a.N + j) * dw : 0.0f;
+          float num = W * F, den = W;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+          }
+          if (lane == 0) s_red[warp][b] = make_float2(num, den);
+        }
+        __syncthreads();
+        if (tid < nb) {
+          float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int w = 0; w < TW / 32; ++w) {
+            acc.x += s_red[w][tid].x;
+            acc.y += s_red[w][tid].y;
+          }
+          a.partial[((int64_t)p * a.n_tiles + tile) * nb + tid] = acc;
+          __threadfence();                         // partial visible before the count below
+        }
+        __syncthreads();
+        if (tid == 0) s_last = (atomicAdd(a.p_done + p, 1u) + 1u == (unsigned)n_tiles_p);
+        __syncthreads();
+        if (s_last) {
+          __threadfence();
+          if (tid < nb) {
+            double num = 0.0, den = 0.0;
+            for (int q = 0; q < n_tiles_p; ++q) {
+              const float2 v = __ldcg(a.partial + ((int64_t)p * a.n_tiles + q) * nb + tid);
+              num += v.x;
+              den += v.y;
+            }
+            a.bands[(int64_t)p * nb + tid] = den > 0.0 ? (float)(num / den) : 0.0f;
+          }
+          if (tid == 0) a.p_done[p] = 0u;           // ready for the next launch
+        }
+      }
+    }
+    __syncthreads();                               // shared state is reused by the next unit
+  }
+  // the last CTA to leave resets the counters for the next launch
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(a.work + 1, 1ULL) + 1ULL == (unsigned long long)gridDim.x) {
+      a.work[0] = 0ULL;
+      a.work[1] = 0ULL;
+      __threadfence();
+    }
+  }
+}
+
+using FusedLauncher = cudaError_t (*)(const FusedArgs&, int, cudaStream_t);
+
+template <int S, int NA, int TW, int MODE>
+cudaError_t launch_fused(const FusedArgs& a, int sm_count, cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emission_fused_kernel<S, NA, TW, MODE>, TW, 0);
+  if (e != cudaSuccess) return e;
+  unsigned long long grid = (unsigned long long)(per_sm < 1 ? 1 : per_sm) * (unsigned long long)sm_count;
+  if (grid > a.n_units) grid = a.n_units;
+  emission_fused_kernel<S, NA, TW, MODE><<<(unsigned)grid, TW, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int S, int NA, int MODE>
+FusedLauncher pick_tw(int tw) {
+  switch (tw) {
+    case 64: return launch_fused<S, NA, 64, MODE>;
+    case 128: return launch_fused<S, NA, 128, MODE>;
+    case 256: return launch_fused<S, NA, 256, MODE>;
+    default: return nullptr;
+  }
+}
+
+template <int S, int MODE>
+FusedLauncher pick_angles(int na, int tw) {
+  switch (na) {
+    case 1: return pick_tw<S, 1, MODE>(tw);
+    case 2: return pick_tw<S, 2, MODE>(tw);
+    case 4: return pick_tw<S, 4, MODE>(tw);
+    case 8: return pick_tw<S, 8, MODE>(tw);
+    case 16: return pick_tw<S, 16, MODE>(tw);
+    default: return nullptr;
+  }
+}
+
+template <int S>
+FusedLauncher pick_fused_mode(int na, int tw, int mode) {
+  switch (mode) {
+    case 0: return pick_angles<S, 0>(na, tw);
+    case 1: return pick_angles<S, 1>(na, tw);
+    case 2: return pick_angles<S, 2>(na, tw);
+    default: return pick_angles<S, 3>(na, tw);
+  }
+}
+
+FusedLauncher pick_fused(int S, int na, int tw, int mode) {
+  switch (S) {
+    case 1: return pick_fused_mode<1>(na, tw, mode);
+    case 2: return pick_fused_mode<2>(na, tw, mode);
+    case 3: return pick_fused_mode<3>(na, tw, mode);
+    case 4: return pick_fused_mode<4>(na, tw, mode);
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c,
+                                   const bart_batch* b, float* spectra, const bart_filters* f, float* bands, int nb) {
+  const int S = g->n_species, L = g->n_layers, M = g->n_temps, n = b->n, NA = c->n_angles;
+  const int64_t N = g->nu.n_nu;
+  const int mode = emission_mode(g, c);
+  if (S > FUSED_MAX_SPECIES || !pick_fused(S, NA, EM_THREADS, mode))
+    return bart_fail(ctx, BART_EUNSUPPORTED, "emission with %d species and %d angles is not instantiated "
+                     "(species 1-4; angles 1, 2, 4, 8, 16)", S, NA);
+  bart_status st;
+  // device table: level pressures, temperature axis, (P_{k+1} - P_k) / 2g
+  std::vector<float> hconst;
+  for (int k = 0; k < L; ++k) hconst.push_back((float)(g->p_bar[k] * bartc::BAR));
+  for (int m = 0; m < M; ++m) hconst.push_back((float)g->t_K[m]);
+  for (int k = 0; k + 1 < L; ++k)
+    hconst.push_back((float)((g->p_bar[k + 1] - g->p_bar[k]) * bartc::BAR / (2.0 * c->g_cgs)));
+  void *p_const, *p_work, *p_done = nullptr, *p_part = nullptr;
+  if ((st = bart_upload_const(ctx, "ff_const", hconst.data(), hconst.size() * sizeof(float), &p_const)) != BART_OK)
+    return st;
+  if ((st = bart_scratch(ctx, "ff_work", 2 * sizeof(unsigned long long), &p_work)) != BART_OK) return st;
+  const int max_tiles = (int)((N + MIN_TILE - 1) / MIN_TILE);    // partials sized for the smallest tile
+  if (nb > 0) {
+    if ((st = bart_scratch(ctx, "ff_done", (size_t)n * sizeof(unsigned int), &p_done)) != BART_OK) return st;
+    if ((st = bart_scratch(ctx, "fw_part", (size_t)n * max_tiles * nb * sizeof(float2), &p_part)) != BART_OK)
+      return st;
+  }
+  FusedArgs a{};
+  a.grid = g->grid;
+  a.L = L;
+  a.M = M;
+  a.N = N;
+  a.theta = b->theta;
+  a.n_theta = 5 + S;
+  a.t_profile = b->t_profile;
+  a.n = n;
+  a.nu_lo = b->nu_lo;
+  a.nu_hi = b->nu_hi;
+  a.offs = b->spec_offsets;
+  a.active = b->active;
+  const float* dc = (const float*)p_const;
+  a.p_cgs = dc;
+  a.t_axis = dc + L;
+  a.dpg = dc + L + M;
+  for (int s = 0; s < S; ++s) a.x0mu[s] = (float)(c->x0[s] / (c->mu_amu * bartc::AMU));
+  std::vector<double> mu, w;
+  gauss_legendre01(NA, mu, w);
+  for (int i = 0; i < NA; ++i) {
+    a.ang[i] = (float)(-1.4426950408889634 / mu[i]);
+    a.ang[NA + i] = (float)(2.0 * bartc::PI * w[i] * mu[i] * 0.5);   // the 1/2 of the layer-mean source
+  }
+  a.inv_g = (float)(1.0 / c->g_cgs);
+  a.tint4 = (float)std::pow(c->t_int_K, 4.0);
+  const double rs = c->r_star_tp_cm, ao = c->a_orbit_cm;
+  a.tirr0 = (rs > 0 && ao > 0) ? (float)(std::sqrt(rs / (2.0 * ao)) * c->t_star_K) : 0.0f;
+  a.t_min = (float)c->t_min_K;
+  a.t_max = (float)std::min(c->t_max_K, 1e30);
+  a.nu_start = g->nu.nu_start_cm;
+  a.dnu = g->nu.dnu_cm;
+  a.spectra = spectra;
+  a.filt = nb ? f->weights : nullptr;
+  a.n_bands = nb;
+  a.partial = (float2*)p_part;
+  a.bands = bands;
+  a.work = (unsigned long long*)p_work;
+  a.p_done = (unsigned int*)p_done;
+  a.status = ctx->d_status;
+  a.ex = emission_extra(g, c);
+
+  auto run = [&](int tw) -> bart_status {
+    a.n_tiles = (int)((N + tw - 1) / tw);
+    a.n_units = (unsigned long long)a.n_tiles * (unsigned long long)n;
+    cudaError_t e = pick_fused(S, NA, tw, mode)(a, ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return bart_fail(ctx, BART_ECUDA, "launch of emission_fused_kernel failed: %s",
+                                           cudaGetErrorString(e));
+    return BART_OK;
+  };
+  // tile width: fixed by the caller, cached per shape, or measured once
+  // (each candidate timed with CUDA events on the stream) outside a capture
+  char key[160];
+  snprintf(key, sizeof(key), "fused S%d A%d L%d/%d M%d N%lld n%d b%d span%d m%d", S, NA, L, a.ex.L_run, M,
+           (long long)N, n, nb, b->nu_lo ? 1 : 0, mode);
+  int tw = ctx->em_tile > 0 ? ctx->em_tile : EM_THREADS;
+  auto it = ctx->tiles.find(key);
+  if (ctx->em_tile > 0) {
+    // fixed by the caller
+  } else if (it != ctx->tiles.end()) {
+    tw = it->second;
+  } else if (ctx->autotune) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BART_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      cudaEvent_t e0, e1;
+      BART_CUDA(ctx, cudaEventCreate(&e0));
+      BART_CUDA(ctx, cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int cand : TILE_CHOICES) {
+        BART_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        if ((st = run(cand)) != BART_OK) return st;
+        BART_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+        BART_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BART_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          tw = cand;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      ctx->tiles[key] = tw;
+    }
+  }
+  return run(tw);
+}

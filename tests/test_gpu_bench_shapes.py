@@ -1,0 +1,154 @@
+"""GPU parity of the per-proposal forward model against the FP64 oracle at the
+shapes the benchmark times: 100 layers over 1e-8..100 bar, 20 temperatures
+over 500..3000 K, 8 Gauss-Legendre angles, 3 and 4 species, 9-parameter
+proposals from the prior box and 10 Gaussian bands (emission), and uneven
+transmission instances of up to 150 levels (Sec. 3 forward model, Sec. 4
+second pass; Sec. 7 nine-parameter model).  The opacity grid is a seeded
+random field (``workloads.opacity_field``) on a 3,000-point slice of the
+0.02 cm^-1 axis, so the oracle can hold it; both sides read the same values.
+The FP32-vs-FP64 error of every case is printed."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import forward as Fw, radiation as R
+from gpu_common import make_ctx, max_rel
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4          # spectra, band values, transit depths (relative)
+N_SLICE = 3000
+N_PROP = 32
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return make_ctx()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def _em_cfg(S):
+    return dict(geometry=0, n_angles=8, g=W.HD189_GRAV_CGS, mu=W.MEAN_MOLECULAR_MASS_AMU, x0=[W.BASE_VMR] * S,
+                t_int=W.T_INT_K, t_star=W.HD189_TSTAR_K, r_star_tp=W.HD189_RSTAR_CM, a_orbit=W.HD189_A_CM,
+                t_min=500.0, t_max=3000.0)
+
+
+@pytest.fixture(scope="module")
+def field4():
+    ax = W.grid_axes(n_nu=N_SLICE)
+    return ax, W.opacity_field(4, ax.p_bar, ax.t_K, N_SLICE)
+
+
+def _oracle_emission(grid, ax, theta, S, filt):
+    nu = W.nu_axis(ax.nu_start, ax.dnu, ax.n_nu)
+    cfg = dict(_em_cfg(S))
+    spec = np.array([Fw.emission_spectrum(grid, ax.p_bar, ax.t_K, nu, th, cfg) for th in theta])
+    bands = np.array([R.band_integrate(F, filt) for F in spec])
+    return spec, bands
+
+
+@pytest.mark.parametrize("S", [3, 4])
+def test_emission_generation_shape(ctx, torch, field4, S):
+    """32 proposals of the 9-parameter prior (the 4th scaling unused at S = 3)
+    on the full 100-layer x 20-temperature grid, 8 angles, 10 bands; every
+    tile width the autotuner can choose, and its own choice."""
+    import paper_2104_12522_gb300 as bart
+    ax, field = field4
+    grid_np = np.ascontiguousarray(field[:S])
+    grid = torch.tensor(grid_np, device="cuda")
+    theta = W.proposals(N_PROP, generation=11, n_species=S)
+    filt = W.gaussian_filters(W.nu_axis(ax.nu_start, ax.dnu, N_SLICE), 10, 1002.0, 1058.0, 2.0, 20.0)
+    spec_o, bands_o = _oracle_emission(grid_np.astype(np.float64), ax, theta, S, filt)
+    nu = bart.NuGrid(ax.nu_start, ax.dnu, N_SLICE)
+    th, fl = torch.tensor(theta, device="cuda"), torch.tensor(filt, device="cuda")
+    for launch in (bart.BART_LAUNCH_FUSED, bart.BART_LAUNCH_SPLIT):
+        ctx.set_emission_launch(launch)
+        for tile in (64, 128, 256, 0):
+            ctx.set_emission_tile(tile)
+            spec = torch.full((N_PROP, N_SLICE), -1.0, dtype=torch.float32, device="cuda")
+            bands = torch.full((N_PROP, 10), -1.0, dtype=torch.float32, device="cuda")
+            for _ in range(2):     # first call may autotune; the second runs the cached choice
+                ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, _em_cfg(S), theta=th, spectra=spec,
+                                          filters=fl, bands=bands)
+            ctx.sync()
+            es, eb = max_rel(spec.cpu().numpy(), spec_o), max_rel(bands.cpu().numpy(), bands_o)
+            print(f"emission S={S} {'fused' if launch == 0 else 'split'} tile={tile or 'auto'}: "
+                  f"FP32 vs FP64 spectra {es:.2e}, bands {eb:.2e}")
+            assert es < RTOL and eb < RTOL, (launch, tile, es, eb)
+    ctx.set_emission_tile(0)
+    ctx.set_emission_launch(bart.BART_LAUNCH_FUSED)
+
+
+def test_fused_generation_replays_from_a_graph(ctx, torch, field4):
+    """The persistent fused generation captured in a CUDA graph (after an
+    eager call of the same shape) and replayed three times on new proposals
+    written into the same input buffer: each replay equals an eager call on
+    those proposals bit for bit, and the oracle within 1e-4."""
+    import paper_2104_12522_gb300 as bart
+    ax, field = field4
+    S = 4
+    grid_np = np.ascontiguousarray(field)
+    grid = torch.tensor(grid_np, device="cuda")
+    nu = bart.NuGrid(ax.nu_start, ax.dnu, N_SLICE)
+    filt = torch.tensor(W.gaussian_filters(W.nu_axis(ax.nu_start, ax.dnu, N_SLICE), 10, 1002.0, 1058.0, 2.0,
+                                           20.0), device="cuda")
+    th = torch.tensor(W.proposals(N_PROP, generation=20, n_species=S), device="cuda")
+    spec = torch.empty((N_PROP, N_SLICE), dtype=torch.float32, device="cuda")
+    bands = torch.empty((N_PROP, 10), dtype=torch.float32, device="cuda")
+    run = lambda: ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, _em_cfg(S), theta=th, spectra=spec,
+                                            filters=filt, bands=bands)
+    run()
+    graph = ctx.capture(run)
+    for gen in (21, 22, 23):
+        th.copy_(torch.tensor(W.proposals(N_PROP, generation=gen, n_species=S), device="cuda"))
+        graph.launch()
+        ctx.sync()
+        s_g, b_g = spec.clone(), bands.clone()
+        run()
+        ctx.sync()
+        assert torch.equal(s_g, spec) and torch.equal(b_g, bands), gen
+    theta = th.cpu().numpy()
+    so, bo = _oracle_emission(grid_np.astype(np.float64), ax, theta[:4], S, filt.cpu().numpy())
+    assert max_rel(s_g.cpu().numpy()[:4], so) < RTOL and max_rel(b_g.cpu().numpy()[:4], bo) < RTOL
+    graph.close()
+
+
+def test_transmission_instances_shape(ctx, torch, field4):
+    """Uneven instances of the transit batch on the 4-species field: 40..150
+    levels (and the 192-level maximum), spans inside the slice, planet and
+    star radii from their ranges; 12 bands."""
+    import paper_2104_12522_gb300 as bart
+    ax, field = field4
+    S = 4
+    grid_np = np.ascontiguousarray(field)
+    inst = W.instances(12, N_SLICE, lmin=40, lmax=150, span_lo=500, span_hi=N_SLICE, seed=4011)
+    inst.n_levels[0], inst.n_levels[1] = 150, 192
+    inst.nu_lo[2], inst.nu_hi[2] = 0, N_SLICE
+    filt = W.gaussian_filters(W.nu_axis(ax.nu_start, ax.dnu, N_SLICE), 12, 1002.0, 1058.0, 2.0, 15.0)
+    cfg = dict(_em_cfg(S), geometry=1, p_ref=W.HD189_PREF_BAR, p_top=1e-8, p_bot=100.0)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    offs = inst.offsets
+    n = len(inst.n_levels)
+    spec = torch.empty(int(offs[-1]), dtype=torch.float32, device="cuda")
+    bands = torch.empty((n, 12), dtype=torch.float32, device="cuda")
+    nu = bart.NuGrid(ax.nu_start, ax.dnu, N_SLICE)
+    ctx.forward_spectra_batch(torch.tensor(grid_np, device="cuda"), ax.p_bar, ax.t_K, nu, cfg,
+                              theta=dev(inst.theta[:, :5 + S]), n_levels=dev(inst.n_levels), nu_lo=dev(inst.nu_lo),
+                              nu_hi=dev(inst.nu_hi), spec_offsets=dev(offs), r_planet=dev(inst.r_planet),
+                              r_star=dev(inst.r_star), spectra=spec, filters=dev(filt), bands=bands)
+    ctx.sync()
+    spec, bands = spec.cpu().numpy(), bands.cpu().numpy()
+    es = eb = 0.0
+    for i in range(n):
+        d = Fw.transmission_spectrum(grid_np.astype(np.float64), ax.p_bar, ax.t_K, ax.nu_start, ax.dnu, inst, i, cfg)
+        es = max(es, max_rel(spec[offs[i]:offs[i + 1]], d))
+        bo = R.band_integrate(d, filt, int(inst.nu_lo[i]))
+        assert np.all(bands[i][bo == 0] == 0)          # bands with no weight on the span
+        eb = max(eb, max_rel(bands[i][bo > 0], bo[bo > 0]))
+    print(f"transmission (40..192 levels, S=4): FP32 vs FP64 depths {es:.2e}, bands {eb:.2e}")
+    assert es < RTOL and eb < RTOL

@@ -29,7 +29,7 @@ def test_abi_version(lib):
     from paper_2104_12522_gb300 import _native
     with open(os.path.join(ROOT, "include", "bartgpu.h")) as fh:
         version = int(re.search(r"#define BART_ABI_VERSION (\d+)", fh.read()).group(1))
-    assert lib.bart_abi_version() == version == 3
+    assert lib.bart_abi_version() == version == 4
     # version 2 appended tau_max, version 3 p_cloud_bar and rayleigh_coef to
     # bart_fwd_cfg: the binding's struct must match
     assert C.sizeof(_native.FwdCfg) == 2 * 4 + 11 * 8 + 8 + 3 * 8

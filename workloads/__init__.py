@@ -232,6 +232,40 @@ def opacity_grid_species(n_species: int = 3, total_lines: int = 5_000_000) -> li
     return [line_list(s, counts[s]) for s in range(n_species)]
 
 
+def opacity_field(n_species: int, p_bar: np.ndarray, t_K: np.ndarray, n_nu: int,
+                  seed: int = 3500) -> np.ndarray:
+    """Seeded stand-in for an opacity grid, float32 [S][L][M][n_nu] in cm^2 per
+    molecule, for tests of the per-proposal forward model at full layer and
+    temperature counts without building a grid from lines.  Random numbers
+    only: per species a base level U[-23.5, -21.5] (log10), a random walk over
+    wavenumber detrended and scaled to +-2.5 decades, sparse spikes of up to
+    +3 decades that fall off by a random factor per point, a random slope in
+    log10 P per (species, layer) and a random temperature trend per
+    (species, wavenumber), clipped to [1e-30, 1e-16].  Optical depths of
+    1 then fall anywhere from 1e-4 to 1e4 bar in the 9-parameter prior."""
+    g = _rng(seed)
+    L, M = len(p_bar), len(t_K)
+    lp = (np.log10(np.asarray(p_bar, np.float64)) + 3.0)[:, None]        # [L, 1]
+    tt = ((np.asarray(t_K, np.float64) - 1750.0) / 1250.0)[:, None]       # [M, 1]
+    out = np.empty((n_species, L, M, n_nu), np.float32)
+    j = np.arange(n_nu)
+    for s in range(n_species):
+        walk = np.cumsum(g.normal(0.0, 0.2, n_nu))
+        walk -= np.polyval(np.polyfit(j, walk, 1), j)
+        walk *= 2.5 / max(np.max(np.abs(walk)), 1e-12)
+        spikes = np.zeros(n_nu)
+        for c in g.integers(0, n_nu, max(1, n_nu // 50)):
+            h, q = g.uniform(0.5, 3.0), g.uniform(0.5, 0.9)
+            spikes = np.maximum(spikes, h * q ** np.abs(j - c))
+        row = g.uniform(-23.5, -21.5) + walk + spikes                        # [n_nu]
+        pslope = g.uniform(-0.3, 0.3, (L, 1))
+        tslope = g.uniform(-1.0, 1.0, (1, n_nu))
+        for k in range(L):
+            lg = row[None, :] + pslope[k] * lp[k] + tslope * tt + g.normal(0.0, 0.05, (M, n_nu))
+            out[s, k] = (10.0 ** np.clip(lg, -30.0, -16.0)).astype(np.float32)
+    return out
+
+
 SURROGATE_WIDTHS = (9, 256, 256, 256, 10)
 
 
