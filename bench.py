@@ -4,10 +4,14 @@
 One step = one pass of the hot path over one batch of synthetic input:
   1. the line-by-line opacity grid (3 species, 5e6 lines, 100 layers x 20
      temperatures x 100,000 wavenumbers, cutoff 25 cm^-1), and
-  2. one generation of 2,048 emission proposals on that grid (five-parameter
-     T(P) + abundance scalings, 8 Gauss-Legendre angles, 10 Gaussian filters).
+  2. one generation of 2,048 emission proposals on that grid plus a fourth
+     species built once at set-up (nine parameters: five-parameter T(P) + four
+     abundance scalings; 8 Gauss-Legendre angles, 10 Gaussian filters), one
+     persistent fused launch replayed from a CUDA graph.
 The headline value is Voigt line-point evaluations per second over the whole
-step (Gline-evals/s); the emission generation's spectra/s is reported beside it.
+step (Gline-evals/s); the generation's spectra/s is reported beside it, with
+the transit batch, the surrogate and the retrieval legs, FP32-vs-FP64 errors
+of sampled full-size results and the oracle's CPU baselines.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -38,24 +42,26 @@ import workloads as W  # noqa: E402
 
 METRIC = ("forward-model spectra/sec at 1e-4 rel err (plain vs surrogate); Voigt Gline-evals/s")
 UNIT = "Gline-evals/s"
-FLOPS_PER_EVAL = 10          # algorithmic FP32 flops of one line-point evaluation
+FLOPS_PER_EVAL = 10          # algorithmic FP32 flops of one line-point evaluation (one-pole form)
+SURVEY_FLOPS_PER_EVAL = 16   # the same evaluation counted on the region-I rational form
 N_PROPOSALS = 2048
 N_ANGLES = 8
 N_BANDS = 10
 OPACITY_LAUNCHES_PER_STEP = 3     # one opacity kernel launch per species
-KERNELS_PER_STEP = 3 * 3 + 3      # per species: window and span prologues + opacity; tp, emission, band reduce
+KERNELS_PER_STEP = 3 * 3 + 1      # per species: window and span prologues + opacity; one fused generation
 # sources the opacity kernel is compiled from (the committed traffic figure is tied to them)
 OPACITY_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
                    for f in ("opacity.cu", "faddeeva.cuh", "bart_internal.cuh")]
 FORWARD_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
-                   for f in ("forward.cu", "forward.cuh", "bart_internal.cuh")]
+                   for f in ("forward_fused.cu", "emission.cuh", "forward.cuh", "bart_internal.cuh")]
 MUFU_PER_CLK = 16                 # MUFU (ex2, rcp) results per clock per SM
 
 
 def workload_desc():
     return ("opacity grid: 3 species, 5e6 lines, 100 layers (1e-8..100 bar) x 20 T (500..3000 K) x "
-            "100000 nu (0.02 cm^-1), cutoff 25 cm^-1; then emission of 2048 proposals x 8 angles x "
-            "10 Gaussian bands on that grid")
+            "100000 nu (0.02 cm^-1), cutoff 25 cm^-1; then one emission generation of 2048 9-parameter "
+            "proposals x 8 angles x 10 Gaussian bands on that grid plus a 4th species (3.2 GB, built once), "
+            "one persistent fused launch replayed from a CUDA graph")
 
 
 # ---------------------------------------------------------------- distributed
@@ -185,51 +191,270 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
+# Everything in this section runs the FP64 oracle on the host cores: the
+# CPU baselines (a reported baseline, never the target) and the FP32-vs-FP64
+# samples of the full-size results.  It runs before the first CUDA call, in
+# spawned worker processes.
 _ORACLE_STATE = {}
+SLICE_N = 3000                  # wavenumbers of the seeded opacity-field slice
+EM_SAMPLE_PROPOSALS = (0, 1024, 2047)
+TR_SAMPLE_INSTANCES = (0, 1)
+SAMPLE_POINTS = 8               # wavenumbers sampled per proposal (shared) / instance
 
 
 def _oracle_init():
     _ORACLE_STATE["ax"] = W.grid_axes()
-    _ORACLE_STATE["species"] = W.opacity_grid_species(3)
+    _ORACLE_STATE["species"] = W.opacity_grid_species(4)
+
+
+def _lines_in_cutoff(ll, nu, cutoff):
+    """Line-point evaluations of the points nu: lines within the cutoff."""
+    nu = np.asarray(nu, np.float64)
+    return int(np.sum(np.searchsorted(ll.nu0, nu + cutoff, side="right") -
+                      np.searchsorted(ll.nu0, nu - cutoff, side="left")))
 
 
 def _oracle_window(args):
-    s, k, m, j0, nwin = args
+    """Oracle opacity of species s at cell (k, m) on the grid points js (a
+    window when contiguous); returns (evaluations, seconds, values)."""
+    s, k, m, js = args
     from oracle import opacity as O
     ax, ll = _ORACLE_STATE["ax"], _ORACLE_STATE["species"][s]
+    js = np.asarray(js, np.int64)
     t = time.perf_counter()
-    O.opacity_cell(ll, ax.p_bar[k], ax.t_K[m], ax.nu_start, ax.dnu, ax.n_nu, ax.cutoff, j0, j0 + nwin)
+    if np.all(np.diff(js) == 1):
+        vals = O.opacity_cell(ll, ax.p_bar[k], ax.t_K[m], ax.nu_start, ax.dnu, ax.n_nu, ax.cutoff,
+                              int(js[0]), int(js[-1]) + 1)
+    else:
+        vals = np.array([O.opacity_cell(ll, ax.p_bar[k], ax.t_K[m], ax.nu_start, ax.dnu, ax.n_nu, ax.cutoff,
+                                        int(j), int(j) + 1)[0] for j in js])
     dt = time.perf_counter() - t
-    nu = W.nu_axis(ax.nu_start, ax.dnu, ax.n_nu)[j0:j0 + nwin]
-    lo = np.searchsorted(ll.nu0, nu[0] - ax.cutoff - ax.dnu)
-    hi = np.searchsorted(ll.nu0, nu[-1] + ax.cutoff + ax.dnu, side="right")
-    d = nu[:, None] - ll.nu0[None, lo:hi]
-    evals = int(np.count_nonzero(np.abs(d) <= ax.cutoff))
-    return evals, dt
+    return _lines_in_cutoff(ll, W.nu_axis(ax.nu_start, ax.dnu, ax.n_nu)[js], ax.cutoff), dt, vals
 
 
-def cpu_oracle_rate(target_s=15.0, nwin=48, seed=0):
-    """Time the oracle (as it stands) on a bounded sample of the opacity-grid
-    workload: random (species, layer, temperature, 48-point window) cells, one
-    process per host core (spawned), about target_s of wall time."""
+def _oracle_emission_task(args):
+    """Oracle emission spectrum and band values of one proposal on the
+    seeded field slice; returns (seconds, spectrum, bands)."""
+    theta, cfg, filt = args
+    from oracle import forward as Fw, radiation as R
+    f = _ORACLE_STATE.get("field")
+    if f is None:
+        ax = W.grid_axes(n_nu=SLICE_N)
+        f = _ORACLE_STATE["field"] = W.opacity_field(4, ax.p_bar, ax.t_K, SLICE_N).astype(np.float64)
+    ax = W.grid_axes(n_nu=SLICE_N)
+    t = time.perf_counter()
+    F = Fw.emission_spectrum(f, ax.p_bar, ax.t_K, W.nu_axis(ax.nu_start, ax.dnu, SLICE_N), theta, cfg)
+    B = R.band_integrate(F, filt)
+    return time.perf_counter() - t, F, B
+
+
+def _oracle_transmission_task(args):
+    """Oracle transit depths of one instance (span clipped into the field
+    slice); returns (seconds, depths, bands)."""
+    inst, cfg, filt = args
+    from oracle import forward as Fw, radiation as R
+    f = _ORACLE_STATE.get("field")
+    if f is None:
+        ax = W.grid_axes(n_nu=SLICE_N)
+        f = _ORACLE_STATE["field"] = W.opacity_field(4, ax.p_bar, ax.t_K, SLICE_N).astype(np.float64)
+    ax = W.grid_axes(n_nu=SLICE_N)
+    t = time.perf_counter()
+    d = Fw.transmission_spectrum(f, ax.p_bar, ax.t_K, ax.nu_start, ax.dnu, inst, 0, cfg)
+    B = R.band_integrate(d, filt, int(inst.nu_lo[0]))
+    return time.perf_counter() - t, d, B
+
+
+def em_cfg(S):
+    """Emission configuration of the benchmark (oracle and library keys)."""
+    return dict(geometry=0, n_angles=N_ANGLES, g=W.HD189_GRAV_CGS, mu=W.MEAN_MOLECULAR_MASS_AMU,
+                x0=[W.BASE_VMR] * S, t_int=W.T_INT_K, t_star=W.HD189_TSTAR_K, r_star_tp=W.HD189_RSTAR_CM,
+                a_orbit=W.HD189_A_CM, t_min=500.0, t_max=3000.0)
+
+
+def tr_cfg(S):
+    return dict(em_cfg(S), geometry=1, p_ref=W.HD189_PREF_BAR, p_top=1e-8, p_bot=100.0)
+
+
+def slice_filters(n_bands, seed=3000):
+    ax = W.grid_axes(n_nu=SLICE_N)
+    return W.gaussian_filters(W.nu_axis(ax.nu_start, ax.dnu, SLICE_N), n_bands, 1002.0, 1058.0, 2.0, 20.0,
+                              seed=seed)
+
+
+def sample_points(lo, hi, seed):
+    """SAMPLE_POINTS sorted grid indices spread over [lo, hi)."""
+    g = np.random.default_rng(seed)
+    edges = np.linspace(lo, hi, SAMPLE_POINTS + 1)
+    return np.array([int(g.integers(int(a), max(int(a) + 1, int(b)))) for a, b in zip(edges[:-1], edges[1:])])
+
+
+def emission_sample_cells(theta, S):
+    """Oracle T(P) of the sampled proposals and the (species, layer,
+    temperature) cells their linear-in-T interpolation reads."""
+    from oracle import forward as Fw
+    ax = W.grid_axes()
+    cfg = em_cfg(S)
+    cells = set()
+    for p in EM_SAMPLE_PROPOSALS:
+        T = Fw.tp_of(theta[p], ax.p_bar, cfg)
+        for k in range(len(ax.p_bar)):
+            m, _ = Fw.bracket(ax.t_K, T[k])
+            for s in range(S):
+                cells.update({(s, k, m), (s, k, min(m + 1, len(ax.t_K) - 1))})
+    return sorted(cells)
+
+
+def transmission_sample_cells(inst, S):
+    from oracle import forward as Fw
+    ax = W.grid_axes()
+    cfg = tr_cfg(S)
+    lp = np.log10(ax.p_bar)
+    cells = set()
+    for i in TR_SAMPLE_INSTANCES:
+        P = Fw.instance_levels(inst.n_levels[i], cfg["p_top"], cfg["p_bot"])
+        T = Fw.tp_of(inst.theta[i], P, cfg)
+        for k in range(len(P)):
+            a, _ = Fw.bracket(lp, np.log10(P[k]))
+            m, _ = Fw.bracket(ax.t_K, T[k])
+            for s in range(S):
+                for aa in (a, min(a + 1, len(lp) - 1)):
+                    for mm in (m, min(m + 1, len(ax.t_K) - 1)):
+                        cells.add((s, aa, mm))
+    return sorted(cells)
+
+
+def cpu_phase(target_s=15.0, nwin=48, seed=0, full=True):
+    """The oracle's part of the benchmark, on the host cores (spawned pool,
+    one process per core), before any CUDA call:
+      * opacity baseline: random (species, layer, T) cells x 48-point windows
+        of the 5e6-line grid (every line within the cutoff), about target_s
+        of work; the values are kept for the full-size opacity parity;
+      * (full) the oracle opacity at the cells and wavenumbers that sampled
+        proposals / instances of the full-size generation and transit batch
+        read, for their FP32-vs-FP64 errors;
+      * (full) emission and transmission baselines on the seeded field slice
+        (the oracle's cost grows linearly with the points of a spectrum, so
+        full-size rates are extrapolated by point count), and the DE-MC
+        retrieval baseline with the oracle forward model."""
     cores = len(os.sched_getaffinity(0))
     rng = np.random.default_rng(seed)
     ctx = mp.get_context("spawn")
-    # one calibration task per core, then enough tasks to fill target_s
+    out = {}
     with ctx.Pool(cores, initializer=_oracle_init) as pool:
         def tasks(n):
-            return [(int(rng.integers(3)), int(rng.integers(100)), int(rng.integers(20)),
-                     int(rng.integers(0, 100_000 - nwin)), nwin) for _ in range(n)]
+            res = []
+            for _ in range(n):
+                j0 = int(rng.integers(0, 100_000 - nwin))
+                res.append((int(rng.integers(3)), int(rng.integers(100)), int(rng.integers(20)),
+                            tuple(range(j0, j0 + nwin))))
+            return res
         cal = pool.map(_oracle_window, tasks(cores))
-        per_task = max(statistics.median(dt for _, dt in cal), 1e-3)
+        per_task = max(statistics.median(dt for _, dt, _ in cal), 1e-3)
         n_tasks = max(cores, int(target_s / per_task) * cores)
+        tk = tasks(n_tasks)
         t = time.perf_counter()
-        res = pool.map(_oracle_window, tasks(n_tasks))
+        res = pool.map(_oracle_window, tk)
         wall = time.perf_counter() - t
-    evals = sum(e for e, _ in res)
-    return {"value": evals / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n_tasks} random (species, layer, T) cells x {nwin}-point windows of the 5e6-line "
-                      f"grid, every line within the cutoff; {evals:.3g} evals in {wall:.1f} s"}
+        evals = sum(e for e, _, _ in res)
+        out["opacity"] = {"value": evals / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                          "sample": f"{n_tasks} random (species, layer, T) cells x {nwin}-point windows of the "
+                                    f"5e6-line grid, every line within the cutoff; {evals:.3g} evals in {wall:.1f} s"}
+        out["opacity_windows"] = [(a[0], a[1], a[2], a[3][0], r[2]) for a, r in zip(tk, res)]
+        if not full:
+            return out
+        # sampled cells of the full-size generation and transit batch
+        S = 4
+        theta = W.proposals(N_PROPOSALS, generation=0, n_species=S)
+        em_shared = sample_points(0, 100_000, 7000)
+        em_js = {p: em_shared for p in EM_SAMPLE_PROPOSALS}
+        em_union = np.unique(np.concatenate(list(em_js.values())))
+        em_cells = emission_sample_cells(theta, S)
+        inst = W.instances(TRANS_INSTANCES, 100_000)
+        tr_js = {i: sample_points(int(inst.nu_lo[i]), int(inst.nu_hi[i]), 7100 + i) for i in TR_SAMPLE_INSTANCES}
+        tr_union = np.unique(np.concatenate(list(tr_js.values())))
+        tr_cells = transmission_sample_cells(inst, S)
+        t = time.perf_counter()
+        em_vals = pool.map(_oracle_window, [(s, k, m, tuple(em_union)) for s, k, m in em_cells])
+        tr_vals = pool.map(_oracle_window, [(s, k, m, tuple(tr_union)) for s, k, m in tr_cells])
+        out["sample_oracle_s"] = time.perf_counter() - t
+        out["em_sample"] = (em_js, em_union, em_cells, [v for _, _, v in em_vals], theta)
+        out["tr_sample"] = (tr_js, tr_union, tr_cells, [v for _, _, v in tr_vals], inst)
+        # emission baseline (config 2 shape: L = 100, M = 20, S = 4, 8 angles, 10 bands)
+        n_em = max(16, cores)
+        th_s = W.proposals(n_em, generation=0, n_species=S)
+        filt = slice_filters(N_BANDS)
+        pool.map(_oracle_emission_task, [(th_s[i], em_cfg(S), filt) for i in range(cores)])   # field built
+        t = time.perf_counter()
+        em = pool.map(_oracle_emission_task, [(th_s[i], em_cfg(S), filt) for i in range(n_em)])
+        wall = time.perf_counter() - t
+        out["em_slice"] = (th_s, filt, np.array([F for _, F, _ in em]), np.array([B for _, _, B in em]))
+        rate = n_em / wall * SLICE_N / 100_000
+        out["emission"] = {"value": rate, "unit": "spectra/s", "cores": cores, "kind": "oracle",
+                           "sample": f"{n_em} proposals of the 9-parameter prior on a {SLICE_N}-point slice of "
+                                     f"a seeded 4-species opacity field (100 layers x 20 T, 8 angles, 10 bands) in "
+                                     f"{wall:.2f} s; rate extrapolated to 100,000 points by point count"}
+        # transmission baseline (config 3: the bench batch's first instances, spans clipped to the slice)
+        n_tr = max(16, cores)
+        tcfg = tr_cfg(S)
+        tfilt = slice_filters(12, seed=3001)
+        clipped, full_span = [], []
+        for i in range(n_tr):
+            span = int(min(inst.nu_hi[i] - inst.nu_lo[i], SLICE_N))
+            lo = (i * 97) % (SLICE_N - span + 1)
+            clipped.append(W.Instances(inst.n_levels[i:i + 1], np.array([lo], np.int64),
+                                       np.array([lo + span], np.int64), inst.r_planet[i:i + 1],
+                                       inst.r_star[i:i + 1], inst.theta[i:i + 1]))
+            full_span.append(int(inst.nu_hi[i] - inst.nu_lo[i]) / span)
+        t = time.perf_counter()
+        tr = pool.map(_oracle_transmission_task, [(c, tcfg, tfilt) for c in clipped])
+        wall = time.perf_counter() - t
+        out["tr_slice"] = (clipped, tfilt, [d for _, d, _ in tr], [B for _, _, B in tr])
+        cpu_s = sum(dt * f for (dt, _, _), f in zip(tr, full_span))     # full-span seconds of one core
+        out["transmission"] = {"value": n_tr / (cpu_s / cores), "unit": "spectra/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"{n_tr} instances of the transit batch (their level counts, spans "
+                                         f"clipped to {SLICE_N} points of the seeded field), {wall:.2f} s; each "
+                                         "instance's time scaled by its full span / clipped span, spread over "
+                                         "the cores"}
+    out["retrieval"] = cpu_retrieval_baseline()
+    return out
+
+
+def cpu_retrieval_baseline(n_gen=100, n_pts=300):
+    """DE-MC (16 chains, 9 parameters) with the oracle forward model on a
+    n_pts-point field slice for n_gen generations on one core; accepted
+    samples/s extrapolated to full-size spectra by point count."""
+    from oracle import forward as Fw, radiation as R, demc as D
+    S = 4
+    ax = W.grid_axes(n_nu=n_pts)
+    f = W.opacity_field(S, ax.p_bar, ax.t_K, n_pts, seed=3600).astype(np.float64)
+    nu = W.nu_axis(ax.nu_start, ax.dnu, n_pts)
+    filt = W.gaussian_filters(nu, N_BANDS, 1000.5, 1005.5, 0.5, 2.0, seed=3002)
+    cfg = em_cfg(S)
+    lo, hi = W.THETA_LO, W.THETA_HI
+    truth = lo + np.random.default_rng(6500).uniform(0.3, 0.7, 9) * (hi - lo)
+    b_true = R.band_integrate(Fw.emission_spectrum(f, ax.p_bar, ax.t_K, nu, truth, cfg), filt)
+    sig = b_true / 50.0
+    data = b_true + np.random.default_rng(6501).normal(size=N_BANDS) * sig
+
+    def loglike(th):
+        b = R.band_integrate(Fw.emission_spectrum(f, ax.p_bar, ax.t_K, nu, th, cfg), filt)
+        return -0.5 * float(np.sum(((b - data) / sig) ** 2))
+    x0 = lo + np.random.default_rng(6000).uniform(size=(16, 9)) * (hi - lo)
+    t = time.perf_counter()
+    _, acc = D.run(loglike, x0, lo, hi, n_gen, np.random.default_rng(6001))
+    wall = time.perf_counter() - t
+    scale = 100_000 / n_pts
+    return {"value": acc / (wall * scale), "unit": "accepted samples/s", "cores": 1, "kind": "oracle",
+            "generations_per_s": n_gen / (wall * scale),
+            "sample": f"16 chains x {n_gen} generations from a uniform start, oracle forward model on a "
+                      f"{n_pts}-point seeded field slice ({acc} accepted in {wall:.1f} s); rates divided by "
+                      f"{scale:.0f} (100,000 / {n_pts} points)"}
+
+
+def cpu_oracle_rate(target_s=15.0, nwin=48, seed=0):
+    """The opacity baseline alone (the reference arm's step)."""
+    return cpu_phase(target_s, nwin, seed, full=False)["opacity"]
 
 
 # ---------------------------------------------------------------- reference arm
@@ -263,10 +488,10 @@ def run_reference(args):
 def run_native(args):
     ws, rank, local = dist_env()
     N = args.gpus if ws == 1 else ws
-    # The CPU baseline runs before any CUDA call (spawned pool, rank 0, N=1 only).
+    # The oracle phase runs before any CUDA call (spawned pool, rank 0, N=1 only).
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(target_s=args.cpu_seconds)
+        cpu = cpu_phase(target_s=args.cpu_seconds, full=not args.no_aux)
 
     import torch
     torch.cuda.set_device(local)
@@ -277,9 +502,10 @@ def run_native(args):
     import paper_2104_12522_gb300 as bart
 
     ax = W.grid_axes()
-    species = W.opacity_grid_species(3)
-    S, L, M, NU = 3, len(ax.p_bar), len(ax.t_K), ax.n_nu
-    evals = eval_count(species, ax)
+    species = W.opacity_grid_species(4)
+    S_OP, S = 3, 4
+    L, M, NU = len(ax.p_bar), len(ax.t_K), ax.n_nu
+    evals = eval_count(species[:S_OP], ax)
     nu = bart.NuGrid(ax.nu_start, ax.dnu, NU)
     stream = torch.cuda.current_stream(dev)
     ctx = bart.Context(local, stream)
@@ -296,20 +522,29 @@ def run_native(args):
     grid = torch.empty((S, L, M, NU), dtype=torch.float32, device=dev)
     bands = torch.empty((N_PROPOSALS, N_BANDS), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    cfg = dict(geometry=0, n_angles=N_ANGLES, g=W.HD189_GRAV_CGS, mu=W.MEAN_MOLECULAR_MASS_AMU,
-               x0=[W.BASE_VMR] * S, t_int=W.T_INT_K, t_star=W.HD189_TSTAR_K, r_star_tp=W.HD189_RSTAR_CM,
-               a_orbit=W.HD189_A_CM, t_min=float(ax.t_K[0]), t_max=float(ax.t_K[-1]))
+    cfg = em_cfg(S)
+    # the 4th molecule of the 4-species generation, built once (the timed
+    # build is the 3-species, 5e6-line grid)
+    ctx.build_opacity_grid(d_lines[S_OP:], ax.p_bar, ax.t_K, nu, ax.cutoff, out=grid[S_OP:])
+    generation = lambda: ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=theta, filters=filt,
+                                                   bands=bands)
+    graph = None
 
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
-        ctx.build_opacity_grid(d_lines, ax.p_bar, ax.t_K, nu, ax.cutoff, out=grid)
+        ctx.build_opacity_grid(d_lines[:S_OP], ax.p_bar, ax.t_K, nu, ax.cutoff, out=grid[:S_OP])
         if ev is not None:
             ev[1].record(stream)
-        ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=theta, filters=filt, bands=bands)
+        if graph is not None:
+            graph.launch()              # one persistent fused launch, replayed from a CUDA graph
+        else:
+            generation()
         if ev is not None:
             ev[2].record(stream)
 
+    step()                              # eager: autotunes the generation's tile width, sizes scratch
+    graph = ctx.capture(generation)
     for _ in range(args.warmup):
         step()
         flush.fill_(1.0)
@@ -344,9 +579,9 @@ def run_native(args):
 
     # end-to-end through the public API with host buffers: H2D of the step's
     # inputs from pinned memory, the step, D2H of the grid and the band values.
-    h_grid = torch.empty(grid.shape, dtype=torch.float32).pin_memory()
+    h_grid = torch.empty((S_OP, L, M, NU), dtype=torch.float32).pin_memory()
     h_bands = torch.empty(bands.shape, dtype=torch.float32).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for h in h_lines for t in h) + \
+    h2d = sum(t.numel() * t.element_size() for h in h_lines[:S_OP] for t in h) + \
         h_theta.numel() * 4 + h_filt.numel() * 4
     d2h = h_grid.numel() * 4 + h_bands.numel() * 4
     e2e_steps = max(1, min(args.steps, 2))
@@ -360,19 +595,19 @@ def run_native(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         stream.wait_stream(copy_stream)          # the previous step's slabs are home
-        for hd, dd in zip(h_lines, d_lines):
+        for hd, dd in zip(h_lines[:S_OP], d_lines[:S_OP]):
             for h, d in zip(hd, (dd.nu0, dd.log10_s296, dd.elow, dd.gamma_ref)):
                 d.copy_(h, non_blocking=True)
         theta.copy_(h_theta, non_blocking=True)
         filt.copy_(h_filt, non_blocking=True)
-        for s_ in range(S):
+        for s_ in range(S_OP):
             ctx.build_opacity_grid(d_lines[s_:s_ + 1], ax.p_bar, ax.t_K, nu, ax.cutoff, out=grid[s_:s_ + 1])
             built = torch.cuda.Event()
             built.record(stream)
             copy_stream.wait_event(built)
             with torch.cuda.stream(copy_stream):
                 h_grid[s_].copy_(grid[s_], non_blocking=True)
-        ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=theta, filters=filt, bands=bands)
+        graph.launch()
         h_bands.copy_(bands, non_blocking=True)
         stream.wait_stream(copy_stream)
         flush.fill_(1.0)
@@ -381,10 +616,16 @@ def run_native(args):
     e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1) / e2e_steps, dev)
     ctx.sync()
     assert np.all(np.isfinite(h_bands.numpy())), "non-finite band values"
+    del h_grid
 
+    fw = forward_model_leg(ctx, bart, torch, stream, grid, ax, nu, cfg, theta, filt, bands, generation, fw_avg, N,
+                           S)
+    parity = {}
+    if cpu is not None:
+        parity["opacity"] = opacity_parity(grid, cpu["opacity_windows"], ax)
     aux = {}
     if not args.no_aux:
-        aux = run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_lines, theta)
+        aux = run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_lines, theta, cpu, parity)
 
     if rank == 0:
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -395,48 +636,35 @@ def run_native(args):
                 peaks = json.load(fh)
         max_mhz = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
         op_launch_ms = op_avg / OPACITY_LAUNCHES_PER_STEP
-        # forward model: the proposals of a wavenumber tile share the grid rows
-        # through L2, so the binding unit is the MUFU (NA ex2 of the angles, ex2
-        # and reciprocal of the Planck function per (proposal, layer,
-        # wavenumber)); DRAM traffic from the committed ncu capture
-        hbm = float(peaks.get("hbm_gbs") or 6800.0)
-        fw_units = N_PROPOSALS * L * NU
-        mufu = fw_units * (N_ANGLES + 2) / (fw_avg / 1e3) / 1e12
-        mufu_peak = n_sm * MUFU_PER_CLK * max_mhz * 1e6 / 1e12
-        fw_dram = committed_traffic(FORWARD_SOURCES, "emission_kernel")
-        fw_dram_frac = fw_dram / (fw_avg / 1e3) / (hbm * 1e9) if fw_dram else None
         achieved = FLOPS_PER_EVAL * evals / OPACITY_LAUNCHES_PER_STEP / (op_launch_ms / 1e3) / 1e12
         peak = fp32_peak_tflops(n_sm, max_mhz)
         traffic = committed_traffic(OPACITY_SOURCES, "opacity_kernel")
+        fw["roofline"] = emission_roofline(fw["ms_per_generation"], n_sm, max_mhz, peaks, L, NU)
+        cb = None
+        if cpu is not None:
+            cb = dict(cpu["opacity"])
+            cb["configs"] = {k: cpu[k] for k in ("emission", "transmission", "retrieval") if k in cpu}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": N, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(), "evals_per_step": evals,
-                       "l2": "256 MiB write between steps; the 2.4 GB grid written and read each step exceeds L2",
+                       "l2": "256 MiB write between steps; the 2.4 GB grid written and the 3.2 GB grid read each "
+                             "step exceed L2",
                        "parallelism": f"replicas x{N} (independent problems, no collective)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "frac_survey16": achieved * SURVEY_FLOPS_PER_EVAL / FLOPS_PER_EVAL / peak,
                          "kernel": "opacity_kernel",
-                         "note": (f"{FLOPS_PER_EVAL} algorithmic FP32 flops per line-point evaluation; peak = "
+                         "note": (f"{FLOPS_PER_EVAL} algorithmic FP32 flops per line-point evaluation "
+                                  f"(frac_survey16: the same time with {SURVEY_FLOPS_PER_EVAL}); peak = "
                                   f"{n_sm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock); "
                                   f"launch time = opacity-build events / {OPACITY_LAUNCHES_PER_STEP}")},
-            "forward_model": {"spectra_per_s": N * N_PROPOSALS / (fw_avg / 1e3), "ms_per_generation": fw_avg,
-                              "proposals": N_PROPOSALS, "angles": N_ANGLES, "bands": N_BANDS,
-                              "species": S,
-                              "roofline": {"bound": "mufu", "achieved": mufu, "peak": mufu_peak, "unit": "Tops/s",
-                                           "frac": mufu / mufu_peak, "traffic": fw_dram,
-                                           "dram_frac": fw_dram_frac, "kernel": "emission_kernel",
-                                           "note": (f"{N_ANGLES + 2} MUFU ops per (proposal, layer, wavenumber): "
-                                                    f"{N_ANGLES} ex2 of the angles, ex2 and reciprocal of the Planck "
-                                                    f"function; peak = {n_sm} SMs x {MUFU_PER_CLK} MUFU results per "
-                                                    f"clock x {max_mhz:.0f} MHz.  The proposals of a wavenumber tile "
-                                                    "share the grid rows through L2, so DRAM moves about the grid "
-                                                    "once per generation: dram_frac = DRAM bytes per generation "
-                                                    "(ncu) / time / measured HBM copy bandwidth")}},
+            "forward_model": fw,
+            "parity": parity,
             "opacity_build_ms": op_avg,
             "opacity_build_ms_per_step": [round(v, 2) for v in op_ms],
-            "cpu_baseline": cpu,
+            "cpu_baseline": cb,
             "e2e": {"value": N * evals / (e2e_ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
@@ -448,6 +676,157 @@ def run_native(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def emission_roofline(ms, n_sm, max_mhz, peaks, L, NU):
+    """MUFU roofline of the fused generation: NA ex2 of the angles plus the
+    Planck function's ex2 and reciprocal per (proposal, layer, wavenumber),
+    against 16 MUFU results per clock per SM; DRAM fraction from the
+    committed ncu capture of the same kernel source."""
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    units = N_PROPOSALS * L * NU
+    mufu = units * (N_ANGLES + 2) / (ms / 1e3) / 1e12
+    mufu_peak = n_sm * MUFU_PER_CLK * max_mhz * 1e6 / 1e12
+    dram = committed_traffic(FORWARD_SOURCES, "emission_fused_kernel")
+    return {"bound": "mufu", "achieved": mufu, "peak": mufu_peak, "unit": "Tops/s", "frac": mufu / mufu_peak,
+            "traffic": dram, "dram_frac": dram / (ms / 1e3) / (hbm * 1e9) if dram else None,
+            "kernel": "emission_fused_kernel",
+            "note": (f"{N_ANGLES + 2} MUFU ops per (proposal, layer, wavenumber): {N_ANGLES} ex2 of the angles, "
+                     f"ex2 and reciprocal of the Planck function; peak = {n_sm} SMs x {MUFU_PER_CLK} MUFU results "
+                     f"per clock x {max_mhz:.0f} MHz.  The proposals of a wavenumber tile share the grid rows "
+                     "through L2, so DRAM moves about the grid once per generation: dram_frac = DRAM bytes per "
+                     "generation (ncu) / time / measured HBM copy bandwidth")}
+
+
+def forward_model_leg(ctx, bart, torch, stream, grid, ax, nu, cfg, theta, filt, bands, generation, fw_ms, N, S):
+    """The 2,048-proposal generation: the graph-replayed fused launch (timed
+    in the step), the same launch eager, the three-launch split path, and the
+    3-species grid with the fourth scaling unused."""
+    res = {"spectra_per_s": N * N_PROPOSALS / (fw_ms / 1e3), "ms_per_generation": fw_ms,
+           "launch": "one persistent fused kernel per generation, replayed from a CUDA graph",
+           "proposals": N_PROPOSALS, "angles": N_ANGLES, "bands": N_BANDS, "species": S}
+    res["eager_ms"] = _event_ms(torch, stream, generation, reps=3)
+    ctx.set_emission_launch(bart.BART_LAUNCH_SPLIT)
+    generation()
+    res["split_three_launches_ms"] = _event_ms(torch, stream, generation, reps=3)
+    ctx.set_emission_launch(bart.BART_LAUNCH_FUSED)
+    g3, th3 = grid[:3], theta[:, :8].contiguous()
+    cfg3 = dict(cfg, x0=cfg["x0"][:3])
+    run3 = lambda: ctx.forward_spectra_batch(g3, ax.p_bar, ax.t_K, nu, cfg3, theta=th3, filters=filt, bands=bands)
+    run3()
+    ms3 = _event_ms(torch, stream, run3, reps=3)
+    res["species3"] = {"ms_per_generation": ms3, "spectra_per_s": N * N_PROPOSALS / (ms3 / 1e3)}
+    generation()               # leave the 4-species bands in place
+    ctx.sync()
+    return res
+
+
+def opacity_parity(grid, windows, ax):
+    """FP32-vs-FP64 error of the full-size grid on the oracle's baseline
+    windows: max relative error over points above 1e-6 of their window's
+    maximum, and the largest relative L2 error of a window."""
+    worst, worst_l2, npts = 0.0, 0.0, 0
+    for s, k, m, j0, vals in windows:
+        got = grid[s, k, m, j0:j0 + len(vals)].double().cpu().numpy()
+        ref = np.asarray(vals, np.float64)
+        big = ref > 1e-6 * ref.max()
+        worst = max(worst, float(np.max(np.abs(got[big] - ref[big]) / ref[big])))
+        worst_l2 = max(worst_l2, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        npts += len(vals)
+    return {"windows": len(windows), "points": npts, "max_rel": worst, "max_window_rel_l2": worst_l2,
+            "tolerance": {"max_rel": 1e-4, "rel_l2": 1e-5}}
+
+
+def emission_sample_parity(ctx, torch, grid, ax, nu, cfg, theta, sample):
+    """FP32-vs-FP64 error of sampled outputs of the full-size generation:
+    the 2,048-proposal fused launch (as timed) with its spectra kept, against
+    the oracle's whole chain (line lists -> opacity at the cells these
+    proposals read -> T interpolation -> emission) at 8 wavenumbers of 3
+    proposals."""
+    from oracle import forward as Fw
+    js, union, cells, vals, theta_np = sample
+    S, L, M = int(grid.shape[0]), len(ax.p_bar), len(ax.t_K)
+    spec = torch.empty((N_PROPOSALS, ax.n_nu), dtype=torch.float32, device=grid.device)
+    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, cfg, theta=theta, spectra=spec)
+    ctx.sync()
+    g_o = np.zeros((S, L, M, len(union)))
+    for (s, k, m), v in zip(cells, vals):
+        g_o[s, k, m] = v
+    nu_u = W.nu_axis(ax.nu_start, ax.dnu, ax.n_nu)[union]
+    worst, n = 0.0, 0
+    for p, jp in js.items():
+        F = Fw.emission_spectrum(g_o, ax.p_bar, ax.t_K, nu_u, theta_np[p], cfg)
+        idx = np.searchsorted(union, jp)
+        got = spec[p, torch.tensor(jp, device=grid.device)].double().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - F[idx]) / F[idx])))
+        n += len(jp)
+    del spec
+    return {"points": n, "proposals": len(js), "max_rel": worst, "tolerance": 1e-4,
+            "note": "oracle chain from the line lists at the sampled wavenumbers of the full-size grid"}
+
+
+def transmission_sample_parity(spec_t, inst_offsets, ax, S, sample):
+    """FP32-vs-FP64 error of sampled transit depths of the full-size batch
+    (the timed launch's output) against the oracle's whole chain at 8
+    wavenumbers of each of 2 instances."""
+    from oracle import forward as Fw
+    js, union, cells, vals, inst = sample
+    L, M = len(ax.p_bar), len(ax.t_K)
+    g_o = np.zeros((S, L, M, len(union)))
+    for (s, k, m), v in zip(cells, vals):
+        g_o[s, k, m] = v
+    cfg = tr_cfg(S)
+    worst, n = 0.0, 0
+    spec = spec_t.cpu().numpy()
+    for i, ji in js.items():
+        # the sampled columns act as the instance's span (no Rayleigh term, so
+        # the wavenumbers themselves do not enter)
+        one = W.Instances(inst.n_levels[i:i + 1], np.array([0], np.int64), np.array([len(union)], np.int64),
+                          inst.r_planet[i:i + 1], inst.r_star[i:i + 1], inst.theta[i:i + 1])
+        d = Fw.transmission_spectrum(g_o, ax.p_bar, ax.t_K, ax.nu_start, ax.dnu, one, 0, cfg)
+        idx = np.searchsorted(union, ji)
+        got = spec[inst_offsets[i] + (ji - int(inst.nu_lo[i]))].astype(np.float64)
+        worst = max(worst, float(np.max(np.abs(got - d[idx]) / d[idx])))
+        n += len(ji)
+    return {"points": n, "instances": len(js), "max_rel": worst, "tolerance": 1e-4,
+            "note": "oracle chain from the line lists at the sampled wavenumbers of the full-size grid"}
+
+
+def slice_parity(ctx, bart, torch, dev, cpu):
+    """FP32-vs-FP64 error of the generation and the transit batch on the
+    seeded opacity-field slice (100 layers x 20 T x 3,000 points, 4 species):
+    every spectrum point and band value of 16+ proposals and instances,
+    through the same fused launch path as the step."""
+    ax = W.grid_axes(n_nu=SLICE_N)
+    field = torch.tensor(W.opacity_field(4, ax.p_bar, ax.t_K, SLICE_N), device=dev)
+    nu = bart.NuGrid(ax.nu_start, ax.dnu, SLICE_N)
+    th, filt, F_o, B_o = cpu["em_slice"]
+    spec = torch.empty((len(th), SLICE_N), dtype=torch.float32, device=dev)
+    bands = torch.empty((len(th), N_BANDS), dtype=torch.float32, device=dev)
+    ctx.forward_spectra_batch(field, ax.p_bar, ax.t_K, nu, em_cfg(4), theta=torch.tensor(th, device=dev),
+                              spectra=spec, filters=torch.tensor(filt, device=dev), bands=bands)
+    ctx.sync()
+    rel = lambda g, o: float(np.max(np.abs(g.astype(np.float64) - o) / np.abs(o)))
+    out = {"emission": {"proposals": len(th), "spectra_max_rel": rel(spec.cpu().numpy(), F_o),
+                        "bands_max_rel": rel(bands.cpu().numpy(), B_o)}}
+    clipped, tfilt, d_o, tb_o = cpu["tr_slice"]
+    n = len(clipped)
+    cat = lambda f: np.concatenate([getattr(c, f) for c in clipped])
+    lo, hi = cat("nu_lo"), cat("nu_hi")
+    offs = np.concatenate([[0], np.cumsum(hi - lo)]).astype(np.int64)
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    tspec = torch.empty(int(offs[-1]), dtype=torch.float32, device=dev)
+    tb = torch.empty((n, 12), dtype=torch.float32, device=dev)
+    ctx.forward_spectra_batch(field, ax.p_bar, ax.t_K, nu, tr_cfg(4), theta=d(cat("theta")),
+                              n_levels=d(cat("n_levels")), nu_lo=d(lo), nu_hi=d(hi), spec_offsets=d(offs),
+                              r_planet=d(cat("r_planet")), r_star=d(cat("r_star")), spectra=tspec,
+                              filters=d(tfilt), bands=tb)
+    ctx.sync()
+    tspec, tb = tspec.cpu().numpy(), tb.cpu().numpy()
+    es = max(rel(tspec[offs[i]:offs[i + 1]], d_o[i]) for i in range(n))
+    eb = max(rel(tb[i][tb_o[i] > 0], tb_o[i][tb_o[i] > 0]) for i in range(n))
+    out["transmission"] = {"instances": n, "depths_max_rel": es, "bands_max_rel": eb}
+    return out
 
 
 def _event_ms(torch, stream, fn, reps=1):
@@ -529,15 +908,23 @@ def transmission_leg(ctx, torch, dev, stream, grid, ax, nu, cfg, S):
     return run_t, tcfg, targs, spec, ms, res
 
 
-def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_lines, theta):
+def run_aux(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, args, d_lines, theta, cpu, parity):
     """Measurements beside the timed step, on the grid the step built:
-    the paper's two approximations (line-strength bound, optical-depth limit),
-    transmission batch, surrogate training and accuracy, screened vs plain
-    retrieval.  Times are CUDA events on the library's stream."""
+    the transit batch, FP32-vs-FP64 samples of the full-size results, the
+    paper's two approximations (line-strength bound, optical-depth limit),
+    cloud deck and Rayleigh scattering, grid spacing, contribution functions,
+    surrogate training and accuracy, screened vs plain retrieval.  Times are
+    CUDA events on the library's stream."""
     S = int(grid.shape[0])
     out = {}
     run_t, tcfg, targs, spec, ms, out["transmission"] = transmission_leg(ctx, torch, dev, stream, grid, ax, nu,
                                                                          cfg, S)
+    if cpu is not None and "em_sample" in cpu:
+        parity["emission"] = emission_sample_parity(ctx, torch, grid, ax, nu, cfg, theta, cpu["em_sample"])
+        parity["transmission"] = transmission_sample_parity(spec, W.instances(TRANS_INSTANCES, ax.n_nu).offsets, ax,
+                                                            S, cpu["tr_sample"])
+        parity["field_slice"] = slice_parity(ctx, bart, torch, dev, cpu)
+        parity["oracle_seconds"] = cpu["sample_oracle_s"]
     out["cloud_rayleigh"] = cloud_rayleigh_leg(ctx, torch, stream, grid, ax, nu, cfg, theta, run_t, ms, tcfg, targs,
                                                spec)
     out["paper_approximations"] = paper_approximations(ctx, torch, stream, grid, ax, nu, cfg, d_lines, theta)
@@ -806,6 +1193,7 @@ def run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net
     xb_, Lb_ = torch.empty_like(x0), torch.empty_like(L0)
     burn.get_state(xb_, Lb_)
     res["burn_in"] = {"generations": n_burn, "ms": burn_ms}
+    kept = {}
     for mode in ("plain", "screened", "demczs"):
         # DEMCzs (Sec. 4): 4 chains from the burnt-in state, its 16 states as the
         # initial archive, every chain moving at each of a generation's two steps
@@ -830,19 +1218,44 @@ def run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net
         st["proposals_per_s"] = st["proposals"] / (ms / 1e3)
         st["generations"] = generations
         st["chains"] = Cm
-        _, gr, ess = ctx.chain_stats(chain)
+        sp, gr, ess = ctx.chain_stats(chain)
         st["ess"] = ess
         st["ess_per_s"] = ess / (ms / 1e3)
         st["gelman_rubin_max"] = float(gr.max())
+        st["ess_per_exact_eval"] = ess / max(st["exact_evals"], 1)
+        if mode != "demczs":
+            kept[mode] = (chain.reshape(-1, 5 + S).double().cpu().numpy(),
+                          (generations * Cm / sp.mean(0)).cpu().numpy())
         if mode == "screened":
             st["screen"] = {"beta": beta, "margin": margin}
         st["ms"] = ms
         if st["accepted"]:
             st["surrogate_err_mean"] = st["surrogate_err_sum"] / st["accepted"]
         res[mode] = st
+    res["posterior_agreement"] = posterior_agreement(*kept["plain"], *kept["screened"])
     res["false_rejection"] = screen_false_rejections(ctx, bart, torch, dev, grid, ax, nu, filt, cfg, S, net, lo, hi,
                                                      xb_, Lb_, data, sigma, beta, margin)
     return res
+
+
+def posterior_agreement(xp, essp, xs, esss):
+    """Plain vs screened posteriors within App. C standard errors: per
+    parameter the difference of the means over s = sqrt(s_p^2 + s_s^2) with
+    s = sigma / sqrt(ESS), and the content of the plain run's central 68%
+    interval in the screened samples against 0.68 with
+    s_C = sqrt(C (1 - C) (1/ESS_p + 1/ESS_s))."""
+    z_mean, z_c, content = [], [], []
+    for j in range(xp.shape[1]):
+        sp_ = xp[:, j].std() / np.sqrt(essp[j])
+        ss_ = xs[:, j].std() / np.sqrt(esss[j])
+        z_mean.append(abs(xp[:, j].mean() - xs[:, j].mean()) / max(np.hypot(sp_, ss_), 1e-300))
+        q16, q84 = np.percentile(xp[:, j], [16, 84])
+        c = float(np.mean((xs[:, j] >= q16) & (xs[:, j] <= q84)))
+        content.append(c)
+        z_c.append(abs(c - 0.68) / np.sqrt(0.68 * 0.32 * (1.0 / essp[j] + 1.0 / esss[j])))
+    return {"mean_z_max": float(max(z_mean)), "c68_z_max": float(max(z_c)),
+            "c68_content_screened": [round(c, 4) for c in content],
+            "agree_within_3_sigma": bool(max(z_mean) < 3.0 and max(z_c) < 3.0)}
 
 
 def screen_false_rejections(ctx, bart, torch, dev, grid, ax, nu, filt, cfg, S, net, lo, hi, x, L, data, sigma,
@@ -882,22 +1295,19 @@ def screen_false_rejections(ctx, bart, torch, dev, grid, ax, nu, filt, cfg, S, n
 
 def run_transmission_case(args):
     """The bench's 1,024-instance transmission batch alone, on the full-size
-    grid: one JSON line (for ncu captures of its launch)."""
+    4-species grid: one JSON line (for ncu captures of its launch)."""
     import torch
     from paper_2104_12522_gb300 import build
     build.build()
     import paper_2104_12522_gb300 as bart
     ax = W.grid_axes()
-    species = W.opacity_grid_species(3)
+    species = W.opacity_grid_species(4)
     ctx = bart.Context(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     nu = bart.NuGrid(ax.nu_start, ax.dnu, ax.n_nu)
     grid = ctx.build_opacity_grid([bart.device_lines(s) for s in species], ax.p_bar, ax.t_K, nu, ax.cutoff)
-    cfg = dict(geometry=0, n_angles=N_ANGLES, g=W.HD189_GRAV_CGS, mu=W.MEAN_MOLECULAR_MASS_AMU,
-               x0=[W.BASE_VMR] * 3, t_int=W.T_INT_K, t_star=W.HD189_TSTAR_K, r_star_tp=W.HD189_RSTAR_CM,
-               a_orbit=W.HD189_A_CM, t_min=float(ax.t_K[0]), t_max=float(ax.t_K[-1]))
-    *_, res = transmission_leg(ctx, torch, dev, stream, grid, ax, nu, cfg, 3)
+    *_, res = transmission_leg(ctx, torch, dev, stream, grid, ax, nu, em_cfg(4), 4)
     print(json.dumps({"transmission": res}), flush=True)
     return 0
 
@@ -905,44 +1315,74 @@ def run_transmission_case(args):
 def run_profile_case(args):
     """Small launches of the hot kernels for ncu captures: one opacity launch
     (species 0, 5e6-line list, 3 layers x 20 temperatures on the full
-    100,000-point grid), one emission generation (2,048 proposals) and one
-    transmission batch (256 instances) on a 4,096-point slice of the grid."""
+    100,000-point grid), one fused emission generation (2,048 proposals, 4
+    species) and one transit batch (256 instances) on a 4,096-point slice of
+    the grid."""
     import torch
     from paper_2104_12522_gb300 import build
     build.build()
     import paper_2104_12522_gb300 as bart
     ax = W.grid_axes()
-    species = W.opacity_grid_species(3)
+    species = W.opacity_grid_species(4)
     dl = [bart.device_lines(s) for s in species]
     ctx = bart.Context(0)
-    ctx.set_autotune(False)          # one emission launch, at the default tile width
+    ctx.set_autotune(False)
+    ctx.set_emission_tile(args.tile)
     nu = bart.NuGrid(ax.nu_start, ax.dnu, ax.n_nu)
     k3 = ax.p_bar[[0, 50, 99]]
     out = ctx.build_opacity_grid(dl[:1], k3, ax.t_K, nu, ax.cutoff)
     nsub = 4096
     nu_s = bart.NuGrid(ax.nu_start, ax.dnu, nsub)
     grid = ctx.build_opacity_grid(dl, ax.p_bar, ax.t_K, nu_s, ax.cutoff)
-    theta = torch.tensor(W.proposals(N_PROPOSALS, generation=0, n_species=3), device="cuda")
+    theta = torch.tensor(W.proposals(N_PROPOSALS, generation=0, n_species=4), device="cuda")
     filt = torch.tensor(W.gaussian_filters(W.nu_axis(ax.nu_start, ax.dnu, nsub), N_BANDS, 1005.0, 1075.0,
                                            2.0, 20.0), device="cuda")
     bands = torch.empty((N_PROPOSALS, N_BANDS), dtype=torch.float32, device="cuda")
-    cfg = dict(geometry=0, n_angles=N_ANGLES, g=W.HD189_GRAV_CGS, mu=W.MEAN_MOLECULAR_MASS_AMU,
-               x0=[W.BASE_VMR] * 3, t_int=W.T_INT_K, t_star=W.HD189_TSTAR_K, r_star_tp=W.HD189_RSTAR_CM,
-               a_orbit=W.HD189_A_CM, t_min=float(ax.t_K[0]), t_max=float(ax.t_K[-1]))
-    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu_s, cfg, theta=theta, filters=filt, bands=bands)
+    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu_s, em_cfg(4), theta=theta, filters=filt, bands=bands)
     # one transmission batch: 256 uneven instances (40..150 levels, 1,000..4,096 points) on the slice
     inst = W.instances(256, nsub, span_lo=1000, span_hi=nsub)
     d = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
     tspec = torch.empty(int(inst.offsets[-1]), dtype=torch.float32, device="cuda")
     tb = torch.empty((256, N_BANDS), dtype=torch.float32, device="cuda")
-    tcfg = dict(cfg, geometry=1, p_ref=W.HD189_PREF_BAR, p_top=1e-8, p_bot=100.0)
-    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu_s, tcfg, theta=d(inst.theta[:, :8]),
+    ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu_s, tr_cfg(4), theta=d(inst.theta),
                               n_levels=d(inst.n_levels), nu_lo=d(inst.nu_lo), nu_hi=d(inst.nu_hi),
                               spec_offsets=d(inst.offsets), r_planet=d(inst.r_planet), r_star=d(inst.r_star),
                               spectra=tspec, filters=filt, bands=tb)
     ctx.sync()
     assert torch.isfinite(out).all() and torch.isfinite(bands).all() and torch.isfinite(tspec).all()
     print("profile case done")
+    return 0
+
+
+def run_generation_case(args):
+    """The 2,048-proposal, 4-species fused generation alone on the full-size
+    grid (the grid filled from the seeded opacity field pattern, tiled over
+    wavenumber, so no line-by-line build is needed): reps graph replays, for
+    DRAM-traffic captures of the fused kernel (one launch)."""
+    import torch
+    from paper_2104_12522_gb300 import build
+    build.build()
+    import paper_2104_12522_gb300 as bart
+    ax = W.grid_axes()
+    dev = torch.device("cuda", 0)
+    ctx = bart.Context(0)
+    if args.tile:
+        ctx.set_emission_tile(args.tile)
+    nu = bart.NuGrid(ax.nu_start, ax.dnu, ax.n_nu)
+    pat = torch.tensor(W.opacity_field(4, ax.p_bar, ax.t_K, 1000), device=dev)
+    grid = pat.repeat(1, 1, 1, ax.n_nu // 1000).contiguous()
+    theta = torch.tensor(W.proposals(N_PROPOSALS, generation=0, n_species=4), device=dev)
+    filt = torch.tensor(W.gaussian_filters(W.nu_axis(ax.nu_start, ax.dnu, ax.n_nu), N_BANDS, 1100.0, 2900.0,
+                                           20.0, 200.0), device=dev)
+    bands = torch.empty((N_PROPOSALS, N_BANDS), dtype=torch.float32, device=dev)
+    gen = lambda: ctx.forward_spectra_batch(grid, ax.p_bar, ax.t_K, nu, em_cfg(4), theta=theta, filters=filt,
+                                            bands=bands)
+    gen()
+    stream = torch.cuda.current_stream(dev)
+    ms = _event_ms(torch, stream, gen, reps=max(1, args.steps))
+    ctx.sync()
+    print(json.dumps({"generation_ms": ms, "spectra_per_s": N_PROPOSALS / (ms / 1e3),
+                      "autotune": ctx.autotune_report()}), flush=True)
     return 0
 
 
@@ -957,16 +1397,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip the transmission/surrogate/retrieval legs")
     ap.add_argument("--train-steps", type=int, default=12000)
-    ap.add_argument("--generations", type=int, default=1000)
+    ap.add_argument("--generations", type=int, default=20000)
     ap.add_argument("--burn", type=int, default=3000, help="exact-model burn-in generations before the retrieval legs")
     ap.add_argument("--screen-beta", type=float, default=1.0)
     ap.add_argument("--screen-margin", type=float, default=1.0)
-    ap.add_argument("--case", choices=["bench", "profile", "transmission"], default="bench",
+    ap.add_argument("--case", choices=["bench", "profile", "transmission", "generation"], default="bench",
                     help="profile: small launches of the hot kernels for ncu; transmission: the "
-                         "1,024-instance transmission batch alone")
+                         "1,024-instance transmission batch alone; generation: the fused 2,048-proposal "
+                         "generation alone on a full-size grid of seeded values")
+    ap.add_argument("--tile", type=int, default=0, help="emission tile width for --case profile/generation "
+                                                          "(0: default / autotuner)")
     args = ap.parse_args()
     if args.case == "profile":
         return run_profile_case(args)
+    if args.case == "generation":
+        return run_generation_case(args)
     if args.case == "transmission":
         return run_transmission_case(args)
     if args.warmup < 3:

@@ -25,6 +25,7 @@ struct LayerTW {
   float w;      // weight of the upper bracket
   float c2_t;   // c2 / T
 };
+static_assert(sizeof(LayerTW) == 16 && alignof(LayerTW) == 8, "LayerTW is loaded as one 16-byte word");
 
 // Per-call options of the emission kernels (Sec. 3 cloud deck and Rayleigh
 // scattering, Sec. 4 item 7 optical-depth limit).

@@ -15,15 +15,20 @@
 //   2. runs one thread per wavenumber down the column: opacity interpolated
 //      in T and summed over species (coalesced grid-row reads, the next
 //      layer's rows requested before the current layer is computed), the
-//      trapezoid optical depth, the Planck source and per Gauss-Legendre angle
-//      the log2 transmittance and the intensity sum (the arithmetic of the
-//      three-launch path in forward.cu);
+//      trapezoid optical depth, the Planck source, per Gauss-Legendre angle
+//      the log2 transmittance, and the flux as a sum over layers of the
+//      layer-mean source times the drop of the quadrature-weighted
+//      transmittance (the angle sum taken inside the layer sum, which keeps
+//      one running value per angle instead of three);
 //   3. writes the spectrum and the tile's band partial sums; the CTA that
 //      finishes a proposal's last tile sums its partials in a fixed order
 //      (FP64) into the band values.
-// Nothing waits on another CTA: the last-tile test is an atomic count, and
-// the last CTA to leave resets the counters, so the launch can be replayed
-// from a CUDA graph unchanged.
+// Nothing waits on another CTA: the last-tile test is an atomic count, a
+// proposal's layer states are published by its first unit with an epoch mark
+// (a unit that does not see the mark computes them itself), and the last CTA
+// to leave resets the counters and advances the epoch, so the launch can be
+// replayed from a CUDA graph unchanged.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -37,6 +42,25 @@ using namespace bartem;
 namespace {
 
 constexpr int FUSED_MAX_SPECIES = 4;
+constexpr int MAX_TILES_PER_UNIT = 8;
+
+// GPU-scope acquire load and release store of a 32-bit flag, and an
+// acquire-release add (PTX memory model): the release makes the writes that
+// the CTA ordered before it by a barrier visible to a thread that acquires
+// the flag, without a full fence in every writing thread.
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
 
 struct FusedArgs {
   const float* grid;                 // [S][L][M][N]
@@ -55,43 +79,61 @@ struct FusedArgs {
   const float* dpg;                  // [L-1] (P_{k+1} - P_k) / (2 g)
   float x0mu[FUSED_MAX_SPECIES];     // X0_s / (mu m_u)
   float ang[2 * MAX_ANGLES];         // -log2(e) / mu_i, then 2 pi w_i mu_i / 2
+  float tw_top;                      // sum_i 2 pi w_i mu_i / 2 (all transmittances 1)
   float inv_g, tint4, tirr0, t_min, t_max;
   double nu_start, dnu;
   float* spectra;
   const float* filt;
   int n_bands;
-  float2* partial;                   // [n][n_tiles][n_bands]
+  float2* partial;                   // [n][n_groups][n_bands]
   float* bands;
-  int n_tiles;                       // tiles per proposal over the whole grid
-  unsigned long long n_units;        // n_tiles x n
-  unsigned long long* work;          // [0] next unit, [1] CTAs finished
+  int tpu;                           // tiles per unit (consecutive tiles of one proposal)
+  int n_groups;                      // units per proposal over the whole grid: ceil(n_tiles / tpu)
+  unsigned long long n_units;        // n_groups x n
+  unsigned long long* work;          // [0] next unit, [1] CTAs finished, [2] launch epoch
   unsigned int* p_done;              // [n] tiles finished per proposal
+  LayerTW* tw_cache;                 // [n][L] layer states published by the first unit of a proposal
+  unsigned int* tw_flag;             // [n] epoch + 1 once tw_cache[p] holds this launch's states
   int* status;
   EmExtra ex;
 };
 
+// Resident threads per SM the register allocation is sized for (1024: four
+// CTAs of 256 threads, at most 64 registers a thread, no spills).
+#ifndef FUSED_OCC_THREADS
+#define FUSED_OCC_THREADS 1024
+#endif
+
 template <int S, int NA, int TW, int MODE>
-__global__ void __launch_bounds__(TW) emission_fused_kernel(const __grid_constant__ FusedArgs a) {
+__global__ void __launch_bounds__(TW, FUSED_OCC_THREADS / TW) emission_fused_kernel(const __grid_constant__ FusedArgs a) {
   __shared__ LayerTW s_tw[MAX_LAYERS];
   __shared__ float s_dpg[MAX_LAYERS];
   __shared__ float s_xs[S];
   __shared__ float2 s_red[TW / 32][MAX_BANDS];
   __shared__ unsigned long long s_unit;
-  __shared__ int s_last;
+  __shared__ int s_last, s_ready;
   constexpr bool WIDE_X = (MODE & 1) != 0, TAU_LIM = (MODE & 2) != 0;
   const int tid = threadIdx.x;
   const int L = a.L, nb = a.n_bands;
   for (int k = tid; k + 1 < L; k += TW) s_dpg[k] = a.dpg[k];
   const int64_t sstride = (int64_t)L * a.M * a.N;
   const int64_t dm = (a.M > 1) ? a.N : 0;          // offset of the upper temperature bracket
+  // the epoch only changes when the last CTA of a launch leaves, so every CTA
+  // of this launch reads the same value
+  const unsigned int ready_mark = (unsigned int)*(volatile unsigned long long*)(a.work + 2) + 1u;
+  unsigned long long next_unit = 0;
+  if (tid == 0) next_unit = atomicAdd(a.work, 1ULL);
 
   for (;;) {
-    if (tid == 0) s_unit = atomicAdd(a.work, 1ULL);
+    if (tid == 0) {
+      s_unit = next_unit;
+      next_unit = atomicAdd(a.work, 1ULL);       // the following unit, fetched while this one runs
+    }
     __syncthreads();
     const unsigned long long u = s_unit;
     if (u >= a.n_units) break;
     const int p = (int)(u % (unsigned long long)a.n);
-    const int tile = (int)(u / (unsigned long long)a.n);
+    const int grp = (int)(u / (unsigned long long)a.n);
     // every value below is uniform over the CTA
     bool skip = a.active && !a.active[p];
     int64_t lo = 0, hi = a.N;
@@ -100,7 +142,7 @@ __global__ void __launch_bounds__(TW) emission_fused_kernel(const __grid_constan
       hi = a.nu_hi ? a.nu_hi[p] : a.N;
       if (lo < 0 || hi > a.N || lo >= hi) {
         // invalid span: report it once, band values 0, spectrum untouched
-        if (tile == 0) {
+        if (grp == 0) {
           if (tid == 0) atomicOr(a.status, BART_DEV_RANGE);
           if (a.bands && tid < nb) a.bands[(int64_t)p * nb + tid] = 0.0f;
         }
@@ -108,139 +150,169 @@ __global__ void __launch_bounds__(TW) emission_fused_kernel(const __grid_constan
       }
     }
     const int n_tiles_p = skip ? 0 : (int)((hi - lo + TW - 1) / TW);
-    if (!skip && tile < n_tiles_p) {
-      // 1. the proposal's layers: T(P) (or the given profile), bracket, c2/T
-      for (int k = tid; k < L; k += TW) {
-        float T;
-        if (a.t_profile) {
-          T = a.t_profile[(int64_t)p * L + k];
-        } else {
-          float th[5];
-#pragma unroll
-          for (int i = 0; i < 5; ++i) th[i] = a.theta[(int64_t)p * a.n_theta + i];
-          T = bartf::tp_temperature(th, a.p_cgs[k], a.inv_g, a.tint4, a.tirr0);
+    const int n_groups_p = (n_tiles_p + a.tpu - 1) / a.tpu;
+    if (!skip && grp < n_groups_p) {
+      // 1. the proposal's layers: T(P) (or the given profile), bracket, c2/T,
+      // computed by the first unit of the proposal and published for the
+      // others (a unit that finds them unpublished computes them itself)
+      if (tid == 0) s_ready = (ld_acquire(a.tw_flag + p) == ready_mark);
+      __syncthreads();
+      if (s_ready) {
+        for (int k = tid; k < L; k += TW) {
+          // one 16-byte L2 load per layer state: row (two words), w, c2/T
+          const int4 v = __ldcg(reinterpret_cast<const int4*>(a.tw_cache + (int64_t)p * L + k));
+          LayerTW r;
+          r.row = (int64_t)(((unsigned long long)(unsigned int)v.y << 32) | (unsigned int)v.x);
+          r.w = __int_as_float(v.z);
+          r.c2_t = __int_as_float(v.w);
+          s_tw[k] = r;
         }
-        s_tw[k] = layer_state(T, k, a.t_axis, a.M, a.N, a.t_min, a.t_max, a.status);
+      } else {
+        for (int k = tid; k < L; k += TW) {
+          float T;
+          if (a.t_profile) {
+            T = a.t_profile[(int64_t)p * L + k];
+          } else {
+            float th[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) th[i] = a.theta[(int64_t)p * a.n_theta + i];
+            T = bartf::tp_temperature(th, a.p_cgs[k], a.inv_g, a.tint4, a.tirr0);
+          }
+          const LayerTW r = layer_state(T, k, a.t_axis, a.M, a.N, a.t_min, a.t_max, a.status);
+          s_tw[k] = r;
+          a.tw_cache[(int64_t)p * L + k] = r;
+        }
+        __syncthreads();
+        if (tid == 0) st_release(a.tw_flag + p, ready_mark);   // publishes the CTA's stores above
       }
       if (tid < S) {
         const float ab = a.theta ? a.theta[(int64_t)p * a.n_theta + 5 + tid] : 0.0f;
         s_xs[tid] = a.x0mu[tid] * exp10f(ab);
       }
       __syncthreads();
-
-      // 2. the column of wavenumber j
-      const int64_t j = lo + (int64_t)tile * TW + tid;
-      const bool act = j < hi;
-      const int64_t jj = act ? j : lo;             // idle lanes compute on a valid index
       float xs[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) xs[s] = s_xs[s];
-      const double nu = a.nu_start + (double)jj * a.dnu;
-      const float nuf = (float)nu;
-      const float c1nu3 = (float)(2.0 * bartc::H * bartc::C * bartc::C * nu * nu * nu);
-      const float chi_r = (float)(a.ex.ray * (nu * nu) * (nu * nu));   // Rayleigh a nu^4 / (mu m_u)
-      float lt[NA], t[NA], I[NA];
+      float2 band_acc = make_float2(0.f, 0.f);      // thread b < nb: band b over the unit's tiles
+      const int t_end = min((grp + 1) * a.tpu, n_tiles_p);
+
+      for (int tile = grp * a.tpu; tile < t_end; ++tile) {
+        // 2. the column of wavenumber j
+        const int64_t j = lo + (int64_t)tile * TW + tid;
+        const bool act = j < hi;
+        const int64_t jj = act ? j : lo;           // idle lanes compute on a valid index
+        const double nu = a.nu_start + (double)jj * a.dnu;
+        const float nuf = (float)nu;
+        const float c1nu3 = (float)(2.0 * bartc::H * bartc::C * bartc::C * nu * nu * nu);
+        const float chi_r = (float)(a.ex.ray * (nu * nu) * (nu * nu));   // Rayleigh a nu^4 / (mu m_u)
+        // per angle the log2 transmittance to the current level (a sum of
+        // positive optical-depth terms times -log2(e)/mu); the flux needs the
+        // transmittances only through their quadrature sum
+        // Tw = sum_i 2 pi w_i mu_i / 2 t_i, so F = sum_k (B_{k-1} + B_k)
+        // (Tw_{k-1} - Tw_k) + 2 B_bottom Tw_bottom
+        float lt[NA];
 #pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        lt[i] = 0.0f;
-        t[i] = 1.0f;
-        I[i] = 0.0f;
-      }
-      const float* gj = a.grid + jj;
-      const int L_run = a.ex.L_run;
-      // grid values of a layer: lower (x) and upper (y) temperature bracket per species
-      auto fetch = [&](int k, float* x, float* y) {
-        const float* g0 = gj + s_tw[k].row;
+        for (int i = 0; i < NA; ++i) lt[i] = 0.0f;
+        float Tw_prev = a.tw_top, F = 0.0f;
+        const float* gj = a.grid + jj;
+        const int L_run = a.ex.L_run;
+        // grid values of a layer: lower (x) and upper (y) temperature bracket per species
+        auto fetch = [&](int k, float* x, float* y) {
+          const float* g0 = gj + s_tw[k].row;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          x[s] = __ldg(g0 + s * sstride);
-          y[s] = __ldg(g0 + s * sstride + dm);
-        }
-      };
-      auto chi_of = [&](int k, const float* x, const float* y) {
-        const float w = s_tw[k].w;
-        float chi = chi_r;
+          for (int s = 0; s < S; ++s) {
+            x[s] = __ldg(g0 + s * sstride);
+            y[s] = __ldg(g0 + s * sstride + dm);
+          }
+        };
+        auto chi_of = [&](int k, const float* x, const float* y) {
+          const float w = s_tw[k].w;
+          float chi = chi_r;
 #pragma unroll
-        for (int s = 0; s < S; ++s) chi = fmaf(xs[s], fmaf(w, y[s] - x[s], x[s]), chi);
-        return chi;
-      };
-      float cx[S], cy[S], nx[S], ny[S];
-      fetch(0, cx, cy);
-      fetch(min(1, L_run - 1), nx, ny);
-      float chi_prev = chi_of(0, cx, cy);
-      float B_prev = planck<WIDE_X>(c1nu3, nuf * s_tw[0].c2_t);
-      float tau_v = 0.0f;                          // vertical optical depth from the top
+          for (int s = 0; s < S; ++s) chi = fmaf(xs[s], fmaf(w, y[s] - x[s], x[s]), chi);
+          return chi;
+        };
+        float cx[S], cy[S], nx[S], ny[S];
+        fetch(0, cx, cy);
+        fetch(min(1, L_run - 1), nx, ny);
+        float chi_prev = chi_of(0, cx, cy);
+        float B_prev = planck<WIDE_X>(c1nu3, nuf * s_tw[0].c2_t);
+        float tau_v = 0.0f;                        // vertical optical depth from the top
 #pragma unroll 2
-      for (int k = 1; k < L_run; ++k) {
+        for (int k = 1; k < L_run; ++k) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          cx[s] = nx[s];
-          cy[s] = ny[s];
-        }
-        fetch(min(k + 1, L_run - 1), nx, ny);      // the next layer's rows are in flight meanwhile
-        const float chi = chi_of(k, cx, cy);
-        const float B = planck<WIDE_X>(c1nu3, nuf * s_tw[k].c2_t);
-        const float dtau = (chi_prev + chi) * s_dpg[k - 1];
-        const float Bsum = B_prev + B;
+          for (int s = 0; s < S; ++s) {
+            cx[s] = nx[s];
+            cy[s] = ny[s];
+          }
+          fetch(min(k + 1, L_run - 1), nx, ny);    // the next layer's rows are in flight meanwhile
+          const float chi = chi_of(k, cx, cy);
+          const float B = planck<WIDE_X>(c1nu3, nuf * s_tw[k].c2_t);
+          const float dtau = (chi_prev + chi) * s_dpg[k - 1];
+          const float Bsum = B_prev + B;
+          float Tw0 = 0.0f, Tw1 = 0.0f;             // two partial sums: a shorter dependence chain
 #pragma unroll
-        for (int i = 0; i < NA; ++i) {
-          lt[i] = fmaf(dtau, a.ang[i], lt[i]);
-          const float te = bartf::ex2_approx(lt[i]);
-          I[i] = fmaf(Bsum, t[i] - te, I[i]);
-          t[i] = te;
+          for (int i = 0; i < NA; ++i) {
+            lt[i] = fmaf(dtau, a.ang[i], lt[i]);
+            if (i & 1) Tw1 = fmaf(a.ang[NA + i], bartf::ex2_approx(lt[i]), Tw1);
+            else Tw0 = fmaf(a.ang[NA + i], bartf::ex2_approx(lt[i]), Tw0);
+          }
+          const float Tw = Tw0 + Tw1;
+          F = fmaf(Bsum, Tw_prev - Tw, F);
+          Tw_prev = Tw;
+          chi_prev = chi;
+          B_prev = B;
+          if (TAU_LIM) {
+            // Sec. 4 item 7: stop at the caller's optical-depth limit; the level
+            // reached is the bottom boundary (its blackbody below)
+            tau_v += dtau;
+            if (tau_v > a.ex.tau_cut) break;
+          }
         }
-        chi_prev = chi;
-        B_prev = B;
-        if (TAU_LIM) {
-          // Sec. 4 item 7: stop at the caller's optical-depth limit; the level
-          // reached is the bottom boundary (its blackbody below)
-          tau_v += dtau;
-          if (tau_v > a.ex.tau_cut) break;
+        F = fmaf(2.0f * B_prev, Tw_prev, F);       // the bottom level's blackbody through the column
+        if (act && a.spectra) {
+          const int64_t base = a.offs ? a.offs[p] : (int64_t)p * a.N;
+          a.spectra[base + (j - lo)] = F;
         }
-      }
-      float F = 0.0f;
+
+        // 3. band sums of the tile, added to the unit's
+        if (nb > 0) {
+          float dw = 0.0f;
+          if (act) dw = (hi - lo == 1) ? 1.0f : ((j == lo || j == hi - 1) ? 0.5f : 1.0f);
+          const int warp = tid >> 5, lane = tid & 31;
+          for (int b = 0; b < nb; ++b) {
+            const float W = act ? __ldg(a.filt + (int64_t)b * a.N + j) * dw : 0.0f;
+            float num = W * F, den = W;
 #pragma unroll
-      for (int i = 0; i < NA; ++i) F = fmaf(a.ang[NA + i], fmaf(2.0f * B_prev, t[i], I[i]), F);
-      if (act && a.spectra) {
-        const int64_t base = a.offs ? a.offs[p] : (int64_t)p * a.N;
-        a.spectra[base + (j - lo)] = F;
+            for (int o = 16; o > 0; o >>= 1) {
+              num += __shfl_xor_sync(0xffffffffu, num, o);
+              den += __shfl_xor_sync(0xffffffffu, den, o);
+            }
+            if (lane == 0) s_red[warp][b] = make_float2(num, den);
+          }
+          __syncthreads();
+          if (tid < nb) {
+#pragma unroll
+            for (int w = 0; w < TW / 32; ++w) {
+              band_acc.x += s_red[w][tid].x;
+              band_acc.y += s_red[w][tid].y;
+            }
+          }
+          __syncthreads();                         // s_red is rewritten by the next tile
+        }
       }
 
-      // 3. band partial sums of the tile; the proposal's last tile reduces them
+      // the unit's band partials; the proposal's last unit reduces them
       if (nb > 0) {
-        float dw = 0.0f;
-        if (act) dw = (hi - lo == 1) ? 1.0f : ((j == lo || j == hi - 1) ? 0.5f : 1.0f);
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int b = 0; b < nb; ++b) {
-          const float W = act ? __ldg(a.filt + (int64_t)b * a.N + j) * dw : 0.0f;
-          float num = W * F, den = W;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            num += __shfl_xor_sync(0xffffffffu, num, o);
-            den += __shfl_xor_sync(0xffffffffu, den, o);
-          }
-          if (lane == 0) s_red[warp][b] = make_float2(num, den);
-        }
+        if (tid < nb) a.partial[((int64_t)p * a.n_groups + grp) * nb + tid] = band_acc;
         __syncthreads();
-        if (tid < nb) {
-          float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int w = 0; w < TW / 32; ++w) {
-            acc.x += s_red[w][tid].x;
-            acc.y += s_red[w][tid].y;
-          }
-          a.partial[((int64_t)p * a.n_tiles + tile) * nb + tid] = acc;
-          __threadfence();                         // partial visible before the count below
-        }
-        __syncthreads();
-        if (tid == 0) s_last = (atomicAdd(a.p_done + p, 1u) + 1u == (unsigned)n_tiles_p);
+        if (tid == 0) s_last = (add_acq_rel(a.p_done + p, 1u) + 1u == (unsigned)n_groups_p);
         __syncthreads();
         if (s_last) {
-          __threadfence();
           if (tid < nb) {
             double num = 0.0, den = 0.0;
-            for (int q = 0; q < n_tiles_p; ++q) {
-              const float2 v = __ldcg(a.partial + ((int64_t)p * a.n_tiles + q) * nb + tid);
+            for (int q = 0; q < n_groups_p; ++q) {
+              const float2 v = __ldcg(a.partial + ((int64_t)p * a.n_groups + q) * nb + tid);
               num += v.x;
               den += v.y;
             }
@@ -258,6 +330,7 @@ __global__ void __launch_bounds__(TW) emission_fused_kernel(const __grid_constan
     if (atomicAdd(a.work + 1, 1ULL) + 1ULL == (unsigned long long)gridDim.x) {
       a.work[0] = 0ULL;
       a.work[1] = 0ULL;
+      a.work[2] += 1ULL;                          // new epoch: published layer states expire
       __threadfence();
     }
   }
@@ -338,7 +411,10 @@ bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const
   void *p_const, *p_work, *p_done = nullptr, *p_part = nullptr;
   if ((st = bart_upload_const(ctx, "ff_const", hconst.data(), hconst.size() * sizeof(float), &p_const)) != BART_OK)
     return st;
-  if ((st = bart_scratch(ctx, "ff_work", 2 * sizeof(unsigned long long), &p_work)) != BART_OK) return st;
+  void *p_twc, *p_flag;
+  if ((st = bart_scratch(ctx, "ff_work", 3 * sizeof(unsigned long long), &p_work)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "ff_twc", (size_t)n * L * sizeof(LayerTW), &p_twc)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "ff_flag", (size_t)n * sizeof(unsigned int), &p_flag)) != BART_OK) return st;
   const int max_tiles = (int)((N + MIN_TILE - 1) / MIN_TILE);    // partials sized for the smallest tile
   if (nb > 0) {
     if ((st = bart_scratch(ctx, "ff_done", (size_t)n * sizeof(unsigned int), &p_done)) != BART_OK) return st;
@@ -365,10 +441,13 @@ bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const
   for (int s = 0; s < S; ++s) a.x0mu[s] = (float)(c->x0[s] / (c->mu_amu * bartc::AMU));
   std::vector<double> mu, w;
   gauss_legendre01(NA, mu, w);
+  float tw_top = 0.0f;
   for (int i = 0; i < NA; ++i) {
     a.ang[i] = (float)(-1.4426950408889634 / mu[i]);
     a.ang[NA + i] = (float)(2.0 * bartc::PI * w[i] * mu[i] * 0.5);   // the 1/2 of the layer-mean source
+    tw_top += a.ang[NA + i];
   }
+  a.tw_top = tw_top;
   a.inv_g = (float)(1.0 / c->g_cgs);
   a.tint4 = (float)std::pow(c->t_int_K, 4.0);
   const double rs = c->r_star_tp_cm, ao = c->a_orbit_cm;
@@ -384,12 +463,20 @@ bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const
   a.bands = bands;
   a.work = (unsigned long long*)p_work;
   a.p_done = (unsigned int*)p_done;
+  a.tw_cache = (LayerTW*)p_twc;
+  a.tw_flag = (unsigned int*)p_flag;
   a.status = ctx->d_status;
   a.ex = emission_extra(g, c);
 
   auto run = [&](int tw) -> bart_status {
-    a.n_tiles = (int)((N + tw - 1) / tw);
-    a.n_units = (unsigned long long)a.n_tiles * (unsigned long long)n;
+    // several consecutive tiles per unit amortise the unit's fixed work (layer
+    // states, band partials and counts), as long as there are enough units to
+    // balance the CTAs (about 8 per CTA of a full grid)
+    const int n_tiles = (int)((N + tw - 1) / tw);
+    const long long target = 8LL * ctx->sm_count * (2048 / tw);
+    a.tpu = (int)std::max(1LL, std::min<long long>(MAX_TILES_PER_UNIT, (long long)n * n_tiles / target));
+    a.n_groups = (n_tiles + a.tpu - 1) / a.tpu;
+    a.n_units = (unsigned long long)a.n_groups * (unsigned long long)n;
     cudaError_t e = pick_fused(S, NA, tw, mode)(a, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return bart_fail(ctx, BART_ECUDA, "launch of emission_fused_kernel failed: %s",
                                            cudaGetErrorString(e));

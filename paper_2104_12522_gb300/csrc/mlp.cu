@@ -6,14 +6,20 @@
 // Layout: flat FP32 master parameters, per layer W_l row-major [out][in] then
 // b_l [out].  The forward pass reads either BF16 copies of the weights (made
 // after every update, round to nearest even) or the FP32 master (test mode).
-// Every layer is one tiled SIMT GEMM with a fused epilogue (bias, GELU,
-// input/target scaling); FP32 accumulation throughout.  The layers are
-// 256 wide and the batches at most a few thousand rows, so one layer is
-// ~1e8 flops: far below what would pay for tensor-core tiles, the GEMMs run on
-// the FP32 pipe.
+//
+// With BF16 weights every GEMM of the forward and backward passes runs on the
+// tensor cores (warp-level mma.sync m16n8k16, BF16 operands, FP32
+// accumulators) with a fused epilogue (bias, GELU, GELU').  FP32 operands
+// (activations, output gradients) are carried as a pair of BF16 numbers,
+// x = hi + lo with hi = bf16(x) and lo = bf16(x - hi), and multiplied term by
+// term (hi*hi + lo*hi + hi*lo), which keeps about 16 bits of the FP32 operand:
+// the products are those of BF16 weights with FP32 activations to ~1e-5.  The
+// FP32-weight test mode keeps a SIMT FP32 GEMM (64 x 64 tiles, 4 x 4 outputs
+// per thread), the reference precision of the gradient tests.
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "bart_internal.cuh"
@@ -51,8 +57,6 @@ __device__ __forceinline__ float gelu_grad(float x) {
 
 template <typename T>
 __device__ __forceinline__ float ld(const T* p) { return (float)p[0]; }
-template <>
-__device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(p[0]); }
 
 // C[M][N] = sum_k A(m, k) B(k, n), with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn].
 // Epilogue modes:
@@ -119,6 +123,133 @@ gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t 
       }
     }
   }
+}
+
+// ---- tensor-core GEMM (BF16 mma.sync, FP32 accumulate)
+constexpr int TC_BM = 64, TC_BN = 64, TC_BK = 32;
+constexpr int TC_THREADS = 128;            // 4 warps, 2 x 2 warp tiles of 32 x 32
+constexpr int TC_LDS = TC_BK + 8;          // smem row stride (bf16): conflict-free fragment loads
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+__device__ __forceinline__ void split_bf16(__nv_bfloat16 v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = v;
+  lo = __float2bfloat16_rn(0.0f);
+}
+
+// D = A (16 x 16, row) * B (16 x 8, col) + D, BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[M][N] = sum_k A(m, k) B(k, n) with the layouts and epilogue modes of
+// gemm_kernel.  A tile is kept as [m][k] and B as [n][k] in shared memory,
+// hi and lo parts apart; an FP32 operand contributes its lo part (a BF16 one
+// has none), so the MMAs per k16 step are hi*hi, lo_A*hi_B and hi_A*lo_B.
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(TC_THREADS)
+tc_gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
+               int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc, int mode,
+               const float* __restrict__ bias, float* __restrict__ H, const float* __restrict__ Z) {
+  constexpr bool A_LO = !std::is_same<TA, __nv_bfloat16>::value;
+  constexpr bool B_LO = !std::is_same<TB, __nv_bfloat16>::value;
+  __shared__ __align__(16) __nv_bfloat16 sAh[TC_BM][TC_LDS], sAl[TC_BM][TC_LDS];
+  __shared__ __align__(16) __nv_bfloat16 sBh[TC_BN][TC_LDS], sBl[TC_BN][TC_LDS];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tig = lane & 3;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+  float acc[2][4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += TC_BK) {
+    // stage the tiles, the contiguous global index fastest
+    for (int e = tid; e < TC_BM * TC_BK; e += TC_THREADS) {
+      const int mm = (sak == 1) ? e / TC_BK : e % TC_BM;
+      const int kk = (sak == 1) ? e % TC_BK : e / TC_BM;
+      const int gm = m0 + mm, gk = k0 + kk;
+      __nv_bfloat16 hi, lo;
+      if (gm < M && gk < K) split_bf16(A[gm * sam + gk * sak], hi, lo);
+      else hi = lo = __float2bfloat16_rn(0.0f);
+      sAh[mm][kk] = hi;
+      sAl[mm][kk] = lo;
+    }
+    for (int e = tid; e < TC_BN * TC_BK; e += TC_THREADS) {
+      const int nn = (sbk == 1) ? e / TC_BK : e % TC_BN;
+      const int kk = (sbk == 1) ? e % TC_BK : e / TC_BN;
+      const int gn = n0 + nn, gk = k0 + kk;
+      __nv_bfloat16 hi, lo;
+      if (gn < N && gk < K) split_bf16(B[gk * sbk + gn * sbn], hi, lo);
+      else hi = lo = __float2bfloat16_rn(0.0f);
+      sBh[nn][kk] = hi;
+      sBl[nn][kk] = lo;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < TC_BK; ks += 16) {
+      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm * 32 + i * 16 + g, c = ks + tig * 2;
+        ah[i][0] = *reinterpret_cast<const uint32_t*>(&sAh[r][c]);
+        ah[i][1] = *reinterpret_cast<const uint32_t*>(&sAh[r + 8][c]);
+        ah[i][2] = *reinterpret_cast<const uint32_t*>(&sAh[r][c + 8]);
+        ah[i][3] = *reinterpret_cast<const uint32_t*>(&sAh[r + 8][c + 8]);
+        if (A_LO) {
+          al[i][0] = *reinterpret_cast<const uint32_t*>(&sAl[r][c]);
+          al[i][1] = *reinterpret_cast<const uint32_t*>(&sAl[r + 8][c]);
+          al[i][2] = *reinterpret_cast<const uint32_t*>(&sAl[r][c + 8]);
+          al[i][3] = *reinterpret_cast<const uint32_t*>(&sAl[r + 8][c + 8]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = wn * 32 + j * 8 + g, c = ks + tig * 2;
+        bh[j][0] = *reinterpret_cast<const uint32_t*>(&sBh[n][c]);
+        bh[j][1] = *reinterpret_cast<const uint32_t*>(&sBh[n][c + 8]);
+        if (B_LO) {
+          bl[j][0] = *reinterpret_cast<const uint32_t*>(&sBl[n][c]);
+          bl[j][1] = *reinterpret_cast<const uint32_t*>(&sBl[n][c + 8]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          mma_bf16(acc[i][j], ah[i], bh[j]);
+          if (A_LO) mma_bf16(acc[i][j], al[i], bh[j]);
+          if (B_LO) mma_bf16(acc[i][j], ah[i], bl[j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gm = m0 + wm * 32 + i * 16 + g + (q >> 1) * 8;
+        const int gn = n0 + wn * 32 + j * 8 + tig * 2 + (q & 1);
+        if (gm >= M || gn >= N) continue;
+        float v = acc[i][j][q];
+        const int64_t o = (int64_t)gm * ldc + gn;
+        if (mode == 1) {
+          v += bias[gn];
+          C[o] = v;
+          H[o] = gelu(v);
+        } else if (mode == 2) {
+          C[o] = v + bias[gn];
+        } else if (mode == 3) {
+          C[o] = v * gelu_grad(Z[o]);
+        } else {
+          C[o] = v;
+        }
+      }
 }
 
 // x_scaled[b][i] = (x[b][i] - shift[i]) * scale[i]
@@ -192,12 +323,22 @@ __global__ void to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// SIMT FP32 GEMM (the FP32-weight mode)
 template <typename TA, typename TB>
 void gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
           int64_t sbn, float* C, int64_t ldc, int mode, const float* bias = nullptr, float* H = nullptr,
           const float* Z = nullptr) {
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
   gemm_kernel<TA, TB><<<grid, MLP_THREADS, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, mode, bias, H, Z);
+}
+
+// tensor-core GEMM (the BF16-weight mode)
+template <typename TA, typename TB>
+void tc_gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
+             int64_t sbn, float* C, int64_t ldc, int mode, const float* bias = nullptr, float* H = nullptr,
+             const float* Z = nullptr) {
+  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
+  tc_gemm_kernel<TA, TB><<<grid, TC_THREADS, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, mode, bias, H, Z);
 }
 
 // Forward pass of B rows already scaled into act layer 0; fills z/h of every layer.
@@ -212,8 +353,8 @@ void run_forward(bart_mlp* net, int B) {
     const float* bias = net->p + net->b_off[l];
     // z[b][o] = sum_i h_prev[b][i] W[o][i]
     if (net->bf16)
-      gemm<float, __nv_bfloat16>(st, B, n_out, n_in, h_prev, n_in, 1, net->wb + net->w_off[l], 1, n_in, z, n_out,
-                                 mode, bias, h);
+      tc_gemm<float, __nv_bfloat16>(st, B, n_out, n_in, h_prev, n_in, 1, net->wb + net->w_off[l], 1, n_in, z,
+                                    n_out, mode, bias, h);
     else
       gemm<float, float>(st, B, n_out, n_in, h_prev, n_in, 1, net->p + net->w_off[l], 1, n_in, z, n_out, mode,
                          bias, h);
@@ -246,7 +387,10 @@ bart_status backward(bart_mlp* net, const float* x, const float* t, int B, float
     // hidden h of layer l is still intact: only slots above l were reused.
     const float* h_prev = net->act + net->h_off[l];
     // dW[o][i] = sum_b dz[b][o] h_prev[b][i]
-    gemm<float, float>(st, no, ni, B, dz, 1, no, h_prev, ni, 1, net->g + net->w_off[l], ni, 0);
+    if (net->bf16)
+      tc_gemm<float, float>(st, no, ni, B, dz, 1, no, h_prev, ni, 1, net->g + net->w_off[l], ni, 0);
+    else
+      gemm<float, float>(st, no, ni, B, dz, 1, no, h_prev, ni, 1, net->g + net->w_off[l], ni, 0);
     bias_grad<<<blocks_for(no, 128), 128, 0, st>>>(dz, B, no, net->g + net->b_off[l]);
     if (l > 0) {
       // dh_prev[b][i] = sum_o dz[b][o] W[o][i]; then dz_prev = dh_prev * GELU'(z_prev)
@@ -254,8 +398,8 @@ bart_status backward(bart_mlp* net, const float* x, const float* t, int B, float
       const float* z_prev = net->act + net->z_off[l];
       // h_prev (this slot) was consumed by the dW GEMM above, which runs first on the stream.
       if (net->bf16)
-        gemm<float, __nv_bfloat16>(st, B, ni, no, dz, no, 1, net->wb + net->w_off[l], ni, 1, dz_prev, ni, 3,
-                                   nullptr, nullptr, z_prev);
+        tc_gemm<float, __nv_bfloat16>(st, B, ni, no, dz, no, 1, net->wb + net->w_off[l], ni, 1, dz_prev, ni, 3,
+                                      nullptr, nullptr, z_prev);
       else
         gemm<float, float>(st, B, ni, no, dz, no, 1, net->p + net->w_off[l], ni, 1, dz_prev, ni, 3, nullptr,
                            nullptr, z_prev);
