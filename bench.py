@@ -54,7 +54,7 @@ OPACITY_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
                    for f in ("opacity.cu", "faddeeva.cuh", "bart_internal.cuh")]
 FORWARD_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
                    for f in ("forward_fused.cu", "emission.cuh", "forward.cuh", "bart_internal.cuh")]
-MUFU_PER_CLK = 16                 # MUFU (ex2, rcp) results per clock per SM
+MUFU_PER_CLK = 32                 # MUFU (ex2, rcp) results per clock per SM on GB300 (ncu: XU-pipe peak 1 warp-inst/clk/SM)
 
 
 def workload_desc():

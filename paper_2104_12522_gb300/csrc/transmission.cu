@@ -8,17 +8,21 @@
 //                   a node), number densities and the bilinear (log10 P, T)
 //                   brackets on the grid; a gray cloud deck cuts the
 //                   instance's level count at its level (opaque below).
+//                   The same CTA then writes every chord of the instance,
+//                   ds_ik = 2 (A - B) / (sqrt A + sqrt B) from altitude
+//                   differences (no cancellation), block by block of 8 rays.
 //   trans_kernel    persistent CTAs pulling (wavenumber tile, instance) units
 //                   from an atomic counter; tile-major order keeps the grid
 //                   slab of a tile in L2 while every instance covering it runs.
-//                   Per unit: shell extinction for 128 wavenumbers (lines
-//                   plus Rayleigh a nu^4 per molecule) into shared memory,
-//                   then the ray optical depths
+//                   Four threads per wavenumber of a 128-point tile: each
+//                   computes a quarter of the levels' extinction (lines plus
+//                   Rayleigh a nu^4 per molecule) into the shared shell means,
+//                   then a quarter of the ray blocks (balanced snake order) of
 //                   tau_i = sum_{k<i} ds_ik (alpha_k + alpha_{k+1}) / 2,
-//                   register-blocked over 8 rays per pass, chords recomputed
-//                   per pass as 2 (A - B) / (sqrt A + sqrt B) from altitude
-//                   differences (no cancellation), then the trapezoid in
-//                   impact parameter and the fused band partial sums.
+//                   8 rays per register block with the chords read as
+//                   broadcast loads, and its share of the trapezoid in impact
+//                   parameter (each ray's weight (z_{i-1} - z_{i+1}) / 2); the
+//                   shares are added and the band partials fused.
 //   trans_band_reduce  per (instance, band): fixed-order FP64 sum of partials.
 #include <cmath>
 #include <vector>
@@ -28,9 +32,15 @@
 
 namespace {
 
-constexpr int TR_THREADS = 128;          // wavenumbers per unit
+constexpr int TR_COLS = 128;             // wavenumbers per unit
+constexpr int TR_SPLIT = 4;              // threads per wavenumber column
+constexpr int TR_THREADS = TR_COLS * TR_SPLIT;
 constexpr int TR_LMAX = 192;             // maximum levels per instance
 constexpr int TR_RB = 8;                 // rays per register block
+constexpr int TR_NBLK = (TR_LMAX - 1 + TR_RB - 1) / TR_RB;   // ray blocks of the deepest column
+// chords of an instance, block by block: block b (rays 1 + 8b ..) needs
+// shells k < kmax_b <= 8 (b + 1), stored [k][8 rays] from 32 b (b + 1)
+constexpr int TR_DS_STRIDE = 32 * TR_NBLK * (TR_NBLK + 1);
 constexpr int TR_MAX_BANDS = 64;
 constexpr int TR_MAX_SPECIES = 8;
 
@@ -57,12 +67,13 @@ __global__ void trans_prologue(const float* __restrict__ theta, int n_theta, int
                                double p_ref, double g, double mu_amu, float inv_g_f, float tint4, float tirr0,
                                float t_min, float t_max, const float* __restrict__ x0, TrLevel* __restrict__ lev,
                                TrInst* __restrict__ inst, const int32_t* __restrict__ act_mask,
-                               int* __restrict__ status, double p_cloud) {
+                               int* __restrict__ status, double p_cloud, float* __restrict__ ds) {
   const int i = blockIdx.x;
   if (i >= n) return;
   if (act_mask && !act_mask[i]) return;      // skipped entry
   __shared__ double s_lnp[TR_LMAX], s_T[TR_LMAX], s_phi[TR_LMAX];
-  __shared__ int s_bad;
+  __shared__ float s_z[TR_LMAX];
+  __shared__ int s_bad, s_leff;
   const int L = n_levels[i];
   const float* th = theta + (int64_t)i * n_theta;
   if (threadIdx.x == 0) s_bad = (L < 2 || L > TR_LMAX || !(r_planet[i] > 0.f) || !(r_star[i] > 0.f));
@@ -154,7 +165,8 @@ __global__ void trans_prologue(const float* __restrict__ theta, int n_theta, int
     for (int k = 0; k < L; ++k) {
       const double cphi = C * (s_phi[k] - cum_ref);
       // r = 1/(1/R_p + C phi): altitude r - R_p written without cancellation
-      lev[(int64_t)i * TR_LMAX + k].z = (float)(-cphi * rp * rp / (1.0 + cphi * rp));
+      s_z[k] = (float)(-cphi * rp * rp / (1.0 + cphi * rp));
+      lev[(int64_t)i * TR_LMAX + k].z = s_z[k];
     }
     // gray cloud deck: the column ends on the first level with P >= p_cloud
     // (at least two levels); altitudes above stay those of the whole column
@@ -176,6 +188,32 @@ __global__ void trans_prologue(const float* __restrict__ theta, int n_theta, int
     for (int s = 0; s < TR_MAX_SPECIES; ++s)
       in.x[s] = s < S ? x0[s] * exp10f(theta[(int64_t)i * n_theta + 5 + s]) : 0.f;
     inst[i] = in;
+    s_leff = L_eff;
+  }
+  __syncthreads();
+  // chords of every ray through the shells above it, block by block of TR_RB
+  // rays: ds_ik = 2 (sqrt(r_k^2 - b^2) - sqrt(r_{k+1}^2 - b^2)), b = r_i,
+  // written as 2 (A - B) / (sqrt A + sqrt B) with A = r_k^2 - b^2 and
+  // B = r_{k+1}^2 - b^2 formed from altitude differences (no cancellation)
+  const int Le = s_leff;
+  const float rp = r_planet[i];
+  float* dsi = ds + (int64_t)i * TR_DS_STRIDE;
+  const int nblk = (Le - 1 + TR_RB - 1) / TR_RB;
+  for (int b = 0; b < nblk; ++b) {
+    const int i0 = 1 + b * TR_RB, nr = min(TR_RB, Le - i0), kmax = i0 + nr - 1;
+    float* db = dsi + 32 * b * (b + 1);
+    for (int e = threadIdx.x; e < kmax * TR_RB; e += blockDim.x) {
+      const int k = e / TR_RB, r = e % TR_RB, ir = i0 + r;
+      float d = 0.f;
+      if (r < nr && k < ir) {
+        const float zb = s_z[ir], zk = s_z[k], zk1 = s_z[k + 1];
+        const float A = (zk - zb) * (2.f * rp + zk + zb);
+        const float B = (k + 1 < ir) ? (zk1 - zb) * (2.f * rp + zk1 + zb) : 0.f;
+        const float AmB = (zk - zk1) * (2.f * rp + zk + zk1);
+        d = 2.f * AmB / (sqrtf(A) + sqrtf(B));
+      }
+      db[e] = d;
+    }
   }
 }
 
@@ -193,23 +231,32 @@ __device__ __forceinline__ float one_minus_exp(float tau) {
   return 1.0f - bartf::ex2_approx(-tau * 1.4426950408889634f);
 }
 
+// Ray block handled by split thread h: snake order over groups of
+// 2 TR_SPLIT blocks (h, 2 TR_SPLIT - 1 - h), so the four threads of a column
+// get shallow and deep blocks alike.
+__device__ __forceinline__ bool my_block(int b, int h) {
+  const int q = b % (2 * TR_SPLIT);
+  return (q < TR_SPLIT) ? (q == h) : (2 * TR_SPLIT - 1 - q == h);
+}
+
 template <int S>
-__global__ void __launch_bounds__(TR_THREADS)
+__global__ void __launch_bounds__(TR_THREADS, 2)
 trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrLevel* __restrict__ lev,
-             const TrInst* __restrict__ inst, int n, const int64_t* __restrict__ nu_lo,
-             const int64_t* __restrict__ nu_hi, const int64_t* __restrict__ offs, float* __restrict__ spectra,
-             const float* __restrict__ filt, int n_bands, float2* __restrict__ partial, int n_gtiles,
-             unsigned long long n_units, unsigned long long* __restrict__ counter,
+             const TrInst* __restrict__ inst, const float* __restrict__ ds, int n,
+             const int64_t* __restrict__ nu_lo, const int64_t* __restrict__ nu_hi, const int64_t* __restrict__ offs,
+             float* __restrict__ spectra, const float* __restrict__ filt, int n_bands, float2* __restrict__ partial,
+             int n_gtiles, unsigned long long n_units, unsigned long long* __restrict__ counter,
              const int32_t* __restrict__ active, int* __restrict__ status, double nu_start, double dnu,
              double ray) {
   extern __shared__ float smem[];
-  float* s_alpha = smem;                                  // [TR_LMAX][TR_THREADS] shell extinction
-  float* s_ds = s_alpha + TR_LMAX * TR_THREADS;           // [TR_LMAX][TR_RB] chords of the ray block
+  float* s_alpha = smem;                                  // [TR_LMAX - 1][TR_COLS] shell extinction
   __shared__ TrLevel s_lev[TR_LMAX];
   __shared__ TrInst s_in;
   __shared__ unsigned long long s_unit;
-  __shared__ float2 s_red[TR_THREADS / 32][TR_MAX_BANDS];
+  __shared__ float s_part[TR_SPLIT - 1][TR_COLS];
+  __shared__ float2 s_red[TR_COLS / 32][TR_MAX_BANDS];
   const int tid = threadIdx.x;
+  const int c = tid % TR_COLS, h = tid / TR_COLS;          // column, quarter
   const int64_t sstride = (int64_t)Lg * M * N;
 
   for (;;) {
@@ -224,13 +271,13 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
       continue;
     }
     const int64_t lo = nu_lo ? nu_lo[i] : 0, hi = nu_hi ? nu_hi[i] : N;
-    const int64_t g0 = (int64_t)g * TR_THREADS;
+    const int64_t g0 = (int64_t)g * TR_COLS;
     if (lo < 0 || hi > N || lo >= hi) {
       if (tid == 0 && g == 0) atomicOr(status, BART_DEV_RANGE);
       __syncthreads();
       continue;
     }
-    if (g0 + TR_THREADS <= lo || g0 >= hi) {      // this tile is outside the instance's span
+    if (g0 + TR_COLS <= lo || g0 >= hi) {         // this tile is outside the instance's span
       __syncthreads();
       continue;
     }
@@ -244,64 +291,58 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
     for (int k = tid; k < L; k += TR_THREADS) s_lev[k] = lev[(int64_t)i * TR_LMAX + k];
     __syncthreads();
 
-    const int64_t j = g0 + tid;
-    const bool active = (j >= lo) && (j < hi);
-    const int64_t jj = active ? j : lo;
+    const int64_t j = g0 + c;
+    const bool act = (j >= lo) && (j < hi);
+    const int64_t jj = act ? j : lo;
     // Rayleigh cross-section per molecule a nu^4, the same at every level
     const double nu = nu_start + (double)jj * dnu;
     const float sig_r = (float)(ray * (nu * nu) * (nu * nu));
-    // extinction at every level, then shell means into shared memory
-    float a_prev = 0.f;
-#pragma unroll 2
-    for (int k = 0; k < L; ++k) {
-      const TrLevel lv = s_lev[k];
-      const float* base = grid + ((int64_t)lv.a * M + lv.m) * N + jj;
+    // extinction at levels k0 .. k1 of this quarter (the boundary level is
+    // evaluated by both neighbours), shell means k0 .. k1-1 into shared memory
+    {
+      const int k0 = (L - 1) * h / TR_SPLIT, k1 = (L - 1) * (h + 1) / TR_SPLIT;
       const int64_t dl = (Lg > 1) ? (int64_t)M * N : 0;
       const int64_t dm = (M > 1) ? N : 0;
-      float sig = sig_r;
+      float a_prev = 0.f;
+      for (int k = k0; k <= k1; ++k) {
+        const TrLevel lv = s_lev[k];
+        const float* base = grid + ((int64_t)lv.a * M + lv.m) * N + jj;
+        float sig = sig_r;
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const float* b = base + s * sstride;
-        const float v00 = __ldg(b), v01 = __ldg(b + dm), v10 = __ldg(b + dl), v11 = __ldg(b + dl + dm);
-        const float lo_l = fmaf(lv.w, v01 - v00, v00);
-        const float hi_l = fmaf(lv.w, v11 - v10, v10);
-        sig = fmaf(s_in.x[s], fmaf(lv.u, hi_l - lo_l, lo_l), sig);
-      }
-      const float a = sig * lv.ndens;
-      if (k > 0) s_alpha[(k - 1) * TR_THREADS + tid] = 0.5f * (a_prev + a);
-      a_prev = a;
-    }
-    // rays: b_i = r_i, i = 0 .. L-1 (ray 0 grazes the top level: tau = 0)
-    const float rp = s_in.r_planet;
-    // trapezoid state: f b of the previous ray and its altitude (b = r_p + z;
-    // widths are taken as altitude differences so they keep full precision)
-    float integ = 0.f, fb_prev = 0.f, z_prev = s_lev[0].z;
-    for (int i0 = 1; i0 < L; i0 += TR_RB) {
-      __syncthreads();                                    // s_ds of the previous block is consumed
-      const int nr = min(TR_RB, L - i0);
-      const int kmax = i0 + nr - 1;                       // shells 0 .. kmax-1
-      for (int e = tid; e < kmax * TR_RB; e += TR_THREADS) {
-        const int k = e / TR_RB, r = e % TR_RB, ir = i0 + r;
-        float ds = 0.f;
-        if (r < nr && k < ir) {
-          const float zb = s_lev[ir].z;
-          const float zk = s_lev[k].z, zk1 = s_lev[k + 1].z;
-          const float A = (zk - zb) * (2.f * rp + zk + zb);
-          const float B = (k + 1 < ir) ? (zk1 - zb) * (2.f * rp + zk1 + zb) : 0.f;
-          const float AmB = (zk - zk1) * (2.f * rp + zk + zk1);
-          ds = 2.f * AmB / (sqrtf(A) + sqrtf(B));
+        for (int s = 0; s < S; ++s) {
+          const float* b = base + s * sstride;
+          const float v00 = __ldg(b), v01 = __ldg(b + dm), v10 = __ldg(b + dl), v11 = __ldg(b + dl + dm);
+          const float lo_l = fmaf(lv.w, v01 - v00, v00);
+          const float hi_l = fmaf(lv.w, v11 - v10, v10);
+          sig = fmaf(s_in.x[s], fmaf(lv.u, hi_l - lo_l, lo_l), sig);
         }
-        s_ds[k * TR_RB + r] = ds;
+        const float a = sig * lv.ndens;
+        if (k > k0) s_alpha[(k - 1) * TR_COLS + c] = 0.5f * (a_prev + a);
+        a_prev = a;
       }
-      __syncthreads();
+    }
+    __syncthreads();
+    // rays b_i = r_i, i = 1 .. L-1 (ray 0 grazes the top level: tau = 0) in
+    // blocks of TR_RB; this thread's share of the trapezoid in impact parameter,
+    // integral (1 - e^-tau) b db = sum_i f_i b_i (z_{i-1} - z_{i+1}) / 2
+    // (altitude differences keep full precision; the deepest ray's weight
+    // is (z_{L-2} - z_{L-1}) / 2)
+    const float rp = s_in.r_planet;
+    const float* dsi = ds + (int64_t)i * TR_DS_STRIDE;
+    const int nblk = (L - 1 + TR_RB - 1) / TR_RB;
+    float integ = 0.f;
+    for (int b = 0; b < nblk; ++b) {
+      if (!my_block(b, h)) continue;
+      const int i0 = 1 + b * TR_RB, nr = min(TR_RB, L - i0), kmax = i0 + nr - 1;
+      const float* db = dsi + 32 * b * (b + 1);
       float tau[TR_RB];
 #pragma unroll
       for (int r = 0; r < TR_RB; ++r) tau[r] = 0.f;
 #pragma unroll 4
       for (int k = 0; k < kmax; ++k) {
-        const float a = s_alpha[k * TR_THREADS + tid];
-        const float4 d0 = *reinterpret_cast<const float4*>(s_ds + k * TR_RB);
-        const float4 d1 = *reinterpret_cast<const float4*>(s_ds + k * TR_RB + 4);
+        const float a = s_alpha[k * TR_COLS + c];
+        const float4 d0 = __ldg(reinterpret_cast<const float4*>(db + k * TR_RB));
+        const float4 d1 = __ldg(reinterpret_cast<const float4*>(db + k * TR_RB + 4));
         tau[0] = fmaf(d0.x, a, tau[0]);
         tau[1] = fmaf(d0.y, a, tau[1]);
         tau[2] = fmaf(d0.z, a, tau[2]);
@@ -314,36 +355,44 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
 #pragma unroll
       for (int r = 0; r < TR_RB; ++r) {
         if (r < nr) {
-          const float zb = s_lev[i0 + r].z;
-          const float fb = one_minus_exp(tau[r]) * (rp + zb);
-          integ = fmaf(0.5f * (fb_prev + fb), z_prev - zb, integ);
-          fb_prev = fb;
-          z_prev = zb;
+          const int ir = i0 + r;
+          const float zb = s_lev[ir].z;
+          const float wgt = 0.5f * (s_lev[ir - 1].z - (ir + 1 < L ? s_lev[ir + 1].z : zb));
+          integ = fmaf(one_minus_exp(tau[r]) * (rp + zb), wgt, integ);
         }
       }
     }
-    const float rbot = rp + s_lev[L - 1].z;
-    const float rs = s_in.r_star;
-    const float delta = (rbot / rs) * (rbot / rs) + 2.f * integ / (rs * rs);
-    if (active && spectra) spectra[(offs ? offs[i] : (int64_t)i * N) + (j - lo)] = delta;
-    if (n_bands > 0) {
-      float dw = 0.f;
-      if (active) dw = (hi - lo == 1) ? 1.f : ((j == lo || j == hi - 1) ? 0.5f : 1.f);
-      const int warp = tid >> 5, lane = tid & 31;
-      for (int b = 0; b < n_bands; ++b) {
-        const float W = active ? __ldg(filt + (int64_t)b * N + j) * dw : 0.f;
-        float num = W * delta, den = W;
+    if (h > 0) s_part[h - 1][c] = integ;
+    __syncthreads();
+    float delta = 0.f;
+    if (h == 0) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          num += __shfl_xor_sync(0xffffffffu, num, o);
-          den += __shfl_xor_sync(0xffffffffu, den, o);
+      for (int q = 0; q < TR_SPLIT - 1; ++q) integ += s_part[q][c];
+      const float rbot = rp + s_lev[L - 1].z;
+      const float rs = s_in.r_star;
+      delta = (rbot / rs) * (rbot / rs) + 2.f * integ / (rs * rs);
+      if (act && spectra) spectra[(offs ? offs[i] : (int64_t)i * N) + (j - lo)] = delta;
+    }
+    if (n_bands > 0) {
+      if (h == 0) {
+        float dw = 0.f;
+        if (act) dw = (hi - lo == 1) ? 1.f : ((j == lo || j == hi - 1) ? 0.5f : 1.f);
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int b = 0; b < n_bands; ++b) {
+          const float W = act ? __ldg(filt + (int64_t)b * N + j) * dw : 0.f;
+          float num = W * delta, den = W;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+          }
+          if (lane == 0) s_red[warp][b] = make_float2(num, den);
         }
-        if (lane == 0) s_red[warp][b] = make_float2(num, den);
       }
       __syncthreads();
       if (tid < n_bands) {
         float2 acc = make_float2(0.f, 0.f);
-        for (int w = 0; w < TR_THREADS / 32; ++w) {
+        for (int w = 0; w < TR_COLS / 32; ++w) {
           acc.x += s_red[w][tid].x;
           acc.y += s_red[w][tid].y;
         }
@@ -367,7 +416,7 @@ __global__ void trans_band_reduce(const float2* __restrict__ partial, const int6
     return;
   }
   double num = 0.0, den = 0.0;
-  for (int64_t g = lo / TR_THREADS; g <= (hi - 1) / TR_THREADS; ++g) {
+  for (int64_t g = lo / TR_COLS; g <= (hi - 1) / TR_COLS; ++g) {
     const float2 v = partial[((int64_t)i * n_gtiles + g) * nb + b];
     num += v.x;
     den += v.y;
@@ -376,19 +425,19 @@ __global__ void trans_band_reduce(const float2* __restrict__ partial, const int6
 }
 
 using TrLauncher = void (*)(int, size_t, cudaStream_t, const float*, int, int, int64_t, const TrLevel*,
-                            const TrInst*, int, const int64_t*, const int64_t*, const int64_t*, float*,
-                            const float*, int, float2*, int, unsigned long long, unsigned long long*,
+                            const TrInst*, const float*, int, const int64_t*, const int64_t*, const int64_t*,
+                            float*, const float*, int, float2*, int, unsigned long long, unsigned long long*,
                             const int32_t*, int*, double, double, double);
 
 template <int S>
 void launch_trans(int grid_dim, size_t smem, cudaStream_t st, const float* grid, int Lg, int M, int64_t N,
-                  const TrLevel* lev, const TrInst* inst, int n, const int64_t* lo, const int64_t* hi,
-                  const int64_t* offs, float* spectra, const float* filt, int nb, float2* partial, int ngt,
-                  unsigned long long nu, unsigned long long* counter, const int32_t* active, int* status,
+                  const TrLevel* lev, const TrInst* inst, const float* ds, int n, const int64_t* lo,
+                  const int64_t* hi, const int64_t* offs, float* spectra, const float* filt, int nb, float2* partial,
+                  int ngt, unsigned long long nu, unsigned long long* counter, const int32_t* active, int* status,
                   double nu_start, double dnu, double ray) {
-  trans_kernel<S><<<grid_dim, TR_THREADS, smem, st>>>(grid, Lg, M, N, lev, inst, n, lo, hi, offs, spectra, filt,
-                                                      nb, partial, ngt, nu, counter, active, status, nu_start,
-                                                      dnu, ray);
+  trans_kernel<S><<<grid_dim, TR_THREADS, smem, st>>>(grid, Lg, M, N, lev, inst, ds, n, lo, hi, offs, spectra,
+                                                      filt, nb, partial, ngt, nu, counter, active, status,
+                                                      nu_start, dnu, ray);
 }
 
 template <int S>
@@ -418,7 +467,7 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
   TrLauncher launch = nullptr;
   cudaError_t ce = cudaSuccess;
   int per_sm = 0;
-  const size_t smem = (size_t)(TR_LMAX * TR_THREADS + TR_LMAX * TR_RB) * sizeof(float);
+  const size_t smem = (size_t)(TR_LMAX - 1) * TR_COLS * sizeof(float);
   switch (S) {
     case 1: launch = launch_trans<1>; ce = set_smem<1>(smem, &per_sm); break;
     case 2: launch = launch_trans<2>; ce = set_smem<2>(smem, &per_sm); break;
@@ -431,13 +480,14 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
   for (int k = 0; k < Lg; ++k) hconst.push_back((float)std::log10(g->p_bar[k]));
   for (int m = 0; m < M; ++m) hconst.push_back((float)g->t_K[m]);
   for (int s = 0; s < S; ++s) hconst.push_back((float)c->x0[s]);
-  const int n_gtiles = (int)((N + TR_THREADS - 1) / TR_THREADS);
-  void *p_const, *p_lev, *p_inst, *p_part = nullptr, *p_counter;
+  const int n_gtiles = (int)((N + TR_COLS - 1) / TR_COLS);
+  void *p_const, *p_lev, *p_inst, *p_part = nullptr, *p_counter, *p_ds;
   bart_status st;
   if ((st = bart_upload_const(ctx, "tr_const", hconst.data(), hconst.size() * sizeof(float), &p_const)) != BART_OK)
     return st;
   if ((st = bart_scratch(ctx, "tr_lev", (size_t)n * TR_LMAX * sizeof(TrLevel), &p_lev)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "tr_inst", (size_t)n * sizeof(TrInst), &p_inst)) != BART_OK) return st;
+  if ((st = bart_scratch(ctx, "tr_ds", (size_t)n * TR_DS_STRIDE * sizeof(float), &p_ds)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "tr_counter", sizeof(unsigned long long), &p_counter)) != BART_OK) return st;
   if (nb > 0 &&
       (st = bart_scratch(ctx, "tr_part", (size_t)n * n_gtiles * nb * sizeof(float2), &p_part)) != BART_OK)
@@ -450,13 +500,14 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
       b->theta, 5 + S, n, S, b->n_levels, b->r_planet_cm, b->r_star_cm, dc, Lg, dc + Lg, M, c->p_top_bar,
       c->p_bot_bar, c->p_ref_bar, c->g_cgs, c->mu_amu, (float)(1.0 / c->g_cgs), (float)std::pow(c->t_int_K, 4.0),
       tirr0, (float)c->t_min_K, (float)std::min(c->t_max_K, 1e30), dc + Lg + M, (TrLevel*)p_lev,
-      (TrInst*)p_inst, b->active, ctx->d_status, c->p_cloud_bar);
+      (TrInst*)p_inst, b->active, ctx->d_status, c->p_cloud_bar, (float*)p_ds);
   if ((st = bart_check_launch(ctx, "trans_prologue")) != BART_OK) return st;
   const unsigned long long n_units = (unsigned long long)n_gtiles * (unsigned long long)n;
   if (per_sm < 1) per_sm = 1;
   int grid_dim = ctx->sm_count * per_sm;
   if ((unsigned long long)grid_dim > n_units) grid_dim = (int)n_units;
-  launch(grid_dim, smem, ctx->stream, g->grid, Lg, M, N, (const TrLevel*)p_lev, (const TrInst*)p_inst, n,
+  launch(grid_dim, smem, ctx->stream, g->grid, Lg, M, N, (const TrLevel*)p_lev, (const TrInst*)p_inst,
+         (const float*)p_ds, n,
          b->nu_lo, b->nu_hi, b->spec_offsets, spectra, nb ? f->weights : nullptr, nb, (float2*)p_part, n_gtiles,
          n_units, (unsigned long long*)p_counter, b->active, ctx->d_status, g->nu.nu_start_cm, g->nu.dnu_cm,
          c->rayleigh_coef);

@@ -127,3 +127,54 @@ def test_screen_cuts_exact_evaluations_and_keeps_posterior(ctx, setup):
     spread = np.sqrt(mp.var(0) + ms.var(0)) / width
     print("posterior mean difference / box width:", np.round(diff, 4))
     assert np.all(diff < 3 * spread + 0.02)
+
+
+def test_screen_gains_ess_per_exact_evaluation_at_equal_posterior(ctx, setup):
+    """What the surrogate buys: after a shared exact-model burn-in, the
+    screened sampler reaches the plain sampler's posterior within the App. C
+    standard errors (means: s = sigma / sqrt(ESS); central 68% interval
+    content: s_C = sqrt(C (1 - C) / ESS)) while spending fewer exact
+    forward-model evaluations per effective sample (Sec. 5 ESS and SPEIS)."""
+    import torch
+    import paper_2104_12522_gb300 as bart
+    lo, hi = W.THETA_LO.astype(np.float32), W.THETA_HI.astype(np.float32)
+    su = setup
+    s0 = _sampler(ctx, su, 6100, False)
+    ctx.retrieval_run(s0, None, su["grid"], su["p"], su["t"], su["nu"], su["cfg"], su["filt"], su["data"],
+                      su["sigma"], 2000, use_graph=True)
+    x_b = torch.empty((16, 9), dtype=torch.float32, device="cuda")
+    L_b = torch.empty(16, dtype=torch.float64, device="cuda")
+    s0.get_state(x_b, L_b)
+    n_gen = 4000
+    out = {}
+    for mode in ("plain", "screened"):
+        s = bart.Demc(ctx, 16, lo, hi, jump_every=10, eps=1e-4, seed=6200)
+        Ls = None
+        if mode == "screened":
+            s.set_screen(1.0, 1.0)
+            Ls = torch.empty(16, dtype=torch.float64, device="cuda")
+            ctx.loglike_bands(su["net"].forward(x_b), su["data"], su["sigma"], Ls)
+        s.set_state(x_b.clone(), L_b.clone(), Ls)
+        chain = torch.empty((n_gen, 16, 9), dtype=torch.float32, device="cuda")
+        st = ctx.retrieval_run(s, su["net"] if mode == "screened" else None, su["grid"], su["p"], su["t"], su["nu"],
+                               su["cfg"], su["filt"], su["data"], su["sigma"], n_gen, use_graph=True, chain=chain)
+        sp, gr, ess = ctx.chain_stats(chain)
+        out[mode] = dict(x=chain.reshape(-1, 9).double().cpu().numpy(),
+                         ess_j=(n_gen * 16 / sp.mean(0)).cpu().numpy(), ess=ess, st=st,
+                         ess_per_eval=ess / st["exact_evals"], gr=float(gr.max()))
+    p, s = out["plain"], out["screened"]
+    print(f"ESS per exact evaluation: plain {p['ess_per_eval']:.3e} ({p['ess']:.0f} / {p['st']['exact_evals']}), "
+          f"screened {s['ess_per_eval']:.3e} ({s['ess']:.0f} / {s['st']['exact_evals']}); R max {p['gr']:.3f} / "
+          f"{s['gr']:.3f}")
+    assert s["ess_per_eval"] > 2.0 * p["ess_per_eval"]
+    z_mean, z_c = [], []
+    for j in range(9):
+        sp_ = p["x"][:, j].std() / np.sqrt(p["ess_j"][j])
+        ss_ = s["x"][:, j].std() / np.sqrt(s["ess_j"][j])
+        z_mean.append(abs(p["x"][:, j].mean() - s["x"][:, j].mean()) / np.hypot(sp_, ss_))
+        q16, q84 = np.percentile(p["x"][:, j], [16, 84])
+        c = np.mean((s["x"][:, j] >= q16) & (s["x"][:, j] <= q84))
+        z_c.append(abs(c - 0.68) / np.sqrt(0.68 * 0.32 * (1 / p["ess_j"][j] + 1 / s["ess_j"][j])))
+    print("posterior agreement z (means):", np.round(z_mean, 2), " (68% content):", np.round(z_c, 2))
+    # nine parameters, two statistics each: 4 standard errors leaves room for chance
+    assert max(z_mean) < 4.0 and max(z_c) < 4.0
