@@ -95,13 +95,21 @@ bart_status bart_set_emission_tile(bart_ctx* ctx, int tile);
  *     the CTA finishing a proposal's last tile reduces its band values.  The
  *     counters reset themselves at the end of the launch, so a captured graph
  *     replays it unchanged.
+ *     A CTA thread takes two wavenumbers and their arithmetic runs on packed
+ *     FP32 pairs.
  *   BART_LAUNCH_SPLIT: three launches (per-proposal profile kernel, one CTA
  *     per (proposal, tile) column kernel, band reduction), kept for
  *     comparison.
+ *   BART_LAUNCH_FUSED_TMA: the fused kernel with the grid rows of each layer
+ *     staged in shared memory by bulk copies (a producer warp, a ring of
+ *     mbarrier-tracked buffers) instead of per-thread loads; used where
+ *     nu.n_nu is a multiple of 4 and the grid is 16-byte aligned (else the
+ *     fused kernel runs).  Kept for comparison: it measures slower on GB300.
  * Results agree to FP32 rounding (band values through the order of partial
  * sums).  Other values return BART_EINVAL. */
 #define BART_LAUNCH_FUSED 0
 #define BART_LAUNCH_SPLIT 1
+#define BART_LAUNCH_FUSED_TMA 2
 bart_status bart_set_emission_launch(bart_ctx* ctx, int mode);
 
 /* Graph capture of library calls.  bart_capture_begin starts capturing the
@@ -432,6 +440,14 @@ bart_status bart_mlp_gradient(bart_mlp* net, const float* x, const float* t, int
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the batch; loss as above. */
 bart_status bart_mlp_train_step(bart_mlp* net, const float* x, const float* t, int B, float lr,
                                 float* loss);
+/* n_steps Adam steps in one call, each on the batch of rows
+ * batch_rows[k][0 .. B-1] (device int32, indices into the n_rows rows of x
+ * [n_rows][in] and t [n_rows][out], device) with learning rate lr[k] (host
+ * [n_steps]); the steps are those of bart_mlp_train_step on the gathered
+ * rows.  loss: device [n_steps] or NULL.  An index outside [0, n_rows) is
+ * replaced by row 0 and makes bart_sync() return BART_ERANGE. */
+bart_status bart_mlp_train_steps(bart_mlp* net, const float* x, const float* t, int64_t n_rows,
+                                 const int32_t* batch_rows, int B, int n_steps, const float* lr, float* loss);
 
 /* ------------------------------------------------------------ sampler */
 

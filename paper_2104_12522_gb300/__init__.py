@@ -15,11 +15,12 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _native
-from ._native import BART_EMISSION, BART_TRANSMISSION, BART_LAUNCH_FUSED, BART_LAUNCH_SPLIT  # noqa: F401
+from ._native import (BART_EMISSION, BART_TRANSMISSION, BART_LAUNCH_FUSED, BART_LAUNCH_SPLIT,  # noqa: F401
+                      BART_LAUNCH_FUSED_TMA)
 
 __all__ = ["Context", "Graph", "BartError", "DeviceLines", "device_lines", "NuGrid", "Mlp", "Demc",
            "forward_emission_noalloc", "BART_EMISSION",
-           "BART_TRANSMISSION", "BART_LAUNCH_FUSED", "BART_LAUNCH_SPLIT"]
+           "BART_TRANSMISSION", "BART_LAUNCH_FUSED", "BART_LAUNCH_SPLIT", "BART_LAUNCH_FUSED_TMA"]
 
 
 class BartError(RuntimeError):
@@ -162,7 +163,8 @@ class Context:
         self._check(self.lib.bart_set_emission_tile(self.h, int(tile)))
 
     def set_emission_launch(self, mode: int):
-        """BART_LAUNCH_FUSED (0, one persistent kernel) or BART_LAUNCH_SPLIT (1, three launches)."""
+        """BART_LAUNCH_FUSED (0, one persistent kernel), BART_LAUNCH_SPLIT (1, three launches) or
+        BART_LAUNCH_FUSED_TMA (2, the fused kernel with bulk-copy staging of the grid rows)."""
         self._check(self.lib.bart_set_emission_launch(self.h, int(mode)))
 
     def capture(self, fn) -> "Graph":
@@ -459,6 +461,21 @@ class Mlp:
         _check_tensor(t, "float32", int(x.shape[0]) * self.widths[-1])
         self.ctx._check(self.lib.bart_mlp_train_step(self.h, _ptr(x), _ptr(t), int(x.shape[0]), float(lr),
                                                      _ptr(loss)))
+        return loss
+
+    def train_steps(self, x, t, batch_rows, lr, loss=None):
+        """bart_mlp_train_steps: len(lr) Adam steps, step k on rows
+        batch_rows[k] (device int32 [n_steps][B]) of x and t."""
+        n_steps, B = (int(v) for v in batch_rows.shape)
+        _check_tensor(x, "float32")
+        _check_tensor(t, "float32", int(x.shape[0]) * self.widths[-1])
+        _check_tensor(batch_rows, "int32")
+        _check_tensor(loss, "float32")
+        if len(lr) != n_steps:
+            raise ValueError("one learning rate per step")
+        lrs = _flt(lr)
+        self.ctx._check(self.lib.bart_mlp_train_steps(self.h, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(batch_rows), B,
+                                                      n_steps, lrs, _ptr(loss)))
         return loss
 
 

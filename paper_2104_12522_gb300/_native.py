@@ -17,7 +17,7 @@ BART_OK, BART_EINVAL, BART_ENOMEM, BART_ECUDA, BART_ETIMEOUT, BART_ERANGE, BART_
 STATUS_NAMES = {0: "BART_OK", 1: "BART_EINVAL", 2: "BART_ENOMEM", 3: "BART_ECUDA",
                 4: "BART_ETIMEOUT", 5: "BART_ERANGE", 6: "BART_EUNSUPPORTED"}
 BART_EMISSION, BART_TRANSMISSION = 0, 1
-BART_LAUNCH_FUSED, BART_LAUNCH_SPLIT = 0, 1
+BART_LAUNCH_FUSED, BART_LAUNCH_SPLIT, BART_LAUNCH_FUSED_TMA = 0, 1, 2
 
 
 class LineList(C.Structure):
@@ -107,6 +107,8 @@ SIGNATURES = {
     "bart_mlp_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
     "bart_mlp_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "bart_mlp_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, C.c_float, c_void_p]),
+    "bart_mlp_train_steps": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int, c_int, P(C.c_float),
+                                     c_void_p]),
     "bart_demc_create": (c_int, [c_void_p, c_int, c_int, P(C.c_float), P(C.c_float), c_double, c_int, c_double,
                                  C.c_uint64, P(c_void_p)]),
     "bart_demc_destroy": (None, [c_void_p]),

@@ -162,7 +162,8 @@ extern "C" bart_status bart_set_emission_tile(bart_ctx* ctx, int tile) {
 
 extern "C" bart_status bart_set_emission_launch(bart_ctx* ctx, int mode) {
   if (!ctx) return BART_EINVAL;
-  BART_REQUIRE(ctx, mode == BART_LAUNCH_FUSED || mode == BART_LAUNCH_SPLIT, "unknown emission launch mode %d", mode);
+  BART_REQUIRE(ctx, mode == BART_LAUNCH_FUSED || mode == BART_LAUNCH_SPLIT || mode == BART_LAUNCH_FUSED_TMA,
+               "unknown emission launch mode %d", mode);
   ctx->em_launch = mode;
   return BART_OK;
 }

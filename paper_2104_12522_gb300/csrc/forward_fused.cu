@@ -1,488 +1,25 @@
-// One persistent fused launch per emission batch: a whole sampler generation
-// of proposals (Sec. 3 forward model -- profile generator, transit and the
-// spectrum integrator -- for every proposal; Sec. 4 items 3 and 7; Sec. 7
-// nine-parameter model) in a single kernel.
-//
-// CTAs (as many as fit on the SMs) take units (wavenumber tile, proposal)
-// from a device counter in tile-major order: the CTAs in flight work on the
-// same tile for neighbouring proposals, so the grid rows they read (the same
-// rows for proposals whose layer temperatures fall in the same bracket) are
-// shared through L2.  For its unit a CTA
-//   1. evaluates the proposal's five-parameter T(P) profile at every layer
-//      (one thread per layer) and keeps each layer's temperature bracket,
-//      weight and c2/T in shared memory, with the abundance coefficients
-//      X_s / (mu m_u) = X0_s 10^{a_s} / (mu m_u);
-//   2. runs one thread per wavenumber down the column: opacity interpolated
-//      in T and summed over species (coalesced grid-row reads, the next
-//      layer's rows requested before the current layer is computed), the
-//      trapezoid optical depth, the Planck source, per Gauss-Legendre angle
-//      the log2 transmittance, and the flux as a sum over layers of the
-//      layer-mean source times the drop of the quadrature-weighted
-//      transmittance (the angle sum taken inside the layer sum, which keeps
-//      one running value per angle instead of three);
-//   3. writes the spectrum and the tile's band partial sums; the CTA that
-//      finishes a proposal's last tile sums its partials in a fixed order
-//      (FP64) into the band values.
-// Nothing waits on another CTA: the last-tile test is an atomic count, a
-// proposal's layer states are published by its first unit with an epoch mark
-// (a unit that does not see the mark computes them itself), and the last CTA
-// to leave resets the counters and advances the epoch, so the launch can be
-// replayed from a CUDA graph unchanged.
+// Host side of the persistent fused emission launch (the kernels are in
+// emission_fused.cuh, instantiated per species count in fused_s1.cu ..
+// fused_s4.cu so the translation units compile in parallel): constant tables,
+// scratch (work counters, published layer states, band partials), the tile
+// autotuner and the launch.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
 
-#include "bart_internal.cuh"
-#include "emission.cuh"
-#include "forward.cuh"
+#include "emission_fused.cuh"
 
 using namespace bartem;
 
 namespace {
 
-constexpr int FUSED_MAX_SPECIES = 4;
-constexpr int MAX_TILES_PER_UNIT = 8;
-
-// GPU-scope acquire load and release store of a 32-bit flag, and an
-// acquire-release add (PTX memory model): the release makes the writes that
-// the CTA ordered before it by a barrier visible to a thread that acquires
-// the flag, without a full fence in every writing thread.
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned int add_acq_rel(unsigned int* p, unsigned int v) {
-  unsigned int old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-
-struct FusedArgs {
-  const float* grid;                 // [S][L][M][N]
-  int L, M;
-  int64_t N;
-  const float* theta;                // [n][n_theta] or NULL
-  int n_theta;
-  const float* t_profile;            // [n][L] or NULL
-  int n;
-  const int64_t* nu_lo;
-  const int64_t* nu_hi;
-  const int64_t* offs;
-  const int32_t* active;
-  const float* p_cgs;                // [L] level pressures, dyn cm^-2
-  const float* t_axis;               // [M]
-  const float* dpg;                  // [L-1] (P_{k+1} - P_k) / (2 g)
-  float x0mu[FUSED_MAX_SPECIES];     // X0_s / (mu m_u)
-  float ang[2 * MAX_ANGLES];         // -log2(e) / mu_i, then 2 pi w_i mu_i / 2
-  float tw_top;                      // sum_i 2 pi w_i mu_i / 2 (all transmittances 1)
-  float inv_g, tint4, tirr0, t_min, t_max;
-  double nu_start, dnu;
-  float* spectra;
-  const float* filt;
-  int n_bands;
-  float2* partial;                   // [n][n_groups][n_bands]
-  float* bands;
-  int tpu;                           // tiles per unit (consecutive tiles of one proposal)
-  int n_groups;                      // units per proposal over the whole grid: ceil(n_tiles / tpu)
-  unsigned long long n_units;        // n_groups x n
-  unsigned long long* work;          // [0] next unit, [1] CTAs finished, [2] launch epoch
-  unsigned int* p_done;              // [n] tiles finished per proposal
-  LayerTW* tw_cache;                 // [n][L] layer states published by the first unit of a proposal
-  unsigned int* tw_flag;             // [n] epoch + 1 once tw_cache[p] holds this launch's states
-  int* status;
-  EmExtra ex;
-};
-
-// Resident threads per SM the register allocation is sized for (768: six
-// CTAs of 128 threads, at most 80 registers a thread; measured faster than
-// 512 threads at 112 registers).
-#ifndef FUSED_OCC_THREADS
-#define FUSED_OCC_THREADS 768
-#endif
-
-// Two wavenumbers per thread, their arithmetic on packed FP32 pairs
-// (FFMA2/FADD2/FMUL2 of sm_100+: one issue slot for both); the MUFU
-// exponentials and reciprocals stay per wavenumber.
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }   // exact
-__device__ __forceinline__ float2 ex2_2(float2 y) {
-  return make_float2(bartf::ex2_approx(y.x), bartf::ex2_approx(y.y));
-}
-
-// Planck function from y = (c2 nu / T) log2(e): B = c1nu3 / (2^y - 1); where
-// c2 nu / T can exceed 20 (WIDE_X), larger arguments take an FP64 expm1.
-template <bool WIDE_X>
-__device__ __forceinline__ float2 planck2(float2 c1nu3, float2 y) {
-  const float2 e = add2(ex2_2(y), f2(-1.0f));
-  float2 B = mul2(c1nu3, make_float2(bartf::rcp_approx(e.x), bartf::rcp_approx(e.y)));
-  if (WIDE_X) {
-    constexpr float Y20 = 20.0f * LOG2E;
-    if (y.x > Y20) B.x = (float)((double)c1nu3.x / expm1((double)y.x * 0.6931471805599453));
-    if (y.y > Y20) B.y = (float)((double)c1nu3.y / expm1((double)y.y * 0.6931471805599453));
-  }
-  return B;
-}
-
-// TW wavenumbers per tile, TW / 2 threads per CTA.
-template <int S, int NA, int TW, int MODE>
-__global__ void __launch_bounds__(TW / 2, FUSED_OCC_THREADS / (TW / 2))
-emission_fused_kernel(const __grid_constant__ FusedArgs a) {
-  constexpr int NT = TW / 2;
-  __shared__ LayerTW s_tw[MAX_LAYERS];
-  __shared__ float4 s_cf[MAX_LAYERS][(2 * S + 3) / 4];   // per layer: X_s (1 - w), X_s w, s = 0 .. S-1
-  __shared__ float s_y[MAX_LAYERS];                       // (c2 / T) log2(e)
-  __shared__ float s_dpg[MAX_LAYERS];
-  __shared__ float s_xs[S];
-  __shared__ float2 s_red[NT / 32 > 0 ? NT / 32 : 1][MAX_BANDS];
-  __shared__ unsigned long long s_unit;
-  __shared__ int s_last, s_ready;
-  constexpr bool WIDE_X = (MODE & 1) != 0, TAU_LIM = (MODE & 2) != 0;
-  const int tid = threadIdx.x;
-  const int L = a.L, nb = a.n_bands;
-  for (int k = tid; k + 1 < L; k += NT) s_dpg[k] = a.dpg[k];
-  const int64_t sstride = (int64_t)L * a.M * a.N;
-  const int64_t dm = (a.M > 1) ? a.N : 0;          // offset of the upper temperature bracket
-  // float2 grid reads need an even row length and an 8-byte aligned grid
-  const bool pair_loads = ((a.N & 1) == 0) && ((reinterpret_cast<uintptr_t>(a.grid) & 7) == 0);
-  // the epoch only changes when the last CTA of a launch leaves, so every CTA
-  // of this launch reads the same value
-  const unsigned int ready_mark = (unsigned int)*(volatile unsigned long long*)(a.work + 2) + 1u;
-  unsigned long long next_unit = 0;
-  if (tid == 0) next_unit = atomicAdd(a.work, 1ULL);
-
-  for (;;) {
-    if (tid == 0) {
-      s_unit = next_unit;
-      next_unit = atomicAdd(a.work, 1ULL);       // the following unit, fetched while this one runs
-    }
-    __syncthreads();
-    const unsigned long long u = s_unit;
-    if (u >= a.n_units) break;
-    const int p = (int)(u % (unsigned long long)a.n);
-    const int grp = (int)(u / (unsigned long long)a.n);
-    // every value below is uniform over the CTA
-    bool skip = a.active && !a.active[p];
-    int64_t lo = 0, hi = a.N;
-    if (!skip) {
-      lo = a.nu_lo ? a.nu_lo[p] : 0;
-      hi = a.nu_hi ? a.nu_hi[p] : a.N;
-      if (lo < 0 || hi > a.N || lo >= hi) {
-        // invalid span: report it once, band values 0, spectrum untouched
-        if (grp == 0) {
-          if (tid == 0) atomicOr(a.status, BART_DEV_RANGE);
-          if (a.bands && tid < nb) a.bands[(int64_t)p * nb + tid] = 0.0f;
-        }
-        skip = true;
-      }
-    }
-    const int64_t lo2 = lo & ~(int64_t)1;          // tiles start on even indices (pairs)
-    const int n_tiles_p = skip ? 0 : (int)((hi - lo2 + TW - 1) / TW);
-    const int n_groups_p = (n_tiles_p + a.tpu - 1) / a.tpu;
-    if (!skip && grp < n_groups_p) {
-      // 1. the proposal's layers: T(P) (or the given profile), bracket, c2/T,
-      // computed by the first unit of the proposal and published for the
-      // others (a unit that finds them unpublished computes them itself)
-      if (tid == 0) s_ready = (ld_acquire(a.tw_flag + p) == ready_mark);
-      if (tid < S) {
-        const float ab = a.theta ? a.theta[(int64_t)p * a.n_theta + 5 + tid] : 0.0f;
-        s_xs[tid] = a.x0mu[tid] * exp10f(ab);
-      }
-      __syncthreads();
-      if (s_ready) {
-        for (int k = tid; k < L; k += NT) {
-          // one 16-byte L2 load per layer state: row (two words), w, c2/T
-          const int4 v = __ldcg(reinterpret_cast<const int4*>(a.tw_cache + (int64_t)p * L + k));
-          LayerTW r;
-          r.row = (int64_t)(((unsigned long long)(unsigned int)v.y << 32) | (unsigned int)v.x);
-          r.w = __int_as_float(v.z);
-          r.c2_t = __int_as_float(v.w);
-          s_tw[k] = r;
-        }
-      } else {
-        for (int k = tid; k < L; k += NT) {
-          float T;
-          if (a.t_profile) {
-            T = a.t_profile[(int64_t)p * L + k];
-          } else {
-            float th[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) th[i] = a.theta[(int64_t)p * a.n_theta + i];
-            T = bartf::tp_temperature(th, a.p_cgs[k], a.inv_g, a.tint4, a.tirr0);
-          }
-          const LayerTW r = layer_state(T, k, a.t_axis, a.M, a.N, a.t_min, a.t_max, a.status);
-          s_tw[k] = r;
-          a.tw_cache[(int64_t)p * L + k] = r;
-        }
-        __syncthreads();
-        if (tid == 0) st_release(a.tw_flag + p, ready_mark);   // publishes the CTA's stores above
-      }
-      __syncthreads();
-      // per layer: the interpolation weights times the abundance coefficients
-      // (chi = sum_s X_s (1 - w) sigma_lo + X_s w sigma_hi) and the Planck exponent
-      for (int k = tid; k < L; k += NT) {
-        const float w = s_tw[k].w;
-        float cf[4 * ((2 * S + 3) / 4)] = {};
-#pragma unroll
-        for (int q = 0; q < S; ++q) {
-          cf[2 * q] = s_xs[q] * (1.0f - w);
-          cf[2 * q + 1] = s_xs[q] * w;
-        }
-#pragma unroll
-        for (int q = 0; q < (2 * S + 3) / 4; ++q) s_cf[k][q] = make_float4(cf[4 * q], cf[4 * q + 1], cf[4 * q + 2], cf[4 * q + 3]);
-        s_y[k] = s_tw[k].c2_t * LOG2E;
-      }
-      __syncthreads();
-      float2 band_acc = make_float2(0.f, 0.f);      // thread b < nb: band b over the unit's tiles
-      const int t_end = min((grp + 1) * a.tpu, n_tiles_p);
-
-      for (int tile = grp * a.tpu; tile < t_end; ++tile) {
-        // 2. the columns of wavenumbers ja and ja + 1
-        const int64_t ja = lo2 + (int64_t)tile * TW + 2 * tid, jb = ja + 1;
-        const bool act_a = ja >= lo && ja < hi, act_b = jb < hi;
-        // idle lanes compute on valid indices
-        const int64_t ka = (ja < hi) ? ja : lo2, kb = (jb < hi) ? jb : ka;
-        const double nua = a.nu_start + (double)ka * a.dnu, nub = a.nu_start + (double)kb * a.dnu;
-        const float2 c1nu3 = make_float2((float)(2.0 * bartc::H * bartc::C * bartc::C * nua * nua * nua),
-                                         (float)(2.0 * bartc::H * bartc::C * bartc::C * nub * nub * nub));
-        const float2 nuf = make_float2((float)nua, (float)nub);
-        // Rayleigh a nu^4 / (mu m_u)
-        const float2 chi_r = make_float2((float)(a.ex.ray * (nua * nua) * (nua * nua)),
-                                         (float)(a.ex.ray * (nub * nub) * (nub * nub)));
-        // per angle the log2 transmittance to the current level (a sum of
-        // positive optical-depth terms times -log2(e)/mu); the flux needs the
-        // transmittances only through their quadrature sum
-        // Tw = sum_i 2 pi w_i mu_i / 2 t_i, so F = sum_k (B_{k-1} + B_k)
-        // (Tw_{k-1} - Tw_k) + 2 B_bottom Tw_bottom
-        float2 lt[NA];
-#pragma unroll
-        for (int i = 0; i < NA; ++i) lt[i] = f2(0.0f);
-        float2 Tw_prev = f2(a.tw_top), F = f2(0.0f);
-        const float* ga = a.grid + ka;
-        const float* gb = a.grid + kb;
-        const int L_run = a.ex.L_run;
-        // grid values of a layer for both wavenumbers: lower (x) and upper (y)
-        // temperature bracket per species
-        auto fetch = [&](int k, float2* x, float2* y) {
-          const int64_t row = s_tw[k].row;
-          if (pair_loads) {                        // ka is even and ka + 1 < N here
-#pragma unroll
-            for (int q = 0; q < S; ++q) {
-              x[q] = __ldg(reinterpret_cast<const float2*>(ga + row + q * sstride));
-              y[q] = __ldg(reinterpret_cast<const float2*>(ga + row + q * sstride + dm));
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < S; ++q) {
-              x[q] = make_float2(__ldg(ga + row + q * sstride), __ldg(gb + row + q * sstride));
-              y[q] = make_float2(__ldg(ga + row + q * sstride + dm), __ldg(gb + row + q * sstride + dm));
-            }
-          }
-        };
-        auto chi_of = [&](int k, const float2* x, const float2* y) {
-          float cf[4 * ((2 * S + 3) / 4)];
-#pragma unroll
-          for (int q = 0; q < (2 * S + 3) / 4; ++q) {
-            const float4 v = s_cf[k][q];
-            cf[4 * q] = v.x;
-            cf[4 * q + 1] = v.y;
-            cf[4 * q + 2] = v.z;
-            cf[4 * q + 3] = v.w;
-          }
-          float2 chi = chi_r;
-#pragma unroll
-          for (int q = 0; q < S; ++q) {
-            chi = fma2(f2(cf[2 * q]), x[q], chi);
-            chi = fma2(f2(cf[2 * q + 1]), y[q], chi);
-          }
-          return chi;
-        };
-        float2 cx[S], cy[S], nx[S], ny[S];
-        fetch(0, cx, cy);
-        fetch(min(1, L_run - 1), nx, ny);
-        float2 chi_prev = chi_of(0, cx, cy);
-        float2 B_prev = planck2<WIDE_X>(c1nu3, mul2(nuf, f2(s_y[0])));
-        float2 tau_v = f2(0.0f);                   // vertical optical depth from the top
-        bool done_a = false, done_b = false;       // lane reached the optical-depth limit
-#pragma unroll 2
-        for (int k = 1; k < L_run; ++k) {
-#pragma unroll
-          for (int q = 0; q < S; ++q) {
-            cx[q] = nx[q];
-            cy[q] = ny[q];
-          }
-          fetch(min(k + 1, L_run - 1), nx, ny);    // the next layer's rows are in flight meanwhile
-          const float2 chi = chi_of(k, cx, cy);
-          const float2 B = planck2<WIDE_X>(c1nu3, mul2(nuf, f2(s_y[k])));
-          const float2 dtau = mul2(add2(chi_prev, chi), f2(s_dpg[k - 1]));
-          const float2 Bsum = add2(B_prev, B);
-          float2 Tw0 = f2(0.0f), Tw1 = f2(0.0f);    // two partial sums: a shorter dependence chain
-#pragma unroll
-          for (int i = 0; i < NA; ++i) {
-            lt[i] = fma2(dtau, f2(a.ang[i]), lt[i]);
-            if (i & 1) Tw1 = fma2(f2(a.ang[NA + i]), ex2_2(lt[i]), Tw1);
-            else Tw0 = fma2(f2(a.ang[NA + i]), ex2_2(lt[i]), Tw0);
-          }
-          const float2 Tw = add2(Tw0, Tw1);
-          const float2 Fn = fma2(Bsum, sub2(Tw_prev, Tw), F);
-          chi_prev = chi;
-          if (!TAU_LIM) {
-            F = Fn;
-            Tw_prev = Tw;
-            B_prev = B;
-          } else {
-            // Sec. 4 item 7: stop at the caller's optical-depth limit; the level
-            // reached is the bottom boundary (its blackbody below).  Each
-            // wavenumber of the pair keeps its state from the level where it
-            // stopped while the other goes on.
-            if (!done_a) {
-              F.x = Fn.x;
-              Tw_prev.x = Tw.x;
-              B_prev.x = B.x;
-            }
-            if (!done_b) {
-              F.y = Fn.y;
-              Tw_prev.y = Tw.y;
-              B_prev.y = B.y;
-            }
-            tau_v = add2(tau_v, dtau);
-            done_a = done_a || tau_v.x > a.ex.tau_cut;
-            done_b = done_b || tau_v.y > a.ex.tau_cut;
-            if (done_a && done_b) break;
-          }
-        }
-        F = fma2(mul2(f2(2.0f), B_prev), Tw_prev, F);   // the bottom level's blackbody through the column
-        if (a.spectra) {
-          const int64_t base = (a.offs ? a.offs[p] : (int64_t)p * a.N) - lo;
-          if (act_a) a.spectra[base + ja] = F.x;
-          if (act_b) a.spectra[base + jb] = F.y;
-        }
-
-        // 3. band sums of the tile, added to the unit's
-        if (nb > 0) {
-          const float dwa = act_a ? ((hi - lo == 1) ? 1.0f : ((ja == lo || ja == hi - 1) ? 0.5f : 1.0f)) : 0.0f;
-          const float dwb = act_b ? ((hi - lo == 1) ? 1.0f : ((jb == lo || jb == hi - 1) ? 0.5f : 1.0f)) : 0.0f;
-          const int warp = tid >> 5, lane = tid & 31;
-          for (int b = 0; b < nb; ++b) {
-            const float Wa = act_a ? __ldg(a.filt + (int64_t)b * a.N + ja) * dwa : 0.0f;
-            const float Wb = act_b ? __ldg(a.filt + (int64_t)b * a.N + jb) * dwb : 0.0f;
-            float num = fmaf(Wa, F.x, Wb * F.y), den = Wa + Wb;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              num += __shfl_xor_sync(0xffffffffu, num, o);
-              den += __shfl_xor_sync(0xffffffffu, den, o);
-            }
-            if (lane == 0) s_red[warp][b] = make_float2(num, den);
-          }
-          __syncthreads();
-          if (tid < nb) {
-#pragma unroll
-            for (int w = 0; w < NT / 32; ++w) {
-              band_acc.x += s_red[w][tid].x;
-              band_acc.y += s_red[w][tid].y;
-            }
-          }
-          __syncthreads();                         // s_red is rewritten by the next tile
-        }
-      }
-
-      // the unit's band partials; the proposal's last unit reduces them
-      if (nb > 0) {
-        if (tid < nb) a.partial[((int64_t)p * a.n_groups + grp) * nb + tid] = band_acc;
-        __syncthreads();
-        if (tid == 0) s_last = (add_acq_rel(a.p_done + p, 1u) + 1u == (unsigned)n_groups_p);
-        __syncthreads();
-        if (s_last) {
-          if (tid < nb) {
-            double num = 0.0, den = 0.0;
-            for (int q = 0; q < n_groups_p; ++q) {
-              const float2 v = __ldcg(a.partial + ((int64_t)p * a.n_groups + q) * nb + tid);
-              num += v.x;
-              den += v.y;
-            }
-            a.bands[(int64_t)p * nb + tid] = den > 0.0 ? (float)(num / den) : 0.0f;
-          }
-          if (tid == 0) a.p_done[p] = 0u;           // ready for the next launch
-        }
-      }
-    }
-    __syncthreads();                               // shared state is reused by the next unit
-  }
-  // the last CTA to leave resets the counters for the next launch
-  if (tid == 0) {
-    __threadfence();
-    if (atomicAdd(a.work + 1, 1ULL) + 1ULL == (unsigned long long)gridDim.x) {
-      a.work[0] = 0ULL;
-      a.work[1] = 0ULL;
-      a.work[2] += 1ULL;                          // new epoch: published layer states expire
-      __threadfence();
-    }
-  }
-}
-
-using FusedLauncher = cudaError_t (*)(const FusedArgs&, int, cudaStream_t);
-
-template <int S, int NA, int TW, int MODE>
-cudaError_t launch_fused(const FusedArgs& a, int sm_count, cudaStream_t st) {
-  int per_sm = 0;
-  cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emission_fused_kernel<S, NA, TW, MODE>, TW / 2, 0);
-  if (e != cudaSuccess) return e;
-  unsigned long long grid = (unsigned long long)(per_sm < 1 ? 1 : per_sm) * (unsigned long long)sm_count;
-  if (grid > a.n_units) grid = a.n_units;
-  emission_fused_kernel<S, NA, TW, MODE><<<(unsigned)grid, TW / 2, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-// Wavenumbers per tile the autotuner chooses from (two per thread; at least
-// 128, so a CTA has a thread for each of up to 64 bands).
-constexpr int FUSED_TILES[3] = {128, 256, 512};
-
-template <int S, int NA, int MODE>
-FusedLauncher pick_tw(int tw) {
-  switch (tw) {
-    case 128: return launch_fused<S, NA, 128, MODE>;
-    case 256: return launch_fused<S, NA, 256, MODE>;
-    case 512: return launch_fused<S, NA, 512, MODE>;
-    default: return nullptr;
-  }
-}
-
-template <int S, int MODE>
-FusedLauncher pick_angles(int na, int tw) {
-  switch (na) {
-    case 1: return pick_tw<S, 1, MODE>(tw);
-    case 2: return pick_tw<S, 2, MODE>(tw);
-    case 4: return pick_tw<S, 4, MODE>(tw);
-    case 8: return pick_tw<S, 8, MODE>(tw);
-    case 16: return pick_tw<S, 16, MODE>(tw);
-    default: return nullptr;
-  }
-}
-
-template <int S>
-FusedLauncher pick_fused_mode(int na, int tw, int mode) {
-  switch (mode) {
-    case 0: return pick_angles<S, 0>(na, tw);
-    case 1: return pick_angles<S, 1>(na, tw);
-    case 2: return pick_angles<S, 2>(na, tw);
-    default: return pick_angles<S, 3>(na, tw);
-  }
-}
-
-FusedLauncher pick_fused(int S, int na, int tw, int mode) {
+FusedLauncher pick_fused(int S, int na, bool tma, int tw, int mode) {
   switch (S) {
-    case 1: return pick_fused_mode<1>(na, tw, mode);
-    case 2: return pick_fused_mode<2>(na, tw, mode);
-    case 3: return pick_fused_mode<3>(na, tw, mode);
-    case 4: return pick_fused_mode<4>(na, tw, mode);
+    case 1: return fused_launcher<1>(na, tma, tw, mode);
+    case 2: return fused_launcher<2>(na, tma, tw, mode);
+    case 3: return fused_launcher<3>(na, tma, tw, mode);
+    case 4: return fused_launcher<4>(na, tma, tw, mode);
     default: return nullptr;
   }
 }
@@ -494,7 +31,11 @@ bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const
   const int S = g->n_species, L = g->n_layers, M = g->n_temps, n = b->n, NA = c->n_angles;
   const int64_t N = g->nu.n_nu;
   const int mode = emission_mode(g, c);
-  if (S > FUSED_MAX_SPECIES || !pick_fused(S, NA, FUSED_TILES[1], mode))
+  // the bulk-copy variant on request, where its 16-byte row starts hold:
+  // n_nu a multiple of 4 and an aligned grid
+  const bool tma = ctx->em_launch == BART_LAUNCH_FUSED_TMA && (N % 4 == 0) &&
+                   (reinterpret_cast<uintptr_t>(g->grid) % 16 == 0);
+  if (S > FUSED_MAX_SPECIES || !pick_fused(S, NA, tma, FUSED_TILES[1], mode))
     return bart_fail(ctx, BART_EUNSUPPORTED, "emission with %d species and %d angles is not instantiated "
                      "(species 1-4; angles 1, 2, 4, 8, 16)", S, NA);
   bart_status st;
@@ -511,7 +52,7 @@ bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const
   if ((st = bart_scratch(ctx, "ff_work", 3 * sizeof(unsigned long long), &p_work)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "ff_twc", (size_t)n * L * sizeof(LayerTW), &p_twc)) != BART_OK) return st;
   if ((st = bart_scratch(ctx, "ff_flag", (size_t)n * sizeof(unsigned int), &p_flag)) != BART_OK) return st;
-  const int max_tiles = (int)((N + 1 + FUSED_TILES[0] - 1) / FUSED_TILES[0]);   // smallest tile, even start
+  const int max_tiles = (int)((N + 3 + FUSED_TILES[0] - 1) / FUSED_TILES[0]);   // smallest tile, aligned start
   if (nb > 0) {
     if ((st = bart_scratch(ctx, "ff_done", (size_t)n * sizeof(unsigned int), &p_done)) != BART_OK) return st;
     if ((st = bart_scratch(ctx, "fw_part", (size_t)n * max_tiles * nb * sizeof(float2), &p_part)) != BART_OK)
@@ -563,17 +104,19 @@ bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const
   a.tw_flag = (unsigned int*)p_flag;
   a.status = ctx->d_status;
   a.ex = emission_extra(g, c);
+  a.wide_x = (mode & 1) != 0;
+  a.tau_lim = (mode & 2) != 0;
 
   auto run = [&](int tw) -> bart_status {
     // several consecutive tiles per unit amortise the unit's fixed work (layer
     // states, band partials and counts), as long as there are enough units to
     // balance the CTAs (about 8 per CTA of a full grid)
-    const int n_tiles = (int)((N + 1 + tw - 1) / tw);                // spans start on an even index
+    const int n_tiles = (int)((N + 3 + tw - 1) / tw);                // tiles start on an aligned index
     const long long target = 8LL * ctx->sm_count * (2 * FUSED_OCC_THREADS / tw);
     a.tpu = (int)std::max(1LL, std::min<long long>(MAX_TILES_PER_UNIT, (long long)n * n_tiles / target));
     a.n_groups = (n_tiles + a.tpu - 1) / a.tpu;
     a.n_units = (unsigned long long)a.n_groups * (unsigned long long)n;
-    cudaError_t e = pick_fused(S, NA, tw, mode)(a, ctx->sm_count, ctx->stream);
+    cudaError_t e = pick_fused(S, NA, tma, tw, mode)(a, ctx->sm_count, ctx->stream);
     if (e != cudaSuccess) return bart_fail(ctx, BART_ECUDA, "launch of emission_fused_kernel failed: %s",
                                            cudaGetErrorString(e));
     return BART_OK;
@@ -581,10 +124,10 @@ bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const
   // tile width: fixed by the caller, cached per shape, or measured once
   // (each candidate timed with CUDA events on the stream) outside a capture
   char key[160];
-  snprintf(key, sizeof(key), "fused S%d A%d L%d/%d M%d N%lld n%d b%d span%d m%d", S, NA, L, a.ex.L_run, M,
-           (long long)N, n, nb, b->nu_lo ? 1 : 0, mode);
+  snprintf(key, sizeof(key), "fused%s S%d A%d L%d/%d M%d N%lld n%d b%d span%d m%d", tma ? " tma" : "", S, NA, L,
+           a.ex.L_run, M, (long long)N, n, nb, b->nu_lo ? 1 : 0, mode);
   // the caller's width is in threads of the one-wavenumber-per-thread
-  // kernels; here a thread takes two
+  // kernels; here a compute thread takes two
   int tw = ctx->em_tile > 0 ? 2 * ctx->em_tile : FUSED_TILES[1];
   auto it = ctx->tiles.find(key);
   if (ctx->em_tile > 0) {

@@ -43,6 +43,8 @@ struct bart_mlp {
   std::vector<int64_t> z_off, h_off;
   float* scale = nullptr;              // in_shift[in], in_scale[in], out_shift[out], out_scale[out]
   float* loss = nullptr;
+  float* xg = nullptr;                 // gathered batch inputs [max_batch][in] (bart_mlp_train_steps)
+  float* tg = nullptr;                 // gathered batch targets [max_batch][out]
 };
 
 namespace {
@@ -323,6 +325,22 @@ __global__ void to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// dst[b][c] = src[idx[b]][c]; an index outside [0, n_rows) is reported and
+// row 0 is taken instead.
+__global__ void gather_rows(const float* __restrict__ src, int64_t n_rows, int n_cols,
+                            const int32_t* __restrict__ idx, int B, float* __restrict__ dst,
+                            int* __restrict__ status) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)B * n_cols) return;
+  const int b = (int)(e / n_cols), c = (int)(e % n_cols);
+  int64_t r = idx[b];
+  if (r < 0 || r >= n_rows) {
+    atomicOr(status, BART_DEV_RANGE);
+    r = 0;
+  }
+  dst[e] = src[r * n_cols + c];
+}
+
 // SIMT FP32 GEMM (the FP32-weight mode)
 template <typename TA, typename TB>
 void gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
@@ -445,7 +463,9 @@ extern "C" bart_status bart_mlp_create(bart_ctx* ctx, const int32_t* widths, int
   bool ok = cudaMalloc(&net->p, o * 4) == cudaSuccess && cudaMalloc(&net->m, o * 4) == cudaSuccess &&
             cudaMalloc(&net->v, o * 4) == cudaSuccess && cudaMalloc(&net->g, o * 4) == cudaSuccess &&
             cudaMalloc(&net->wb, o * 2) == cudaSuccess && cudaMalloc(&net->act, a * 4) == cudaSuccess &&
-            cudaMalloc(&net->scale, n_scale * 4) == cudaSuccess && cudaMalloc(&net->loss, 4) == cudaSuccess;
+            cudaMalloc(&net->scale, n_scale * 4) == cudaSuccess && cudaMalloc(&net->loss, 4) == cudaSuccess &&
+            cudaMalloc(&net->xg, (size_t)max_batch * widths[0] * 4) == cudaSuccess &&
+            cudaMalloc(&net->tg, (size_t)max_batch * widths[n_widths - 1] * 4) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     bart_mlp_destroy(net);
@@ -468,7 +488,7 @@ extern "C" void bart_mlp_destroy(bart_mlp* net) {
   cudaSetDevice(net->ctx->device);
   cudaStreamSynchronize(net->ctx->stream);
   for (void* q : {(void*)net->p, (void*)net->m, (void*)net->v, (void*)net->g, (void*)net->wb, (void*)net->act,
-                  (void*)net->scale, (void*)net->loss})
+                  (void*)net->scale, (void*)net->loss, (void*)net->xg, (void*)net->tg})
     if (q) cudaFree(q);
   delete net;
 }
@@ -541,13 +561,11 @@ extern "C" bart_status bart_mlp_gradient(bart_mlp* net, const float* x, const fl
   return BART_OK;
 }
 
-extern "C" bart_status bart_mlp_train_step(bart_mlp* net, const float* x, const float* t, int B, float lr,
-                                           float* loss) {
-  if (!net) return BART_EINVAL;
-  BART_REQUIRE(net->ctx, x && t, "NULL x or t");
-  BART_REQUIRE(net->ctx, lr > 0 && std::isfinite(lr), "lr must be > 0");
-  bart_status st = check_batch(net, B);
-  if (st != BART_OK) return st;
+namespace {
+
+// One Adam step on the batch (x, t): gradient, moments, BF16 copy.
+bart_status adam_step(bart_mlp* net, const float* x, const float* t, int B, float lr, float* loss) {
+  bart_status st;
   if ((st = backward(net, x, t, B, loss)) != BART_OK) return st;
   net->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -558,4 +576,39 @@ extern "C" bart_status bart_mlp_train_step(bart_mlp* net, const float* x, const 
                                                             b2, 1e-8f, c1, c2);
   to_bf16<<<blocks_for(net->n_params, 256), 256, 0, s>>>(net->p, net->wb, net->n_params);
   return bart_check_launch(net->ctx, "adam");
+}
+
+}  // namespace
+
+extern "C" bart_status bart_mlp_train_step(bart_mlp* net, const float* x, const float* t, int B, float lr,
+                                           float* loss) {
+  if (!net) return BART_EINVAL;
+  BART_REQUIRE(net->ctx, x && t, "NULL x or t");
+  BART_REQUIRE(net->ctx, lr > 0 && std::isfinite(lr), "lr must be > 0");
+  bart_status st = check_batch(net, B);
+  if (st != BART_OK) return st;
+  return adam_step(net, x, t, B, lr, loss);
+}
+
+extern "C" bart_status bart_mlp_train_steps(bart_mlp* net, const float* x, const float* t, int64_t n_rows,
+                                            const int32_t* batch_rows, int B, int n_steps, const float* lr,
+                                            float* loss) {
+  if (!net) return BART_EINVAL;
+  BART_REQUIRE(net->ctx, x && t && batch_rows && lr, "NULL x, t, batch_rows or lr");
+  BART_REQUIRE(net->ctx, n_rows >= 1 && n_steps >= 0, "n_rows must be >= 1 and n_steps >= 0");
+  bart_status st = check_batch(net, B);
+  if (st != BART_OK) return st;
+  for (int k = 0; k < n_steps; ++k)
+    BART_REQUIRE(net->ctx, lr[k] > 0 && std::isfinite(lr[k]), "lr[%d] must be > 0", k);
+  const int ni = net->widths[0], no = net->widths[net->n_layers];
+  cudaStream_t s = net->ctx->stream;
+  for (int k = 0; k < n_steps; ++k) {
+    const int32_t* rows = batch_rows + (int64_t)k * B;
+    gather_rows<<<blocks_for((int64_t)B * ni, 256), 256, 0, s>>>(x, n_rows, ni, rows, B, net->xg,
+                                                                 net->ctx->d_status);
+    gather_rows<<<blocks_for((int64_t)B * no, 256), 256, 0, s>>>(t, n_rows, no, rows, B, net->tg,
+                                                                 net->ctx->d_status);
+    if ((st = adam_step(net, net->xg, net->tg, B, lr[k], loss ? loss + k : nullptr)) != BART_OK) return st;
+  }
+  return bart_check_launch(net->ctx, "mlp train steps");
 }

@@ -66,7 +66,8 @@ def test_emission_generation_shape(ctx, torch, field4, S):
     spec_o, bands_o = _oracle_emission(grid_np.astype(np.float64), ax, theta, S, filt)
     nu = bart.NuGrid(ax.nu_start, ax.dnu, N_SLICE)
     th, fl = torch.tensor(theta, device="cuda"), torch.tensor(filt, device="cuda")
-    for launch in (bart.BART_LAUNCH_FUSED, bart.BART_LAUNCH_SPLIT):
+    names = {bart.BART_LAUNCH_FUSED: "fused", bart.BART_LAUNCH_SPLIT: "split", bart.BART_LAUNCH_FUSED_TMA: "tma"}
+    for launch in (bart.BART_LAUNCH_FUSED, bart.BART_LAUNCH_SPLIT, bart.BART_LAUNCH_FUSED_TMA):
         ctx.set_emission_launch(launch)
         for tile in (64, 128, 256, 0):
             ctx.set_emission_tile(tile)
@@ -77,7 +78,7 @@ def test_emission_generation_shape(ctx, torch, field4, S):
                                           filters=fl, bands=bands)
             ctx.sync()
             es, eb = max_rel(spec.cpu().numpy(), spec_o), max_rel(bands.cpu().numpy(), bands_o)
-            print(f"emission S={S} {'fused' if launch == 0 else 'split'} tile={tile or 'auto'}: "
+            print(f"emission S={S} {names[launch]} tile={tile or 'auto'}: "
                   f"FP32 vs FP64 spectra {es:.2e}, bands {eb:.2e}")
             assert es < RTOL and eb < RTOL, (launch, tile, es, eb)
     ctx.set_emission_tile(0)

@@ -112,3 +112,24 @@ def test_training_reduces_loss(ctx, torch):
     l1 = float(loss.cpu())
     print(f"training: loss {l0:.3e} -> {l1:.3e}")
     assert l1 < 0.05 * l0
+
+
+def test_train_steps_equal_single_steps(ctx, torch):
+    """bart_mlp_train_steps (the step loop in the library, batches gathered
+    on the device) gives the parameters of the same sequence of single
+    bart_mlp_train_step calls, bit for bit."""
+    th, t = _data(600, seed=3)
+    x_dev, t_dev = torch.tensor(th, device="cuda"), torch.tensor(t, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(11)
+    rows = torch.randint(0, 600, (5, 128), device="cuda", generator=g, dtype=torch.int32)
+    lrs = [1e-3, 8e-4, 6e-4, 4e-4, 2e-4]
+    a = _net(ctx, torch, True, W.mlp_init(WIDTHS))
+    loss = torch.empty(5, device="cuda")
+    a.train_steps(x_dev, t_dev, rows, lrs, loss)
+    b = _net(ctx, torch, True, W.mlp_init(WIDTHS))
+    for k in range(5):
+        r = rows[k].long()
+        b.train_step(x_dev[r].contiguous(), t_dev[r].contiguous(), lrs[k])
+    ctx.sync()
+    assert torch.equal(a.get_params(), b.get_params())
+    assert torch.isfinite(loss).all()
