@@ -53,7 +53,8 @@ KERNELS_PER_STEP = 3 * 3 + 1      # per species: window and span prologues + opa
 OPACITY_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
                    for f in ("opacity.cu", "faddeeva.cuh", "bart_internal.cuh")]
 FORWARD_SOURCES = [os.path.join(ROOT, "paper_2104_12522_gb300", "csrc", f)
-                   for f in ("forward_fused.cu", "emission.cuh", "forward.cuh", "bart_internal.cuh")]
+                   for f in ("emission_fused.cuh", "forward_fused.cu", "emission.cuh", "forward.cuh",
+                             "bart_internal.cuh")]
 MUFU_PER_CLK = 32                 # MUFU (ex2, rcp) results per clock per SM on GB300 (ncu: XU-pipe peak 1 warp-inst/clk/SM)
 
 
@@ -1385,6 +1386,34 @@ def run_generation_case(args):
     return 0
 
 
+def run_mlp_case(args):
+    """The surrogate's training step alone (9 -> 256 -> 256 -> 256 -> 10,
+    batch 1,024, BF16 weights) for captures of its tensor-core GEMMs: 64
+    steps through bart_mlp_train_steps on seeded inputs and targets."""
+    import torch
+    from paper_2104_12522_gb300 import build
+    build.build()
+    import paper_2104_12522_gb300 as bart
+    ctx = bart.Context(0)
+    dev = torch.device("cuda", 0)
+    widths = list(W.SURROGATE_WIDTHS)
+    net = bart.Mlp(ctx, widths, bf16_weights=True, log_outputs=True, max_batch=1024)
+    lo, hi = W.THETA_LO.astype(np.float32), W.THETA_HI.astype(np.float32)
+    net.set_scaling(0.5 * (lo + hi), 2.0 / (hi - lo), np.full(10, 4.0, np.float32), np.full(10, 2.0, np.float32))
+    net.set_params(torch.tensor(W.mlp_init(widths), device=dev))
+    x = torch.tensor(W.proposals(8192, generation=100, n_species=4), device=dev)
+    t = torch.tensor((10 ** np.random.default_rng(5).uniform(3.5, 4.5, (8192, 10))).astype(np.float32), device=dev)
+    g = torch.Generator(device=dev).manual_seed(1)
+    rows = torch.randint(0, 8192, (64, 1024), device=dev, generator=g, dtype=torch.int32)
+    net.train_steps(x, t, rows, [1e-3] * 64)
+    stream = torch.cuda.current_stream(dev)
+    ms = _event_ms(torch, stream, lambda: net.train_steps(x, t, rows, [1e-3] * 64))
+    ctx.sync()
+    flops = 6 * 1024 * sum(widths[l] * widths[l + 1] for l in range(len(widths) - 1)) * 64
+    print(json.dumps({"train_ms_per_step": ms / 64, "train_tflops": flops / (ms / 1e3) / 1e12}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1400,10 +1429,11 @@ def main():
     ap.add_argument("--burn", type=int, default=3000, help="exact-model burn-in generations before the retrieval legs")
     ap.add_argument("--screen-beta", type=float, default=1.0)
     ap.add_argument("--screen-margin", type=float, default=1.0)
-    ap.add_argument("--case", choices=["bench", "profile", "transmission", "generation"], default="bench",
+    ap.add_argument("--case", choices=["bench", "profile", "transmission", "generation", "mlp"], default="bench",
                     help="profile: small launches of the hot kernels for ncu; transmission: the "
                          "1,024-instance transmission batch alone; generation: the fused 2,048-proposal "
-                         "generation alone on a full-size grid of seeded values")
+                         "generation alone on a full-size grid of seeded values; mlp: 64 surrogate training "
+                         "steps")
     ap.add_argument("--tile", type=int, default=0, help="emission tile width for --case profile/generation "
                                                           "(0: default / autotuner)")
     args = ap.parse_args()
@@ -1411,6 +1441,8 @@ def main():
         return run_profile_case(args)
     if args.case == "generation":
         return run_generation_case(args)
+    if args.case == "mlp":
+        return run_mlp_case(args)
     if args.case == "transmission":
         return run_transmission_case(args)
     if args.warmup < 3:

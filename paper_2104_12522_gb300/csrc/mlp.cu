@@ -18,6 +18,7 @@
 // per thread), the reference precision of the gradient tests.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -43,6 +44,8 @@ struct bart_mlp {
   std::vector<int64_t> z_off, h_off;
   float* scale = nullptr;              // in_shift[in], in_scale[in], out_shift[out], out_scale[out]
   float* loss = nullptr;
+  float* part = nullptr;               // K-slice partial sums of the tensor-core GEMMs
+  int64_t part_elems = 0;
   float* xg = nullptr;                 // gathered batch inputs [max_batch][in] (bart_mlp_train_steps)
   float* tg = nullptr;                 // gathered batch targets [max_batch][out]
 };
@@ -154,11 +157,15 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
 // gemm_kernel.  A tile is kept as [m][k] and B as [n][k] in shared memory,
 // hi and lo parts apart; an FP32 operand contributes its lo part (a BF16 one
 // has none), so the MMAs per k16 step are hi*hi, lo_A*hi_B and hi_A*lo_B.
+// Split over K: CTA slice z (blockIdx.z) covers k in [z k_per, (z + 1) k_per);
+// with P set it writes its raw sums to P[z][M][N] (the epilogue then runs in
+// split_k_reduce), else it applies the epilogue itself.
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(TC_THREADS)
-tc_gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
-               int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc, int mode,
-               const float* __restrict__ bias, float* __restrict__ H, const float* __restrict__ Z) {
+tc_gemm_kernel(int M, int N, int K, int k_per, const TA* __restrict__ A, int64_t sam, int64_t sak,
+               const TB* __restrict__ B, int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc, int mode,
+               const float* __restrict__ bias, float* __restrict__ H, const float* __restrict__ Z,
+               float* __restrict__ P) {
   constexpr bool A_LO = !std::is_same<TA, __nv_bfloat16>::value;
   constexpr bool B_LO = !std::is_same<TB, __nv_bfloat16>::value;
   __shared__ __align__(16) __nv_bfloat16 sAh[TC_BM][TC_LDS], sAl[TC_BM][TC_LDS];
@@ -168,14 +175,15 @@ tc_gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64
   const int wm = warp >> 1, wn = warp & 1;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
   float acc[2][4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += TC_BK) {
+  const int k_begin = blockIdx.z * k_per, k_end = min(K, k_begin + k_per);
+  for (int k0 = k_begin; k0 < k_end; k0 += TC_BK) {
     // stage the tiles, the contiguous global index fastest
     for (int e = tid; e < TC_BM * TC_BK; e += TC_THREADS) {
       const int mm = (sak == 1) ? e / TC_BK : e % TC_BM;
       const int kk = (sak == 1) ? e % TC_BK : e / TC_BM;
       const int gm = m0 + mm, gk = k0 + kk;
       __nv_bfloat16 hi, lo;
-      if (gm < M && gk < K) split_bf16(A[gm * sam + gk * sak], hi, lo);
+      if (gm < M && gk < k_end) split_bf16(A[gm * sam + gk * sak], hi, lo);
       else hi = lo = __float2bfloat16_rn(0.0f);
       sAh[mm][kk] = hi;
       sAl[mm][kk] = lo;
@@ -185,7 +193,7 @@ tc_gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64
       const int kk = (sbk == 1) ? e % TC_BK : e / TC_BN;
       const int gn = n0 + nn, gk = k0 + kk;
       __nv_bfloat16 hi, lo;
-      if (gn < N && gk < K) split_bf16(B[gk * sbk + gn * sbn], hi, lo);
+      if (gn < N && gk < k_end) split_bf16(B[gk * sbk + gn * sbn], hi, lo);
       else hi = lo = __float2bfloat16_rn(0.0f);
       sBh[nn][kk] = hi;
       sBl[nn][kk] = lo;
@@ -239,6 +247,10 @@ tc_gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64
         const int gn = n0 + wn * 32 + j * 8 + tig * 2 + (q & 1);
         if (gm >= M || gn >= N) continue;
         float v = acc[i][j][q];
+        if (P) {
+          P[((int64_t)blockIdx.z * M + gm) * N + gn] = v;
+          continue;
+        }
         const int64_t o = (int64_t)gm * ldc + gn;
         if (mode == 1) {
           v += bias[gn];
@@ -252,6 +264,29 @@ tc_gemm_kernel(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64
           C[o] = v;
         }
       }
+}
+
+// Sum of the K slices in a fixed order, then the epilogue of tc_gemm_kernel.
+__global__ void split_k_reduce(int M, int N, int n_split, const float* __restrict__ P, float* __restrict__ C,
+                               int64_t ldc, int mode, const float* __restrict__ bias, float* __restrict__ H,
+                               const float* __restrict__ Z) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * N) return;
+  const int gm = (int)(e / N), gn = (int)(e % N);
+  float v = 0.0f;
+  for (int z = 0; z < n_split; ++z) v += P[(int64_t)z * M * N + e];
+  const int64_t o = (int64_t)gm * ldc + gn;
+  if (mode == 1) {
+    v += bias[gn];
+    C[o] = v;
+    H[o] = gelu(v);
+  } else if (mode == 2) {
+    C[o] = v + bias[gn];
+  } else if (mode == 3) {
+    C[o] = v * gelu_grad(Z[o]);
+  } else {
+    C[o] = v;
+  }
 }
 
 // x_scaled[b][i] = (x[b][i] - shift[i]) * scale[i]
@@ -296,13 +331,23 @@ __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict_
   if (threadIdx.x == 0 && loss) *loss = (float)(red[0] / ((double)B * n));
 }
 
-// db[n] = sum_b dz[b][n], fixed order per column.
+// db[n] = sum_b dz[b][n]: a CTA per 32 columns, 8 rows of threads each summing
+// every 8th row of its column (coalesced), then the 8 partial sums in order.
 __global__ void bias_grad(const float* __restrict__ dz, int B, int n, float* __restrict__ db) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  __shared__ float part[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + tx;
   float s = 0.f;
-  for (int b = 0; b < B; ++b) s += dz[(int64_t)b * n + j];
-  db[j] = s;
+  if (j < n)
+    for (int b = ty; b < B; b += 8) s += dz[(int64_t)b * n + j];
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && j < n) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][tx];
+    db[j] = t;
+  }
 }
 
 __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
@@ -350,13 +395,34 @@ void gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t sam, int64_
   gemm_kernel<TA, TB><<<grid, MLP_THREADS, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, mode, bias, H, Z);
 }
 
-// tensor-core GEMM (the BF16-weight mode)
+// Slices over K for a grid of n_tiles CTA tiles: enough CTAs to fill the SMs
+// about twice, each slice at least one K step.
+int k_slices(int n_tiles, int K, int sm_count) {
+  int z = 1;
+  while (z * 2 <= K / TC_BK && n_tiles * z * 2 <= 2 * sm_count) z *= 2;
+  return z;
+}
+
+// tensor-core GEMM (the BF16-weight mode), split over K when the tile grid
+// alone would leave SMs idle (the partial sums go to net->part)
 template <typename TA, typename TB>
-void tc_gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
+void tc_gemm(bart_mlp* net, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
              int64_t sbn, float* C, int64_t ldc, int mode, const float* bias = nullptr, float* H = nullptr,
              const float* Z = nullptr) {
-  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
-  tc_gemm_kernel<TA, TB><<<grid, TC_THREADS, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, mode, bias, H, Z);
+  cudaStream_t st = net->ctx->stream;
+  const int gx = (N + TC_BN - 1) / TC_BN, gy = (M + TC_BM - 1) / TC_BM;
+  int z = k_slices(gx * gy, K, net->ctx->sm_count);
+  while (z > 1 && (int64_t)z * M * N > net->part_elems) z /= 2;
+  const int k_per = ((K + z - 1) / z + TC_BK - 1) / TC_BK * TC_BK;
+  z = (K + k_per - 1) / k_per;
+  dim3 grid(gx, gy, z);
+  float* P = z > 1 ? net->part : nullptr;
+  tc_gemm_kernel<TA, TB><<<grid, TC_THREADS, 0, st>>>(M, N, K, k_per, A, sam, sak, B, sbk, sbn, C, ldc, mode, bias, H,
+                                                      Z, P);
+  if (P) {
+    const int64_t tot = (int64_t)M * N;
+    split_k_reduce<<<blocks_for(tot, 256), 256, 0, st>>>(M, N, z, P, C, ldc, mode, bias, H, Z);
+  }
 }
 
 // Forward pass of B rows already scaled into act layer 0; fills z/h of every layer.
@@ -371,7 +437,7 @@ void run_forward(bart_mlp* net, int B) {
     const float* bias = net->p + net->b_off[l];
     // z[b][o] = sum_i h_prev[b][i] W[o][i]
     if (net->bf16)
-      tc_gemm<float, __nv_bfloat16>(st, B, n_out, n_in, h_prev, n_in, 1, net->wb + net->w_off[l], 1, n_in, z,
+      tc_gemm<float, __nv_bfloat16>(net, B, n_out, n_in, h_prev, n_in, 1, net->wb + net->w_off[l], 1, n_in, z,
                                     n_out, mode, bias, h);
     else
       gemm<float, float>(st, B, n_out, n_in, h_prev, n_in, 1, net->p + net->w_off[l], 1, n_in, z, n_out, mode,
@@ -406,17 +472,17 @@ bart_status backward(bart_mlp* net, const float* x, const float* t, int B, float
     const float* h_prev = net->act + net->h_off[l];
     // dW[o][i] = sum_b dz[b][o] h_prev[b][i]
     if (net->bf16)
-      tc_gemm<float, float>(st, no, ni, B, dz, 1, no, h_prev, ni, 1, net->g + net->w_off[l], ni, 0);
+      tc_gemm<float, float>(net, no, ni, B, dz, 1, no, h_prev, ni, 1, net->g + net->w_off[l], ni, 0);
     else
       gemm<float, float>(st, no, ni, B, dz, 1, no, h_prev, ni, 1, net->g + net->w_off[l], ni, 0);
-    bias_grad<<<blocks_for(no, 128), 128, 0, st>>>(dz, B, no, net->g + net->b_off[l]);
+    bias_grad<<<blocks_for(no, 32), 256, 0, st>>>(dz, B, no, net->g + net->b_off[l]);
     if (l > 0) {
       // dh_prev[b][i] = sum_o dz[b][o] W[o][i]; then dz_prev = dh_prev * GELU'(z_prev)
       float* dz_prev = net->act + net->h_off[l];
       const float* z_prev = net->act + net->z_off[l];
       // h_prev (this slot) was consumed by the dW GEMM above, which runs first on the stream.
       if (net->bf16)
-        tc_gemm<float, __nv_bfloat16>(st, B, ni, no, dz, no, 1, net->wb + net->w_off[l], ni, 1, dz_prev, ni, 3,
+        tc_gemm<float, __nv_bfloat16>(net, B, ni, no, dz, no, 1, net->wb + net->w_off[l], ni, 1, dz_prev, ni, 3,
                                       nullptr, nullptr, z_prev);
       else
         gemm<float, float>(st, B, ni, no, dz, no, 1, net->p + net->w_off[l], ni, 1, dz_prev, ni, 3, nullptr,
@@ -460,10 +526,19 @@ extern "C" bart_status bart_mlp_create(bart_ctx* ctx, const int32_t* widths, int
     a += (int64_t)max_batch * widths[l];
   }
   const int n_scale = 2 * widths[0] + 2 * widths[n_widths - 1];
+  // K-slice partials: up to 16 slices of a weight-gradient GEMM [out][in], or
+  // of an activation GEMM [max_batch][width]
+  int64_t wmax = 0, amax = 0;
+  for (int l = 0; l < net->n_layers; ++l) {
+    wmax = std::max<int64_t>(wmax, (int64_t)widths[l] * widths[l + 1]);
+    amax = std::max<int64_t>(amax, (int64_t)max_batch * std::max(widths[l], widths[l + 1]));
+  }
+  net->part_elems = std::max(16 * wmax, 16 * amax);
   bool ok = cudaMalloc(&net->p, o * 4) == cudaSuccess && cudaMalloc(&net->m, o * 4) == cudaSuccess &&
             cudaMalloc(&net->v, o * 4) == cudaSuccess && cudaMalloc(&net->g, o * 4) == cudaSuccess &&
             cudaMalloc(&net->wb, o * 2) == cudaSuccess && cudaMalloc(&net->act, a * 4) == cudaSuccess &&
             cudaMalloc(&net->scale, n_scale * 4) == cudaSuccess && cudaMalloc(&net->loss, 4) == cudaSuccess &&
+            cudaMalloc(&net->part, (size_t)net->part_elems * 4) == cudaSuccess &&
             cudaMalloc(&net->xg, (size_t)max_batch * widths[0] * 4) == cudaSuccess &&
             cudaMalloc(&net->tg, (size_t)max_batch * widths[n_widths - 1] * 4) == cudaSuccess;
   if (!ok) {
@@ -488,7 +563,7 @@ extern "C" void bart_mlp_destroy(bart_mlp* net) {
   cudaSetDevice(net->ctx->device);
   cudaStreamSynchronize(net->ctx->stream);
   for (void* q : {(void*)net->p, (void*)net->m, (void*)net->v, (void*)net->g, (void*)net->wb, (void*)net->act,
-                  (void*)net->scale, (void*)net->loss, (void*)net->xg, (void*)net->tg})
+                  (void*)net->scale, (void*)net->loss, (void*)net->part, (void*)net->xg, (void*)net->tg})
     if (q) cudaFree(q);
   delete net;
 }
