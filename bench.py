@@ -1164,7 +1164,8 @@ def train_surrogate(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, n
 def run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net, generations, n_burn, beta,
                   margin):
     """DE-MC with 16 chains on synthetic band data (S/N = 50): an exact-model
-    burn-in, then plain and surrogate-screened runs from the same state."""
+    burn-in, then plain and surrogate-screened runs from the same state, and
+    the same pair with DEMCzs (4 chains, the burnt-in states as its archive)."""
     lo, hi = W.THETA_LO[:5 + S].astype(np.float32), W.THETA_HI[:5 + S].astype(np.float32)
     rng = np.random.default_rng(6500)
     truth = (lo + rng.uniform(0.3, 0.7, 5 + S) * (hi - lo)).astype(np.float32)
@@ -1194,23 +1195,25 @@ def run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net
     burn.get_state(xb_, Lb_)
     res["burn_in"] = {"generations": n_burn, "ms": burn_ms}
     kept = {}
-    for mode in ("plain", "screened", "demczs"):
+    for mode in ("plain", "screened", "demczs", "demczs_screened"):
         # DEMCzs (Sec. 4): 4 chains from the burnt-in state, its 16 states as the
         # initial archive, every chain moving at each of a generation's two steps
-        Cm = 4 if mode == "demczs" else C
+        zs, screened = mode.startswith("demczs"), mode.endswith("screened")
+        Cm = 4 if zs else C
         s = bart.Demc(ctx, Cm, lo, hi, jump_every=10, eps=1e-4, seed=6000)
         s.set_screen(beta, margin)
-        if mode == "demczs":
+        if zs:
             s.set_archive(xb_, capacity=C + Cm * (2 * generations // 10 + 1), thin=10, p_snooker=0.1)
         Ls0 = None
-        if mode == "screened":
+        if screened:
             Ls0 = torch.empty(C, dtype=torch.float64, device=dev)
             ctx.loglike_bands(net.forward(xb_), data, sigma, Ls0)
+            Ls0 = Ls0[:Cm].contiguous()
         s.set_state(xb_[:Cm].contiguous(), Lb_[:Cm].contiguous(), Ls0)
         chain = torch.empty((generations, Cm, 5 + S), dtype=torch.float32, device=dev)
         st = {}
         def run():
-            st.update(ctx.retrieval_run(s, net if mode == "screened" else None, grid, ax.p_bar, ax.t_K, nu, cfg,
+            st.update(ctx.retrieval_run(s, net if screened else None, grid, ax.p_bar, ax.t_K, nu, cfg,
                                         filt, data, sigma, generations, use_graph=True, chain=chain))
         ms = _event_ms(torch, stream, run)
         ctx.sync()
@@ -1223,16 +1226,16 @@ def run_retrieval(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, net
         st["ess_per_s"] = ess / (ms / 1e3)
         st["gelman_rubin_max"] = float(gr.max())
         st["ess_per_exact_eval"] = ess / max(st["exact_evals"], 1)
-        if mode != "demczs":
-            kept[mode] = (chain.reshape(-1, 5 + S).double().cpu().numpy(),
-                          (generations * Cm / sp.mean(0)).cpu().numpy())
-        if mode == "screened":
+        kept[mode] = (chain.reshape(-1, 5 + S).double().cpu().numpy(),
+                      (generations * Cm / sp.mean(0)).cpu().numpy())
+        if screened:
             st["screen"] = {"beta": beta, "margin": margin}
         st["ms"] = ms
         if st["accepted"]:
             st["surrogate_err_mean"] = st["surrogate_err_sum"] / st["accepted"]
         res[mode] = st
     res["posterior_agreement"] = posterior_agreement(*kept["plain"], *kept["screened"])
+    res["posterior_agreement_demczs"] = posterior_agreement(*kept["demczs"], *kept["demczs_screened"])
     res["false_rejection"] = screen_false_rejections(ctx, bart, torch, dev, grid, ax, nu, filt, cfg, S, net, lo, hi,
                                                      xb_, Lb_, data, sigma, beta, margin)
     return res
