@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import dataclasses
+import sys
 from typing import Optional, Sequence
 
 import numpy as np
@@ -59,6 +60,18 @@ def device_lines(lines, device="cuda") -> DeviceLines:
 
 def NuGrid(nu_start: float, dnu: float, n_nu: int) -> _native.NuGrid:
     return _native.NuGrid(float(nu_start), float(dnu), int(n_nu))
+
+
+def _release(obj):
+    """Frees a library object when it is garbage-collected, except while the
+    interpreter shuts down: the CUDA runtime may already be torn down then, and
+    the process exit returns the device memory anyway."""
+    if sys.is_finalizing():
+        return
+    try:
+        obj.close()
+    except Exception:
+        pass
 
 
 def _ptr(t) -> Optional[int]:
@@ -115,10 +128,7 @@ class Graph:
             self.h = None
 
     def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+        _release(self)
 
 
 class Context:
@@ -143,10 +153,7 @@ class Context:
             self.h = None
 
     def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+        _release(self)
 
     def _check(self, st: int):
         if st != 0:
@@ -413,10 +420,7 @@ class Mlp:
             self.h = None
 
     def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+        _release(self)
 
     def set_scaling(self, in_shift, in_scale, out_shift, out_scale):
         self.ctx._check(self.lib.bart_mlp_set_scaling(self.h, _flt(in_shift), _flt(in_scale), _flt(out_shift),
@@ -505,10 +509,7 @@ class VoigtTable:
             self.h = None
 
     def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+        _release(self)
 
 
 class Demc:
@@ -528,10 +529,7 @@ class Demc:
             self.h = None
 
     def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+        _release(self)
 
     def set_state(self, x, loglike, loglike_s=None):
         _check_tensor(x, "float32", self.C * self.d)
