@@ -96,7 +96,9 @@ bart_status bart_set_emission_tile(bart_ctx* ctx, int tile);
  *     counters reset themselves at the end of the launch, so a captured graph
  *     replays it unchanged.
  *     A CTA thread takes two wavenumbers and their arithmetic runs on packed
- *     FP32 pairs.
+ *     FP32 pairs.  It addresses grid rows by 32-bit element offsets: grids
+ *     with n_species * n_layers * n_temps * n_nu + n_nu >= 2^32 (16 GiB and
+ *     more) take the BART_LAUNCH_SPLIT path instead.
  *   BART_LAUNCH_SPLIT: three launches (per-proposal profile kernel, one CTA
  *     per (proposal, tile) column kernel, band reduction), kept for
  *     comparison.
@@ -104,7 +106,8 @@ bart_status bart_set_emission_tile(bart_ctx* ctx, int tile);
  *     staged in shared memory by bulk copies (a producer warp, a ring of
  *     mbarrier-tracked buffers) instead of per-thread loads; used where
  *     nu.n_nu is a multiple of 4 and the grid is 16-byte aligned (else the
- *     fused kernel runs).  Kept for comparison: it measures slower on GB300.
+ *     fused kernel runs; the same grid-size limit).  Kept for comparison: it
+ *     measures slower on GB300.
  * Results agree to FP32 rounding (band values through the order of partial
  * sums).  Other values return BART_EINVAL. */
 #define BART_LAUNCH_FUSED 0

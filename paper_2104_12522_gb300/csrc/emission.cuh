@@ -92,6 +92,12 @@ EmExtra emission_extra(const bart_grid_desc* g, const bart_fwd_cfg* c);
 // exceed 20 on the grid), bit 1 the optical-depth limit.
 int emission_mode(const bart_grid_desc* g, const bart_fwd_cfg* c);
 
+// The fused kernel addresses a layer's grid rows by 32-bit element offsets
+// from the tile's column: it takes grids with S L M n_nu + n_nu < 2^32.
+inline bool fused_offsets_fit(const bart_grid_desc* g) {
+  return (int64_t)g->n_species * g->n_layers * g->n_temps * g->nu.n_nu + g->nu.n_nu <= (int64_t)UINT32_MAX;
+}
+
 // The persistent fused launch of an emission batch (forward_fused.cu).
 bart_status fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const bart_fwd_cfg* c, const bart_batch* b,
                            float* spectra, const bart_filters* f, float* bands, int nb);

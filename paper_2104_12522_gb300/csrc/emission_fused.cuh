@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "bart_internal.cuh"
 #include "emission.cuh"
@@ -185,15 +186,42 @@ __device__ __forceinline__ float2 planck2(float2 c1nu3, float2 y, bool wide) {
   return (ALLOW_WIDE && wide) ? planck2<true>(c1nu3, y) : planck2<false>(c1nu3, y);
 }
 
+// Per layer of the unit's proposal, in shared memory: the 32-bit element
+// offsets of the 2 S grid rows the layer reads (species s: the lower
+// temperature bracket at (k M + m) n_nu + s L M n_nu, the upper n_nu further;
+// the host takes this kernel only where S L M n_nu + n_nu < 2^32), the
+// interpolation weights times the abundance coefficients
+// (chi = sum_s X_s (1 - w) sigma_lo + X_s w sigma_hi), and the Planck terms:
+// y = (c2 / T) log2(e), (P_k - P_{k-1}) / 2g and r = 2^(y dnu), the ratio of
+// exp(c2 nu / T) between neighbouring wavenumbers.
+template <int S>
+struct __align__(16) LayerRec {
+  static constexpr int NCF = (2 * S + 3) / 4;
+  uint4 off[NCF];    // lower, upper bracket of species 0, of species 1, ...
+  float4 cf[NCF];    // X_s (1 - w), X_s w, s = 0 .. S-1
+  float4 pl;         // y, (P_k - P_{k-1}) / 2g, r, unused
+};
+
+// Planck function of a pair of neighbouring wavenumbers (nu, nu + dnu) at
+// one temperature from 2^(nu y) and r = 2^(dnu y): one exponential and one
+// reciprocal for both, B_a = c1nu3_a (e_b - 1) / ((e_a - 1)(e_b - 1)) and
+// B_b = c1nu3_b (e_a - 1) / (...).  Used where c2 nu / T <= 20, so the
+// product stays below 2.4e17.
+__device__ __forceinline__ float2 planck_pair(float2 c1nu3, float nu_a, float y, float r) {
+  const float ea = bartf::ex2_approx(nu_a * y);
+  const float eb = ea * r;
+  const float2 em1 = add2(make_float2(eb, ea), f2(-1.0f));   // (e_b - 1, e_a - 1)
+  const float R = bartf::rcp_approx(em1.x * em1.y);
+  return mul2(mul2(c1nu3, f2(R)), em1);
+}
+
 // TW wavenumbers per tile, TW / 2 threads per CTA.
 template <int S, int NA, int TW, int MODE>
 __global__ void __launch_bounds__(TW / 2, FUSED_OCC_THREADS / (TW / 2))
 emission_fused_kernel(const __grid_constant__ FusedArgs a) {
   constexpr int NT = TW / 2;
-  __shared__ LayerTW s_tw[MAX_LAYERS];
-  __shared__ float4 s_cf[MAX_LAYERS][(2 * S + 3) / 4];   // per layer: X_s (1 - w), X_s w, s = 0 .. S-1
-  __shared__ float s_y[MAX_LAYERS];                       // (c2 / T) log2(e)
-  __shared__ float s_dpg[MAX_LAYERS];
+  constexpr int NCF = LayerRec<S>::NCF;
+  __shared__ LayerRec<S> s_rec[MAX_LAYERS];
   __shared__ float s_xs[S];
   __shared__ float2 s_red[NT / 32 > 0 ? NT / 32 : 1][MAX_BANDS];
   __shared__ unsigned long long s_unit;
@@ -201,9 +229,9 @@ emission_fused_kernel(const __grid_constant__ FusedArgs a) {
   constexpr bool WIDE_X = (MODE & 1) != 0, TAU_LIM = (MODE & 2) != 0;
   const int tid = threadIdx.x;
   const int L = a.L, nb = a.n_bands;
-  for (int k = tid; k + 1 < L; k += NT) s_dpg[k] = a.dpg[k];
   const int64_t sstride = (int64_t)L * a.M * a.N;
-  const int64_t dm = (a.M > 1) ? a.N : 0;          // offset of the upper temperature bracket
+  const unsigned int dm = (a.M > 1) ? (unsigned int)a.N : 0u;   // offset of the upper temperature bracket
+  const float dnu_f = (float)a.dnu;
   // float2 grid reads need an even row length and an 8-byte aligned grid
   const bool pair_loads = ((a.N & 1) == 0) && ((reinterpret_cast<uintptr_t>(a.grid) & 7) == 0);
   // the epoch only changes when the last CTA of a launch leaves, so every CTA
@@ -243,25 +271,24 @@ emission_fused_kernel(const __grid_constant__ FusedArgs a) {
     if (!skip && grp < n_groups_p) {
       // 1. the proposal's layers: T(P) (or the given profile), bracket, c2/T,
       // computed by the first unit of the proposal and published for the
-      // others (a unit that finds them unpublished computes them itself)
+      // others (a unit that finds them unpublished computes them itself),
+      // and from them the layer records
       if (tid == 0) s_ready = (ld_acquire(a.tw_flag + p) == ready_mark);
       if (tid < S) {
         const float ab = a.theta ? a.theta[(int64_t)p * a.n_theta + 5 + tid] : 0.0f;
         s_xs[tid] = a.x0mu[tid] * exp10f(ab);
       }
       __syncthreads();
-      if (s_ready) {
-        for (int k = tid; k < L; k += NT) {
+      const bool ready = s_ready;
+      for (int k = tid; k < L; k += NT) {
+        LayerTW r;
+        if (ready) {
           // one 16-byte L2 load per layer state: row (two words), w, c2/T
           const int4 v = __ldcg(reinterpret_cast<const int4*>(a.tw_cache + (int64_t)p * L + k));
-          LayerTW r;
           r.row = (int64_t)(((unsigned long long)(unsigned int)v.y << 32) | (unsigned int)v.x);
           r.w = __int_as_float(v.z);
           r.c2_t = __int_as_float(v.w);
-          s_tw[k] = r;
-        }
-      } else {
-        for (int k = tid; k < L; k += NT) {
+        } else {
           float T;
           if (a.t_profile) {
             T = a.t_profile[(int64_t)p * L + k];
@@ -271,80 +298,85 @@ emission_fused_kernel(const __grid_constant__ FusedArgs a) {
             for (int i = 0; i < 5; ++i) th[i] = a.theta[(int64_t)p * a.n_theta + i];
             T = bartf::tp_temperature(th, a.p_cgs[k], a.inv_g, a.tint4, a.tirr0);
           }
-          const LayerTW r = layer_state(T, k, a.t_axis, a.M, a.N, a.t_min, a.t_max, a.status);
-          s_tw[k] = r;
+          r = layer_state(T, k, a.t_axis, a.M, a.N, a.t_min, a.t_max, a.status);
           a.tw_cache[(int64_t)p * L + k] = r;
         }
-        __syncthreads();
-        if (tid == 0) st_release(a.tw_flag + p, ready_mark);   // publishes the CTA's stores above
-      }
-      __syncthreads();
-      // per layer: the interpolation weights times the abundance coefficients
-      // (chi = sum_s X_s (1 - w) sigma_lo + X_s w sigma_hi) and the Planck exponent
-      for (int k = tid; k < L; k += NT) {
-        const float w = s_tw[k].w;
-        float cf[4 * ((2 * S + 3) / 4)] = {};
+        unsigned int of[4 * NCF] = {};
+        float cf[4 * NCF] = {};
 #pragma unroll
         for (int q = 0; q < S; ++q) {
-          cf[2 * q] = s_xs[q] * (1.0f - w);
-          cf[2 * q + 1] = s_xs[q] * w;
+          of[2 * q] = (unsigned int)(r.row + q * sstride);
+          of[2 * q + 1] = of[2 * q] + dm;
+          cf[2 * q] = s_xs[q] * (1.0f - r.w);
+          cf[2 * q + 1] = s_xs[q] * r.w;
         }
 #pragma unroll
-        for (int q = 0; q < (2 * S + 3) / 4; ++q) s_cf[k][q] = make_float4(cf[4 * q], cf[4 * q + 1], cf[4 * q + 2], cf[4 * q + 3]);
-        s_y[k] = s_tw[k].c2_t * LOG2E;
+        for (int q = 0; q < NCF; ++q) {
+          s_rec[k].off[q] = make_uint4(of[4 * q], of[4 * q + 1], of[4 * q + 2], of[4 * q + 3]);
+          s_rec[k].cf[q] = make_float4(cf[4 * q], cf[4 * q + 1], cf[4 * q + 2], cf[4 * q + 3]);
+        }
+        const float y = r.c2_t * LOG2E;
+        s_rec[k].pl = make_float4(y, k > 0 ? __ldg(a.dpg + k - 1) : 0.0f, exp2f(y * dnu_f), 0.0f);
       }
       __syncthreads();
+      if (!ready && tid == 0) st_release(a.tw_flag + p, ready_mark);   // publishes the CTA's stores above
       float2 band_acc = make_float2(0.f, 0.f);      // thread b < nb: band b over the unit's tiles
       const int t_end = min((grp + 1) * a.tpu, n_tiles_p);
 
-      for (int tile = grp * a.tpu; tile < t_end; ++tile) {
-        // 2. the columns of wavenumbers ja and ja + 1
+      // 2. the columns of wavenumbers ja and ja + 1 of one tile; PAIR: both
+      // read by one 8-byte load per row
+      auto column = [&](auto pair_c, int tile) {
+        constexpr bool PAIR = decltype(pair_c)::value;
         const int64_t ja = lo2 + (int64_t)tile * TW + 2 * tid, jb = ja + 1;
         const bool act_a = ja >= lo && ja < hi, act_b = jb < hi;
         // idle lanes compute on valid indices
         const int64_t ka = (ja < hi) ? ja : lo2, kb = (jb < hi) ? jb : ka;
-        const double nua = a.nu_start + (double)ka * a.dnu, nub = a.nu_start + (double)kb * a.dnu;
-        const float2 c1nu3 = make_float2((float)(2.0 * bartc::H * bartc::C * bartc::C * nua * nua * nua),
-                                         (float)(2.0 * bartc::H * bartc::C * bartc::C * nub * nub * nub));
-        const float2 nuf = make_float2((float)nua, (float)nub);
-        // Rayleigh a nu^4 / (mu m_u)
-        const float2 chi_r = make_float2((float)(a.ex.ray * (nua * nua) * (nua * nua)),
-                                         (float)(a.ex.ray * (nub * nub) * (nub * nub)));
-        // per angle the log2 transmittance to the current level (a sum of
-        // positive optical-depth terms times -log2(e)/mu); the flux needs the
-        // transmittances only through their quadrature sum
-        // Tw = sum_i 2 pi w_i mu_i / 2 t_i, so F = sum_k (B_{k-1} + B_k)
-        // (Tw_{k-1} - Tw_k) + 2 B_bottom Tw_bottom
-        float2 lt[NA];
-#pragma unroll
-        for (int i = 0; i < NA; ++i) lt[i] = f2(0.0f);
-        float2 Tw_prev = f2(a.tw_top), F = f2(0.0f);
+        // the wavenumbers from their FP64 positions, the rest in FP32
+        const float2 nuf = make_float2((float)(a.nu_start + (double)ka * a.dnu), (float)(a.nu_start + (double)kb * a.dnu));
+        constexpr float C1 = (float)(2.0 * bartc::H * bartc::C * bartc::C);
+        const float2 c1nu3 = mul2(mul2(f2(C1), nuf), mul2(nuf, nuf));
+        // Rayleigh a nu^4 / (mu m_u) (in FP64: a / (mu m_u) may be below the FP32 range)
+        float2 chi_r = f2(0.0f);
+        if (a.ex.ray != 0.0) {
+          const double nua = a.nu_start + (double)ka * a.dnu, nub = a.nu_start + (double)kb * a.dnu;
+          chi_r = make_float2((float)(a.ex.ray * (nua * nua) * (nua * nua)), (float)(a.ex.ray * (nub * nub) * (nub * nub)));
+        }
         const float* ga = a.grid + ka;
-        const float* gb = a.grid + kb;
+        const unsigned int dkb = (unsigned int)(kb - ka);
+        // the flux needs the per-angle transmittances t_i = 2^(tau ang_i)
+        // (tau the vertical optical depth from the top, ang_i = -log2(e)/mu_i)
+        // only through their quadrature sum Tw = sum_i 2 pi w_i mu_i / 2 t_i,
+        // so F = sum_k (B_{k-1} + B_k) (Tw_{k-1} - Tw_k) + 2 B_bottom Tw_bottom
+        float2 tau = f2(0.0f), Tw_prev = f2(a.tw_top), F = f2(0.0f);
         const int L_run = a.ex.L_run;
         // grid values of a layer for both wavenumbers: lower (x) and upper (y)
         // temperature bracket per species
         auto fetch = [&](int k, float2* x, float2* y) {
-          const int64_t row = s_tw[k].row;
-          if (pair_loads) {                        // ka is even and ka + 1 < N here
+          unsigned int of[4 * NCF];
 #pragma unroll
-            for (int q = 0; q < S; ++q) {
-              x[q] = __ldg(reinterpret_cast<const float2*>(ga + row + q * sstride));
-              y[q] = __ldg(reinterpret_cast<const float2*>(ga + row + q * sstride + dm));
-            }
-          } else {
+          for (int q = 0; q < NCF; ++q) {
+            const uint4 v = s_rec[k].off[q];
+            of[4 * q] = v.x;
+            of[4 * q + 1] = v.y;
+            of[4 * q + 2] = v.z;
+            of[4 * q + 3] = v.w;
+          }
 #pragma unroll
-            for (int q = 0; q < S; ++q) {
-              x[q] = make_float2(__ldg(ga + row + q * sstride), __ldg(gb + row + q * sstride));
-              y[q] = make_float2(__ldg(ga + row + q * sstride + dm), __ldg(gb + row + q * sstride + dm));
+          for (int q = 0; q < S; ++q) {
+            if (PAIR) {                            // ka is even and ka + 1 < N here
+              x[q] = __ldg(reinterpret_cast<const float2*>(ga + of[2 * q]));
+              y[q] = __ldg(reinterpret_cast<const float2*>(ga + of[2 * q + 1]));
+            } else {
+              x[q] = make_float2(__ldg(ga + of[2 * q]), __ldg(ga + (of[2 * q] + dkb)));
+              y[q] = make_float2(__ldg(ga + of[2 * q + 1]), __ldg(ga + (of[2 * q + 1] + dkb)));
             }
           }
         };
         auto chi_of = [&](int k, const float2* x, const float2* y) {
-          float cf[4 * ((2 * S + 3) / 4)];
+          float cf[4 * NCF];
 #pragma unroll
-          for (int q = 0; q < (2 * S + 3) / 4; ++q) {
-            const float4 v = s_cf[k][q];
+          for (int q = 0; q < NCF; ++q) {
+            const float4 v = s_rec[k].cf[q];
             cf[4 * q] = v.x;
             cf[4 * q + 1] = v.y;
             cf[4 * q + 2] = v.z;
@@ -358,12 +390,15 @@ emission_fused_kernel(const __grid_constant__ FusedArgs a) {
           }
           return chi;
         };
+        auto planck_k = [&](const float4& pl) {
+          if (WIDE_X) return planck2<true>(c1nu3, mul2(nuf, f2(pl.x)));
+          return planck_pair(c1nu3, nuf.x, pl.x, pl.z);
+        };
         float2 cx[S], cy[S], nx[S], ny[S];
         fetch(0, cx, cy);
         fetch(min(1, L_run - 1), nx, ny);
         float2 chi_prev = chi_of(0, cx, cy);
-        float2 B_prev = planck2<WIDE_X>(c1nu3, mul2(nuf, f2(s_y[0])));
-        float2 tau_v = f2(0.0f);                   // vertical optical depth from the top
+        float2 B_prev = planck_k(s_rec[0].pl);
         bool done_a = false, done_b = false;       // lane reached the optical-depth limit
 #pragma unroll 2
         for (int k = 1; k < L_run; ++k) {
@@ -374,15 +409,17 @@ emission_fused_kernel(const __grid_constant__ FusedArgs a) {
           }
           fetch(min(k + 1, L_run - 1), nx, ny);    // the next layer's rows are in flight meanwhile
           const float2 chi = chi_of(k, cx, cy);
-          const float2 B = planck2<WIDE_X>(c1nu3, mul2(nuf, f2(s_y[k])));
-          const float2 dtau = mul2(add2(chi_prev, chi), f2(s_dpg[k - 1]));
+          const float4 pl = s_rec[k].pl;
+          const float2 B = planck_k(pl);
+          const float2 dtau = mul2(add2(chi_prev, chi), f2(pl.y));
           const float2 Bsum = add2(B_prev, B);
+          tau = add2(tau, dtau);
           float2 Tw0 = f2(0.0f), Tw1 = f2(0.0f);    // two partial sums: a shorter dependence chain
 #pragma unroll
           for (int i = 0; i < NA; ++i) {
-            lt[i] = fma2(dtau, f2(a.ang[i]), lt[i]);
-            if (i & 1) Tw1 = fma2(f2(a.ang[NA + i]), ex2_2(lt[i]), Tw1);
-            else Tw0 = fma2(f2(a.ang[NA + i]), ex2_2(lt[i]), Tw0);
+            const float2 t = ex2_2(mul2(tau, f2(a.ang[i])));
+            if (i & 1) Tw1 = fma2(f2(a.ang[NA + i]), t, Tw1);
+            else Tw0 = fma2(f2(a.ang[NA + i]), t, Tw0);
           }
           const float2 Tw = add2(Tw0, Tw1);
           const float2 Fn = fma2(Bsum, sub2(Tw_prev, Tw), F);
@@ -406,9 +443,8 @@ emission_fused_kernel(const __grid_constant__ FusedArgs a) {
               Tw_prev.y = Tw.y;
               B_prev.y = B.y;
             }
-            tau_v = add2(tau_v, dtau);
-            done_a = done_a || tau_v.x > a.ex.tau_cut;
-            done_b = done_b || tau_v.y > a.ex.tau_cut;
+            done_a = done_a || tau.x > a.ex.tau_cut;
+            done_b = done_b || tau.y > a.ex.tau_cut;
             if (done_a && done_b) break;
           }
         }
@@ -445,6 +481,10 @@ emission_fused_kernel(const __grid_constant__ FusedArgs a) {
           }
           __syncthreads();                         // s_red is rewritten by the next tile
         }
+      };
+      for (int tile = grp * a.tpu; tile < t_end; ++tile) {
+        if (pair_loads) column(std::true_type{}, tile);
+        else column(std::false_type{}, tile);
       }
 
       // the unit's band partials; the proposal's last unit reduces them

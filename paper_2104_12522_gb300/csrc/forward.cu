@@ -645,7 +645,8 @@ extern "C" bart_status bart_forward_spectra_batch(bart_ctx* ctx, const bart_grid
     return bart_fail(ctx, BART_EUNSUPPORTED, "emission with %d species and %d angles is not instantiated "
                      "(species 1-4; angles 1, 2, 4, 8, 16)", S, c->n_angles);
   BART_CUDA(ctx, cudaSetDevice(ctx->device));
-  if (ctx->em_launch != BART_LAUNCH_SPLIT) return fused_emission(ctx, g, c, b, spectra, f, bands, nb);
+  if (ctx->em_launch != BART_LAUNCH_SPLIT && fused_offsets_fit(g))
+    return fused_emission(ctx, g, c, b, spectra, f, bands, nb);
 
   const int NA = c->n_angles;
   EmPrep pr;
