@@ -680,10 +680,12 @@ def run_native(args):
 
 
 def emission_roofline(ms, n_sm, max_mhz, peaks, L, NU):
-    """MUFU roofline of the fused generation: NA ex2 of the angles plus the
-    Planck function's ex2 and reciprocal per (proposal, layer, wavenumber),
-    against 16 MUFU results per clock per SM; DRAM fraction from the
-    committed ncu capture of the same kernel source."""
+    """MUFU roofline of the fused generation: the method's NA ex2 of the
+    angles plus the Planck function's ex2 and reciprocal per (proposal, layer,
+    wavenumber), against MUFU_PER_CLK results per clock per SM (the kernel
+    executes NA + 1 of them: one ex2 and one reciprocal give the Planck
+    function of a wavenumber pair); DRAM fraction from the committed ncu
+    capture of the same kernel source."""
     hbm = float(peaks.get("hbm_gbs") or 6800.0)
     units = N_PROPOSALS * L * NU
     mufu = units * (N_ANGLES + 2) / (ms / 1e3) / 1e12
@@ -693,7 +695,9 @@ def emission_roofline(ms, n_sm, max_mhz, peaks, L, NU):
             "traffic": dram, "dram_frac": dram / (ms / 1e3) / (hbm * 1e9) if dram else None,
             "kernel": "emission_fused_kernel",
             "note": (f"{N_ANGLES + 2} MUFU ops per (proposal, layer, wavenumber): {N_ANGLES} ex2 of the angles, "
-                     f"ex2 and reciprocal of the Planck function; peak = {n_sm} SMs x {MUFU_PER_CLK} MUFU results "
+                     f"ex2 and reciprocal of the Planck function (the kernel executes {N_ANGLES + 1}: the Planck "
+                     f"function of a wavenumber pair takes one ex2 and one reciprocal); peak = {n_sm} SMs x "
+                     f"{MUFU_PER_CLK} MUFU results "
                      f"per clock x {max_mhz:.0f} MHz.  The proposals of a wavenumber tile share the grid rows "
                      "through L2, so DRAM moves about the grid once per generation: dram_frac = DRAM bytes per "
                      "generation (ncu) / time / measured HBM copy bandwidth")}

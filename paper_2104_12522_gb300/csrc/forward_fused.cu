@@ -107,13 +107,25 @@ bart_status bartem::fused_emission(bart_ctx* ctx, const bart_grid_desc* g, const
   a.wide_x = (mode & 1) != 0;
   a.tau_lim = (mode & 2) != 0;
 
+  // The CTAs in flight work on the same wavenumber span for neighbouring
+  // proposals, which between them read the rows of every layer and
+  // temperature bracket of that span: a unit spans at most as many
+  // wavenumbers as keep those rows (S L M x span x 4 B) within half of L2.
+  int l2_bytes = 0;
+  if (cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    l2_bytes = 0;
+  }
+  const long long span_cap =
+      (l2_bytes > 0 ? (long long)l2_bytes / 2 : (64LL << 20)) / ((long long)S * L * M * (long long)sizeof(float));
   auto run = [&](int tw) -> bart_status {
     // several consecutive tiles per unit amortise the unit's fixed work (layer
     // states, band partials and counts), as long as there are enough units to
     // balance the CTAs (about 8 per CTA of a full grid)
     const int n_tiles = (int)((N + 3 + tw - 1) / tw);                // tiles start on an aligned index
     const long long target = 8LL * ctx->sm_count * (2 * FUSED_OCC_THREADS / tw);
-    a.tpu = (int)std::max(1LL, std::min<long long>(MAX_TILES_PER_UNIT, (long long)n * n_tiles / target));
+    const long long tpu_cap = std::max(1LL, std::min<long long>(MAX_TILES_PER_UNIT, span_cap / tw));
+    a.tpu = (int)std::max(1LL, std::min<long long>(tpu_cap, (long long)n * n_tiles / target));
     a.n_groups = (n_tiles + a.tpu - 1) / a.tpu;
     a.n_units = (unsigned long long)a.n_groups * (unsigned long long)n;
     cudaError_t e = pick_fused(S, NA, tma, tw, mode)(a, ctx->sm_count, ctx->stream);
