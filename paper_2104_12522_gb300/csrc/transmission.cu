@@ -14,12 +14,14 @@
 //   trans_kernel    persistent CTAs pulling (wavenumber tile, instance) units
 //                   from an atomic counter; tile-major order keeps the grid
 //                   slab of a tile in L2 while every instance covering it runs.
-//                   Four threads per wavenumber of a 128-point tile: each
-//                   computes a quarter of the levels' extinction (lines plus
-//                   Rayleigh a nu^4 per molecule) into the shared shell means,
-//                   then a quarter of the ray blocks (balanced snake order) of
+//                   Eight threads per pair of neighbouring wavenumbers of a
+//                   128-point tile, the pair's arithmetic on packed FP32 and
+//                   its grid values read as 8-byte pairs: each computes an
+//                   eighth of the levels' extinction (lines plus Rayleigh
+//                   a nu^4 per molecule) into the shared shell means, then an
+//                   eighth of the ray blocks (balanced snake order) of
 //                   tau_i = sum_{k<i} ds_ik (alpha_k + alpha_{k+1}) / 2,
-//                   8 rays per register block with the chords read as
+//                   4 rays per register block with the chords read as
 //                   broadcast loads, and its share of the trapezoid in impact
 //                   parameter (each ray's weight (z_{i-1} - z_{i+1}) / 2); the
 //                   shares are added and the band partials fused.
@@ -33,14 +35,17 @@
 namespace {
 
 constexpr int TR_COLS = 128;             // wavenumbers per unit
-constexpr int TR_SPLIT = 4;              // threads per wavenumber column
-constexpr int TR_THREADS = TR_COLS * TR_SPLIT;
+constexpr int TR_PAIRS = TR_COLS / 2;    // wavenumber pairs per unit
+constexpr int TR_SPLIT = 8;              // threads per pair column
+constexpr int TR_THREADS = TR_PAIRS * TR_SPLIT;
 constexpr int TR_LMAX = 192;             // maximum levels per instance
-constexpr int TR_RB = 8;                 // rays per register block
+constexpr int TR_RB = 4;                 // rays per register block
 constexpr int TR_NBLK = (TR_LMAX - 1 + TR_RB - 1) / TR_RB;   // ray blocks of the deepest column
-// chords of an instance, block by block: block b (rays 1 + 8b ..) needs
-// shells k < kmax_b <= 8 (b + 1), stored [k][8 rays] from 32 b (b + 1)
-constexpr int TR_DS_STRIDE = 32 * TR_NBLK * (TR_NBLK + 1);
+// chords of an instance, block by block: block b (rays 1 + TR_RB b ..) needs
+// shells k < kmax_b <= TR_RB (b + 1), stored [k][TR_RB rays] from
+// TR_RB^2 b (b + 1) / 2
+__host__ __device__ constexpr int tr_block_offset(int b) { return TR_RB * TR_RB * b * (b + 1) / 2; }
+constexpr int TR_DS_STRIDE = tr_block_offset(TR_NBLK);
 constexpr int TR_MAX_BANDS = 64;
 constexpr int TR_MAX_SPECIES = 8;
 
@@ -201,7 +206,7 @@ __global__ void trans_prologue(const float* __restrict__ theta, int n_theta, int
   const int nblk = (Le - 1 + TR_RB - 1) / TR_RB;
   for (int b = 0; b < nblk; ++b) {
     const int i0 = 1 + b * TR_RB, nr = min(TR_RB, Le - i0), kmax = i0 + nr - 1;
-    float* db = dsi + 32 * b * (b + 1);
+    float* db = dsi + tr_block_offset(b);
     for (int e = threadIdx.x; e < kmax * TR_RB; e += blockDim.x) {
       const int k = e / TR_RB, r = e % TR_RB, ir = i0 + r;
       float d = 0.f;
@@ -232,12 +237,15 @@ __device__ __forceinline__ float one_minus_exp(float tau) {
 }
 
 // Ray block handled by split thread h: snake order over groups of
-// 2 TR_SPLIT blocks (h, 2 TR_SPLIT - 1 - h), so the four threads of a column
-// get shallow and deep blocks alike.
+// 2 TR_SPLIT blocks (h, 2 TR_SPLIT - 1 - h), so the threads of a column get
+// shallow and deep blocks alike.
 __device__ __forceinline__ bool my_block(int b, int h) {
   const int q = b % (2 * TR_SPLIT);
   return (q < TR_SPLIT) ? (q == h) : (2 * TR_SPLIT - 1 - q == h);
 }
+
+__device__ __forceinline__ float2 tr_f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 tr_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 template <int S>
 __global__ void __launch_bounds__(TR_THREADS, 2)
@@ -248,16 +256,18 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
              int n_gtiles, unsigned long long n_units, unsigned long long* __restrict__ counter,
              const int32_t* __restrict__ active, int* __restrict__ status, double nu_start, double dnu,
              double ray) {
-  extern __shared__ float smem[];
-  float* s_alpha = smem;                                  // [TR_LMAX - 1][TR_COLS] shell extinction
+  extern __shared__ float2 smem2[];
+  float2* s_alpha = smem2;                                // [TR_LMAX - 1][TR_PAIRS] shell extinction pairs
   __shared__ TrLevel s_lev[TR_LMAX];
   __shared__ TrInst s_in;
   __shared__ unsigned long long s_unit;
-  __shared__ float s_part[TR_SPLIT - 1][TR_COLS];
-  __shared__ float2 s_red[TR_COLS / 32][TR_MAX_BANDS];
+  __shared__ float2 s_part[TR_SPLIT - 1][TR_PAIRS];
+  __shared__ float2 s_red[TR_PAIRS / 32][TR_MAX_BANDS];
   const int tid = threadIdx.x;
-  const int c = tid % TR_COLS, h = tid / TR_COLS;          // column, quarter
+  const int c = tid % TR_PAIRS, h = tid / TR_PAIRS;         // pair column, part
   const int64_t sstride = (int64_t)Lg * M * N;
+  // float2 grid reads need an even row length and an 8-byte aligned grid
+  const bool pair_loads = ((N & 1) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 7) == 0);
 
   for (;;) {
     if (tid == 0) s_unit = atomicAdd(counter, 1ULL);
@@ -291,33 +301,52 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
     for (int k = tid; k < L; k += TR_THREADS) s_lev[k] = lev[(int64_t)i * TR_LMAX + k];
     __syncthreads();
 
-    const int64_t j = g0 + c;
-    const bool act = (j >= lo) && (j < hi);
-    const int64_t jj = act ? j : lo;
+    // the pair (ja, ja + 1); idle lanes compute on a valid pair
+    const int64_t ja = g0 + 2 * c, jb = ja + 1;
+    const bool act_a = (ja >= lo) && (ja < hi), act_b = (jb >= lo) && (jb < hi);
+    const int64_t lo2 = lo & ~(int64_t)1;
+    const int64_t ka = (ja < N) ? ja : lo2;       // even; with an even N, ka + 1 < N
+    const int64_t kb = (ka + 1 < N) ? ka + 1 : ka;
     // Rayleigh cross-section per molecule a nu^4, the same at every level
-    const double nu = nu_start + (double)jj * dnu;
-    const float sig_r = (float)(ray * (nu * nu) * (nu * nu));
-    // extinction at levels k0 .. k1 of this quarter (the boundary level is
+    float2 sig_r = tr_f2(0.f);
+    if (ray != 0.0) {
+      const double nua = nu_start + (double)ka * dnu, nub = nu_start + (double)kb * dnu;
+      sig_r = make_float2((float)(ray * (nua * nua) * (nua * nua)), (float)(ray * (nub * nub) * (nub * nub)));
+    }
+    // extinction at levels k0 .. k1 of this part (the boundary level is
     // evaluated by both neighbours), shell means k0 .. k1-1 into shared memory
     {
       const int k0 = (L - 1) * h / TR_SPLIT, k1 = (L - 1) * (h + 1) / TR_SPLIT;
       const int64_t dl = (Lg > 1) ? (int64_t)M * N : 0;
       const int64_t dm = (M > 1) ? N : 0;
-      float a_prev = 0.f;
+      const int64_t dkb = kb - ka;
+      float2 a_prev = tr_f2(0.f);
       for (int k = k0; k <= k1; ++k) {
         const TrLevel lv = s_lev[k];
-        const float* base = grid + ((int64_t)lv.a * M + lv.m) * N + jj;
-        float sig = sig_r;
+        const float* base = grid + ((int64_t)lv.a * M + lv.m) * N + ka;
+        float2 sig = sig_r;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          const float* b = base + s * sstride;
-          const float v00 = __ldg(b), v01 = __ldg(b + dm), v10 = __ldg(b + dl), v11 = __ldg(b + dl + dm);
-          const float lo_l = fmaf(lv.w, v01 - v00, v00);
-          const float hi_l = fmaf(lv.w, v11 - v10, v10);
-          sig = fmaf(s_in.x[s], fmaf(lv.u, hi_l - lo_l, lo_l), sig);
+        for (int q = 0; q < S; ++q) {
+          const float* b = base + q * sstride;
+          float2 v00, v01, v10, v11;
+          if (pair_loads) {
+            v00 = __ldg(reinterpret_cast<const float2*>(b));
+            v01 = __ldg(reinterpret_cast<const float2*>(b + dm));
+            v10 = __ldg(reinterpret_cast<const float2*>(b + dl));
+            v11 = __ldg(reinterpret_cast<const float2*>(b + dl + dm));
+          } else {
+            v00 = make_float2(__ldg(b), __ldg(b + dkb));
+            v01 = make_float2(__ldg(b + dm), __ldg(b + dm + dkb));
+            v10 = make_float2(__ldg(b + dl), __ldg(b + dl + dkb));
+            v11 = make_float2(__ldg(b + dl + dm), __ldg(b + dl + dm + dkb));
+          }
+          const float2 lo_l = tr_fma2(tr_f2(lv.w), __fadd2_rn(v01, __fmul2_rn(v00, tr_f2(-1.f))), v00);
+          const float2 hi_l = tr_fma2(tr_f2(lv.w), __fadd2_rn(v11, __fmul2_rn(v10, tr_f2(-1.f))), v10);
+          const float2 pl = tr_fma2(tr_f2(lv.u), __fadd2_rn(hi_l, __fmul2_rn(lo_l, tr_f2(-1.f))), lo_l);
+          sig = tr_fma2(tr_f2(s_in.x[q]), pl, sig);
         }
-        const float a = sig * lv.ndens;
-        if (k > k0) s_alpha[(k - 1) * TR_COLS + c] = 0.5f * (a_prev + a);
+        const float2 a = __fmul2_rn(sig, tr_f2(lv.ndens));
+        if (k > k0) s_alpha[(k - 1) * TR_PAIRS + c] = __fmul2_rn(tr_f2(0.5f), __fadd2_rn(a_prev, a));
         a_prev = a;
       }
     }
@@ -330,27 +359,22 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
     const float rp = s_in.r_planet;
     const float* dsi = ds + (int64_t)i * TR_DS_STRIDE;
     const int nblk = (L - 1 + TR_RB - 1) / TR_RB;
-    float integ = 0.f;
+    float2 integ = tr_f2(0.f);
     for (int b = 0; b < nblk; ++b) {
       if (!my_block(b, h)) continue;
       const int i0 = 1 + b * TR_RB, nr = min(TR_RB, L - i0), kmax = i0 + nr - 1;
-      const float* db = dsi + 32 * b * (b + 1);
-      float tau[TR_RB];
+      const float* db = dsi + tr_block_offset(b);
+      float2 tau[TR_RB];
 #pragma unroll
-      for (int r = 0; r < TR_RB; ++r) tau[r] = 0.f;
+      for (int r = 0; r < TR_RB; ++r) tau[r] = tr_f2(0.f);
 #pragma unroll 4
       for (int k = 0; k < kmax; ++k) {
-        const float a = s_alpha[k * TR_COLS + c];
-        const float4 d0 = __ldg(reinterpret_cast<const float4*>(db + k * TR_RB));
-        const float4 d1 = __ldg(reinterpret_cast<const float4*>(db + k * TR_RB + 4));
-        tau[0] = fmaf(d0.x, a, tau[0]);
-        tau[1] = fmaf(d0.y, a, tau[1]);
-        tau[2] = fmaf(d0.z, a, tau[2]);
-        tau[3] = fmaf(d0.w, a, tau[3]);
-        tau[4] = fmaf(d1.x, a, tau[4]);
-        tau[5] = fmaf(d1.y, a, tau[5]);
-        tau[6] = fmaf(d1.z, a, tau[6]);
-        tau[7] = fmaf(d1.w, a, tau[7]);
+        const float2 a = s_alpha[k * TR_PAIRS + c];
+        const float4 d = __ldg(reinterpret_cast<const float4*>(db + k * TR_RB));
+        tau[0] = tr_fma2(tr_f2(d.x), a, tau[0]);
+        tau[1] = tr_fma2(tr_f2(d.y), a, tau[1]);
+        tau[2] = tr_fma2(tr_f2(d.z), a, tau[2]);
+        tau[3] = tr_fma2(tr_f2(d.w), a, tau[3]);
       }
 #pragma unroll
       for (int r = 0; r < TR_RB; ++r) {
@@ -358,29 +382,36 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
           const int ir = i0 + r;
           const float zb = s_lev[ir].z;
           const float wgt = 0.5f * (s_lev[ir - 1].z - (ir + 1 < L ? s_lev[ir + 1].z : zb));
-          integ = fmaf(one_minus_exp(tau[r]) * (rp + zb), wgt, integ);
+          const float2 f = make_float2(one_minus_exp(tau[r].x), one_minus_exp(tau[r].y));
+          integ = tr_fma2(f, tr_f2((rp + zb) * wgt), integ);
         }
       }
     }
     if (h > 0) s_part[h - 1][c] = integ;
     __syncthreads();
-    float delta = 0.f;
+    float2 delta = tr_f2(0.f);
     if (h == 0) {
 #pragma unroll
-      for (int q = 0; q < TR_SPLIT - 1; ++q) integ += s_part[q][c];
+      for (int q = 0; q < TR_SPLIT - 1; ++q) integ = __fadd2_rn(integ, s_part[q][c]);
       const float rbot = rp + s_lev[L - 1].z;
       const float rs = s_in.r_star;
-      delta = (rbot / rs) * (rbot / rs) + 2.f * integ / (rs * rs);
-      if (act && spectra) spectra[(offs ? offs[i] : (int64_t)i * N) + (j - lo)] = delta;
+      const float d0 = (rbot / rs) * (rbot / rs);
+      delta = make_float2(d0 + 2.f * integ.x / (rs * rs), d0 + 2.f * integ.y / (rs * rs));
+      if (spectra) {
+        const int64_t o = (offs ? offs[i] : (int64_t)i * N) - lo;
+        if (act_a) spectra[o + ja] = delta.x;
+        if (act_b) spectra[o + jb] = delta.y;
+      }
     }
     if (n_bands > 0) {
       if (h == 0) {
-        float dw = 0.f;
-        if (act) dw = (hi - lo == 1) ? 1.f : ((j == lo || j == hi - 1) ? 0.5f : 1.f);
+        const float dwa = act_a ? ((hi - lo == 1) ? 1.f : ((ja == lo || ja == hi - 1) ? 0.5f : 1.f)) : 0.f;
+        const float dwb = act_b ? ((hi - lo == 1) ? 1.f : ((jb == lo || jb == hi - 1) ? 0.5f : 1.f)) : 0.f;
         const int warp = tid >> 5, lane = tid & 31;
         for (int b = 0; b < n_bands; ++b) {
-          const float W = act ? __ldg(filt + (int64_t)b * N + j) * dw : 0.f;
-          float num = W * delta, den = W;
+          const float Wa = act_a ? __ldg(filt + (int64_t)b * N + ja) * dwa : 0.f;
+          const float Wb = act_b ? __ldg(filt + (int64_t)b * N + jb) * dwb : 0.f;
+          float num = fmaf(Wa, delta.x, Wb * delta.y), den = Wa + Wb;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
             num += __shfl_xor_sync(0xffffffffu, num, o);
@@ -392,7 +423,7 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
       __syncthreads();
       if (tid < n_bands) {
         float2 acc = make_float2(0.f, 0.f);
-        for (int w = 0; w < TR_COLS / 32; ++w) {
+        for (int w = 0; w < TR_PAIRS / 32; ++w) {
           acc.x += s_red[w][tid].x;
           acc.y += s_red[w][tid].y;
         }
@@ -467,7 +498,7 @@ bart_status bart_transmission_batch(bart_ctx* ctx, const bart_grid_desc* g, cons
   TrLauncher launch = nullptr;
   cudaError_t ce = cudaSuccess;
   int per_sm = 0;
-  const size_t smem = (size_t)(TR_LMAX - 1) * TR_COLS * sizeof(float);
+  const size_t smem = (size_t)(TR_LMAX - 1) * TR_PAIRS * sizeof(float2);
   switch (S) {
     case 1: launch = launch_trans<1>; ce = set_smem<1>(smem, &per_sm); break;
     case 2: launch = launch_trans<2>; ce = set_smem<2>(smem, &per_sm); break;
