@@ -321,6 +321,7 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
       const int64_t dm = (M > 1) ? N : 0;
       const int64_t dkb = kb - ka;
       float2 a_prev = tr_f2(0.f);
+#pragma unroll 2
       for (int k = k0; k <= k1; ++k) {
         const TrLevel lv = s_lev[k];
         const float* base = grid + ((int64_t)lv.a * M + lv.m) * N + ka;
