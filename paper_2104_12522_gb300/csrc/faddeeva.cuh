@@ -119,6 +119,67 @@ __device__ __forceinline__ float taylor_re(float x, float y, const float2* __res
   return ar;
 }
 
+// Re w(x + i y) for 0 <= y <= 0.02 and any x >= 0, from the expansion in y
+// about the real axis (w is analytic, so d/dy = i d/dz):
+//   Re w = e^{-x^2} (1 + y^2 (1 - 2 x^2)) + y G(x)
+//          + (y^3 / 6) (4 / sqrt(pi) + G(x) (6 - 4 x^2)) + O(y^4),
+// G(x) = -Im w'(x) = (2 / sqrt(pi)) (2 x F(x) - 1), F Dawson's integral.
+// For x < 5, e^{-x^2} = Re w(x) and w'(x) come from the Taylor table's
+// real-axis row (Horner in the real offset from the nearest node, no
+// cancellation: the row holds the derivative coefficients themselves); for
+// x >= 5, G from its asymptotic series
+//   G = (2 / sqrt(pi)) sum_{k=1}^{10} (2k-1)!! / (2 x^2)^k
+// (truncation <= 2.7e-7 relative at x = 5) and e^{-x^2} with a compensated
+// exponent.  One branch-free form for the core and the wings of a line with
+// small y.  Relative error of Re w (FP32 against the FP64 Faddeeva function)
+// <= 2.3e-6 for x >= 0, 1e-10 <= y <= 0.02.
+constexpr float SMALL_Y = 0.02f;
+__device__ __forceinline__ float small_y_re(float x, float y, const float2* __restrict__ tab) {
+  constexpr float L2E = 1.4426950408889634f;
+  constexpr float L2E_LO = (float)(1.4426950408889634 - (double)L2E);
+  constexpr float LN2 = 0.6931471805599453f;
+  constexpr float TWO_SQRTPI = 1.1283791670955126f;   // 2 / sqrt(pi)
+  float e, g;
+  if (x < 5.0f) {
+    const int ix = min((int)(x * (1.0f / wtab::H) + 0.5f), wtab::NX - 1);
+    const float a = x - (float)ix * wtab::H;
+    const float2* c = tab + (size_t)ix * wtab::NT;   // nodes on the real axis (iy = 0)
+    float2 cn = __ldg(c + wtab::NT - 1);
+    float r = cn.x, d = (float)(wtab::NT - 1) * cn.y;
+#pragma unroll
+    for (int n = wtab::NT - 2; n >= 1; --n) {
+      cn = __ldg(c + n);
+      r = fmaf(r, a, cn.x);
+      d = fmaf(d, a, (float)n * cn.y);
+    }
+    e = fmaf(r, a, __ldg(c).x);                     // Re w(x) = e^{-x^2}
+    g = -d;                                          // -Im w'(x)
+  } else {
+    const float hi = x * x, lo = fmaf(x, x, -hi);   // x^2 = hi + lo exactly
+    const float ah = -hi * L2E;
+    const float al = -fmaf(hi, L2E, ah) - fmaf(lo, L2E, hi * L2E_LO);
+    float e2;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e2) : "f"(ah));
+    e = e2 * fmaf(al, LN2, 1.0f);
+    const float t = rcp_approx(hi);
+    // (2k-1)!! / 2^k, k = 10 .. 1
+    float sum = 639383.8623046875f;
+    sum = fmaf(sum, t, 67303.564453125f);
+    sum = fmaf(sum, t, 7918.06640625f);
+    sum = fmaf(sum, t, 1055.7421875f);
+    sum = fmaf(sum, t, 162.421875f);
+    sum = fmaf(sum, t, 29.53125f);
+    sum = fmaf(sum, t, 6.5625f);
+    sum = fmaf(sum, t, 1.875f);
+    sum = fmaf(sum, t, 0.75f);
+    sum = fmaf(sum, t, 0.5f);
+    g = TWO_SQRTPI * t * sum;
+  }
+  const float x2 = x * x, y2 = y * y;
+  const float gy = fmaf(y2 * (1.0f / 6.0f), fmaf(g, fmaf(-4.0f, x2, 6.0f), 2.0f * TWO_SQRTPI), g);
+  return fmaf(e, fmaf(y2, fmaf(-2.0f, x2, 1.0f), 1.0f), y * gy);
+}
+
 // Accurate branch for x^2 + y^2 < 576 (also valid beyond).
 __device__ __forceinline__ float core_re(float x, float y, const float2* __restrict__ tab) {
   x = fabsf(x);

@@ -32,9 +32,11 @@
 //    far-field forms are not accurate enough, or a line's core (|z| < 24) go
 //    to a fixup pass.  Lines with one-pole points only: lanes take the points
 //    of their blocks and sum over the lines in registers (one add per point).
-//    Lines with a core: point by point, core points gathered into two
-//    per-warp lists (Taylor table, continued fraction) and evaluated 32 at a
-//    time, so lanes do not diverge across the branches.  All fixup sums go to
+//    Lines with a core: point by point; where y <= 0.02 (Doppler-dominated
+//    cells) one branch-free form over the line's whole range (the expansion
+//    of Re w in y about the real axis), elsewhere core points gathered into
+//    two per-warp lists (Taylor table, continued fraction) and evaluated 32
+//    at a time, so lanes do not diverge across the branches.  All fixup sums go to
 //    a warp-private accumulator in a fixed order: deterministic.
 //  * Partial sums are plain FP32 over 4 chunks of 32 lines and folded into a
 //    TwoSum (hi, lo) pair per point kept in shared memory: compensated
@@ -423,7 +425,6 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
   const int w0 = (int)w0l, w1 = w0 + OP_SPAN - 1;
   const int j0 = w0 + lane * OP_R;          // first point of this lane
   const float j0r = (float)(lane * OP_R);   // its offset in the span
-  const float tc = j0r + 0.5f * (OP_R - 1);  // offset of its block centre
   const int cell = blockIdx.y;
   const CellConst cc = cells[cell];
   // line-strength bound: lines with ln S below this are left out
@@ -768,8 +769,19 @@ opacity_kernel(const LineWin* __restrict__ win, const float* __restrict__ gref,
       const float4 b = g1[fl];
       const int4 e = g2[fl];
       const int pa = e.x, pb = e.y;
-      // one-pole points on both sides of the core window [klo, khi]
       const float2 c = g3[fl];
+      if (c.x <= bartw::SMALL_Y) {
+        // small y (Doppler-dominated cells): one branch-free form, the
+        // expansion of Re w in y about the real axis, over the whole range,
+        // core and wings alike; no deferred points
+        for (int p = pa + lane; p <= pb; p += 32) {
+          const float x = fabsf(fmaf((float)(p - w0) - a.w, a.x, a.y));
+          fix[p - w0] += c.y * bartw::small_y_re(x, c.x, wtab);
+        }
+        __syncwarp();          // the next line's lanes may touch the same points
+        continue;
+      }
+      // one-pole points on both sides of the core window [klo, khi]
       const int ka = e.z, kb = e.w;
       const int n_left = max(ka - pa, 0), n_far = n_left + max(pb - kb, 0);
       for (int k = lane; k < n_far; k += 32) {
