@@ -1159,7 +1159,7 @@ def train_surrogate(ctx, bart, torch, dev, stream, grid, ax, nu, filt, cfg, S, n
     report = {"widths": widths, "train_spectra": n_train, "train_steps": n_steps, "batch": B,
                         "spectra_gen_ms": gen_ms, "train_ms": train_ms,
                         "train_tflops": flops * n_steps / (train_ms / 1e3) / 1e12,
-                        "gemm": "BF16 tensor cores (mma.sync m16n8k16), FP32 operands as hi/lo BF16 pairs",
+                        "gemm": "BF16 tcgen05.mma, FP32 accumulators in tensor memory, 128 x 32 tiles; FP32 operands as hi/lo BF16 pairs",
                         "band_rel_err_median": float(np.median(err)), "band_rel_err_p99": float(np.percentile(err, 99)),
                         "inference_spectra_per_s": N_PROPOSALS / (inf_ms / 1e3)}
     return net, report
