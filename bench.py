@@ -47,6 +47,7 @@ SURVEY_FLOPS_PER_EVAL = 16   # the same evaluation counted on the region-I ratio
 N_PROPOSALS = 2048
 N_ANGLES = 8
 N_BANDS = 10
+FW_SPECIES = 4                    # species of the forward-model generation's grid
 OPACITY_LAUNCHES_PER_STEP = 3     # one opacity kernel launch per species
 KERNELS_PER_STEP = 3 * 3 + 1      # per species: window and span prologues + opacity; one fused generation
 # sources the opacity kernel is compiled from (the committed traffic figure is tied to them)
@@ -691,16 +692,22 @@ def emission_roofline(ms, n_sm, max_mhz, peaks, L, NU):
     mufu = units * (N_ANGLES + 2) / (ms / 1e3) / 1e12
     mufu_peak = n_sm * MUFU_PER_CLK * max_mhz * 1e6 / 1e12
     dram = committed_traffic(FORWARD_SOURCES, "emission_fused_kernel")
+    # the grid reads counted as if every (proposal, layer, wavenumber) streamed
+    # its 2 S values (lower and upper temperature bracket per species)
+    alg_bytes = units * 2 * FW_SPECIES * 4
     return {"bound": "mufu", "achieved": mufu, "peak": mufu_peak, "unit": "Tops/s", "frac": mufu / mufu_peak,
             "traffic": dram, "dram_frac": dram / (ms / 1e3) / (hbm * 1e9) if dram else None,
+            "algorithmic_bytes": alg_bytes, "algorithmic_gbs": alg_bytes / (ms / 1e3) / 1e9,
+            "hbm_frac_algorithmic": alg_bytes / (ms / 1e3) / (hbm * 1e9),
             "kernel": "emission_fused_kernel",
             "note": (f"{N_ANGLES + 2} MUFU ops per (proposal, layer, wavenumber): {N_ANGLES} ex2 of the angles, "
                      f"ex2 and reciprocal of the Planck function (the kernel executes {N_ANGLES + 1}: the Planck "
                      f"function of a wavenumber pair takes one ex2 and one reciprocal); peak = {n_sm} SMs x "
                      f"{MUFU_PER_CLK} MUFU results "
                      f"per clock x {max_mhz:.0f} MHz.  The proposals of a wavenumber tile share the grid rows "
-                     "through L2, so DRAM moves about the grid once per generation: dram_frac = DRAM bytes per "
-                     "generation (ncu) / time / measured HBM copy bandwidth")}
+                     "through L2, so DRAM moves about the grid twice per generation: dram_frac = DRAM bytes per "
+                     "generation (ncu) / time / measured HBM copy bandwidth; hbm_frac_algorithmic counts the grid "
+                     "reads as if every (proposal, layer, wavenumber) streamed its 2 S values")}
 
 
 def forward_model_leg(ctx, bart, torch, stream, grid, ax, nu, cfg, theta, filt, bands, generation, fw_ms, N, S):
