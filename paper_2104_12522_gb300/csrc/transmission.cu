@@ -19,7 +19,8 @@
 //                   its grid values read as 8-byte pairs: each computes an
 //                   eighth of the levels' extinction (lines plus Rayleigh
 //                   a nu^4 per molecule) into the shared shell means, then an
-//                   eighth of the ray blocks (balanced snake order) of
+//                   eighth of the ray blocks (a shallow and a deep block per
+//                   group of 2 x 8, run in one pass over the shells) of
 //                   tau_i = sum_{k<i} ds_ik (alpha_k + alpha_{k+1}) / 2,
 //                   4 rays per register block with the chords read as
 //                   broadcast loads, and its share of the trapezoid in impact
@@ -236,14 +237,6 @@ __device__ __forceinline__ float one_minus_exp(float tau) {
   return 1.0f - bartf::ex2_approx(-tau * 1.4426950408889634f);
 }
 
-// Ray block handled by split thread h: snake order over groups of
-// 2 TR_SPLIT blocks (h, 2 TR_SPLIT - 1 - h), so the threads of a column get
-// shallow and deep blocks alike.
-__device__ __forceinline__ bool my_block(int b, int h) {
-  const int q = b % (2 * TR_SPLIT);
-  return (q < TR_SPLIT) ? (q == h) : (2 * TR_SPLIT - 1 - q == h);
-}
-
 __device__ __forceinline__ float2 tr_f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 tr_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
@@ -361,22 +354,8 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
     const float* dsi = ds + (int64_t)i * TR_DS_STRIDE;
     const int nblk = (L - 1 + TR_RB - 1) / TR_RB;
     float2 integ = tr_f2(0.f);
-    for (int b = 0; b < nblk; ++b) {
-      if (!my_block(b, h)) continue;
-      const int i0 = 1 + b * TR_RB, nr = min(TR_RB, L - i0), kmax = i0 + nr - 1;
-      const float* db = dsi + tr_block_offset(b);
-      float2 tau[TR_RB];
-#pragma unroll
-      for (int r = 0; r < TR_RB; ++r) tau[r] = tr_f2(0.f);
-#pragma unroll 4
-      for (int k = 0; k < kmax; ++k) {
-        const float2 a = s_alpha[k * TR_PAIRS + c];
-        const float4 d = __ldg(reinterpret_cast<const float4*>(db + k * TR_RB));
-        tau[0] = tr_fma2(tr_f2(d.x), a, tau[0]);
-        tau[1] = tr_fma2(tr_f2(d.y), a, tau[1]);
-        tau[2] = tr_fma2(tr_f2(d.z), a, tau[2]);
-        tau[3] = tr_fma2(tr_f2(d.w), a, tau[3]);
-      }
+    // this thread's share of the trapezoid from a block's path sums
+    auto add_rays = [&](int i0, int nr, const float2* tau) {
 #pragma unroll
       for (int r = 0; r < TR_RB; ++r) {
         if (r < nr) {
@@ -387,6 +366,58 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
           integ = tr_fma2(f, tr_f2((rp + zb) * wgt), integ);
         }
       }
+    };
+    // the snake order gives this thread the blocks 2 TR_SPLIT g + h (shallow)
+    // and 2 TR_SPLIT g + 2 TR_SPLIT - 1 - h (deep) of each group g: both run
+    // in one pass over the shells (each shell's extinction read once for
+    // both, eight independent sums)
+    for (int g = 0; 2 * TR_SPLIT * g + h < nblk; ++g) {
+      const int ba = 2 * TR_SPLIT * g + h, bb = 2 * TR_SPLIT * g + 2 * TR_SPLIT - 1 - h;
+      const int i0a = 1 + ba * TR_RB, nra = min(TR_RB, L - i0a), kma = i0a + nra - 1;
+      const float* da = dsi + tr_block_offset(ba);
+      float2 ta[TR_RB], tb[TR_RB];
+#pragma unroll
+      for (int r = 0; r < TR_RB; ++r) ta[r] = tb[r] = tr_f2(0.f);
+      if (bb < nblk) {
+        const int i0b = 1 + bb * TR_RB, nrb = min(TR_RB, L - i0b), kmb = i0b + nrb - 1;   // kmb > kma
+        const float* dbp = dsi + tr_block_offset(bb);
+        int k = 0;
+#pragma unroll 2
+        for (; k < kma; ++k) {
+          const float2 a = s_alpha[k * TR_PAIRS + c];
+          const float4 d = __ldg(reinterpret_cast<const float4*>(da + k * TR_RB));
+          const float4 e = __ldg(reinterpret_cast<const float4*>(dbp + k * TR_RB));
+          ta[0] = tr_fma2(tr_f2(d.x), a, ta[0]);
+          ta[1] = tr_fma2(tr_f2(d.y), a, ta[1]);
+          ta[2] = tr_fma2(tr_f2(d.z), a, ta[2]);
+          ta[3] = tr_fma2(tr_f2(d.w), a, ta[3]);
+          tb[0] = tr_fma2(tr_f2(e.x), a, tb[0]);
+          tb[1] = tr_fma2(tr_f2(e.y), a, tb[1]);
+          tb[2] = tr_fma2(tr_f2(e.z), a, tb[2]);
+          tb[3] = tr_fma2(tr_f2(e.w), a, tb[3]);
+        }
+#pragma unroll 4
+        for (; k < kmb; ++k) {
+          const float2 a = s_alpha[k * TR_PAIRS + c];
+          const float4 e = __ldg(reinterpret_cast<const float4*>(dbp + k * TR_RB));
+          tb[0] = tr_fma2(tr_f2(e.x), a, tb[0]);
+          tb[1] = tr_fma2(tr_f2(e.y), a, tb[1]);
+          tb[2] = tr_fma2(tr_f2(e.z), a, tb[2]);
+          tb[3] = tr_fma2(tr_f2(e.w), a, tb[3]);
+        }
+        add_rays(i0b, nrb, tb);
+      } else {
+#pragma unroll 4
+        for (int k = 0; k < kma; ++k) {
+          const float2 a = s_alpha[k * TR_PAIRS + c];
+          const float4 d = __ldg(reinterpret_cast<const float4*>(da + k * TR_RB));
+          ta[0] = tr_fma2(tr_f2(d.x), a, ta[0]);
+          ta[1] = tr_fma2(tr_f2(d.y), a, ta[1]);
+          ta[2] = tr_fma2(tr_f2(d.z), a, ta[2]);
+          ta[3] = tr_fma2(tr_f2(d.w), a, ta[3]);
+        }
+      }
+      add_rays(i0a, nra, ta);
     }
     if (h > 0) s_part[h - 1][c] = integ;
     __syncthreads();
