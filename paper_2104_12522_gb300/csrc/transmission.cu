@@ -440,16 +440,34 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
         const float dwa = act_a ? ((hi - lo == 1) ? 1.f : ((ja == lo || ja == hi - 1) ? 0.5f : 1.f)) : 0.f;
         const float dwb = act_b ? ((hi - lo == 1) ? 1.f : ((jb == lo || jb == hi - 1) ? 0.5f : 1.f)) : 0.f;
         const int warp = tid >> 5, lane = tid & 31;
-        for (int b = 0; b < n_bands; ++b) {
-          const float Wa = act_a ? __ldg(filt + (int64_t)b * N + ja) * dwa : 0.f;
-          const float Wb = act_b ? __ldg(filt + (int64_t)b * N + jb) * dwb : 0.f;
-          float num = fmaf(Wa, delta.x, Wb * delta.y), den = Wa + Wb;
+        // four bands at a time: their filter weights are loaded together
+        for (int b0 = 0; b0 < n_bands; b0 += 4) {
+          float Wa[4], Wb[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int b = b0 + q;
+            Wa[q] = (act_a && b < n_bands) ? __ldg(filt + (int64_t)b * N + ja) * dwa : 0.f;
+            Wb[q] = (act_b && b < n_bands) ? __ldg(filt + (int64_t)b * N + jb) * dwb : 0.f;
+          }
+          float num[4], den[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            num[q] = fmaf(Wa[q], delta.x, Wb[q] * delta.y);
+            den[q] = Wa[q] + Wb[q];
+          }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
-            num += __shfl_xor_sync(0xffffffffu, num, o);
-            den += __shfl_xor_sync(0xffffffffu, den, o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              num[q] += __shfl_xor_sync(0xffffffffu, num[q], o);
+              den[q] += __shfl_xor_sync(0xffffffffu, den[q], o);
+            }
           }
-          if (lane == 0) s_red[warp][b] = make_float2(num, den);
+          if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (b0 + q < n_bands) s_red[warp][b0 + q] = make_float2(num[q], den[q]);
+          }
         }
       }
       __syncthreads();
