@@ -421,53 +421,54 @@ trans_kernel(const float* __restrict__ grid, int Lg, int M, int64_t N, const TrL
     }
     if (h > 0) s_part[h - 1][c] = integ;
     __syncthreads();
-    float2 delta = tr_f2(0.f);
     if (h == 0) {
 #pragma unroll
       for (int q = 0; q < TR_SPLIT - 1; ++q) integ = __fadd2_rn(integ, s_part[q][c]);
       const float rbot = rp + s_lev[L - 1].z;
       const float rs = s_in.r_star;
       const float d0 = (rbot / rs) * (rbot / rs);
-      delta = make_float2(d0 + 2.f * integ.x / (rs * rs), d0 + 2.f * integ.y / (rs * rs));
+      const float2 delta = make_float2(d0 + 2.f * integ.x / (rs * rs), d0 + 2.f * integ.y / (rs * rs));
       if (spectra) {
         const int64_t o = (offs ? offs[i] : (int64_t)i * N) - lo;
         if (act_a) spectra[o + ja] = delta.x;
         if (act_b) spectra[o + jb] = delta.y;
       }
+      s_part[0][c] = delta;                       // the column's depths for every part's bands
     }
     if (n_bands > 0) {
-      if (h == 0) {
-        const float dwa = act_a ? ((hi - lo == 1) ? 1.f : ((ja == lo || ja == hi - 1) ? 0.5f : 1.f)) : 0.f;
-        const float dwb = act_b ? ((hi - lo == 1) ? 1.f : ((jb == lo || jb == hi - 1) ? 0.5f : 1.f)) : 0.f;
-        const int warp = tid >> 5, lane = tid & 31;
-        // four bands at a time: their filter weights are loaded together
-        for (int b0 = 0; b0 < n_bands; b0 += 4) {
-          float Wa[4], Wb[4];
+      __syncthreads();
+      // band sums of the tile: part h takes bands h, h + TR_SPLIT, ..., four
+      // at a time with their filter weights loaded together
+      const float2 delta = s_part[0][c];
+      const float dwa = act_a ? ((hi - lo == 1) ? 1.f : ((ja == lo || ja == hi - 1) ? 0.5f : 1.f)) : 0.f;
+      const float dwb = act_b ? ((hi - lo == 1) ? 1.f : ((jb == lo || jb == hi - 1) ? 0.5f : 1.f)) : 0.f;
+      const int wp = (tid & (TR_PAIRS - 1)) >> 5, lane = tid & 31;   // warp within the part
+      for (int b0 = h; b0 < n_bands; b0 += 4 * TR_SPLIT) {
+        float Wa[4], Wb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int b = b0 + q * TR_SPLIT;
+          Wa[q] = (act_a && b < n_bands) ? __ldg(filt + (int64_t)b * N + ja) * dwa : 0.f;
+          Wb[q] = (act_b && b < n_bands) ? __ldg(filt + (int64_t)b * N + jb) * dwb : 0.f;
+        }
+        float num[4], den[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          num[q] = fmaf(Wa[q], delta.x, Wb[q] * delta.y);
+          den[q] = Wa[q] + Wb[q];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const int b = b0 + q;
-            Wa[q] = (act_a && b < n_bands) ? __ldg(filt + (int64_t)b * N + ja) * dwa : 0.f;
-            Wb[q] = (act_b && b < n_bands) ? __ldg(filt + (int64_t)b * N + jb) * dwb : 0.f;
+            num[q] += __shfl_xor_sync(0xffffffffu, num[q], o);
+            den[q] += __shfl_xor_sync(0xffffffffu, den[q], o);
           }
-          float num[4], den[4];
+        }
+        if (lane == 0) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            num[q] = fmaf(Wa[q], delta.x, Wb[q] * delta.y);
-            den[q] = Wa[q] + Wb[q];
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              num[q] += __shfl_xor_sync(0xffffffffu, num[q], o);
-              den[q] += __shfl_xor_sync(0xffffffffu, den[q], o);
-            }
-          }
-          if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (b0 + q < n_bands) s_red[warp][b0 + q] = make_float2(num[q], den[q]);
-          }
+          for (int q = 0; q < 4; ++q)
+            if (b0 + q * TR_SPLIT < n_bands) s_red[wp][b0 + q * TR_SPLIT] = make_float2(num[q], den[q]);
         }
       }
       __syncthreads();
