@@ -9,17 +9,19 @@
 // rows for proposals whose layer temperatures fall in the same bracket) are
 // shared through L2.  For its unit a CTA
 //   1. evaluates the proposal's five-parameter T(P) profile at every layer
-//      (one thread per layer) and keeps each layer's temperature bracket,
-//      weight and c2/T in shared memory, with the abundance coefficients
-//      X_s / (mu m_u) = X0_s 10^{a_s} / (mu m_u);
-//   2. runs one thread per wavenumber down the column: opacity interpolated
-//      in T and summed over species (coalesced grid-row reads, the next
-//      layer's rows requested before the current layer is computed), the
-//      trapezoid optical depth, the Planck source, per Gauss-Legendre angle
-//      the log2 transmittance, and the flux as a sum over layers of the
-//      layer-mean source times the drop of the quadrature-weighted
-//      transmittance (the angle sum taken inside the layer sum, which keeps
-//      one running value per angle instead of three);
+//      (one thread per layer) and keeps, per layer, the grid row offsets of
+//      its temperature bracket, the interpolation weights times the
+//      abundance coefficients X_s / (mu m_u) = X0_s 10^{a_s} / (mu m_u) and
+//      the Planck terms in a shared-memory record;
+//   2. runs one thread per pair of neighbouring wavenumbers down the column,
+//      the pair's arithmetic on packed FP32: opacity interpolated in T and
+//      summed over species (8-byte grid-row reads, the next layer's rows
+//      requested before the current layer is computed), the trapezoid
+//      optical depth, the Planck source, the transmittance at each
+//      Gauss-Legendre angle from the running vertical optical depth, and the
+//      flux as a sum over layers of the layer-mean source times the drop of
+//      the quadrature-weighted transmittance (the angle sum taken inside the
+//      layer sum, so no per-angle state is kept);
 //   3. writes the spectrum and the tile's band partial sums; the CTA that
 //      finishes a proposal's last tile sums its partials in a fixed order
 //      (FP64) into the band values.

@@ -1,7 +1,10 @@
 // Per-proposal forward model on the opacity grid (Sec. 3 second pass; Sec. 4
 // items 3, 8 and 9) and the spectrum integrator (Sec. 3).
 //
-// Emission path, per batch:
+// Emission path, per batch: by default one persistent fused launch
+// (forward_fused.cu, emission_fused.cuh); the three launches below remain
+// as BART_LAUNCH_SPLIT, the path for grids too large for the fused kernel's
+// 32-bit row offsets, and the kernels of the allocation-free entry point:
 //   tp_kernel        one thread per (proposal, layer): T from the five-parameter
 //                    profile (or the given profile), clamp, temperature bracket
 //                    (m, w) on the grid axis; per proposal the mass-opacity
