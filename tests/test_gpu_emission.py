@@ -127,6 +127,50 @@ def test_batched_emission_from_grid(ctx, torch, grid_case, n_angles):
     assert es < RTOL and eb < RTOL
 
 
+@pytest.mark.parametrize("S,n_angles,N", [(1, 16, 701), (1, 1, 700), (3, 2, 702), (4, 16, 701)])
+def test_fused_instantiations(ctx, torch, S, n_angles, N):
+    """Species counts and angle counts of the fused generation beyond the
+    other tests (one species, 1, 2 and 16 angles), on odd and even n_nu
+    (4-byte and 8-byte grid reads), with spans that start and end inside a
+    pair and a tile, against the oracle on the same seeded opacity field."""
+    import paper_2104_12522_gb300 as bart
+    L, M, dnu = 30, 7, 0.05
+    p = W.log_pressures(L, 1e-8, 100.0)
+    t = np.linspace(500.0, 3000.0, M)
+    field = W.opacity_field(S, p, t, N, seed=3600 + S)
+    g_dev = torch.tensor(field, device="cuda")
+    nu = bart.NuGrid(1000.0, dnu, N)
+    n = 11
+    theta = W.proposals(n, generation=31, n_species=S)
+    lo = np.array([0, 1, 3, 255, 0, 7] + [0] * (n - 6), np.int64)
+    hi = np.array([N, N - 1, 260, 514, 1, N] + [N] * (n - 6), np.int64)
+    offs = np.concatenate([[0], np.cumsum(hi - lo)]).astype(np.int64)
+    filt = W.gaussian_filters(W.nu_axis(1000.0, dnu, N), 3, 1003.0, 1030.0, 2.0, 10.0)
+    x0 = [W.BASE_VMR] * S
+    cfg = _cfg(n_angles, x0)
+    dev = lambda a: torch.tensor(a, device="cuda")
+    spec = torch.empty(int(offs[-1]), dtype=torch.float32, device="cuda")
+    bands = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    ctx.forward_spectra_batch(g_dev, p, t, nu, cfg, theta=dev(theta), nu_lo=dev(lo), nu_hi=dev(hi),
+                              spec_offsets=dev(offs), spectra=spec, filters=dev(filt), bands=bands)
+    ctx.sync()
+    spec, bands = spec.cpu().numpy(), bands.cpu().numpy()
+    ocfg = dict(g=cfg["g"], t_int=cfg["t_int"], t_star=cfg["t_star"], r_star_tp=cfg["r_star_tp"],
+                a_orbit=cfg["a_orbit"], t_min=500.0, t_max=3000.0, x0=x0, mu=cfg["mu"], n_angles=n_angles)
+    g_ora = field.astype(np.float64)
+    nu_ax = W.nu_axis(1000.0, dnu, N)
+    es, eb = 0.0, 0.0
+    for i in range(n):
+        F = Fw.emission_spectrum(g_ora[..., lo[i]:hi[i]], p, t, nu_ax[lo[i]:hi[i]], theta[i], ocfg)
+        es = max(es, max_rel(spec[offs[i]:offs[i + 1]], F))
+        Bo = R.band_integrate(F, filt, nu_lo=lo[i])
+        ok = Bo != 0
+        if ok.any():
+            eb = max(eb, max_rel(bands[i][ok], Bo[ok]))
+    print(f"fused S={S}, {n_angles} angles, n_nu={N}: spectra {es:.2e}, bands {eb:.2e}")
+    assert es < RTOL and eb < RTOL
+
+
 def test_band_integrate_standalone(ctx, torch):
     rng = np.random.default_rng(9)
     N, n = 1000, 5
