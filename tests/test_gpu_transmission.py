@@ -79,6 +79,55 @@ def test_uneven_instances(ctx, torch, case):
     assert es < RTOL and eb < RTOL
 
 
+@pytest.mark.parametrize("S,N,nb", [(1, 901, 40), (2, 900, 12), (3, 901, 5)])
+def test_instantiations(ctx, torch, S, N, nb):
+    """Species counts beyond the other tests on odd and even n_nu (4-byte and
+    8-byte grid reads), up to 40 bands (a second round of each part's bands),
+    with spans that start and end inside a pair, against the oracle on the
+    same seeded opacity field."""
+    import dataclasses
+    import paper_2104_12522_gb300 as bart
+    Lg, M, dnu = 30, 6, 0.05
+    p = W.log_pressures(Lg, 1e-8, 100.0)
+    t = np.linspace(500.0, 3000.0, M)
+    field = W.opacity_field(S, p, t, N, seed=3700 + S)
+    g_dev = torch.tensor(field, device="cuda")
+    nu = bart.NuGrid(1000.0, dnu, N)
+    inst = W.instances(8, N, lmin=40, lmax=150, span_lo=1, span_hi=N, seed=4100 + S)
+    inst = dataclasses.replace(inst, theta=np.ascontiguousarray(inst.theta[:, :5 + S]))
+    inst.nu_lo[0], inst.nu_hi[0] = 3, 130
+    inst.nu_lo[1], inst.nu_hi[1] = 0, N
+    inst.nu_lo[2], inst.nu_hi[2] = N - 1, N
+    filt = W.gaussian_filters(W.nu_axis(1000.0, dnu, N), nb, 1001.0, 1044.0, 2.0, 15.0)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")
+    offs = inst.offsets
+    n = len(inst.n_levels)
+    spec = torch.empty(int(offs[-1]), dtype=torch.float32, device="cuda")
+    bands = torch.empty((n, nb), dtype=torch.float32, device="cuda")
+    cfg = _cfg(S)
+    ctx.forward_spectra_batch(g_dev, p, t, nu, cfg, theta=dev(inst.theta), n_levels=dev(inst.n_levels),
+                              nu_lo=dev(inst.nu_lo), nu_hi=dev(inst.nu_hi), spec_offsets=dev(offs),
+                              r_planet=dev(inst.r_planet), r_star=dev(inst.r_star), spectra=spec,
+                              filters=dev(filt), bands=bands)
+    ctx.sync()
+    spec, bands = spec.cpu().numpy(), bands.cpu().numpy()
+    ocfg = dict(g=cfg["g"], t_int=cfg["t_int"], t_star=cfg["t_star"], r_star_tp=cfg["r_star_tp"],
+                a_orbit=cfg["a_orbit"], t_min=500.0, t_max=3000.0, x0=cfg["x0"], mu=cfg["mu"],
+                p_ref=cfg["p_ref"], p_top=1e-8, p_bot=100.0)
+    g_ora = field.astype(np.float64)
+    es, eb = 0.0, 0.0
+    for i in range(n):
+        d = Fw.transmission_spectrum(g_ora, p, t, 1000.0, dnu, inst, i, ocfg)
+        es = max(es, max_rel(spec[offs[i]:offs[i + 1]], d))
+        Bo = R.band_integrate(d, filt, nu_lo=int(inst.nu_lo[i]))
+        ok = Bo != 0
+        if ok.any():
+            eb = max(eb, max_rel(bands[i][ok], Bo[ok]))
+        assert np.all(bands[i][~ok] == 0.0)
+    print(f"transmission S={S}, n_nu={N}, {nb} bands: spectra {es:.2e}, bands {eb:.2e}")
+    assert es < RTOL and eb < RTOL
+
+
 def test_zero_opacity_gives_bottom_radius(ctx, torch, case):
     S, p, t, N, dnu, nu, g_dev, g_ora = case
     zero = torch.zeros_like(g_dev)
