@@ -129,8 +129,13 @@ __device__ __forceinline__ float taylor_re(float x, float y, const float2* __res
 // cancellation: the row holds the derivative coefficients themselves); for
 // x >= 5, G from its asymptotic series
 //   G = (2 / sqrt(pi)) sum_{k=1}^{10} (2k-1)!! / (2 x^2)^k
-// (truncation <= 2.7e-7 relative at x = 5) and e^{-x^2} with a compensated
-// exponent.  One branch-free form for the core and the wings of a line with
+// (truncation <= 2.7e-7 relative at x = 5), e^{-x^2} with a compensated
+// exponent.  The bracket of the y^3 term, 4 / sqrt(pi) + G (6 - 4 x^2), is
+// O(x^-4) while its two parts are O(1): in FP32 it cancels with an absolute
+// error ~ x^2 eps, which far in a line's wings would exceed the term itself.
+// So the y^3 term is taken only below x = 40 (cancellation error there below
+// 3e-8 of Re w); beyond, the whole term is below y^2 / x^2 <= 2.5e-7 of Re w
+// and is left out.  One branch-free form for the core and the wings of a line with
 // small y.  Relative error of Re w (FP32 against the FP64 Faddeeva function)
 // <= 2.3e-6 for x >= 0, 1e-10 <= y <= 0.02.
 constexpr float SMALL_Y = 0.02f;
@@ -176,7 +181,8 @@ __device__ __forceinline__ float small_y_re(float x, float y, const float2* __re
     g = TWO_SQRTPI * t * sum;
   }
   const float x2 = x * x, y2 = y * y;
-  const float gy = fmaf(y2 * (1.0f / 6.0f), fmaf(g, fmaf(-4.0f, x2, 6.0f), 2.0f * TWO_SQRTPI), g);
+  const float cub = x < 40.0f ? fmaf(g, fmaf(-4.0f, x2, 6.0f), 2.0f * TWO_SQRTPI) : 0.0f;
+  const float gy = fmaf(y2 * (1.0f / 6.0f), cub, g);
   return fmaf(e, fmaf(y2, fmaf(-2.0f, x2, 1.0f), 1.0f), y * gy);
 }
 

@@ -8,7 +8,9 @@ Faddeeva function: the expansion of Re w(x + i y) in y about the real axis,
 with G and e^{-x^2} below x = 5 from the real-axis Taylor coefficients of w
 (derived here independently, from wofz and the derivative recurrence
 w' = -2 z w + 2i / sqrt(pi)), above x = 5 from the asymptotic series of G
-and a compensated exponent.  The arithmetic is emulated in FP32 step by
+and a compensated exponent; the y^3 term only below x = 40 (its bracket
+4 / sqrt(pi) + G (6 - 4 x^2) cancels like x^2 eps in FP32, and a line's
+fixup range can reach its cutoff edge, thousands of Doppler widths out).  The arithmetic is emulated in FP32 step by
 step as the kernel performs it, which pins the relative error bound stated
 for the kernel (2.3e-6) and catches a dropped or mis-signed term."""
 import math
@@ -69,13 +71,14 @@ def small_y_re(x, y):
             s = F32(s * t + F32(SERIES[k]))
         g = F32(F32(2.0 / SQRTPI) * t * s)
     x2, y2 = F32(x * x), F32(y * y)
-    gy = F32(y2 * F32(1.0 / 6.0)) * F32(g * F32(6.0 - 4.0 * x2) + F32(4.0 / SQRTPI)) + g
+    cub = F32(g * F32(6.0 - 4.0 * x2) + F32(4.0 / SQRTPI)) if x < 40.0 else F32(0.0)
+    gy = F32(y2 * F32(1.0 / 6.0)) * cub + g
     return float(F32(e * F32(F32(1.0) + y2 * F32(1.0 - 2.0 * x2)) + y * F32(gy)))
 
 
 def test_small_y_form_against_wofz():
     worst = 0.0
-    xs = np.concatenate([np.linspace(0.0, 7.0, 1401), np.linspace(7.0, 40.0, 167)])
+    xs = np.concatenate([np.linspace(0.0, 7.0, 1401), np.linspace(7.0, 40.0, 167), np.geomspace(40.0, 5000.0, 120)])
     for y in (1e-10, 1e-8, 1e-6, 1e-4, 1e-3, 5e-3, 1e-2, 2e-2):
         for x in xs:
             ref = wofz(complex(x, y)).real
