@@ -103,3 +103,44 @@ def test_scale_height_law():
     g_eff = G * (1.138 * 7.1492e9 / R1) ** 2
     H = K_BOLTZ * 1200.0 / (2.3 * AMU * g_eff)
     assert abs((R2 - R1) / (2 * H) - 1) < 0.02
+
+
+@pytest.mark.parametrize("lk,lg1,lg2,alpha", [(-1.0, 0.6, -1.2, 0.3), (-2.5, -1.4, 0.9, 0.8), (0.0, 0.0, -0.5, 0.0)])
+def test_irradiated_profile_is_gray_radiative_equilibrium(lk, lg1, lg2, alpha):
+    """The profile is the gray two-stream solution in radiative equilibrium
+    with an irradiating beam of isotropic incidence, attenuated exactly, in
+    two visible channels.  In units where B = T^4:
+      thermal field (Eddington closure): dJ/dtau = 3 H,  J(0) = 2 H(0);
+      radiative equilibrium: J - B = -sum_c w_c gamma_c J_c;
+      visible channel c: J_c = c0 E2(gamma_c tau), H_c = -c0 E3(gamma_c tau);
+      flux conservation: H = H_int - sum_c w_c H_c,
+    with w = (1 - alpha, alpha), H_int = T_int^4 / 4 and c0 = T_irr^4 / 2 (the
+    absorbed stellar flux c0 E3(0) = T_irr^4 / 4 in the units of H_int).  The
+    oracle's T is checked against these relations, E3 integrated by
+    quadrature; a changed term of the profile breaks one of them."""
+    beta, t_int = 1.05, 100.0
+    th = [lk, lg1, lg2, alpha, beta]
+    kappa = 10.0 ** lk
+    gam = np.array([10.0 ** lg1, 10.0 ** lg2])
+    w = np.array([1.0 - alpha, alpha])
+    t_irr = beta * np.sqrt(0.756 * 6.957e10 / (2 * 0.0312 * 1.495978707e13)) * 5000.0
+    c0, h_int = t_irr ** 4 / 2.0, t_int ** 4 / 4.0
+
+    def tau_to_p(tau):
+        return np.asarray(tau) * G / (kappa * 1e6)
+
+    def J(tau):
+        B = _T(th, tau_to_p(tau), t_int) ** 4
+        return B - c0 * sum(w[c] * gam[c] * expn(2, gam[c] * np.asarray(tau)) for c in range(2))
+
+    def H(t):
+        return h_int + c0 * sum(w[c] * expn(3, gam[c] * t) for c in range(2))
+
+    scale = _T(th, tau_to_p(np.array([1e3])), t_int)[0] ** 4
+    j0 = J(np.array([1e-15]))[0]
+    assert abs(j0 - 2.0 * H(0.0)) < 1e-12 * scale
+    taus = np.concatenate([[1e-15], np.geomspace(1e-4, 60.0 / gam.min(), 25)])
+    jt = J(taus)
+    for a, b, ja, jb in zip(taus[:-1], taus[1:], jt[:-1], jt[1:]):
+        flux, _ = integrate.quad(H, a, b, epsabs=0.0, epsrel=1e-13, limit=200)
+        assert abs((jb - ja) - 3.0 * flux) < 1e-11 * scale
