@@ -20,9 +20,11 @@ def _case(L=40, seed=2):
     return p, T, nu, chi
 
 
-@pytest.mark.parametrize("tau_max", [None, 2.0])
-def test_contributions_add_up_to_the_flux(tau_max):
+@pytest.mark.parametrize("tau_max,thin", [(None, False), (2.0, False), (50.0, True)])
+def test_contributions_add_up_to_the_flux(tau_max, thin):
     p, T, nu, chi = _case()
+    if thin:                 # the limit is never reached and the bottom shows
+        chi = chi * 1e-5
     C = R.emission_contributions(chi, p, T, nu, G, 8, tau_max=tau_max)
     F = R.emission_flux(chi, p, T, nu, G, 8, tau_max=tau_max)
     assert np.allclose(C.sum(axis=0), F, rtol=1e-12)
@@ -34,6 +36,21 @@ def test_contributions_add_up_to_the_flux(tau_max):
             over = np.nonzero(tau[r, 1:] > tau_max)[0]
             kb = over[0] + 1 if over.size else len(p) - 1
             assert np.all(C[kb + 1:, r] == 0.0) and C[kb, r] > 0
+            assert thin == (over.size == 0)
+
+
+def test_contributions_stop_at_the_first_level_that_exceeds_the_limit():
+    # tau_k = k exactly (g = 1e6, chi = 1, pressures 1, 2, 3, ... bar): with
+    # tau_max = 3 the level with tau = 3 does not stop the sum, level 4 does.
+    L = 10
+    p = np.arange(1.0, L + 1.0)
+    T = np.linspace(700.0, 1600.0, L)
+    nu = np.linspace(1000, 3000, 5)
+    chi = np.ones((L, 5))
+    C = R.emission_contributions(chi, p, T, nu, 1e6, 4, tau_max=3.0)
+    assert np.all(C[5:] == 0.0) and np.all(C[4] > 0)
+    F = R.emission_flux(chi[:5], p[:5], T[:5], nu, 1e6, 4)
+    assert np.allclose(C.sum(axis=0), F, rtol=1e-13)
 
 
 def test_transparent_atmosphere_shows_only_the_bottom():

@@ -111,6 +111,46 @@ def test_band_constant_and_linear():
                        rtol=1e-12, atol=1e-12)
 
 
+def test_optical_depth_exact_for_opacity_linear_in_pressure():
+    # tau(P) = int_{P0}^{P} chi dP' / g; for chi = a + b P the layer trapezoid
+    # is exact, so every level's tau equals the integral in closed form.
+    p = np.sort(np.random.default_rng(8).uniform(1e-3, 50.0, 23))
+    a, b, g = 0.7, 0.031, 2182.73
+    P = p * 1e6
+    tau = R.optical_depth(a + b * P, p, g)
+    exact = (a * (P - P[0]) + 0.5 * b * (P ** 2 - P[0] ** 2)) / g
+    assert tau[0] == 0.0
+    assert np.max(np.abs(tau - exact) / np.maximum(exact, 1e-300)) < 1e-13
+
+
+@pytest.mark.parametrize("n,nu_lo", [(1, 4), (2, 0), (3, 5), (7, 11), (40, 3)])
+def test_band_of_linear_spectrum_over_whole_span_is_the_continuous_mean(n, nu_lo):
+    # A top-hat covering the whole span and a spectrum linear in nu: the band
+    # value is the mean of the linear function over [nu_first, nu_last],
+    # (f_first + f_last) / 2, which the trapezoid reproduces exactly only with
+    # half weights at both ends of the span.
+    W = np.zeros((1, 64), np.float32)
+    W[0, nu_lo:nu_lo + n] = 1.0
+    nu = 1000.0 + np.arange(nu_lo, nu_lo + n)
+    f = 5.0 + 0.37 * nu
+    got = R.band_integrate(f, W, nu_lo=nu_lo)[0]
+    assert abs(got / (0.5 * (f[0] + f[-1])) - 1) < 1e-14
+
+
+def test_band_value_is_invariant_to_the_filter_scale():
+    # B_b is a weighted mean: scaling a filter by any positive factor, however
+    # small its weight sum becomes, leaves the band value unchanged.
+    rng = np.random.default_rng(9)
+    f = rng.uniform(1, 2, 50)
+    W = rng.uniform(0, 1, (3, 50))
+    ref = R.band_integrate(f, W)
+    for s in (1e-3, 1e-9, 1e6):
+        assert np.allclose(R.band_integrate(f, W * s), ref, rtol=1e-13)
+    one = np.zeros((1, 50))
+    one[0, 17] = 1e-4                       # a single point of small weight
+    assert abs(R.band_integrate(f, one)[0] / f[17] - 1) < 1e-15
+
+
 def test_band_on_span_with_no_overlap_is_zero():
     W = np.zeros((1, 100), np.float32)
     W[0, 80:] = 1.0
@@ -154,4 +194,33 @@ def test_tau_limit_beyond_the_column_changes_nothing():
     chi = 10 ** rng.uniform(-3, 1, (30, 13))
     a = R.emission_flux(chi, p, T, nu, 2182.73, 4)
     b = R.emission_flux(chi, p, T, nu, 2182.73, 4, tau_max=1e300)
+    assert np.max(np.abs(a / b - 1)) < 1e-15
+
+
+def test_tau_limit_stops_at_the_first_level_that_exceeds_it():
+    # g = 1e6 and pressures 1, 2, 3, ... bar with chi = 1 give tau_k = k
+    # exactly.  A level whose tau equals the limit does not stop the
+    # integration; the first level with tau > tau_max is the bottom.
+    L = 12
+    p = np.arange(1.0, L + 1.0)
+    T = np.linspace(600.0, 1500.0, L)
+    nu = np.linspace(1000, 3000, 5)
+    chi = np.ones((L, 5))
+    assert np.array_equal(R.optical_depth(chi[:, 0], p, 1e6), np.arange(L, dtype=float))
+    got = R.emission_flux(chi, p, T, nu, 1e6, 4, tau_max=3.0)
+    exp = R.emission_flux(chi[:5], p[:5], T[:5], nu, 1e6, 4)       # levels 0..4 (tau = 4 > 3)
+    assert np.max(np.abs(got / exp - 1)) < 1e-14
+
+
+def test_tau_limit_above_a_thin_column_keeps_every_level():
+    # A column thin enough that its bottom level shows: a finite limit above
+    # the column's total optical depth changes nothing.
+    p = np.logspace(-6, 2, 30)
+    T = np.linspace(1800, 600, 30)
+    nu = np.linspace(1000, 3000, 7)
+    chi = np.full((30, 7), 1e-6)
+    tau = R.optical_depth(chi[:, 0], p, 2182.73)
+    assert 0.01 < tau[-1] < 0.1
+    a = R.emission_flux(chi, p, T, nu, 2182.73, 4)
+    b = R.emission_flux(chi, p, T, nu, 2182.73, 4, tau_max=5.0)
     assert np.max(np.abs(a / b - 1)) < 1e-15
