@@ -144,3 +144,46 @@ def test_irradiated_profile_is_gray_radiative_equilibrium(lk, lg1, lg2, alpha):
     for a, b, ja, jb in zip(taus[:-1], taus[1:], jt[:-1], jt[1:]):
         flux, _ = integrate.quad(H, a, b, epsabs=0.0, epsrel=1e-13, limit=200)
         assert abs((jb - ja) - 3.0 * flux) < 1e-11 * scale
+
+
+def test_radii_exact_for_temperature_linear_in_log_pressure():
+    # Hydrostatic balance with g = g_ref (R_p / r)^2:
+    #   d(1/r)/d ln P = k T / (mu m_u g_ref R_p^2),  r = R_p at P_ref;
+    # for T = a + b ln P the solution is closed form (and the level trapezoid
+    # with the reference pressure inserted as a node is exact).
+    p = np.logspace(-7, 2, 37)
+    a, b = 1400.0, 45.0
+    T = a + b * np.log(p)
+    rp = 1.21 * 7.1492e9
+    r = Tr.radii(p, T, rp, 0.1, G, 2.3)
+    C = K_BOLTZ / (2.3 * AMU * G * rp ** 2)
+    lp, lr = np.log(p), np.log(0.1)
+    exact = 1.0 / (1.0 / rp + C * (a * (lp - lr) + 0.5 * b * (lp ** 2 - lr ** 2)))
+    assert np.max(np.abs(r / exact - 1)) < 1e-13
+
+
+@pytest.mark.parametrize("alpha", [1e-11, 3e-10, 1e-8])
+def test_transit_depth_constant_extinction(alpha):
+    # Constant extinction alpha (cm^-1) in every shell: the chord through the
+    # shells above impact parameter b telescopes to the chord through the top
+    # sphere, tau(b) = 2 alpha sqrt(r_top^2 - b^2), at every level.  With the
+    # levels' trapezoid in b the depth is then fixed in closed form; and with
+    # many levels it converges (like h^1.5: the integrand has a square-root
+    # edge at the top sphere) to the continuous integral
+    #   R*^2 delta = r_bot^2 + U^2 - (1 - e^{-2 alpha U} (1 + 2 alpha U)) / (2 alpha^2),
+    # U^2 = r_top^2 - r_bot^2.
+    L = 3000
+    p = np.logspace(-8, 2, L)
+    T = np.linspace(900.0, 1700.0, L)
+    rp, rs, mu = 1.138 * 7.1492e9, 0.756 * 6.957e10, 2.3
+    r = Tr.radii(p, T, rp, 0.1, G, mu)
+    rho = p * 1e6 * mu * AMU / (K_BOLTZ * T)
+    chi = (alpha / rho)[:, None]
+    got = Tr.transit_depth(chi, p, T, r, rs, mu)[0]
+    f = -np.expm1(-2.0 * alpha * np.sqrt(np.maximum(r[0] ** 2 - r ** 2, 0.0)))
+    trap = np.sum((f[:-1] * r[:-1] + f[1:] * r[1:]) * (r[:-1] - r[1:]))
+    assert abs(got / ((r[-1] ** 2 + trap) / rs ** 2) - 1) < 1e-12
+    U2 = r[0] ** 2 - r[-1] ** 2
+    U = np.sqrt(U2)
+    cont = (r[-1] ** 2 + U2 - (1 - np.exp(-2 * alpha * U) * (1 + 2 * alpha * U)) / (2 * alpha ** 2)) / rs ** 2
+    assert abs(got / cont - 1) < 1e-5
