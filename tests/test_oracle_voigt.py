@@ -62,3 +62,15 @@ def test_faddeeva_vs_brute_force_convolution(x, y):
     # outside is accounted for by comparing relative to the peak scale
     got = V.voigt(nu, sig, gam)
     assert abs(got - ref) <= 1e-8 * got + 1e-12 * V.voigt(0.0, sig, gam)
+
+
+@pytest.mark.parametrize("x,y", [(0.0, 1e-3), (0.7, 0.05), (2.2, 0.6), (5.5, 2.0), (30.0, 0.3), (1.3, 8.0)])
+def test_faddeeva_re_is_the_voigt_function(x, y):
+    # Re w(x + i y) = K(x, y) = (y / pi) int exp(-t^2) / ((x - t)^2 + y^2) dt,
+    # by quadrature; on the real axis K(x, 0) = exp(-x^2).
+    f = lambda t: np.exp(-t * t) / ((x - t) ** 2 + y * y)
+    val, _ = integrate.quad(f, -12.0, 12.0, points=sorted({0.0, min(x, 11.9)}), limit=4000,
+                            epsabs=0, epsrel=1e-12)
+    k = y / np.pi * val
+    assert abs(V.faddeeva_re(x, y) / k - 1) < 1e-9
+    assert abs(V.faddeeva_re(x, 0.0) - np.exp(-x * x)) <= 1e-15 * max(np.exp(-x * x), 1e-300)

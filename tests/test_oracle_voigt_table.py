@@ -61,13 +61,29 @@ def test_the_shift_is_the_only_change():
 
 def test_nearest_node_by_brute_force():
     rng = np.random.default_rng(7)
-    lo, hi, n = 0.003, 0.05, 60
-    nodes = VT.width_nodes(lo, hi, n)
-    assert abs(nodes[0] - lo) < 1e-15 and abs(nodes[-1] / hi - 1) < 1e-14
-    v = np.exp(rng.uniform(math.log(lo) - 0.5, math.log(hi) + 0.5, 2000))
-    k = VT.nearest_node(v, lo, hi, n)
-    brute = np.argmin(np.abs(np.log(v)[:, None] - np.log(nodes)[None, :]), axis=1)
-    assert np.array_equal(k, brute)
+    lo, hi = 0.003, 0.05
+    for n in (1, 2, 3, 60):
+        nodes = VT.width_nodes(lo, hi, n)
+        assert len(nodes) == n
+        assert abs(nodes[0] - lo) < 1e-15 and (n == 1 or abs(nodes[-1] / hi - 1) < 1e-14)
+        v = np.exp(rng.uniform(math.log(lo) - 0.5, math.log(hi) + 0.5, 2000))
+        k = VT.nearest_node(v, lo, hi, n)
+        brute = np.argmin(np.abs(np.log(v)[:, None] - np.log(nodes)[None, :]), axis=1)
+        assert np.array_equal(k, brute)
+
+
+def test_window_of_a_single_point_and_the_inclusive_cutoff():
+    # A cutoff shorter than the grid step leaves each line at most one point,
+    # or two at exactly one cutoff on either side (|d| <= cutoff); the grid
+    # step and offsets are exact binary fractions.
+    dnu = 0.25
+    ll = _lines([1500.0 + 40 * dnu, 1500.0 + 120.5 * dnu], [-20.0, -20.5], [700.0, 100.0], [0.07, 0.07])
+    tab = _exact_table(ll, 0.2, 1100.0, 2)
+    got = VT.opacity_cell_table(ll, 0.2, 1100.0, 1500.0, dnu, 200, 0.5 * dnu, tab)
+    assert list(np.nonzero(got)[0]) == [40, 120, 121]
+    S = O.line_strength(ll.log10_s296, ll.nu0, ll.elow, 1100.0)
+    v0 = S[0] * O.voigt(0.0, tab["sigma_lo"], tab["gamma_lo"])
+    assert abs(got[40] / v0 - 1) < 1e-12
 
 
 def test_quantised_centre_is_within_half_a_sample():
