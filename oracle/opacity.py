@@ -51,10 +51,6 @@ def lorentz_gamma(gamma_ref, p_bar, T):
     return np.asarray(gamma_ref, np.float64) * p_bar * math.sqrt(T_REF / T)
 
 
-def grid_nu(nu_start, dnu, n_nu):
-    return nu_start + np.arange(n_nu, dtype=np.float64) * dnu
-
-
 def opacity_cell(lines, p_bar, T, nu_start, dnu, n_nu, cutoff, j_lo=0, j_hi=None, rel_threshold=0.0):
     """Opacity of one species at one (P, T) on grid points j in [j_lo, j_hi).
 

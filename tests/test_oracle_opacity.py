@@ -159,3 +159,80 @@ def test_threshold_is_relative_to_each_temperature():
     ok = a > 0
     assert np.array_equal(ok, b > 0)
     assert np.allclose(b[ok] / a[ok], 100.0, rtol=1e-12)
+
+
+def test_strength_follows_the_population_difference():
+    # Absorption minus stimulated emission: S(T) Q(T) is proportional to the
+    # Boltzmann population difference of the lower and upper levels,
+    # exp(-c2 E'' / T) - exp(-c2 (E'' + nu0) / T), with Q ~ T^1.5 and the
+    # textbook c2 = 1.438776877 cm K.  Low nu0 makes the stimulated term large.
+    c2 = 1.438776877
+    for nu0, E in ((150.0, 0.0), (420.0, 900.0), (2500.0, 3000.0)):
+        for T in (500.0, 1600.0, 3000.0):
+            ratio = O.line_strength(0.0, nu0, E, T) / O.line_strength(0.0, nu0, E, 296.0)
+            pop = lambda t: (np.exp(-c2 * E / t) - np.exp(-c2 * (E + nu0) / t)) / t ** 1.5
+            assert abs(ratio / (pop(T) / pop(296.0)) - 1) < 1e-8
+
+
+def _brute_force(lines, p, T, nu_start, dnu, n_nu, cutoff, rel_threshold=0.0):
+    # The point-sampled sum written out: every line against every point.
+    nu = nu_start + np.arange(n_nu) * dnu
+    S = O.line_strength(lines.log10_s296, lines.nu0, lines.elow, T)
+    floor = rel_threshold * S.max() if rel_threshold > 0 else 0.0
+    out = np.zeros(n_nu)
+    for j in range(n_nu):
+        terms = []
+        for i in range(len(lines.nu0)):
+            d = nu[j] - lines.nu0[i]
+            if abs(d) <= cutoff and S[i] >= floor:
+                sig = O.doppler_sigma(lines.nu0[i], T, lines.mass_amu)
+                gam = O.lorentz_gamma(lines.gamma_ref[i], p, T)
+                terms.append(S[i] * V.voigt(d, sig, gam))
+        out[j] = sum(sorted(terms))
+    return out
+
+
+def test_dense_list_against_every_line_at_every_point():
+    # Lines inside the grid, beyond both ends and exactly one cutoff (plus or
+    # minus one grid step) from grid points; binary-exact grid and offsets, a
+    # sub-range starting inside the grid.
+    rng = np.random.default_rng(12)
+    dnu, cut, n = 0.25, 3.0, 160
+    edge = 1000.0 + np.array([-cut - dnu, -cut, -cut + dnu, 17 * dnu - cut, 40 * dnu + cut,
+                              (n - 1) * dnu + cut, (n - 1) * dnu + cut + dnu])
+    nu0 = np.sort(np.concatenate([edge, rng.uniform(995.0, 1045.0, 45)]))
+    ll = _lines(nu0, rng.uniform(-23, -19, nu0.size), rng.uniform(0, 3000, nu0.size),
+                rng.uniform(0.05, 0.1, nu0.size))
+    for p, T in ((1e-4, 800.0), (3.0, 2100.0)):
+        exp = _brute_force(ll, p, T, 1000.0, dnu, n, cut)
+        got = O.opacity_cell(ll, p, T, 1000.0, dnu, n, cut)
+        assert np.max(np.abs(got - exp)) <= 1e-14 * np.max(exp)
+        assert np.array_equal(got > 0, exp > 0)
+        part = O.opacity_cell(ll, p, T, 1000.0, dnu, n, cut, j_lo=37, j_hi=121)
+        assert np.array_equal(part, got[37:121])
+        one = O.opacity_cell(ll, p, T, 1000.0, dnu, n, cut, j_lo=59, j_hi=60)
+        assert np.array_equal(one, got[59:60])
+        assert O.opacity_cell(ll, p, T, 1000.0, dnu, n, cut, j_lo=70, j_hi=70).size == 0
+
+
+def test_threshold_at_exactly_one_keeps_the_strongest_line():
+    # The bound keeps lines at or above rel_threshold x the strongest: at
+    # exactly 1 the strongest line alone survives.
+    ll = _random_lines(30, 35)
+    T = 1250.0
+    exp = _brute_force(ll, 0.2, T, 1499.0, 0.01, 1200, 2.0, rel_threshold=1.0)
+    got = O.opacity_cell(ll, 0.2, T, 1499.0, 0.01, 1200, 2.0, rel_threshold=1.0)
+    assert np.count_nonzero(got) > 0
+    assert np.max(np.abs(got - exp)) <= 1e-14 * np.max(exp)
+
+
+def test_cells_keep_lines_of_any_strength_by_default():
+    # No bound unless asked: a line 1e-8 times weaker than its neighbour
+    # still adds its own opacity.
+    strong = _lines([1500.0], [-19.0], [300.0], [0.07])
+    weak = _lines([1500.5], [-27.0], [300.0], [0.07])
+    both = _lines([1500.0, 1500.5], [-19.0, -27.0], [300.0, 300.0], [0.07, 0.07])
+    args = ([0.05], [1000.0], 1495.0, 0.01, 1000, 5.0)
+    o_s, o_w, o_b = (O.opacity_cells([x], *args)[0, 0] for x in (strong, weak, both))
+    assert np.max(np.abs(o_b - (o_s + o_w))) <= 1e-14 * np.max(o_b)
+    assert np.max(np.abs(o_b - o_s)) > 0.5 * np.max(o_w)
