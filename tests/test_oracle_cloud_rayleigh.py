@@ -150,3 +150,36 @@ def test_rayleigh_transit_slope_is_four_scale_heights():
     R_eff = [np.sqrt(_iso_transit(np.array([v, v + 1.0]), T=T)[0]) * RS for v in nus]
     H = K_BOLTZ * T * (0.5 * (R_eff[0] + R_eff[1])) ** 2 / (MU * AMU * G * RP ** 2)
     assert abs((R_eff[1] - R_eff[0]) / (4 * H) - 1) < 0.01
+
+
+def test_transit_span_maps_each_point_to_its_wavenumber():
+    # A span starting inside the grid with a step other than 1: each point
+    # of the instance's spectrum is the Rayleigh transit of the wavenumber
+    # nu_start + (nu_lo + j) dnu, evaluated alone.
+    n_grid, lo, hi, dnu, nu_start = 12, 3, 10, 750.0, 9000.0
+    grid = np.zeros((1, 2, 1, n_grid))
+    inst = SimpleNamespace(n_levels=np.array([300]), theta=np.zeros((1, 6)), nu_lo=np.array([lo]),
+                           nu_hi=np.array([hi]), r_planet=np.array([RP]), r_star=np.array([RS]))
+    cfg = _cfg(t_min=1200.0, t_max=1200.0, rayleigh_coef=A_H2)
+    span = Fw.transmission_spectrum(grid, [1e-8, 100.0], [1000.0], nu_start, dnu, inst, 0, cfg)
+    assert span.size == hi - lo
+    for j in (0, 4, hi - lo - 1):
+        v = nu_start + (lo + j) * dnu
+        alone = _iso_transit(np.array([v, v + 1.0]), L=300)[0]
+        assert abs(span[j] / alone - 1) < 1e-13
+    assert np.all(np.diff(span) > 0)               # sigma_R grows with nu
+
+
+def test_contributions_carry_rayleigh_and_the_deck():
+    # The per-layer contributions of a cloudy, Rayleigh-scattering column add
+    # up to its flux, and nothing below the deck contributes.
+    p, T, nu, _ = _emission_case()
+    rng = np.random.default_rng(6)
+    grid = rng.uniform(0, 1e-24, (1, 30, 1, nu.size))
+    cfg = _cfg(rayleigh_coef=1e4 * A_H2, p_cloud=p[21])
+    C = Fw.emission_contributions(grid, p, [1000.0], nu, np.zeros(6), cfg, T=T)
+    F = Fw.emission_spectrum(grid, p, [1000.0], nu, np.zeros(6), cfg, T=T)
+    assert np.allclose(C.sum(axis=0), F, rtol=1e-12)
+    assert np.all(C[22:] == 0.0)
+    off = Fw.emission_contributions(grid, p, [1000.0], nu, np.zeros(6), _cfg(p_cloud=p[21]), T=T)
+    assert np.max(np.abs(C.sum(axis=0) / off.sum(axis=0) - 1)) > 1e-3

@@ -71,6 +71,30 @@ def test_interpolation_exact_on_linear_grids():
     assert np.allclose(got, exp, rtol=1e-12)
 
 
+@pytest.mark.parametrize("n_t,n_p", [(1, 5), (6, 1), (1, 1), (2, 2), (2, 5)])
+def test_interpolation_on_degenerate_and_two_node_axes(n_t, n_p):
+    # A grid with one node along an axis is constant along it; with two
+    # nodes the bracket is the single interval.  Grids linear in the other
+    # axis are reproduced exactly, in (log10 P, T) and, for layer_opacity, in T.
+    rng = np.random.default_rng(n_t * 10 + n_p)
+    t_ax = np.linspace(700, 2500, n_t)
+    p_ax = np.logspace(-6, 1, n_p)
+    a, b, c = rng.uniform(1, 2, (3, 2, 5))
+    bt = b if n_t > 1 else 0 * b
+    cp = c if n_p > 1 else 0 * c
+    grid = (a[:, None, None, :] + bt[:, None, None, :] * t_ax[None, None, :, None]
+            + cp[:, None, None, :] * np.log10(p_ax)[None, :, None, None])
+    T = rng.uniform(700, 2500, 6)
+    Pl = 10 ** rng.uniform(-6, 1, 6)
+    got = Fw.level_opacity_bilinear(grid, p_ax, t_ax, Pl, T)
+    exp = a[:, None, :] + bt[:, None, :] * T[None, :, None] + cp[:, None, :] * np.log10(Pl)[None, :, None]
+    assert np.allclose(got, exp, rtol=1e-12)
+    lay = Fw.layer_opacity(grid, t_ax, T[:n_p])
+    exp_l = (a[:, None, :] + bt[:, None, :] * T[:n_p][None, :, None]
+             + cp[:, None, :] * np.log10(p_ax)[None, :, None])
+    assert np.allclose(lay, exp_l, rtol=1e-12)
+
+
 def _iso_atm(L=200, T=1200.0, mu=2.3, g=G, rp=1.138 * 7.1492e9):
     p = np.logspace(-8, 2, L)
     return p, np.full(L, T), Tr.radii(p, np.full(L, T), rp, 0.1, g, mu)
