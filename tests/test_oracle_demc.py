@@ -1,6 +1,9 @@
-"""Pins of the oracle sampler: it recovers a correlated Gaussian's mean,
-variances and 68.27% credible-region content within the App. C standard
-errors, with and without a (deliberately wrong) surrogate screen."""
+"""Pins of the oracle sampler: from an overdispersed start it recovers a
+correlated Gaussian's mean, variances and 68.27% credible-region content
+within the App. C standard errors, with and without a (deliberately wrong)
+surrogate screen; at stationarity its acceptance rates equal those of its
+proposals computed by plain Monte Carlo from independent draws of the
+target."""
 import numpy as np
 import pytest
 from scipy.stats import chi2
@@ -34,10 +37,12 @@ def test_recovers_gaussian(screened, beta, margin):
     # a surrogate with the wrong scale: delayed acceptance keeps the exact target
     Ls = (lambda v: -0.5 * 0.7 * (v - mu) @ inv @ (v - mu)) if screened else None
     rng = np.random.default_rng(6000)
-    x0 = mu + rng.normal(size=(16, 9)) * np.sqrt(np.diag(cov))
+    # overdispersed start: a sampler that does not move fails the check
+    x0 = mu + rng.normal(size=(16, 9)) * np.sqrt(np.diag(cov)) * 3.0
     hist, acc = D.run(L, x0, lo, hi, 3000, rng, surrogate=Ls, beta=beta, margin=margin)
     e = _check(hist, mu, cov, burn=500)
     assert e > 300
+    assert np.all(D.gelman_rubin(hist[500:]) < 1.05)
 
 
 def test_speis_of_white_noise_and_ar1():
@@ -60,7 +65,7 @@ def test_demczs_recovers_gaussian_with_three_chains():
     rng = np.random.default_rng(6010)
     sd = np.sqrt(np.diag(cov))
     z0 = mu + rng.normal(size=(90, 9)) * sd * 2.0
-    x0 = mu + rng.normal(size=(3, 9)) * sd
+    x0 = mu + rng.normal(size=(3, 9)) * sd * 3.0
     hist, acc, Z = D.run_zs(L, x0, z0, lo, hi, 12000, rng, thin=10)
     e = _check(hist, mu, cov, burn=2000)
     assert e > 150
@@ -76,7 +81,7 @@ def test_demczs_snooker_only_keeps_the_target():
     rng = np.random.default_rng(6011)
     sd = np.sqrt(np.diag(cov))
     z0 = mu + rng.normal(size=(90, 9)) * sd
-    x0 = mu + rng.normal(size=(4, 9)) * sd
+    x0 = mu + rng.normal(size=(4, 9)) * sd * 3.0
     hist, acc, _ = D.run_zs(L, x0, z0, lo, hi, 12000, rng, thin=10, p_snooker=1.0)
     _check(hist, mu, cov, burn=2000)
 
@@ -89,7 +94,169 @@ def test_gelman_rubin_limits():
     assert np.all(D.gelman_rubin(apart) > 2.0)
     # closed form for two chains of constant-variance noise with means +-a:
     # W = 1, B = n * 2 a^2, V = (n - 1)/n + 2 a^2, R = sqrt(V)
+    # and for within-chain variance s^2 = 4: V = (n - 1)/n s^2 + 2 a^2, R = sqrt(V / s^2)
     n, a = 4000, 0.5
     two = np.stack([rng.normal(size=n), rng.normal(size=n)], axis=1)[:, :, None]
-    two = (two - two.mean(0)) / two.std(0, ddof=1) + np.array([a, -a])[None, :, None]
-    assert abs(D.gelman_rubin(two)[0] - np.sqrt((n - 1) / n + 2 * a * a)) < 1e-12
+    two = (two - two.mean(0)) / two.std(0, ddof=1)
+    assert abs(D.gelman_rubin(two + np.array([a, -a])[None, :, None])[0] - np.sqrt((n - 1) / n + 2 * a * a)) < 1e-12
+    wide = 2.0 * two + np.array([a, -a])[None, :, None]
+    assert abs(D.gelman_rubin(wide)[0] - np.sqrt(((n - 1) / n * 4.0 + 2 * a * a) / 4.0)) < 1e-12
+
+
+# ---- acceptance rates at stationarity
+#
+# With every chain (and archive state) distributed as the target pi and
+# mutually independent, one proposal is accepted with probability
+# E[min(1, pi(y) q(y -> x) / (pi(x) q(x -> y)))], an expectation over
+# independent draws of pi that plain Monte Carlo estimates without the
+# sampler.  A wrong jump scale, direction or Jacobian changes that number.
+
+def _gauss():
+    mu, cov, lo, hi = target()
+    inv = np.linalg.inv(cov)
+    Lc = np.linalg.cholesky(cov)
+    L = lambda v: -0.5 * (v - mu) @ inv @ (v - mu)
+    draw = lambda rng, n: mu + rng.normal(size=(n, 9)) @ Lc.T
+    Lv = lambda v: -0.5 * np.einsum("ij,jk,ik->i", v - mu, inv, v - mu)
+    return mu, cov, lo, hi, L, draw, Lv
+
+
+def test_de_acceptance_rate_matches_its_proposal():
+    # parallel DE move y = x + gamma (x_r1 - x_r2), gamma = 2.38 / sqrt(2 d)
+    mu, cov, lo, hi, L, draw, Lv = _gauss()
+    rng = np.random.default_rng(21)
+    n_gen, C = 1500, 16
+    x0 = draw(rng, C)
+    _, acc = D.run(L, x0, lo, hi, n_gen, rng, jump_every=0, eps=1e-9)
+    rate = acc / (n_gen * C)
+    m = np.random.default_rng(22)
+    x, a, b = draw(m, 400000), draw(m, 400000), draw(m, 400000)
+    g = 2.38 / np.sqrt(18.0)
+    mc = np.mean(np.minimum(1.0, np.exp(Lv(x + g * (a - b)) - Lv(x))))
+    assert abs(rate - mc) < 0.015, (rate, mc)
+
+
+def test_snooker_acceptance_rate_matches_its_proposal():
+    # snooker move about z with z1, z2 from a frozen archive of target draws:
+    # y = x + g_s ((z1 - z2) . e) e, e = (x - z) / |x - z|, g_s ~ U[1.2, 2.2],
+    # accepted with the extra factor (|y - z| / |x - z|)^(d - 1)
+    mu, cov, lo, hi, L, draw, Lv = _gauss()
+    rng = np.random.default_rng(23)
+    z0 = draw(rng, 3000)
+    C, n_steps = 8, 2500
+    _, acc, Z = D.run_zs(L, draw(rng, C), z0, lo, hi, n_steps, rng, capacity=len(z0), p_snooker=1.0)
+    assert len(Z) == len(z0)
+    rate = acc / (n_steps * C)
+    m = np.random.default_rng(24)
+    n = 400000
+    x, z, z1, z2 = (draw(m, n) for _ in range(4))
+    e = x - z
+    nn = np.sum(e * e, axis=1)
+    gs = 1.2 + m.uniform(size=n)
+    y = x + (gs * np.sum((z1 - z2) * e, axis=1) / nn)[:, None] * e
+    logq = 8 * 0.5 * (np.log(np.sum((y - z) ** 2, axis=1)) - np.log(nn))
+    mc = np.mean(np.minimum(1.0, np.exp(Lv(y) - Lv(x) + logq)))
+    assert abs(rate - mc) < 0.015, (rate, mc)
+
+
+def test_de_acceptance_rate_with_unit_jumps_every_tenth_generation():
+    # With jump_every = 10 one generation in ten uses gamma = 1: the rate is
+    # the 9:1 mixture of the two proposals' stationary acceptance.
+    mu, cov, lo, hi, L, draw, Lv = _gauss()
+    rng = np.random.default_rng(25)
+    n_gen, C = 3000, 16
+    _, acc = D.run(L, draw(rng, C), lo, hi, n_gen, rng, jump_every=10, eps=1e-9)
+    rate = acc / (n_gen * C)
+    m = np.random.default_rng(26)
+    x, a, b = draw(m, 400000), draw(m, 400000), draw(m, 400000)
+    mc = [np.mean(np.minimum(1.0, np.exp(Lv(x + g * (a - b)) - Lv(x)))) for g in (2.38 / np.sqrt(18.0), 1.0)]
+    assert abs(rate - (0.9 * mc[0] + 0.1 * mc[1])) < 0.008, (rate, mc)
+
+
+def test_delayed_acceptance_snooker_rate_matches_its_two_stages():
+    # Two-stage acceptance with a surrogate (Christen & Fox 2005) of a
+    # snooker move: the move is accepted with probability
+    #   min(a1(x -> y), exp(L_y - L_x) q a1(y -> x)),
+    #   a1(x -> y) = min(1, exp(beta (ls_y - ls_x) + margin) q),
+    #   a1(y -> x) = min(1, exp(beta (ls_x - ls_y) + margin) / q),
+    # q = (|y - z| / |x - z|)^(d - 1), here with a surrogate of the wrong
+    # scale and a shifted centre.
+    mu, cov, lo, hi, L, draw, Lv = _gauss()
+    inv = np.linalg.inv(cov)
+    off = 0.2 * np.sqrt(np.diag(cov))
+    Ls = lambda v: -0.5 * 0.6 * (v - mu - off) @ inv @ (v - mu - off)
+    Lsv = lambda v: -0.5 * 0.6 * np.einsum("ij,jk,ik->i", v - mu - off, inv, v - mu - off)
+    beta, margin = 0.5, 0.7
+    rng = np.random.default_rng(27)
+    z0 = draw(rng, 3000)
+    C, n_steps = 8, 2500
+    _, acc, _ = D.run_zs(L, draw(rng, C), z0, lo, hi, n_steps, rng, capacity=len(z0), p_snooker=1.0,
+                         surrogate=Ls, beta=beta, margin=margin)
+    rate = acc / (n_steps * C)
+    m = np.random.default_rng(28)
+    n = 400000
+    x, z, z1, z2 = (draw(m, n) for _ in range(4))
+    e = x - z
+    nn = np.sum(e * e, axis=1)
+    y = x + ((1.2 + m.uniform(size=n)) * np.sum((z1 - z2) * e, axis=1) / nn)[:, None] * e
+    logq = 8 * 0.5 * (np.log(np.sum((y - z) ** 2, axis=1)) - np.log(nn))
+    dls = Lsv(y) - Lsv(x)
+    a1xy = np.minimum(1.0, np.exp(beta * dls + margin + logq))
+    a1yx = np.minimum(1.0, np.exp(-beta * dls + margin - logq))
+    mc = np.mean(np.minimum(a1xy, np.exp(Lv(y) - Lv(x) + logq) * a1yx))
+    assert abs(rate - mc) < 0.015, (rate, mc)
+
+
+@pytest.mark.parametrize("p_snooker", [0.1, 1.0])
+def test_screened_demczs_recovers_gaussian(p_snooker):
+    # delayed acceptance with a wrong-scale surrogate keeps the exact target
+    mu, cov, lo, hi = target()
+    inv = np.linalg.inv(cov)
+    L = lambda v: -0.5 * (v - mu) @ inv @ (v - mu)
+    Ls = lambda v: -0.5 * 0.7 * (v - mu) @ inv @ (v - mu)
+    rng = np.random.default_rng(6020)
+    sd = np.sqrt(np.diag(cov))
+    z0 = mu + rng.normal(size=(90, 9)) * sd * 2.0
+    x0 = mu + rng.normal(size=(4, 9)) * sd * 3.0
+    hist, _, _ = D.run_zs(L, x0, z0, lo, hi, 10000, rng, thin=10, p_snooker=p_snooker, surrogate=Ls,
+                          beta=0.5, margin=1.0)
+    _check(hist, mu, cov, burn=2000)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_snooker_keeps_a_low_dimensional_target(d):
+    # In few dimensions the (|y - z| / |x - z|)^(d - 1) factor decides the
+    # radial law: snooker moves about archive draws of N(0, I) must keep
+    # E |x|^2 = d (without the factor, or with d - 2, it falls by ~30%).
+    L = lambda v: -0.5 * v @ v
+    rng = np.random.default_rng(40 + d)
+    z0 = rng.normal(size=(4000, d))
+    hist, _, _ = D.run_zs(L, rng.normal(size=(8, d)), z0, np.full(d, -12.0), np.full(d, 12.0), 6000, rng,
+                          capacity=len(z0), p_snooker=1.0)
+    s = hist[500:].reshape(-1, d)
+    assert abs(np.mean(np.sum(s * s, axis=1)) / d - 1) < 0.05
+
+
+def test_archive_grows_by_the_population_every_thin_steps():
+    # Every `thin` steps the chains' current states are appended to Z, until
+    # Z holds `capacity` states.
+    mu, cov, lo, hi, L, draw, Lv = _gauss()
+    rng = np.random.default_rng(29)
+    z0 = draw(rng, 50)
+    C, thin = 3, 7
+    hist, _, Z = D.run_zs(L, draw(rng, C), z0, lo, hi, 40, rng, thin=thin, capacity=len(z0) + 4 * C)
+    assert len(Z) == len(z0) + 4 * C
+    assert np.array_equal(Z[:len(z0)], z0)
+    for k in range(4):
+        assert np.array_equal(Z[len(z0) + k * C:len(z0) + (k + 1) * C], hist[(k + 1) * thin])
+
+
+def test_credible_content_error_is_the_binomial_spread():
+    # For N independent samples the estimated content of a region of
+    # probability C scatters over repeated experiments with standard
+    # deviation sqrt(C (1 - C) / N): replicate experiments by plain sampling.
+    rng = np.random.default_rng(30)
+    N, reps, C = 400, 4000, 0.6827
+    inside = rng.uniform(size=(reps, N)) < C
+    spread = inside.mean(axis=1).std(ddof=1)
+    assert abs(spread / D.credible_content_se(C, N) - 1) < 0.05
