@@ -239,7 +239,7 @@ def test_snooker_keeps_a_low_dimensional_target(d):
 
 def test_archive_grows_by_the_population_every_thin_steps():
     # Every `thin` steps the chains' current states are appended to Z, until
-    # Z holds `capacity` states.
+    # Z holds `capacity` states (by default, room for every append).
     mu, cov, lo, hi, L, draw, Lv = _gauss()
     rng = np.random.default_rng(29)
     z0 = draw(rng, 50)
@@ -249,6 +249,24 @@ def test_archive_grows_by_the_population_every_thin_steps():
     assert np.array_equal(Z[:len(z0)], z0)
     for k in range(4):
         assert np.array_equal(Z[len(z0) + k * C:len(z0) + (k + 1) * C], hist[(k + 1) * thin])
+    _, _, Z = D.run_zs(L, draw(rng, 4), z0, lo, hi, 70, rng, thin=thin)
+    assert len(Z) == len(z0) + 4 * (70 // thin)
+
+
+def test_demczs_acceptance_rate_with_unit_jumps():
+    # Parallel moves from a frozen archive of target draws, gamma = 1 every
+    # tenth step: the 9:1 mixture of the two proposals' acceptance.
+    mu, cov, lo, hi, L, draw, Lv = _gauss()
+    rng = np.random.default_rng(31)
+    z0 = draw(rng, 3000)
+    C, n_steps = 8, 4000
+    _, acc, _ = D.run_zs(L, draw(rng, C), z0, lo, hi, n_steps, rng, capacity=len(z0), p_snooker=0.0,
+                         jump_every=10, eps=1e-9)
+    rate = acc / (n_steps * C)
+    m = np.random.default_rng(32)
+    x, a, b = draw(m, 400000), draw(m, 400000), draw(m, 400000)
+    mc = [np.mean(np.minimum(1.0, np.exp(Lv(x + g * (a - b)) - Lv(x)))) for g in (2.38 / np.sqrt(18.0), 1.0)]
+    assert abs(rate - (0.9 * mc[0] + 0.1 * mc[1])) < 0.008, (rate, mc)
 
 
 def test_credible_content_error_is_the_binomial_spread():
@@ -260,3 +278,16 @@ def test_credible_content_error_is_the_binomial_spread():
     inside = rng.uniform(size=(reps, N)) < C
     spread = inside.mean(axis=1).std(ddof=1)
     assert abs(spread / D.credible_content_se(C, N) - 1) < 0.05
+
+
+def test_rejected_proposals_leave_the_chains_and_the_count_alone():
+    # A likelihood that is -inf everywhere except at the starting states:
+    # nothing is accepted and every chain stays where it started.
+    mu, cov, lo, hi, _, draw, _ = _gauss()
+    rng = np.random.default_rng(33)
+    x0 = draw(rng, 6)
+    L = lambda v: 0.0 if any(np.array_equal(v, s) for s in x0) else -np.inf
+    hist, acc = D.run(L, x0, lo, hi, 30, rng)
+    assert acc == 0 and np.all(hist == x0[None])
+    hist, acc, _ = D.run_zs(L, x0, draw(rng, 40), lo, hi, 30, rng)
+    assert acc == 0 and np.all(hist == x0[None])
