@@ -43,7 +43,7 @@ import workloads as W  # noqa: E402
 METRIC = ("forward-model spectra/sec at 1e-4 rel err (plain vs surrogate); Voigt Gline-evals/s")
 UNIT = "Gline-evals/s"
 FLOPS_PER_EVAL = 10          # algorithmic FP32 flops of one line-point evaluation (one-pole form)
-SURVEY_FLOPS_PER_EVAL = 16   # the same evaluation counted on the region-I rational form
+RATIONAL_FLOPS_PER_EVAL = 16  # the same evaluation counted on the region-I rational form
 N_PROPOSALS = 2048
 N_ANGLES = 8
 N_BANDS = 10
@@ -656,10 +656,10 @@ def run_native(args):
                        "parallelism": f"replicas x{N} (independent problems, no collective)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "frac_survey16": achieved * SURVEY_FLOPS_PER_EVAL / FLOPS_PER_EVAL / peak,
+                         "frac_16flop": achieved * RATIONAL_FLOPS_PER_EVAL / FLOPS_PER_EVAL / peak,
                          "kernel": "opacity_kernel",
                          "note": (f"{FLOPS_PER_EVAL} algorithmic FP32 flops per line-point evaluation "
-                                  f"(frac_survey16: the same time with {SURVEY_FLOPS_PER_EVAL}); peak = "
+                                  f"(frac_16flop: the same time with {RATIONAL_FLOPS_PER_EVAL}); peak = "
                                   f"{n_sm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock); "
                                   f"launch time = opacity-build events / {OPACITY_LAUNCHES_PER_STEP}")},
             "forward_model": fw,
