@@ -32,3 +32,62 @@ def test_grid_axes_and_split():
     assert len(ax.p_bar) == 100 and len(ax.t_K) == 20 and ax.n_nu == 100_000
     assert np.isclose(ax.p_bar[0], 1e-8) and np.isclose(ax.p_bar[-1], 100.0)
     assert W.split_lines(5_000_000, 3) == [1_666_667, 1_666_667, 1_666_666]
+
+
+def test_line_list_ranges_and_masses():
+    for s, mass in enumerate((18.0, 28.0, 44.0, 16.0)):
+        ll = W.line_list(s, 20_000)
+        assert ll.mass_amu == mass and ll.nu0.dtype == np.float64
+        assert 1000.0 <= ll.nu0.min() and ll.nu0.max() <= 3000.0
+        assert 0.0 <= ll.elow.min() and ll.elow.max() <= 5000.0
+        assert 0.05 <= ll.gamma_ref.min() and ll.gamma_ref.max() <= 0.1
+        # uniform centres: about a tenth of the lines in each tenth of the range
+        counts = np.histogram(ll.nu0, bins=10, range=(1000.0, 3000.0))[0]
+        assert np.all(np.abs(counts - 2000) < 6 * np.sqrt(2000))
+
+
+def test_grid_axes_recipe():
+    ax = W.grid_axes()
+    assert np.allclose(np.diff(np.log10(ax.p_bar)), 10.0 / 99.0, rtol=1e-12)   # 100 levels over 10 decades
+    assert np.allclose(ax.t_K, np.linspace(500.0, 3000.0, 20))
+    assert ax.nu_start == 1000.0 and ax.dnu == 0.02 and ax.cutoff == 25.0
+    nu = W.nu_axis(ax.nu_start, ax.dnu, ax.n_nu)
+    assert abs(nu[-1] - 2999.98) < 1e-9
+
+
+def test_proposals_fill_the_prior_box():
+    th = W.proposals(2048, generation=5)
+    assert th.shape == (2048, 9) and th.dtype == np.float32
+    lo, hi = W.THETA_LO.astype(np.float32), W.THETA_HI.astype(np.float32)
+    assert np.all(th >= lo) and np.all(th <= hi)
+    u = (th - lo) / (hi - lo)
+    assert np.all(np.abs(u.mean(axis=0) - 0.5) < 0.03)
+    assert np.array_equal(W.proposals(16, generation=5), W.proposals(16, generation=5))
+    assert not np.array_equal(W.proposals(16, generation=5), W.proposals(16, generation=6))
+    # log10 kappa [-3, 0], log10 gamma1,2 [-1.5, 1], alpha [0, 1], beta [0.7, 1.3], a_s [-3, 3]
+    assert np.array_equal(W.THETA_LO, [-3.0, -1.5, -1.5, 0.0, 0.7, -3.0, -3.0, -3.0, -3.0])
+    assert np.array_equal(W.THETA_HI, [0.0, 1.0, 1.0, 1.0, 1.3, 3.0, 3.0, 3.0, 3.0])
+
+
+def test_gaussian_filters_recipe():
+    nu = W.nu_axis(1000.0, 0.5, 4000)
+    w = W.gaussian_filters(nu, 10, 1100.0, 2900.0, 20.0, 200.0)
+    assert w.shape == (10, 4000) and np.all(w >= 0) and np.all(w <= 1)
+    for b in range(10):
+        on = nu[w[b] > 0]
+        cen = nu[np.argmax(w[b])]
+        assert 1100.0 - 0.5 <= cen <= 2900.0 + 0.5
+        # truncated at 3 sigma: the support spans 6 sigma = 6 FWHM / 2.3548
+        fwhm = (on[-1] - on[0]) / 6.0 * 2.0 * np.sqrt(2.0 * np.log(2.0))
+        assert 20.0 - 1.0 <= fwhm <= 200.0 + 1.0
+
+
+def test_transit_instances_recipe():
+    inst = W.instances(1024, 100_000)
+    assert np.all((inst.n_levels >= 40) & (inst.n_levels <= 150))
+    span = inst.nu_hi - inst.nu_lo
+    assert np.all((span >= 10_000) & (span <= 100_000))
+    assert np.all(inst.nu_lo >= 0) and np.all(inst.nu_hi <= 100_000)
+    assert np.all((inst.r_planet >= np.float32(1.0 * W.R_JUP_CM)) & (inst.r_planet <= np.float32(1.4 * W.R_JUP_CM)))
+    assert np.all((inst.r_star >= np.float32(0.7 * W.R_SUN_CM)) & (inst.r_star <= np.float32(1.2 * W.R_SUN_CM)))
+    assert inst.offsets[-1] == span.sum() and inst.offsets[0] == 0
