@@ -1257,7 +1257,8 @@ def posterior_agreement(xp, essp, xs, esss):
     parameter the difference of the means over s = sqrt(s_p^2 + s_s^2) with
     s = sigma / sqrt(ESS), and the content of the plain run's central 68%
     interval in the screened samples against 0.68 with
-    s_C = sqrt(C (1 - C) (1/ESS_p + 1/ESS_s))."""
+    s_C = sqrt(C (1 - C) (1/ESS_p + 1/ESS_s)) (App. C's content error in its
+    large-ESS form, without the + 3 of the Beta posterior)."""
     z_mean, z_c, content = [], [], []
     for j in range(xp.shape[1]):
         sp_ = xp[:, j].std() / np.sqrt(essp[j])

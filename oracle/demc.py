@@ -30,7 +30,9 @@ Statistics (Sec. 5 "Bayesian samplers and convergence", App. C):
   small positive threshold: SPEIS = 1 + 2 sum_{k>=1} rho_k; ESS = N / SPEIS;
 * standard error of a mean, s = sigma / sqrt(ESS) (App. C, Eq. C3 reading);
 * accuracy of a credible region's probability content,
-  s_C = sqrt(C (1 - C) / ESS) (Sec. 5, the ESS relation solved for s_C);
+  s_C = sqrt(C (1 - C) / (ESS + 3)) (App. C: the standard deviation of the
+  Beta posterior of a binomial proportion under a flat prior, with the ESS
+  as the number of trials; Sec. 5 drops the 3 when sizing a run);
 * the Gelman-Rubin statistic (Sec. 5, GR 1992) of m chains of length n:
   W = mean within-chain variance, B = n x variance of the chain means,
   V = (n - 1)/n W + B/n, R = sqrt(V / W).
@@ -101,7 +103,7 @@ def ess(samples_per_chain):
 
 
 def credible_content_se(c_hat, ess_value):
-    return np.sqrt(c_hat * (1.0 - c_hat) / ess_value)
+    return np.sqrt(c_hat * (1.0 - c_hat) / (ess_value + 3.0))
 
 
 def run_zs(loglike, x0, z0, lo, hi, n_steps, rng, thin=10, capacity=None, p_snooker=0.1, gamma=None,

@@ -133,7 +133,7 @@ def test_screen_gains_ess_per_exact_evaluation_at_equal_posterior(ctx, setup):
     """What the surrogate buys: after a shared exact-model burn-in, the
     screened DE-MC sampler reaches the plain sampler's posterior within the
     App. C standard errors (means: s = sigma / sqrt(ESS); central 68% interval
-    content: s_C = sqrt(C (1 - C) / ESS)) while spending fewer exact
+    content: s_C = sqrt(C (1 - C) / ESS), the large-ESS form) while spending fewer exact
     forward-model evaluations per effective sample (Sec. 5 ESS and SPEIS).
     The data here are the model at the seeded truth with noise at S/N = 10 per
     band, so that 16 chains mix within the run and the ESS estimates hold."""

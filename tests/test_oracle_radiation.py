@@ -1,6 +1,6 @@
 """Pins of the oracle's emission RT, Planck function, quadrature and band
 integration: f08isothermal (Sec. 6.1.3), f05abundance (Sec. 6.1.2, Eqs. 12-13,
-Table 2), Stefan-Boltzmann and Wien laws."""
+the varying-abundance table), Stefan-Boltzmann and Wien laws."""
 import json
 import os
 
@@ -69,9 +69,9 @@ def test_f05_thin_layer_ratio_closed_form():
 
 
 def test_f05_trend_matches_paper_table():
-    # Table 2 (f05abundance) prints f slightly below the abundance ratio n with
+    # The varying-abundance table (f05abundance) prints f slightly below the abundance ratio n with
     # a deficit growing with n; the thin-layer law gives the same signature.
-    with open(os.path.join(GOLDEN, "f05_abundance_table2.json")) as fh:
+    with open(os.path.join(GOLDEN, "f05_abundance_table.json")) as fh:
         table = json.load(fh)["f_vs_0.01pct"]
     n_vals = sorted(int(k) for k in table)
     deficits = [n - table[str(n)] for n in n_vals]
