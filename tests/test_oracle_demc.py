@@ -307,3 +307,10 @@ def test_credible_content_error_reproduces_the_papers_retrieval_table():
     for name, _, ess, *printed in table["rows"]:
         for C, pct in zip((0.6827, 0.9545, 0.9973), printed):
             assert abs(100.0 * D.credible_content_se(C, ess) - pct) <= 0.005 + 1e-9, (name, C)
+
+
+def test_credible_content_error_meets_the_sizing_examples():
+    # App. C (and Sec. 5) size runs by ESS ~ C (1 - C) / s_C^2: 68.27% to 2%
+    # needs ~500, 95.45% to 0.5% ~1700, 99.73% to 0.1% ~2700 samples.
+    for C, s, n in ((0.6827, 0.02, 500), (0.9545, 0.005, 1700), (0.9973, 0.001, 2700)):
+        assert abs(D.credible_content_se(C, n) / s - 1) < 0.05
