@@ -456,6 +456,8 @@ class Mlp:
             grad = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
         if loss is None:
             loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check_tensor(grad, "float32", self.n_params)
+        _check_tensor(loss, "float32", 1)
         self.ctx._check(self.lib.bart_mlp_gradient(self.h, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(grad),
                                                    _ptr(loss)))
         return grad, loss
@@ -463,6 +465,7 @@ class Mlp:
     def train_step(self, x, t, lr, loss=None):
         _check_tensor(x, "float32")
         _check_tensor(t, "float32", int(x.shape[0]) * self.widths[-1])
+        _check_tensor(loss, "float32", 1)
         self.ctx._check(self.lib.bart_mlp_train_step(self.h, _ptr(x), _ptr(t), int(x.shape[0]), float(lr),
                                                      _ptr(loss)))
         return loss
@@ -538,6 +541,9 @@ class Demc:
         self.ctx._check(self.lib.bart_demc_set_state(self.h, _ptr(x), _ptr(loglike), _ptr(loglike_s)))
 
     def get_state(self, x=None, loglike=None, loglike_s=None):
+        _check_tensor(x, "float32", self.C * self.d)
+        _check_tensor(loglike, "float64", self.C)
+        _check_tensor(loglike_s, "float64", self.C)
         self.ctx._check(self.lib.bart_demc_get_state(self.h, _ptr(x), _ptr(loglike), _ptr(loglike_s)))
         return x, loglike, loglike_s
 
@@ -557,12 +563,22 @@ class Demc:
         self.ctx._check(self.lib.bart_demc_set_screen(self.h, float(beta), float(margin)))
 
     def propose(self, half_step, y, inbox):
+        _check_tensor(y, "float32", self.C * self.d)
+        _check_tensor(inbox, "int32", self.C)
         self.ctx._check(self.lib.bart_demc_propose(self.h, int(half_step), _ptr(y), _ptr(inbox)))
 
     def screen(self, half_step, inbox, ls_y, passed):
+        _check_tensor(inbox, "int32", self.C)
+        _check_tensor(ls_y, "float64", self.C)
+        _check_tensor(passed, "int32", self.C)
         self.ctx._check(self.lib.bart_demc_screen(self.h, int(half_step), _ptr(inbox), _ptr(ls_y), _ptr(passed)))
 
     def accept(self, half_step, y, passed, L_y, ls_y=None, accepted=None):
+        _check_tensor(y, "float32", self.C * self.d)
+        _check_tensor(passed, "int32", self.C)
+        _check_tensor(L_y, "float64", self.C)
+        _check_tensor(ls_y, "float64", self.C)
+        _check_tensor(accepted, "int32", self.C)
         self.ctx._check(self.lib.bart_demc_accept(self.h, int(half_step), _ptr(y), _ptr(passed), _ptr(L_y),
                                                   _ptr(ls_y), _ptr(accepted)))
 

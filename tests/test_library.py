@@ -84,3 +84,75 @@ def test_missing_library_fails_loudly(tmp_path):
             _native.load(str(tmp_path / "nope.so"))
     finally:
         _native._lib = saved
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor on a machine without one: only the
+    attributes the binding's argument checks read."""
+
+    def __init__(self, dtype, numel, contiguous=True):
+        self.dtype, self._n, self._c = "torch." + dtype, numel, contiguous
+        self.is_cuda, self.device = True, "cpu"     # device: where defaults are allocated
+
+    def is_contiguous(self):
+        return self._c
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):
+        raise AssertionError("the library was reached with a bad argument")
+
+
+def test_sampler_and_surrogate_methods_check_their_arguments():
+    # Wrong dtype, size or layout of an output or input buffer is rejected
+    # in Python, before any pointer reaches the library.
+    import pytest
+    import paper_2104_12522_gb300 as bart
+    F = _FakeDeviceTensor
+    class _Stub:                      # context and library: any attribute, any call
+        def __getattr__(self, name):
+            return lambda *a: 0
+    s = object.__new__(bart.Demc)
+    s.C, s.d, s.ctx, s.lib, s.h = 6, 4, _Stub(), _Stub(), None
+    good_y, good_i, good_l = F("float32", 24), F("int32", 6), F("float64", 6)
+    bad = [
+        lambda: s.propose(0, F("float64", 24), good_i),
+        lambda: s.propose(0, good_y, F("int32", 5)),
+        lambda: s.screen(0, good_i, F("float32", 6), good_i),
+        lambda: s.screen(0, good_i, good_l, F("int64", 6)),
+        lambda: s.accept(0, F("float32", 23), good_i, good_l),
+        lambda: s.accept(0, good_y, good_i, F("float32", 6)),
+        lambda: s.accept(0, good_y, good_i, good_l, good_l, F("int32", 7)),
+        lambda: s.get_state(F("float32", 24, contiguous=False)),
+        lambda: s.get_state(good_y, F("float64", 5)),
+    ]
+    m = object.__new__(bart.Mlp)
+    m.widths, m.n_params, m.ctx, m.lib, m.h = [9, 4, 10], 90, _Stub(), _Stub(), None
+    x = F("float32", 2 * 9)
+    x.shape = (2, 9)
+    t = F("float32", 2 * 10)
+    bad += [
+        lambda: m.gradient(x, t, grad=F("float32", 89)),
+        lambda: m.gradient(x, t, grad=F("float32", 90), loss=F("float64", 1)),
+        lambda: m.train_step(x, t, 1e-3, loss=F("float32", 2)),
+    ]
+    for call in bad:
+        with pytest.raises((TypeError, ValueError)):
+            call()
+    # arguments of the documented dtypes and sizes pass the checks and reach
+    # the library (the stand-in stops there)
+    good = [
+        lambda: s.propose(0, good_y, good_i),
+        lambda: s.screen(0, good_i, good_l, good_i),
+        lambda: s.screen(0, good_i, None, good_i),
+        lambda: s.accept(0, good_y, good_i, good_l),
+        lambda: s.accept(0, good_y, good_i, good_l, good_l, good_i),
+        lambda: s.get_state(good_y),
+        lambda: s.get_state(good_y, good_l, good_l),
+        lambda: m.gradient(x, t, grad=F("float32", 90), loss=F("float32", 1)),
+        lambda: m.train_step(x, t, 1e-3, loss=F("float32", 1)),
+    ]
+    for call in good:
+        with pytest.raises(AssertionError, match="library was reached"):
+            call()
