@@ -11,7 +11,7 @@
 //               w ~ (i/sqrt(pi)) z / (z^2 - 1/2), whose real part is written
 //               without cancellation as
 //               Re w = (y/sqrt(pi)) (u + 1) / (u^2 + 2 y^2),  u = x^2 + y^2 - 1/2;
-//               relative error <= 2.5/|z|^4 <= 8e-6.
+//               relative error <= 2.52/|z|^4 <= 7.6e-6.
 //  * 5 <= |z| < 24  the same continued fraction to depth 4 (|z| >= 8) or 6,
 //               evaluated in complex FP32; Re w = Im t / (sqrt(pi) |t|^2)
 //               where t is the fraction's denominator.  All imaginary parts
@@ -73,7 +73,7 @@ __device__ __forceinline__ float cf_re(float x, float y, int depth) {
 // where every term of the numerator carries the factor y (no cancellation near
 // the real axis; (u - 1)(u - 3/2) > -1/16 is negligible against x^2 for
 // |z| >= 14).  Relative error of Re w against the Faddeeva function (FP64):
-// <= 7.2e-7 for 14 <= |z| < 24 (the truncation is ~5.25 / x^6 near the real
+// <= 7.3e-7 for 14 <= |z| < 24 (the truncation is ~5.25 / x^6 near the real
 // axis), plus the FP32 rounding of about ten operations.  The Gaussian term
 // exp(-x^2) is below the FP32 range there.
 __device__ __forceinline__ float cf2_re(float x, float y) {

@@ -233,7 +233,8 @@ struct __align__(8) LineG3 {    // accurate branch (expansion lines: -2 dx, dx^2
 // most LFIX_MAX of them) has x^2 + y^2 large enough for the shifted Lorentz form
 //   Re w = (y/sqrt pi) / (x^2 + y^2 - 3/2)
 // (the asymptotic series w ~ (i/sqrt pi)(1/z + 1/(2 z^3) + ...) to second
-// order: relative error <= (2 y^2 + 3/2) / (x^2 + y^2)^2, required <= EPS_L);
+// order: relative error (2 y^2 + 3/2) / (x^2 + y^2)^2 to leading order, at most
+// 0.6% more; the selection keeps it <= EPS_L with a 0.1% margin on x^2 + y^2);
 // "P": the one-pole form.  "F": the window covers the whole span and no block
 // is left to the fixup (no per-lane weight); "M": the lane weight is taken
 // from the line's lane mask.
@@ -244,7 +245,7 @@ constexpr int CLS_F2 = 5, CLS_F4 = 6, CLS_F8 = 7;   // expansion about a block o
 // 16 points is expanded to degree FF_DEG in the point offset t about the
 // block centre, f(t) = (A/s) sum_n P_n t^n with s = xc^2 + y^2 - 3/2,
 // alpha = 2 xc dx / s, beta = dx^2 / s, P_0 = 1, P_1 = -alpha,
-// P_n = -alpha P_{n-1} - beta P_{n-2}; truncation error <= 2.5e-6 relative for
+// P_n = -alpha P_{n-1} - beta P_{n-2}; truncation error <= 2.6e-6 relative for
 // |xc| >= 12 h (h = 7.5 dx, half a block), i.e. |x| >= 11 h on the block.
 // The lane sums the coefficients over lines and expands them once per chunk.
 // Lines farther away are expanded about the centre of a group of G = 2, 4 or
