@@ -14,9 +14,15 @@ cited by section and equation.  Where the paper defers to its companion papers
 parameterisation), the oracle takes the reading stated in its docstring.
 
 Pins (tests/test_oracle_*.py) tie each function to something other than itself:
-closed forms, limits, invariants, brute-force quadrature and textbook constants.
-The steps between the grid and the radiative transfer (temperature
-interpolation, abundances, mass opacity) are pinned through the composed
-emission and transit paths (tests/test_oracle_composed.py).  The MLP and DE-MC
-parts are pinned by finite differences and by sampling a known Gaussian target.  Nothing here is "parity unpinned".
+closed forms, limits, invariants, brute-force quadrature, textbook constants
+and values the paper prints (tests/golden/).  The steps between the grid and
+the radiative transfer (temperature interpolation, abundances, mass opacity)
+are pinned through the composed emission and transit paths
+(tests/test_oracle_composed.py); the T(P) profile by the radiative-equilibrium
+relations it solves.  The MLP is pinned by finite differences and closed
+forms, the samplers by sampling known Gaussian targets and by their
+stationary acceptance rates, the chain statistics by App. C's printed table.
+tests/oracle_mutation.py plants one mistake at a time in a copy of this
+package and reports any that no pin notices.  Nothing here is "parity
+unpinned".
 """
