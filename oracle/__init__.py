@@ -21,7 +21,8 @@ are pinned through the composed emission and transit paths
 (tests/test_oracle_composed.py); the T(P) profile by the radiative-equilibrium
 relations it solves.  The MLP is pinned by finite differences and closed
 forms, the samplers by sampling known Gaussian targets and by their
-stationary acceptance rates, the chain statistics by App. C's printed table.
+stationary acceptance rates, App. C's content error by the retrieval table
+of Sec. 6.3.
 tests/oracle_mutation.py plants one mistake at a time in a copy of this
 package and reports any that no pin notices.  Nothing here is "parity
 unpinned".
