@@ -1,7 +1,7 @@
 """Surrogate network of the screened sampler, in FP64 (test infrastructure).
 
 The paper has no learned component (ML surrogates appear only as related work,
-Sec. 1); the network follows the benchmark spec: a multilayer perceptron
+Sec. 1); the library's surrogate is a multilayer perceptron
 theta (9) -> 256 -> 256 -> 256 -> band values (10), GELU activations, trained
 by Adam on spectra produced by the forward model.  This module writes out the
 plain definitions the GPU kernels must reproduce:

@@ -76,7 +76,7 @@ extern "C" bart_status bart_retrieval_run(bart_ctx* ctx, bart_demc* s, bart_mlp*
   BART_REQUIRE(ctx, cfg->geometry == BART_EMISSION || cfg->geometry == BART_TRANSMISSION, "bad geometry");
   const int C = bart_demc_chains(s), d = bart_demc_params(s), nb = filters->n_bands;
   BART_REQUIRE(ctx, d == 5 + grid->n_species, "the sampler needs 5 + n_species parameters");
-  BART_REQUIRE(ctx, cfg->geometry == BART_EMISSION, "the driver runs the emission geometry");
+  BART_REQUIRE(ctx, cfg->geometry == BART_EMISSION, "the retrieval loop runs the emission geometry");
   BART_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   bart_status r;
