@@ -381,7 +381,7 @@ def cpu_phase(target_s=15.0, nwin=48, seed=0, full=True):
         out["sample_oracle_s"] = time.perf_counter() - t
         out["em_sample"] = (em_js, em_union, em_cells, [v for _, _, v in em_vals], theta)
         out["tr_sample"] = (tr_js, tr_union, tr_cells, [v for _, _, v in tr_vals], inst)
-        # emission baseline (config 2 shape: L = 100, M = 20, S = 4, 8 angles, 10 bands)
+        # emission baseline (the 2,048-proposal generation's shape: L = 100, M = 20, S = 4, 8 angles, 10 bands)
         n_em = max(16, cores)
         th_s = W.proposals(n_em, generation=0, n_species=S)
         filt = slice_filters(N_BANDS)
@@ -395,7 +395,7 @@ def cpu_phase(target_s=15.0, nwin=48, seed=0, full=True):
                            "sample": f"{n_em} proposals of the 9-parameter prior on a {SLICE_N}-point slice of "
                                      f"a seeded 4-species opacity field (100 layers x 20 T, 8 angles, 10 bands) in "
                                      f"{wall:.2f} s; rate extrapolated to 100,000 points by point count"}
-        # transmission baseline (config 3: the bench batch's first instances, spans clipped to the slice)
+        # transmission baseline (the transit batch's first instances, spans clipped to the slice)
         n_tr = max(16, cores)
         tcfg = tr_cfg(S)
         tfilt = slice_filters(12, seed=3001)
