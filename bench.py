@@ -645,7 +645,7 @@ def run_native(args):
         cb = None
         if cpu is not None:
             cb = dict(cpu["opacity"])
-            cb["configs"] = {k: cpu[k] for k in ("emission", "transmission", "retrieval") if k in cpu}
+            cb["workloads"] = {k: cpu[k] for k in ("emission", "transmission", "retrieval") if k in cpu}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": N, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
