@@ -314,3 +314,15 @@ def test_credible_content_error_meets_the_sizing_examples():
     # needs ~500, 95.45% to 0.5% ~1700, 99.73% to 0.1% ~2700 samples.
     for C, s, n in ((0.6827, 0.02, 500), (0.9545, 0.005, 1700), (0.9973, 0.001, 2700)):
         assert abs(D.credible_content_se(C, n) / s - 1) < 0.05
+
+
+def test_speis_and_ess_of_a_square_wave_in_closed_form():
+    # A chain of +1, +1, +1, +1, -1, -1, -1, -1, ... of length n = 8m has mean
+    # 0 and variance 1; counting sign changes, the lag-1 sum of products is
+    # n/2 + 1 (rho_1 = 1/2 + 1/n) and the lag-2 sum is 2 (rho_2 = 2/n, below
+    # the 0.01 threshold), so SPEIS = 1 + 2 rho_1 = 2 + 2/n exactly.
+    for n in (800, 8000):
+        c = np.tile([1.0, 1.0, 1.0, 1.0, -1.0, -1.0, -1.0, -1.0], n // 8)
+        assert abs(D.speis(c) - (2.0 + 2.0 / n)) < 1e-12
+        chains = np.stack([c, -c, c], axis=1)[:, :, None]          # [n][3 chains][1 parameter]
+        assert abs(D.ess(chains) - n * 3 / (2.0 + 2.0 / n)) < 1e-9
