@@ -79,7 +79,10 @@ def run(loglike, x0, lo, hi, n_gen, rng, gamma=None, jump_every=10, eps=1e-4, su
 
 
 def speis(chain, threshold=0.01):
-    """Steps per effectively independent sample of a 1-D chain."""
+    """Steps per effectively independent sample of a 1-D chain.  A chain of
+    zero variance (it never moved) has no autocorrelation to sum; it gets 1,
+    the same convention as the GPU statistics kernel, so a stuck chain must be
+    caught by its acceptance count, not by its ESS."""
     c = np.asarray(chain, np.float64) - np.mean(chain)
     n = c.size
     var = np.dot(c, c) / n
