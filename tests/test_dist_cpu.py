@@ -51,3 +51,24 @@ def test_single_process_has_no_collective():
     import bench
     assert bench.init_dist(1, "gloo") is None
     assert bench.max_over_ranks(None, 12.5) == 12.5
+
+
+def test_reference_arm_under_torchrun_prints_once_from_rank_zero():
+    # `bench.py --impl reference` launched as two ranks: rank 0 times the
+    # oracle and prints one JSON line, the other rank exits 0 without work.
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-seconds", "0.5"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, OMP_NUM_THREADS="1"))
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
