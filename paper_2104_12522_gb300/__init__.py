@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import dataclasses
+import json
 import sys
 from typing import Optional, Sequence
 
@@ -525,6 +526,10 @@ class Demc:
         ctx._check(self.lib.bart_demc_create(ctx.h, self.C, self.d, _flt(lo), _flt(hi), float(gamma),
                                              int(jump_every), float(eps), C.c_uint64(int(seed)), C.byref(h)))
         self.h = h
+        self._config = dict(n_chains=self.C, lo=[float(v) for v in np.asarray(lo, np.float32)],
+                            hi=[float(v) for v in np.asarray(hi, np.float32)], gamma=float(gamma),
+                            jump_every=int(jump_every), eps=float(eps), seed=int(seed), beta=1.0, margin=0.0)
+        self._zs = False
 
     def close(self):
         if getattr(self, "h", None):
@@ -553,6 +558,7 @@ class Demc:
         _check_tensor(z0, "float32", n0 * self.d)
         self.ctx._check(self.lib.bart_demc_set_archive(self.h, _ptr(z0), n0, int(capacity), int(thin),
                                                        float(p_snooker)))
+        self._zs = True
 
     def archive_size(self) -> int:
         n = C.c_int64()
@@ -561,6 +567,42 @@ class Demc:
 
     def set_screen(self, beta=1.0, margin=0.0):
         self.ctx._check(self.lib.bart_demc_set_screen(self.h, float(beta), float(margin)))
+        self._config.update(beta=float(beta), margin=float(margin))
+
+    def checkpoint(self, next_half_step: int) -> dict:
+        """Everything a DE-MC run needs to continue, as host values: the
+        sampler's configuration, seed and screen, the chains' states with their
+        exact and surrogate log-likelihoods, and the half-step to run next.
+        Random numbers are keyed by (seed, half-step, chain, draw), so a sampler
+        rebuilt by from_checkpoint continues exactly as this one would.  A
+        DEMCzs archive is device state the library does not export, so a
+        DEMCzs sampler raises instead."""
+        import torch
+        if self._zs:
+            raise ValueError("the archive of a DEMCzs sampler cannot be checkpointed")
+        dev = torch.device("cuda", self.ctx.device)
+        x = torch.empty((self.C, self.d), dtype=torch.float32, device=dev)
+        L = torch.empty(self.C, dtype=torch.float64, device=dev)
+        Ls = torch.empty(self.C, dtype=torch.float64, device=dev)
+        self.get_state(x, L, Ls)
+        self.ctx.sync()
+        return dict(self._config, x=x.cpu().numpy(), loglike=L.cpu().numpy(), loglike_s=Ls.cpu().numpy(),
+                    next_half_step=int(next_half_step))
+
+    @classmethod
+    def from_checkpoint(cls, ctx: Context, ck: dict) -> "Demc":
+        """A sampler in the state `ck` describes (see checkpoint); the run
+        continues with half-step ck["next_half_step"]."""
+        import torch
+        s = cls(ctx, int(ck["n_chains"]), np.asarray(ck["lo"], np.float32), np.asarray(ck["hi"], np.float32),
+                gamma=float(ck["gamma"]), jump_every=int(ck["jump_every"]), eps=float(ck["eps"]),
+                seed=int(ck["seed"]))
+        s.set_screen(float(ck["beta"]), float(ck["margin"]))
+        dev = torch.device("cuda", ctx.device)
+        s.set_state(torch.tensor(np.ascontiguousarray(ck["x"], np.float32), device=dev),
+                    torch.tensor(np.ascontiguousarray(ck["loglike"], np.float64), device=dev),
+                    torch.tensor(np.ascontiguousarray(ck["loglike_s"], np.float64), device=dev))
+        return s
 
     def propose(self, half_step, y, inbox):
         _check_tensor(y, "float32", self.C * self.d)
@@ -581,6 +623,21 @@ class Demc:
         _check_tensor(accepted, "int32", self.C)
         self.ctx._check(self.lib.bart_demc_accept(self.h, int(half_step), _ptr(y), _ptr(passed), _ptr(L_y),
                                                   _ptr(ls_y), _ptr(accepted)))
+
+
+def save_checkpoint(path: str, ck: dict) -> None:
+    """Writes a sampler checkpoint (Demc.checkpoint) to `path` (.npz)."""
+    arrays = {k: np.asarray(ck[k]) for k in ("x", "loglike", "loglike_s")}
+    meta = {k: v for k, v in ck.items() if k not in arrays}
+    np.savez(path, meta=np.array(json.dumps(meta)), **arrays)
+
+
+def load_checkpoint(path: str) -> dict:
+    """Reads a sampler checkpoint written by save_checkpoint."""
+    with np.load(path, allow_pickle=False) as f:
+        ck = json.loads(str(f["meta"]))
+        ck.update({k: f[k].copy() for k in ("x", "loglike", "loglike_s")})
+    return ck
 
 
 def forward_emission_noalloc(grid, p_bar, t_K, nu, cfg, theta=None, t_profile=None, nu_lo=None, nu_hi=None,

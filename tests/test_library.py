@@ -156,3 +156,30 @@ def test_sampler_and_surrogate_methods_check_their_arguments():
     for call in good:
         with pytest.raises(AssertionError, match="library was reached"):
             call()
+
+
+def test_sampler_checkpoint_file_round_trip(tmp_path):
+    import numpy as np
+    import paper_2104_12522_gb300 as bart
+    rng = np.random.default_rng(3)
+    ck = dict(n_chains=8, lo=[0.0, -1.0], hi=[1.0, 2.0], gamma=0.0, jump_every=10, eps=1e-4, seed=6123,
+              beta=0.5, margin=1.0, next_half_step=4242, x=rng.uniform(size=(8, 2)).astype(np.float32),
+              loglike=rng.normal(size=8), loglike_s=np.zeros(8))
+    path = str(tmp_path / "ck.npz")
+    bart.save_checkpoint(path, ck)
+    back = bart.load_checkpoint(path)
+    for k, v in ck.items():
+        if isinstance(v, np.ndarray):
+            assert back[k].dtype == v.dtype and np.array_equal(back[k], v)
+        else:
+            assert back[k] == v
+
+
+def test_demczs_sampler_refuses_to_checkpoint():
+    # its archive is device state the library does not export
+    import pytest
+    import paper_2104_12522_gb300 as bart
+    s = object.__new__(bart.Demc)
+    s._zs = True
+    with pytest.raises(ValueError, match="archive"):
+        s.checkpoint(10)
