@@ -91,3 +91,18 @@ def test_transit_instances_recipe():
     assert np.all((inst.r_planet >= np.float32(1.0 * W.R_JUP_CM)) & (inst.r_planet <= np.float32(1.4 * W.R_JUP_CM)))
     assert np.all((inst.r_star >= np.float32(0.7 * W.R_SUN_CM)) & (inst.r_star <= np.float32(1.2 * W.R_SUN_CM)))
     assert inst.offsets[-1] == span.sum() and inst.offsets[0] == 0
+
+
+def test_opacity_field_recipe():
+    # seeded random numbers only: a grid [S][L][M][n_nu] of cross sections in
+    # [1e-30, 1e-16] cm^2, reproducible by seed, varying over every axis
+    ax = W.grid_axes(n_layers=20, n_temps=5, n_nu=3000)
+    f = W.opacity_field(4, ax.p_bar, ax.t_K, ax.n_nu, seed=3600)
+    assert f.shape == (4, 20, 5, 3000) and np.all(np.isfinite(f))
+    assert f.min() >= 1e-30 and f.max() <= 1e-16
+    assert np.array_equal(f, W.opacity_field(4, ax.p_bar, ax.t_K, ax.n_nu, seed=3600))
+    assert not np.array_equal(f, W.opacity_field(4, ax.p_bar, ax.t_K, ax.n_nu, seed=3601))
+    lf = np.log10(f)
+    for axis in range(4):
+        assert np.ptp(lf.mean(axis=tuple(a for a in range(4) if a != axis))) > 0.0
+    assert np.ptp(lf) > 3.0                      # several decades of dynamic range
