@@ -553,7 +553,7 @@ typedef struct {
  * model on `grid` integrated over `filters` and compared with `data` +-
  * `sigma` (device [n_bands]) by bart_loglike_bands.  With a surrogate, its
  * band values screen proposals first (delayed acceptance) and only survivors
- * reach the exact model; the exact model judges every accepted sample and
+ * reach the exact model; the exact model decides every acceptance and
  * the surrogate's band error on them is accumulated in `stats`.  The sampler
  * needs 5 + n_species parameters.  use_graph = 1 captures one generation in a
  * CUDA graph after an eager first generation and replays it (call this before
